@@ -1,0 +1,275 @@
+"""CPU oracle for the generalized Kohn-Sham eigensolve and density matrix.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the benchmark's
+CPU-baseline leg.  The product path never imports this module and shares no code with
+it.  Everything here is plain FP64:
+
+* the eigensolve (paper Sec. 2, H C = S C eps; Sec. 2 Bloch form per k; Sec. 2/3.2
+  noncollinear spinor with S_NC = I_2 (x) S) runs in the unblocked C code of
+  gks_oracle.c (Cholesky, explicit substitution, Householder, implicit QL, back
+  substitution);
+* occupations, chemical potential, band energy and density matrix (paper Sec. 3.1
+  Parts 3 and 4; Sec. 2 density-matrix definition) are direct numpy sums.
+
+Readings where the paper is silent (each listed in the design notes):
+* Fermi-Dirac f(x) = 1/(1+e^x), x = (eps - mu)/kT (the paper names f_i only);
+* spin factor g_s = 2 collinear, 1 noncollinear (Sec. 2 electron density, with and
+  without the factor 2);
+* mu by bisection on the increasing electron count, shared by all k of a system,
+  weights w_k (default 1/nk); bracket [min eps - 1, max eps + 1], stop when
+  hi - lo <= 4u max(1, |mu|) or after 200 halvings;
+* rho_k = C_k diag(g_s f_k) C_k^H over the columns with f >= f_cut = 1e-16.  The paper's
+  n_lm = sum_i f_i c*_li c_mi is conj(rho)/g_s, i.e. its transpose for Hermitian rho.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libgks_oracle.so")
+_lib = None
+
+F_CUT = 1e-16
+U_ROUND = 2.0 ** -53
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, no architecture-specific flags)."""
+    src = os.path.join(_HERE, "gks_oracle.c")
+    inc = os.path.join(_HERE, "oracle_core.inc")
+    newest = max(os.path.getmtime(src), os.path.getmtime(inc))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        for sfx in ("d", "z"):
+            getattr(lib, f"oracle_solve_{sfx}").argtypes = [ctypes.c_int, P, P, P, P]
+            getattr(lib, f"oracle_chol_{sfx}").argtypes = [ctypes.c_int, P]
+            getattr(lib, f"oracle_reduce_{sfx}").argtypes = [ctypes.c_int, P, P]
+            getattr(lib, f"oracle_tridiag_{sfx}").argtypes = [ctypes.c_int, P, P, P, P, P]
+            getattr(lib, f"oracle_backtransform_{sfx}").argtypes = [ctypes.c_int, P, P, P, P, P]
+            getattr(lib, f"oracle_unreduce_{sfx}").argtypes = [ctypes.c_int, P, P]
+            getattr(lib, f"oracle_unreduce_{sfx}").restype = None
+            getattr(lib, f"oracle_reduce_{sfx}").restype = None
+            getattr(lib, f"oracle_tridiag_{sfx}").restype = None
+            getattr(lib, f"oracle_backtransform_{sfx}").restype = None
+        lib.oracle_tridiag_eig.argtypes = [ctypes.c_int, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _sfx(a):
+    return "z" if np.iscomplexobj(a) else "d"
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+# ----------------------------- single-pencil stages -----------------------------
+
+def cholesky(S: np.ndarray) -> np.ndarray:
+    """Step 1: S = L L^H (lower triangle of S read)."""
+    L = np.array(S, dtype=S.dtype, order="C", copy=True)
+    rc = getattr(_load(), f"oracle_chol_{_sfx(L)}")(L.shape[0], _ptr(L))
+    if rc:
+        raise OracleError(f"S not positive definite at column {rc - 1}")
+    return L
+
+
+def reduce_standard(L: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """Step 2: H' = L^-1 H L^-H."""
+    A = np.array(H, dtype=L.dtype, order="C", copy=True)
+    getattr(_load(), f"oracle_reduce_{_sfx(A)}")(A.shape[0], _ptr(np.ascontiguousarray(L)), _ptr(A))
+    return A
+
+
+def tridiagonalize(A: np.ndarray):
+    """Step 3: Householder reduction. Returns (d, sub, U, beta)."""
+    A = np.array(A, order="C", copy=True)
+    n = A.shape[0]
+    d = np.zeros(n)
+    sub = np.zeros(max(n - 1, 1), dtype=A.dtype)
+    U = np.zeros((n, n), dtype=A.dtype)
+    beta = np.zeros(n)
+    getattr(_load(), f"oracle_tridiag_{_sfx(A)}")(n, _ptr(A), _ptr(d), _ptr(sub), _ptr(U), _ptr(beta))
+    return d, sub[: max(n - 1, 0)], U, beta
+
+
+def tridiagonal_eig(d: np.ndarray, e: np.ndarray):
+    """Step 4-5: implicit QL on the real tridiagonal; ascending eigenvalues, vectors Z."""
+    n = d.shape[0]
+    dd = np.array(d, dtype=np.float64, copy=True)
+    ee = np.zeros(max(n, 1))
+    ee[: n - 1] = e
+    Z = np.eye(n)
+    rc = _load().oracle_tridiag_eig(n, _ptr(dd), _ptr(ee), _ptr(Z))
+    if rc:
+        raise OracleError(f"implicit QL did not converge (block at {rc - 1})")
+    return dd, Z
+
+
+def back_transform(sub, U, beta, Z):
+    """Step 6a: X = Q D Z."""
+    n = Z.shape[0]
+    X = np.zeros((n, n), dtype=U.dtype)
+    s = np.zeros(max(n, 1), dtype=U.dtype)
+    s[: n - 1] = sub
+    getattr(_load(), f"oracle_backtransform_{_sfx(U)}")(n, _ptr(s), _ptr(U), _ptr(beta),
+                                                        _ptr(np.ascontiguousarray(Z)), _ptr(X))
+    return X
+
+
+def unreduce(L, X):
+    """Step 6b: C = L^-H X."""
+    C = np.array(X, order="C", copy=True)
+    getattr(_load(), f"oracle_unreduce_{_sfx(C)}")(C.shape[0], _ptr(np.ascontiguousarray(L)), _ptr(C))
+    return C
+
+
+def eigh_generalized(H: np.ndarray, S: np.ndarray):
+    """All eigenpairs of one Hermitian pencil (H, S): eps ascending, C with C^H S C = I."""
+    cplx = np.iscomplexobj(H) or np.iscomplexobj(S)
+    dt = np.complex128 if cplx else np.float64
+    H = np.ascontiguousarray(H, dtype=dt)
+    S = np.ascontiguousarray(S, dtype=dt)
+    n = H.shape[0]
+    eps = np.zeros(n)
+    C = np.zeros((n, n), dtype=dt)
+    rc = getattr(_load(), f"oracle_solve_{_sfx(H)}")(n, _ptr(H), _ptr(S), _ptr(eps), _ptr(C))
+    if rc < 0:
+        raise OracleError(f"S not positive definite at column {-rc - 1}")
+    if rc > 0:
+        raise OracleError("implicit QL did not converge")
+    return eps, phase_fix(C)
+
+
+def phase_fix(C: np.ndarray) -> np.ndarray:
+    """Column phase convention: the largest-modulus entry (lowest index on ties) is real
+    and positive."""
+    C = np.array(C, copy=True)
+    idx = np.argmax(np.abs(C), axis=0)
+    piv = C[idx, np.arange(C.shape[1])]
+    mag = np.abs(piv)
+    ph = np.where(mag > 0, piv / np.where(mag > 0, mag, 1), 1)
+    return C / ph[None, :]
+
+
+# ----------------------------- occupations and density -----------------------------
+
+def fermi(x: np.ndarray) -> np.ndarray:
+    """f(x) = 1/(1+e^x), written so that exp never overflows."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    pos = x > 0
+    ex = np.exp(-x[pos])
+    out[pos] = ex / (1.0 + ex)
+    out[~pos] = 1.0 / (1.0 + np.exp(x[~pos]))
+    return out
+
+
+def electron_count(mu, eps, w, gs, kT):
+    return float(sum(w[k] * gs * fermi((eps[k] - mu) / kT).sum() for k in range(eps.shape[0])))
+
+
+def chemical_potential(eps: np.ndarray, w: np.ndarray, gs: float, kT: float, n_elec: float):
+    """Bisection on N(mu) = sum_k w_k g_s sum_i f((eps_ik - mu)/kT) = n_elec."""
+    M = eps.shape[1]
+    if not (kT > 0):
+        raise OracleError("kT must be positive")
+    if not (0.0 < n_elec < gs * M * float(np.sum(w))):
+        raise OracleError("n_elec out of range")
+    lo = float(eps.min()) - 1.0
+    hi = float(eps.max()) + 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if hi - lo <= 4.0 * U_ROUND * max(1.0, abs(mid)):
+            break
+        if electron_count(mid, eps, w, gs, kT) < n_elec:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def density_matrix(C: np.ndarray, occ: np.ndarray, gs: float, f_cut: float = F_CUT):
+    """rho = C diag(g_s f) C^H over the columns with f >= f_cut (direct weighted sum)."""
+    keep = occ >= f_cut
+    Ck = C[:, keep]
+    return (Ck * (gs * occ[keep])[None, :]) @ Ck.conj().T
+
+
+@dataclass
+class Result:
+    eps: np.ndarray        # (nk, M)
+    C: np.ndarray          # (nk, M, M)
+    mu: float
+    occ: np.ndarray        # (nk, M)
+    rho: np.ndarray        # (nk, M, M)
+    e_band: float
+    n_rho: np.ndarray      # (nk,) columns kept in rho
+
+
+def spinor_overlap(S: np.ndarray) -> np.ndarray:
+    """S_NC = diag(S, S) (paper Sec. 3.2)."""
+    n = S.shape[0]
+    out = np.zeros((2 * n, 2 * n), dtype=np.complex128)
+    out[:n, :n] = S
+    out[n:, n:] = S
+    return out
+
+
+def solve(H, S, kT: float, n_elec: float, spin: str = "collinear", kweights=None,
+          f_cut: float = F_CUT) -> Result:
+    """Full path for nk pencils sharing one chemical potential.
+
+    H: (nk, M, M); S: (nk, N, N) with M = N (collinear) or 2N (noncollinear)."""
+    H = np.asarray(H)
+    S = np.asarray(S)
+    if H.ndim == 2:
+        H = H[None]
+        S = S[None]
+    nk, M = H.shape[0], H.shape[1]
+    gs = 2.0 if spin == "collinear" else 1.0
+    w = np.full(nk, 1.0 / nk) if kweights is None else np.asarray(kweights, float)
+    eps = np.zeros((nk, M))
+    dt = np.complex128 if (np.iscomplexobj(H) or np.iscomplexobj(S) or spin != "collinear") else np.float64
+    C = np.zeros((nk, M, M), dtype=dt)
+    for k in range(nk):
+        Sk = spinor_overlap(S[k]) if spin == "noncollinear" else S[k]
+        eps[k], C[k] = eigh_generalized(H[k].astype(dt), Sk.astype(dt))
+    mu = chemical_potential(eps, w, gs, kT, n_elec)
+    occ = np.stack([fermi((eps[k] - mu) / kT) for k in range(nk)])
+    rho = np.stack([density_matrix(C[k], occ[k], gs, f_cut) for k in range(nk)])
+    e_band = float(sum(w[k] * gs * np.sum(occ[k] * eps[k]) for k in range(nk)))
+    n_rho = np.array([int(np.sum(occ[k] >= f_cut)) for k in range(nk)])
+    return Result(eps, C, mu, occ, rho, e_band, n_rho)
+
+
+# ----------------------------- error measures -----------------------------
+
+def eig_condition(H, S, eps, C):
+    """beta_i = u (||H||_2 + |eps_i| ||S||_2) ||c_i||_2^2: first-order FP64 floor of eps_i
+    for a backward-stable method on an S-normalized eigenpair."""
+    nh = np.linalg.norm(H, 2)
+    ns = np.linalg.norm(S, 2)
+    cn = np.sum(np.abs(C) ** 2, axis=0)
+    return U_ROUND * (nh + np.abs(eps) * ns) * cn

@@ -1,0 +1,367 @@
+"""Pins for the CPU oracle: closed forms, exact brute force, invariants and an
+independent LAPACK cross-check.  Each test fixes something the oracle cannot know from
+itself, chosen so that a dropped term, a wrong sign or index, or a transposed operand in
+any stage fails at least one of them."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from oracle import oracle as O
+from paper_2606_09058_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _match_columns(A, B):
+    """max over columns of min(|a - b|, |a + b|) after unit-modulus phase alignment."""
+    err = 0.0
+    for j in range(A.shape[1]):
+        a, b = A[:, j], B[:, j]
+        ph = np.vdot(b, a)
+        ph = ph / abs(ph) if abs(ph) > 0 else 1.0
+        err = max(err, np.abs(a - ph * b).max())
+    return err
+
+
+# ------------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 50, 161])
+def test_chain_closed_form(n):
+    """S = I chain: eps_j = e0 + 2t cos(j pi/(n+1)), c_ij = sqrt(2/(n+1)) sin(i j pi/(n+1))."""
+    e0, t = 0.3, -1.0
+    H, S = I.chain(n, e0, t)
+    eps, C = O.eigh_generalized(H, S)
+    j = np.arange(1, n + 1)
+    ref = e0 + 2 * t * np.cos(j * np.pi / (n + 1))          # ascending for t < 0
+    assert np.abs(eps - ref).max() <= 1e-13 * max(1, n)
+    i = np.arange(1, n + 1)
+    V = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(i, j) * np.pi / (n + 1))
+    assert _match_columns(C, V) <= 1e-12 * max(1, n)
+
+
+@pytest.mark.parametrize("n,s", [(5, 0.2), (40, -0.3), (120, 0.45)])
+def test_generalized_chain_closed_form(n, s):
+    """S tridiagonal (1, s): eps_j = (e0 + 2t cos th_j)/(1 + 2s cos th_j), th_j = j pi/(n+1)."""
+    e0, t = -0.5, 0.7
+    H, S = I.chain(n, e0, t, s)
+    eps, C = O.eigh_generalized(H, S)
+    th = np.arange(1, n + 1) * np.pi / (n + 1)
+    ref = np.sort((e0 + 2 * t * np.cos(th)) / (1 + 2 * s * np.cos(th)))
+    assert np.abs(eps - ref).max() <= 1e-12 * max(1, np.abs(ref).max())
+    assert np.abs(C.T @ S @ C - np.eye(n)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n,phi", [(6, 0.3), (31, 1.1), (64, 2.5)])
+def test_twisted_ring_closed_form(n, phi):
+    """Complex Hermitian ring with H_{j,j+1} = t e^{i phi/n}: eps_m = e0 + 2t cos((2 pi m + phi)/n)."""
+    e0, t = 0.1, 0.8
+    H, S = I.twisted_ring(n, e0, t, phi)
+    eps, C = O.eigh_generalized(H, S)
+    ref = np.sort(e0 + 2 * t * np.cos((2 * np.pi * np.arange(n) + phi) / n))
+    assert np.abs(eps - ref).max() <= 1e-13 * n
+    assert np.abs(H @ C - C * eps).max() <= 1e-12 * n
+
+
+# ------------------------------------------------------------------ exact brute force
+
+def _rational_pencil(n, seed, cplx):
+    import sympy as sp
+    rng = np.random.default_rng(seed)
+    def rat(x):
+        return sp.Rational(int(x), 8)
+    Hre = rng.integers(-16, 17, size=(n, n))
+    Him = rng.integers(-16, 17, size=(n, n)) if cplx else np.zeros((n, n), int)
+    B = rng.integers(-8, 9, size=(n, n))
+    H = sp.zeros(n, n)
+    for i in range(n):
+        for j in range(i + 1):
+            if i == j:
+                H[i, i] = rat(Hre[i, i])
+            else:
+                v = rat(Hre[i, j]) + (sp.I * rat(Him[i, j]) if cplx else 0)
+                H[i, j] = v
+                H[j, i] = sp.conjugate(v)
+    Bm = sp.Matrix(n, n, lambda i, j: rat(B[i, j]) + (sp.I * rat(B[j, i]) if cplx else 0))
+    S = Bm * Bm.H + sp.eye(n)
+    return H, S
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_bruteforce_characteristic_roots(n, cplx):
+    """Roots of det(H - lam S) in exact rational arithmetic (real symmetric, or complex
+    Hermitian with Gaussian-rational entries), isolated and evaluated to 30 digits."""
+    sp = pytest.importorskip("sympy")
+    Hs, Ss = _rational_pencil(n, 1000 + n + (50 if cplx else 0), cplx)
+    lam = sp.Symbol("lam")
+    poly = sp.Poly(sp.expand((Hs - lam * Ss).det()), lam)
+    coeffs = [sp.re(c) for c in poly.all_coeffs()]
+    assert all(sp.im(c) == 0 for c in poly.all_coeffs())
+    roots = sorted(float(r.evalf(30)) for r in sp.Poly(coeffs, lam).real_roots())
+    assert len(roots) == n
+    H = np.array(Hs.evalf(), dtype=complex if cplx else float)
+    S = np.array(Ss.evalf(), dtype=complex if cplx else float)
+    eps, C = O.eigh_generalized(H, S)
+    scale = np.abs(np.array(roots)).max() + 1.0
+    assert np.abs(eps - np.array(roots)).max() <= 1e-13 * scale
+    assert np.abs(C.conj().T @ S @ C - np.eye(n)).max() <= 1e-13
+
+
+# ------------------------------------------------------------------ each stage on its own
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_stage_cholesky(cplx):
+    _, S = I.random_pencil(37, 5, cplx, cond=1e6)
+    L = O.cholesky(S)
+    assert np.allclose(np.triu(L, 1), 0)
+    assert np.all(np.real(np.diag(L)) > 0) and np.abs(np.imag(np.diag(L))).max() == 0
+    assert np.abs(L @ L.conj().T - S).max() <= 1e-14 * np.abs(S).max() * 37
+    # the Cholesky factor is unique: LAPACK's must agree
+    assert np.abs(L - np.linalg.cholesky(S)).max() <= 1e-10
+
+
+def test_stage_cholesky_reports_column():
+    S = np.eye(6)
+    S[3, 3] = -1.0
+    with pytest.raises(O.OracleError, match="column 3"):
+        O.cholesky(S)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_stage_reduce(cplx):
+    H, S = I.random_pencil(29, 7, cplx, cond=1e3)
+    L = O.cholesky(S)
+    Hp = O.reduce_standard(L, H)
+    assert np.abs(Hp - Hp.conj().T).max() == 0
+    assert np.abs(L @ Hp @ L.conj().T - H).max() <= 1e-12
+    ref = sl.solve_triangular(L, sl.solve_triangular(L, H, lower=True).conj().T, lower=True)
+    assert np.abs(Hp - ref).max() <= 1e-10
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64])
+def test_stage_tridiag_and_backtransform(cplx, n):
+    H, _ = I.random_pencil(n, 11 + n, cplx)
+    d, sub, U, beta = O.tridiagonalize(H)
+    Q = np.eye(n, dtype=H.dtype)
+    for k in range(n - 2):                       # Q = P_0 P_1 ... P_{n-3}
+        u = U[k]
+        Q = Q @ (np.eye(n) - beta[k] * np.outer(u, u.conj()))
+    T = np.diag(d).astype(H.dtype)
+    if n > 1:
+        T += np.diag(sub, -1) + np.diag(sub.conj(), 1)
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() <= 1e-13 * max(1, n)
+    assert np.abs(Q @ T @ Q.conj().T - H).max() <= 1e-13 * max(1, n) * np.abs(H).max()
+    lam, Z = O.tridiagonal_eig(d, np.abs(sub))
+    X = O.back_transform(sub, U, beta, Z)
+    assert np.abs(H @ X - X * lam).max() <= 1e-12 * max(1, n) * np.abs(H).max()
+    assert np.abs(X.conj().T @ X - np.eye(n)).max() <= 1e-13 * max(1, n)
+
+
+@pytest.mark.parametrize("kind", ["random", "wilkinson", "clustered", "split", "zero"])
+def test_stage_tridiagonal_ql(kind):
+    rng = np.random.default_rng(3)
+    n = 60
+    if kind == "random":
+        d, e = rng.standard_normal(n), rng.standard_normal(n - 1)
+    elif kind == "wilkinson":                    # W+_n: pairs of eigenvalues agreeing to many digits
+        n = 21
+        d, e = np.abs(np.arange(n) - 10).astype(float), np.ones(n - 1)
+    elif kind == "clustered":
+        d, e = np.ones(n) + 1e-12 * rng.standard_normal(n), 1e-9 * rng.standard_normal(n - 1)
+    elif kind == "split":
+        d, e = rng.standard_normal(n), rng.standard_normal(n - 1)
+        e[[5, 20, 21, 40]] = 0.0
+    else:
+        d, e = np.zeros(n), np.zeros(n - 1)
+    lam, Z = O.tridiagonal_eig(d, e)
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    assert np.all(np.diff(lam) >= 0)
+    assert np.abs(Z.T @ Z - np.eye(n)).max() <= 1e-13 * n
+    assert np.abs(T @ Z - Z * lam).max() <= 1e-14 * n * max(1.0, np.abs(T).max())
+    ref = sl.eigh_tridiagonal(d, e, eigvals_only=True)
+    assert np.abs(lam - ref).max() <= 1e-13 * n * max(1.0, np.abs(T).max())
+
+
+# ------------------------------------------------------------------ pencils and invariants
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("cond", [1e1, 1e6, 1e10])
+def test_lapack_cross_check(cplx, cond):
+    """Independent LAPACK solve (Cholesky-based sygvd/hegvd).  A random H is not bounded
+    relative to an ill-conditioned S, so ||H'|| = max|eps| >> ||H||/||S|| and both
+    Cholesky-based solvers carry errors of order u ||S|| ||H'|| ||c_i||^2 (the two-sided
+    reduction's backward error), which is the bound used here."""
+    n = 48
+    H, S = I.random_pencil(n, 21, cplx, cond)
+    eps, C = O.eigh_generalized(H, S)
+    ref = sl.eigh(H, S, eigvals_only=True)
+    cn = np.sum(np.abs(C) ** 2, axis=0)
+    bound = O.U_ROUND * (np.linalg.norm(H, 2) + np.abs(eps).max() * np.linalg.norm(S, 2)) * cn
+    assert np.all(np.abs(eps - ref) <= np.maximum(1e-12, 8 * bound))
+
+
+def _scaled_checks(H, S, eps, C):
+    nh, ns = np.linalg.norm(H, 2), np.linalg.norm(S, 2)
+    cn = np.linalg.norm(C, axis=0)
+    G = C.conj().T @ S @ C - np.eye(C.shape[1])
+    orth = np.abs(G / np.outer(cn, cn) / ns).max()
+    R = H @ C - (S @ C) * eps
+    bwd = (np.linalg.norm(R, axis=0) / ((nh + np.abs(eps) * ns) * cn)).max()
+    return orth, bwd
+
+
+@pytest.mark.parametrize("tiling", [(1, 1, 1), (2, 1, 1)])
+def test_cluster_invariants(tiling):
+    """Scaled S-orthonormality and backward error, and Tr(rho S) = n_elec, on the Si
+    Gaussian basis (kappa(S) ~ 1e9 .. 1e10)."""
+    p = I.collinear_gamma(tiling, 0, 0.01)
+    H, S = p.H[0].numpy(), p.S[0].numpy()
+    r = O.solve(H, S, p.kT, p.n_elec)
+    orth, bwd = _scaled_checks(H, S, r.eps[0], r.C[0])
+    M = H.shape[0]
+    assert orth <= 1e-12 * math.sqrt(M)
+    assert bwd <= 1e-12 * math.sqrt(M)
+    tr = np.trace(r.rho[0] @ S).real
+    beta = O.eig_condition(H, S, r.eps[0], r.C[0])
+    assert abs(tr - p.n_elec) <= 1e-9 * p.n_elec * max(1.0, beta.max() / 1e-10)
+    ref = sl.eigh(H, S, eigvals_only=True)
+    assert np.all(np.abs(r.eps[0] - ref) <= np.maximum(1e-10, 8 * beta))
+    # E_band = Tr(rho H) for a single k-point
+    assert abs(r.e_band - np.trace(r.rho[0] @ H).real) <= 1e-9 * max(1.0, abs(r.e_band)) * max(1.0, beta.max() / 1e-10)
+
+
+def test_kpoint_time_reversal_pairs():
+    """H(-k) = conj H(k): the 8 Monkhorst-Pack points form 4 pairs with equal spectra."""
+    p = I.periodic((1, 1, 1), 1, 0.01)
+    kf = p.meta["kpoints"]
+    r = O.solve(p.H.numpy(), p.S.numpy(), p.kT, p.n_elec, kweights=p.kweights)
+    for a in range(p.nk):
+        b = int(np.argmin(np.abs(kf + kf[a]).sum(1)))
+        assert np.allclose(kf[b], -kf[a])
+        beta = O.eig_condition(p.H[a].numpy(), p.S[a].numpy(), r.eps[a], r.C[a])
+        assert np.all(np.abs(r.eps[a] - r.eps[b]) <= np.maximum(1e-10, 16 * beta))
+    tr = sum(p.kweights[k] * np.trace(r.rho[k] @ p.S[k].numpy()).real for k in range(p.nk))
+    assert abs(tr - p.n_elec) <= 1e-6 * p.n_elec
+
+
+def test_noncollinear_zero_mixing_doubles_collinear():
+    """Delta = lambda = 0: every collinear eigenvalue appears exactly twice."""
+    p = I.noncollinear((1, 1, 1), 2, 0.01, delta=0.0, lam=0.0)
+    Hc, Sc = p.meta["H"].numpy(), p.meta["S"].numpy()
+    ec, Cc = O.eigh_generalized(Hc, Sc)
+    r = O.solve(p.H.numpy(), p.S.numpy(), p.kT, p.n_elec, spin="noncollinear")
+    beta = O.eig_condition(Hc, Sc, ec, Cc)
+    assert np.all(np.abs(r.eps[0][0::2] - ec) <= np.maximum(1e-10, 16 * beta))
+    assert np.all(np.abs(r.eps[0][1::2] - ec) <= np.maximum(1e-10, 16 * beta))
+
+
+def test_noncollinear_collinear_moments_split():
+    """All m parallel to z and lambda = 0: spec = spec(H + D Sz, S) U spec(H - D Sz, S)."""
+    import torch
+    p = I.noncollinear((1, 1, 1), 2, 0.01)
+    H, S = p.meta["H"], p.meta["S"]
+    natoms = p.meta["atoms"]
+    m = np.zeros((natoms, 3))
+    m[:, 2] = np.where(np.arange(natoms) % 3 == 0, -1.0, 1.0)
+    HN = I.spinor_hamiltonian(H, S, m, p.meta["KA"], 0.05, 0.0).numpy()
+    n = H.shape[0]
+    r = O.solve(HN[None], S.numpy()[None].astype(complex), 0.01, 4.0 * natoms, spin="noncollinear")
+    up = HN[:n, :n].real
+    dn = HN[n:, n:].real
+    assert np.abs(HN[:n, n:]).max() == 0
+    eu, Cu = O.eigh_generalized(up, S.numpy())
+    ed, Cd = O.eigh_generalized(dn, S.numpy())
+    both = np.sort(np.concatenate([eu, ed]))
+    beta = np.concatenate([O.eig_condition(up, S.numpy(), eu, Cu), O.eig_condition(dn, S.numpy(), ed, Cd)])
+    assert np.all(np.abs(r.eps[0] - both) <= np.maximum(1e-10, 16 * beta.max()))
+
+
+def test_noncollinear_uniform_chain_closed_form():
+    """S = I chain with one uniform unit moment: eps = e0 + 2t cos th_j +- Delta."""
+    n, e0, t, delta = 24, 0.2, -0.6, 0.05
+    H, S = I.chain(n, e0, t)
+    import torch
+    m = np.array([[0.6, 0.0, 0.8]])
+    HN = I.spinor_hamiltonian(torch.tensor(H), torch.tensor(S), m, np.zeros((1, n, n)), delta, 0.0,
+                              block=n).numpy()
+    r = O.solve(HN[None], S[None].astype(complex), 0.01, float(n), spin="noncollinear")
+    base = e0 + 2 * t * np.cos(np.arange(1, n + 1) * np.pi / (n + 1))
+    ref = np.sort(np.concatenate([base + delta, base - delta]))
+    assert np.abs(r.eps[0] - ref).max() <= 1e-13 * n
+
+
+# ------------------------------------------------------------------ occupations and mu
+
+def test_fermi_function():
+    x = np.array([-800.0, -40.0, -1.0, 0.0, 1.0, 40.0, 800.0])
+    f = O.fermi(x)
+    assert f[3] == 0.5
+    assert np.all(np.isfinite(f))
+    assert np.abs(f + O.fermi(-x) - 1).max() <= 1e-16
+    assert abs(f[4] - 1 / (1 + math.e)) <= 1e-16
+
+
+def test_mu_particle_hole_symmetry():
+    """Half-filled bipartite chain (e0 = 0): mu = 0 by particle-hole symmetry."""
+    n = 40
+    H, S = I.chain(n, 0.0, -1.0)
+    r = O.solve(H, S, 0.05, float(n))
+    assert abs(r.mu) <= 1e-12
+    assert abs(np.trace(r.rho[0]).real - n) <= 1e-10
+
+
+def test_mu_two_levels():
+    """Two levels, one electron pair: f(e1 - mu) + f(e2 - mu) = 1 gives mu = (e1 + e2)/2."""
+    H = np.diag([-0.3, 0.5])
+    r = O.solve(H, np.eye(2), 0.07, 2.0)
+    assert abs(r.mu - 0.1) <= 1e-14
+    assert abs(r.occ[0].sum() - 1.0) <= 1e-14
+
+
+def test_mu_rejects_bad_arguments():
+    H = np.diag([-0.3, 0.5])
+    with pytest.raises(O.OracleError):
+        O.solve(H, np.eye(2), 0.0, 2.0)
+    with pytest.raises(O.OracleError):
+        O.solve(H, np.eye(2), 0.01, 4.0)
+
+
+def test_density_matrix_convention_and_truncation():
+    """rho = C diag(g_s f) C^H; the paper's n_lm = sum_i f_i c*_li c_mi equals conj(rho)/g_s."""
+    H, S = I.random_pencil(12, 4, True, 10.0)
+    r = O.solve(H, S, 0.5, 6.0)
+    C, f = r.C[0], r.occ[0]
+    n_paper = np.einsum("i,li,mi->lm", f, C.conj(), C)
+    assert np.abs(n_paper - r.rho[0].conj() / 2.0).max() <= 1e-12
+    assert np.abs(r.rho[0] - r.rho[0].conj().T).max() <= 1e-13
+
+
+# ------------------------------------------------------------------ workload structure
+
+def _golden():
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_sizes.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                out[k] = float(v)
+    return out
+
+
+def test_paper_workload_sizes():
+    g = _golden()
+    assert I.N_PER_ATOM == g["basis_per_atom"]
+    assert abs(I.A_BOHR / 1.8897261 - g["lattice_angstrom"]) < 2e-3
+    rng = np.random.default_rng(0)
+    assert len(I.diamond_positions((5, 5, 6), rng)) == g["atoms_collinear_big"]
+    assert g["atoms_collinear_big"] * I.N_PER_ATOM == g["basis_collinear_big"]
+    assert len(I.diamond_positions((4, 4, 5), rng)) == g["atoms_nc_big"]
+    assert g["atoms_nc_big"] * I.N_PER_ATOM == g["basis_nc_big"]
+    n = 6656
+    assert np.zeros((n, n), np.complex128).nbytes == g["bytes_per_complex_n2"] * n * n
+    assert np.zeros((2 * n, 2 * n), np.complex128).nbytes == g["bytes_per_nc_n2"] * n * n
+    assert len(I.mp_kpoints((2, 2, 2))) == g["kmesh"] ** 3
