@@ -1,0 +1,117 @@
+/* gks.h -- C ABI of the GB300 generalized Kohn-Sham eigensolver and density matrix.
+ *
+ * Problem (arXiv 2606.09058, Sec. 2, generalized eigenvalue problem H C = S C eps; its
+ * Bloch form per k-point, Eq. eigenval_problem; the noncollinear spinor form of Sec. 2
+ * and Sec. 3.2 with S_NC = diag(S, S)); occupations and chemical potential (Sec. 3.1
+ * Part 3, Sec. 3.2 Part 4); density matrix (Sec. 2 n_lm, Sec. 3.1 Part 4).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers allocated and owned by the caller, contiguous
+ *    and row-major.  Complex data is interleaved (re, im) double pairs.
+ *  - Hermitian inputs are read from their LOWER triangle only (row >= column).
+ *  - M is the matrix order: M = n (collinear) or 2n (noncollinear).
+ *  - All work is enqueued on the stream given at context creation.  gks_solve returns
+ *    host-side validation status; device-side failures (S not positive definite, no
+ *    convergence, invalid occupation parameters) are returned by gks_sync.
+ *  - Errors never cross the ABI as exceptions and never trap on the device.  The text
+ *    of the last error (with the failing column / batch item) is in gks_last_error.
+ *  - One context per host thread.  A context owns its workspace (device memory sized
+ *    for the last problem shape) until gks_destroy.
+ */
+#ifndef GKS_H
+#define GKS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gks_ctx gks_ctx;
+
+typedef enum {
+  GKS_OK = 0,
+  GKS_EINVAL = 1,    /* bad argument (shape, pointer, kT <= 0, n_elec out of range, NaN) */
+  GKS_ENOTSPD = 2,   /* S is not positive definite (column in gks_last_error) */
+  GKS_ENOCONV = 3,   /* an iteration did not converge */
+  GKS_ENOMEM = 4,    /* device allocation failed */
+  GKS_ECUDA = 5,     /* CUDA runtime error */
+  GKS_ETIMEOUT = 6,  /* a bounded device-side wait expired */
+  GKS_ENOTIMPL = 7   /* option not implemented */
+} gks_status;
+
+typedef enum { GKS_R64 = 0, GKS_C128 = 1 } gks_dtype;        /* real symmetric / complex Hermitian */
+typedef enum { GKS_COLLINEAR = 0, GKS_NONCOLLINEAR = 1 } gks_spin; /* g_s = 2 / g_s = 1 */
+typedef enum { GKS_FP64 = 0 } gks_prec;
+
+typedef struct {
+  int device;          /* CUDA device ordinal */
+  void* cuda_stream;   /* cudaStream_t to enqueue on (NULL = legacy default stream) */
+  int precision;       /* gks_prec */
+  double f_cut;        /* occupations below f_cut are left out of rho (default 1e-16) */
+} gks_opts;
+
+/* Create a context bound to opts->device and opts->cuda_stream.  opts may be NULL
+ * (device 0, default stream).  On success *ctx is set; release with gks_destroy. */
+gks_status gks_create(gks_ctx** ctx, const gks_opts* opts);
+
+/* Release the context and its workspace.  NULL is accepted. */
+gks_status gks_destroy(gks_ctx* ctx);
+
+/* Message describing the last error on this context ("" if none).  Valid until the next
+ * call on the same context. */
+const char* gks_last_error(const gks_ctx* ctx);
+
+/* Full hot path for nk pencils that share one chemical potential (paper Sec. 3.1 Parts
+ * 2-4; Sec. 3.2 Parts 3-5):
+ *   Cholesky S_k = L_k L_k^H; H'_k = L_k^-1 H_k L_k^-H; Householder tridiagonalization;
+ *   divide-and-conquer tridiagonal eigensolve; C_k = L_k^-H Q_k D_k Z_k;
+ *   mu from sum_k w_k g_s sum_i f((eps_ki - mu)/kT) = n_elec, f(x) = 1/(1+e^x);
+ *   rho_k = C_k diag(g_s f_k) C_k^H over the columns with f >= f_cut;
+ *   E_band = sum_k w_k g_s sum_i f_ki eps_ki.
+ * Arguments:
+ *   H       (nk, M, M) dtype, Hermitian, lower triangle read.  Noncollinear: spin-major
+ *           2 x 2 blocks [[H_aa, H_ab], [H_ba, H_bb]] (paper Sec. 3.2 H_NC).
+ *   S       (nk, n, n) dtype, Hermitian positive definite, lower triangle read.
+ *           Noncollinear: the n x n S; S_NC = diag(S, S) is implied.
+ *   n, nk   basis size per spin and number of k-points (n >= 1, nk >= 1).
+ *   dtype   GKS_R64 (collinear Gamma only) or GKS_C128.  Noncollinear requires C128.
+ *   kT      Fermi smearing (Hartree), > 0.  n_elec in (0, g_s M).
+ *   kweights device (nk) doubles summing to 1, or NULL for 1/nk.
+ *   flags   reserved, pass 0.
+ * Outputs (device, caller-allocated):
+ *   eps (nk, M) ascending per k; C (nk, M, M) dtype, column i = eigenvector i with
+ *   C^H S C = I and its largest-modulus entry real positive; mu (1); rho (nk, M, M) full
+ *   Hermitian storage; e_band (1) or NULL.
+ *   rho follows C diag(g_s f) C^H; the paper's n_lm = sum_i f_i c*_li c_mi equals
+ *   conj(rho)/g_s (its transpose for Hermitian rho).
+ * The inputs are not modified.  Returns GKS_OK or a host validation error; device
+ * status comes from gks_sync. */
+gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int64_t nk, int dtype, int spin_mode,
+                     double kT, double n_elec, const double* kweights, unsigned flags, double* eps, void* C,
+                     double* mu, void* rho, double* e_band);
+
+/* Wait for the context's stream and report the first device-side failure of the work
+ * enqueued since the previous gks_sync (GKS_ENOTSPD with the failing column and
+ * k-point, GKS_ENOCONV, GKS_EINVAL for occupation parameters found invalid). */
+gks_status gks_sync(gks_ctx* ctx);
+
+/* Stage entry points (same conventions; `count` independent matrices of order m,
+ * stride m*m elements).  Used to check each stage on its own. */
+
+/* In place: A_b = L_b L_b^H, L in the lower triangle (upper triangle untouched). */
+gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype);
+
+/* In place: H_b <- L_b^-1 H_b L_b^-H (lower triangle written; upper untouched), with L_b
+ * the Cholesky factor of S_b.  S_b is overwritten by L_b. */
+gks_status gks_reduce(gks_ctx* ctx, void* H, void* S, int64_t m, int64_t count, int dtype);
+
+/* Real symmetric tridiagonal eigensolve by divide and conquer: d (count, m) diagonal,
+ * e (count, m) with e[b][i] = T_{i+1,i} (last entry ignored); lam (count, m) ascending,
+ * Z (count, m, m) real, column j = eigenvector j.  d and e are not modified. */
+gks_status gks_stedc(gks_ctx* ctx, const double* d, const double* e, int64_t m, int64_t count, double* lam,
+                     double* Z);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKS_H */

@@ -1,0 +1,457 @@
+// Runtime and C ABI: context, workspace arena, stage orchestration, status reporting.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dense.h"
+#include "gks.h"
+
+using namespace gks;
+
+namespace {
+constexpr int NB = 64;  // panel / reflector block width
+
+struct Arena {
+  size_t off = 0;
+  template <typename X>
+  size_t take(size_t n) {
+    size_t o = (off + 255) & ~size_t(255);
+    off = o + sizeof(X) * (n ? n : 1);
+    return o;
+  }
+};
+}  // namespace
+
+struct gks_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double f_cut = 1e-16;
+  std::string err;
+  // workspace for the current shape
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int m = -1, n = -1, nk = -1, es = -1, nc = -1;
+  DcPlan* dc = nullptr;
+  DevStatus* st = nullptr;
+  // offsets (bytes) of per-item arrays; each holds nk items
+  size_t oA, oL, oDinv, oF, oP, oQ, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho,
+      ow, oeb, odc;
+  long long sMM, sDinv, sF, sP, sQ, sV, sG, sT, sY, sVec;
+};
+
+namespace {
+
+gks_status fail(gks_ctx* c, gks_status code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+gks_status cuda_check(gks_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, GKS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return GKS_OK;
+}
+
+void release_ws(gks_ctx* c) {
+  if (c->ws) cudaFree(c->ws);
+  if (c->st) cudaFree(c->st);
+  dc_plan_destroy(c->dc);
+  c->ws = nullptr;
+  c->st = nullptr;
+  c->dc = nullptr;
+  c->ws_bytes = 0;
+  c->m = -1;
+}
+
+// Workspace for nk problems of order m (element size es, n = basis per spin).
+gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
+  if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc) return GKS_OK;
+  release_ws(c);
+  const size_t MM = (size_t)m * m;
+  const int nblk = (m + NB - 1) / NB;
+  c->sMM = (long long)MM;
+  c->sDinv = (long long)nblk * NB * NB;
+  c->sF = NB * NB;
+  c->sP = (long long)m * NB;
+  c->sQ = (long long)NB * m;
+  c->sV = (long long)m * NB;
+  c->sG = NB * NB;
+  c->sT = NB * NB;
+  c->sY = (long long)NB * m;
+  c->sVec = m;
+  Arena a;
+  auto elems = [&](long long per) { return (size_t)per * nk * es; };
+  c->oA = a.take<char>(elems(c->sMM));
+  c->oL = a.take<char>(elems(c->sMM));
+  c->oDinv = a.take<char>(elems(c->sDinv));
+  c->oF = a.take<char>(elems(c->sF));
+  c->oP = a.take<char>(elems(c->sP));
+  c->oQ = a.take<char>(elems(c->sQ));
+  c->oV = a.take<char>(elems(c->sV));
+  c->oG = a.take<char>(elems(c->sG));
+  c->oT = a.take<char>(elems(c->sT));
+  c->oY = a.take<char>(elems(c->sY));
+  c->oY2 = a.take<char>(elems(c->sY));
+  c->ou = a.take<char>(elems(m));
+  c->op = a.take<char>(elems(m));
+  c->oph = a.take<char>(elems(m));
+  c->otau = a.take<double>((size_t)m * nk);
+  c->otb = a.take<double>((size_t)NB * nk);
+  c->od = a.take<double>((size_t)m * nk);
+  c->oe = a.take<double>((size_t)m * nk);
+  c->oZ = a.take<double>(MM * nk);
+  c->oocc = a.take<double>((size_t)m * nk);
+  c->oks = a.take<double>((size_t)m * nk);
+  c->onrho = a.take<int>((size_t)nk);
+  c->ow = a.take<double>((size_t)nk);
+  c->oeb = a.take<double>(4);
+  c->dc = dc_plan_create(m, nk);
+  c->odc = a.take<char>(dc_workspace_bytes(c->dc));
+  c->ws_bytes = a.off;
+  if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->ws = nullptr;
+    dc_plan_destroy(c->dc);
+    c->dc = nullptr;
+    return fail(c, GKS_ENOMEM, "workspace allocation of " + std::to_string(c->ws_bytes) + " bytes failed");
+  }
+  if (cudaMalloc(&c->st, sizeof(DevStatus) * nk) != cudaSuccess) {
+    cudaGetLastError();
+    release_ws(c);
+    return fail(c, GKS_ENOMEM, "status allocation failed");
+  }
+  cudaMemset(c->st, 0, sizeof(DevStatus) * nk);
+  std::vector<double> w(nk, 1.0 / nk);
+  cudaMemcpy(c->ws + c->ow, w.data(), sizeof(double) * nk, cudaMemcpyHostToDevice);
+  c->m = m;
+  c->n = n;
+  c->nk = nk;
+  c->es = es;
+  c->nc = nc;
+  return cuda_check(c, "workspace setup");
+}
+
+template <typename X>
+X* at(gks_ctx* c, size_t off) {
+  return reinterpret_cast<X*>(c->ws + off);
+}
+
+template <typename T>
+void gm(cudaStream_t s, int count, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda,
+        long long sA, const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC, int lower = 0,
+        const double* ks = nullptr, long long sK = 0, const int* kdev = nullptr) {
+  if (M <= 0 || N <= 0) return;
+  GemmBatch g{};
+  g.base = GemmDesc{A, B, C, ks, M, N, K, lda, ldb, ldc};
+  g.list = nullptr;
+  g.sA = sA;
+  g.sB = sB;
+  g.sC = sC;
+  g.sK = sK;
+  g.kdev = kdev;
+  g.count = count;
+  g.opA = opA;
+  g.opB = opB;
+  g.lower = lower;
+  g.alpha = alpha;
+  g.beta = beta;
+  gemm<T>(g, M, N, s);
+}
+
+// Blocked right-looking Cholesky of L (in place, lower) with the inverse diagonal blocks.
+template <typename T>
+void potrf_run(gks_ctx* c, T* L, int M, int nk) {
+  cudaStream_t s = c->stream;
+  T* Dinv = at<T>(c, c->oDinv);
+  T* P = at<T>(c, c->oP);
+  for (int k0 = 0; k0 < M; k0 += NB) {
+    const int kb = std::min(NB, M - k0), blk = k0 / NB;
+    T* Db = Dinv + (size_t)blk * NB * NB;
+    potf2_inv<T>(L, M, c->sMM, k0, kb, Db, NB, c->sDinv, c->st, nk, s);
+    const int rows = M - k0 - kb;
+    if (rows <= 0) continue;
+    T* L21 = L + (size_t)(k0 + kb) * M + k0;
+    gm<T>(s, nk, OP_N, OP_C, rows, kb, kb, 1.0, L21, M, c->sMM, Db, NB, c->sDinv, 0.0, P, NB, c->sP);
+    copy2d<T>(L21, M, c->sMM, P, NB, c->sP, rows, kb, nk, s);
+    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, P, NB, c->sP, P, NB, c->sP, 1.0, L21 + kb, M, c->sMM, 1);
+  }
+}
+
+// Two-sided blocked reduction A <- L^-1 A L^-H (lower triangle), then the deferred
+// block-triangular solve of the strictly lower block part.
+template <typename T>
+void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
+  cudaStream_t s = c->stream;
+  T* Dinv = at<T>(c, c->oDinv);
+  T* F = at<T>(c, c->oF);
+  T* P = at<T>(c, c->oP);
+  T* Q = at<T>(c, c->oQ);
+  for (int k0 = 0; k0 < M; k0 += NB) {
+    const int kb = std::min(NB, M - k0), blk = k0 / NB;
+    const T* Db = Dinv + (size_t)blk * NB * NB;
+    hegst_diag<T>(A, M, c->sMM, k0, kb, Db, NB, c->sDinv, F, NB, c->sF, nk, s);
+    const int rows = M - k0 - kb;
+    if (rows <= 0) continue;
+    const T* L21 = L + (size_t)(k0 + kb) * M + k0;
+    T* A21 = A + (size_t)(k0 + kb) * M + k0;
+    T* A22 = A21 + kb;
+    gm<T>(s, nk, OP_N, OP_C, rows, kb, kb, 1.0, A21, M, c->sMM, Db, NB, c->sDinv, 0.0, P, NB, c->sP);
+    gm<T>(s, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, P, NB, c->sP);
+    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, P, NB, c->sP, 1.0, A22, M, c->sMM, 1);
+    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, P, NB, c->sP, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gm<T>(s, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, P, NB, c->sP);
+    copy2d<T>(A21, M, c->sMM, P, NB, c->sP, rows, kb, nk, s);
+  }
+  for (int r0 = NB; r0 < M; r0 += NB) {
+    const int rb = std::min(NB, M - r0), blk = r0 / NB;
+    const T* Db = Dinv + (size_t)blk * NB * NB;
+    T* Ai = A + (size_t)r0 * M;
+    copy2d<T>(Q, M, c->sQ, Ai, M, c->sMM, rb, r0, nk, s);
+    gm<T>(s, nk, OP_N, OP_N, rb, r0, rb, 1.0, Db, NB, c->sDinv, Q, M, c->sQ, 0.0, Ai, M, c->sMM);
+    const int below = M - r0 - rb;
+    if (below > 0)
+      gm<T>(s, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM, 1.0,
+            A + (size_t)(r0 + rb) * M, M, c->sMM);
+  }
+}
+
+// X <- Q X with Q = P_{M-1} ... P_2 (reflectors stored by the reduction), blocked WY.
+template <typename T>
+void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
+  cudaStream_t s = c->stream;
+  T* V = at<T>(c, c->oV);
+  T* G = at<T>(c, c->oG);
+  T* Tm = at<T>(c, c->oT);
+  T* Y = at<T>(c, c->oY);
+  T* Y2 = at<T>(c, c->oY2);
+  double* tau = at<double>(c, c->otau);
+  double* tb = at<double>(c, c->otb);
+  for (int j0 = 2; j0 <= M - 1; j0 += NB) {
+    const int j1 = std::min(j0 + NB - 1, M - 1), nbb = j1 - j0 + 1;
+    gather_reflectors<T>(A, M, c->sMM, tau, M, j0, j1, V, NB, c->sV, tb, NB, nk, s);
+    gm<T>(s, nk, OP_C, OP_N, nbb, nbb, j1, 1.0, V, NB, c->sV, V, NB, c->sV, 0.0, G, NB, c->sG);
+    larft<T>(G, NB, c->sG, tb, NB, nbb, Tm, NB, c->sT, nk, s);
+    gm<T>(s, nk, OP_C, OP_N, nbb, M, j1, 1.0, V, NB, c->sV, X, M, c->sMM, 0.0, Y, M, c->sY);
+    gm<T>(s, nk, OP_N, OP_N, nbb, M, nbb, 1.0, Tm, NB, c->sT, Y, M, c->sY, 0.0, Y2, M, c->sY);
+    gm<T>(s, nk, OP_N, OP_N, j1, M, nbb, -1.0, V, NB, c->sV, Y2, M, c->sY, 1.0, X, M, c->sMM);
+  }
+}
+
+// X <- L^-H X by block back substitution with the inverse diagonal blocks.
+template <typename T>
+void unreduce_run(gks_ctx* c, const T* L, T* X, int M, int nk) {
+  cudaStream_t s = c->stream;
+  T* Dinv = at<T>(c, c->oDinv);
+  T* Q = at<T>(c, c->oQ);
+  const int nblk = (M + NB - 1) / NB;
+  for (int blk = nblk - 1; blk >= 0; blk--) {
+    const int r0 = blk * NB, rb = std::min(NB, M - r0);
+    const T* Db = Dinv + (size_t)blk * NB * NB;
+    T* Xi = X + (size_t)r0 * M;
+    copy2d<T>(Q, M, c->sQ, Xi, M, c->sMM, rb, M, nk, s);
+    gm<T>(s, nk, OP_C, OP_N, rb, M, rb, 1.0, Db, NB, c->sDinv, Q, M, c->sQ, 0.0, Xi, M, c->sMM);
+    if (r0 > 0)
+      gm<T>(s, nk, OP_C, OP_N, r0, M, rb, -1.0, L + (size_t)r0 * M, M, c->sMM, Xi, M, c->sMM, 1.0, X, M, c->sMM);
+  }
+}
+
+template <typename T>
+gks_status solve_t(gks_ctx* c, const T* H, const T* S, int n, int nk, bool nc, double kT, double n_elec,
+                   const double* kw, double* eps, T* C, double* mu, T* rho, double* e_band) {
+  const int M = nc ? 2 * n : n;
+  gks_status rc = ensure_ws(c, M, n, nk, (int)sizeof(T), nc ? 1 : 0);
+  if (rc) return rc;
+  cudaStream_t s = c->stream;
+  T* A = at<T>(c, c->oA);
+  T* L = at<T>(c, c->oL);
+  cudaMemsetAsync(c->st, 0, sizeof(DevStatus) * nk, s);
+  copy2d<T>(A, M, c->sMM, H, M, (long long)M * M, M, M, nk, s);
+  if (nc) spinor_overlap<T>(L, c->sMM, S, n, (long long)n * n, n, nk, s);
+  else copy2d<T>(L, M, c->sMM, S, n, (long long)n * n, n, n, nk, s);
+  // (a1) Cholesky of S, (a2) reduction to the standard problem
+  potrf_run<T>(c, L, M, nk);
+  hegst_run<T>(c, A, L, M, nk);
+  // (a3-a4) Householder tridiagonalization with a real-making phase
+  T* u = at<T>(c, c->ou);
+  T* p = at<T>(c, c->op);
+  double* tau = at<double>(c, c->otau);
+  for (int j = M - 1; j >= 2; j--) hetrd_step<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, nk, s);
+  double* d = at<double>(c, c->od);
+  double* e = at<double>(c, c->oe);
+  T* ph = at<T>(c, c->oph);
+  hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, nk, s);
+  // (a5) divide and conquer on the real tridiagonal
+  double* Z = at<double>(c, c->oZ);
+  dc_solve(c->dc, d, e, M, eps, Z, c->sMM, c->ws + c->odc, c->st, s);
+  // (a6) X = Q D Z, C = L^-H X
+  apply_phase<T>(C, M, c->sMM, Z, M, c->sMM, ph, M, M, nk, s);
+  backtransform_run<T>(c, A, C, M, nk);
+  unreduce_run<T>(c, L, C, M, nk);
+  column_phase<T>(C, M, c->sMM, M, M, nk, s);
+  // (a8) occupations and chemical potential, (a9) density matrix
+  double* occ = at<double>(c, c->oocc);
+  double* ks = at<double>(c, c->oks);
+  int* nrho = at<int>(c, c->onrho);
+  const double* w = kw ? kw : at<double>(c, c->ow);
+  double* eb = e_band ? e_band : at<double>(c, c->oeb);
+  fermi_mu(eps, M, nk, w, nc ? 1.0 : 2.0, kT, n_elec, c->f_cut, occ, ks, mu, eb, nrho, c->st, 1, s);
+  GemmBatch g{};
+  g.base = GemmDesc{C, C, rho, ks, M, M, M, M, M, M};
+  g.sA = c->sMM;
+  g.sB = c->sMM;
+  g.sC = c->sMM;
+  g.sK = M;
+  g.kdev = nrho;
+  g.count = nk;
+  g.opA = OP_N;
+  g.opB = OP_C;
+  g.lower = 1;
+  g.alpha = 1.0;
+  g.beta = 0.0;
+  gemm<T>(g, M, M, s);
+  mirror_lower<T>(rho, M, c->sMM, M, nk, s);
+  return cuda_check(c, "gks_solve launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
+  if (!ctx) return GKS_EINVAL;
+  gks_ctx* c = new gks_ctx();
+  if (opts) {
+    c->device = opts->device;
+    c->stream = static_cast<cudaStream_t>(opts->cuda_stream);
+    if (opts->f_cut > 0.0) c->f_cut = opts->f_cut;
+    if (opts->precision != GKS_FP64) {
+      delete c;
+      return GKS_ENOTIMPL;
+    }
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return GKS_ECUDA;
+  }
+  *ctx = c;
+  return GKS_OK;
+}
+
+gks_status gks_destroy(gks_ctx* ctx) {
+  if (!ctx) return GKS_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  release_ws(ctx);
+  delete ctx;
+  return GKS_OK;
+}
+
+const char* gks_last_error(const gks_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int64_t nk, int dtype, int spin_mode,
+                     double kT, double n_elec, const double* kweights, unsigned flags, double* eps, void* C,
+                     double* mu, void* rho, double* e_band) {
+  if (!ctx) return GKS_EINVAL;
+  ctx->err.clear();
+  if (!H || !S || !eps || !C || !mu || !rho) return fail(ctx, GKS_EINVAL, "null array argument");
+  if (n < 1 || nk < 1 || n > 46340 || nk > 65535) return fail(ctx, GKS_EINVAL, "n or nk out of range");
+  if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
+  if (spin_mode != GKS_COLLINEAR && spin_mode != GKS_NONCOLLINEAR) return fail(ctx, GKS_EINVAL, "unknown spin mode");
+  const bool nc = spin_mode == GKS_NONCOLLINEAR;
+  if (nc && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
+  if (nc && 2 * n > 46340) return fail(ctx, GKS_EINVAL, "2n out of range");
+  if (!(kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
+  const double gs = nc ? 1.0 : 2.0;
+  const double M = nc ? 2.0 * n : (double)n;
+  if (!(n_elec > 0.0) || !(n_elec < gs * M)) return fail(ctx, GKS_EINVAL, "n_elec must lie in (0, g_s M)");
+  if (flags != 0) return fail(ctx, GKS_ENOTIMPL, "flags must be 0");
+  cudaSetDevice(ctx->device);
+  if (dtype == GKS_R64)
+    return solve_t<double>(ctx, static_cast<const double*>(H), static_cast<const double*>(S), (int)n, (int)nk, nc, kT,
+                           n_elec, kweights, eps, static_cast<double*>(C), mu, static_cast<double*>(rho), e_band);
+  return solve_t<zc>(ctx, static_cast<const zc*>(H), static_cast<const zc*>(S), (int)n, (int)nk, nc, kT, n_elec,
+                     kweights, eps, static_cast<zc*>(C), mu, static_cast<zc*>(rho), e_band);
+}
+
+gks_status gks_sync(gks_ctx* ctx) {
+  if (!ctx) return GKS_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(ctx, GKS_ECUDA, std::string("synchronize: ") + cudaGetErrorString(e));
+  if (!ctx->st) return GKS_OK;
+  std::vector<DevStatus> h(ctx->nk);
+  if (cudaMemcpy(h.data(), ctx->st, sizeof(DevStatus) * ctx->nk, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(ctx, GKS_ECUDA, "status read failed");
+  for (int k = 0; k < ctx->nk; k++) {
+    if (h[k].code == ST_OK) continue;
+    gks_status code = (gks_status)h[k].code;
+    std::string what = code == GKS_ENOTSPD ? "S is not positive definite at column " + std::to_string(h[k].info)
+                       : code == GKS_ENOCONV ? "iteration did not converge (index " + std::to_string(h[k].info) + ")"
+                       : code == GKS_EINVAL ? std::string("invalid occupation parameters or non-finite eigenvalues")
+                                            : "device status " + std::to_string(h[k].code);
+    cudaMemset(ctx->st, 0, sizeof(DevStatus) * ctx->nk);
+    return fail(ctx, code, what + " (batch item " + std::to_string(k) + ")");
+  }
+  return GKS_OK;
+}
+
+gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype) {
+  if (!ctx || !A || m < 1 || count < 1 || m > 46340) return fail(ctx, GKS_EINVAL, "bad arguments");
+  cudaSetDevice(ctx->device);
+  if (dtype == GKS_R64) {
+    gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 8, 0);
+    if (rc) return rc;
+    cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
+    potrf_run<double>(ctx, static_cast<double*>(A), (int)m, (int)count);
+  } else if (dtype == GKS_C128) {
+    gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 16, 0);
+    if (rc) return rc;
+    cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
+    potrf_run<zc>(ctx, static_cast<zc*>(A), (int)m, (int)count);
+  } else {
+    return fail(ctx, GKS_EINVAL, "unknown dtype");
+  }
+  return cuda_check(ctx, "gks_potrf");
+}
+
+gks_status gks_reduce(gks_ctx* ctx, void* H, void* S, int64_t m, int64_t count, int dtype) {
+  if (!ctx || !H || !S || m < 1 || count < 1 || m > 46340) return fail(ctx, GKS_EINVAL, "bad arguments");
+  cudaSetDevice(ctx->device);
+  if (dtype == GKS_R64) {
+    gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 8, 0);
+    if (rc) return rc;
+    cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
+    potrf_run<double>(ctx, static_cast<double*>(S), (int)m, (int)count);
+    hegst_run<double>(ctx, static_cast<double*>(H), static_cast<double*>(S), (int)m, (int)count);
+  } else if (dtype == GKS_C128) {
+    gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 16, 0);
+    if (rc) return rc;
+    cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
+    potrf_run<zc>(ctx, static_cast<zc*>(S), (int)m, (int)count);
+    hegst_run<zc>(ctx, static_cast<zc*>(H), static_cast<zc*>(S), (int)m, (int)count);
+  } else {
+    return fail(ctx, GKS_EINVAL, "unknown dtype");
+  }
+  return cuda_check(ctx, "gks_reduce");
+}
+
+gks_status gks_stedc(gks_ctx* ctx, const double* d, const double* e, int64_t m, int64_t count, double* lam,
+                     double* Z) {
+  if (!ctx || !d || !e || !lam || !Z || m < 1 || count < 1 || m > 46340) return fail(ctx, GKS_EINVAL, "bad arguments");
+  cudaSetDevice(ctx->device);
+  gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 8, 0);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, s);
+  double* dw = at<double>(ctx, ctx->od);
+  double* ew = at<double>(ctx, ctx->oe);
+  copy2d<double>(dw, (int)m, m, d, (int)m, m, 1, (int)m, (int)count, s);
+  copy2d<double>(ew, (int)m, m, e, (int)m, m, 1, (int)m, (int)count, s);
+  dc_solve(ctx->dc, dw, ew, m, lam, Z, m * m, ctx->ws + ctx->odc, ctx->st, s);
+  return cuda_check(ctx, "gks_stedc");
+}
+
+}  // extern "C"

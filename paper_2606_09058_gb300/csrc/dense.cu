@@ -1,0 +1,288 @@
+// Small dense kernels around the GEMM core: diagonal-block Cholesky with triangular
+// inverse, the two-sided reduction of a diagonal block, the compact-WY T factor, and
+// elementwise helpers (phase application, Hermitian mirror, eigenvector phase).
+#include "dense.h"
+
+namespace gks {
+
+// One CTA per batch item: factor the nb x nb diagonal block of A at (k0, k0) in place
+// (lower, A = L L^H) and write inv(L11) (lower) to Dinv.  A non-positive pivot records
+// GKS_ENOTSPD with the global column and leaves the rest of the block untouched.
+template <typename T>
+__global__ void potf2_inv_kernel(T* A, int lda, long long sA, int k0, int nb, T* Dinv, int ldD,
+                                 long long sD, DevStatus* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* a = reinterpret_cast<T*>(smem_raw);
+  T* x = a + nb * (nb + 1);
+  __shared__ int fail;
+  const int z = blockIdx.x, ld = nb + 1, tid = threadIdx.x, nt = blockDim.x;
+  A += z * sA;
+  Dinv += z * sD;
+  for (int e = tid; e < nb * nb; e += nt) {
+    int i = e / nb, j = e % nb;
+    a[i * ld + j] = (j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j] : zero<T>();
+  }
+  if (tid == 0) fail = -1;
+  __syncthreads();
+  for (int j = 0; j < nb; j++) {
+    if (tid == 0) {
+      double piv = re(a[j * ld + j]);
+      if (!(piv > 0.0) || !isfinite(piv)) fail = j;
+      else a[j * ld + j] = from_real<T>(sqrt(piv));
+    }
+    __syncthreads();
+    if (fail >= 0) break;
+    const double ljj = re(a[j * ld + j]);
+    for (int i = j + 1 + tid; i < nb; i += nt) a[i * ld + j] = a[i * ld + j] * (1.0 / ljj);
+    __syncthreads();
+    const int m = nb - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      int r = j + 1 + e / m, c = j + 1 + e % m;
+      if (c <= r) a[r * ld + c] -= a[r * ld + j] * conjg(a[c * ld + j]);
+    }
+    __syncthreads();
+  }
+  if (fail >= 0) {
+    if (tid == 0) set_status(st ? st + z : nullptr, ST_ENOTSPD, k0 + fail);
+    return;
+  }
+  for (int e = tid; e < nb * nb; e += nt) {
+    int i = e / nb, j = e % nb;
+    if (j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = a[i * ld + j];
+  }
+  // inverse of the lower-triangular factor, one column per thread
+  for (int c = tid; c < nb; c += nt) {
+    for (int i = 0; i < c; i++) x[i * ld + c] = zero<T>();
+    for (int i = c; i < nb; i++) {
+      T s = (i == c) ? from_real<T>(1.0) : zero<T>();
+      for (int k = c; k < i; k++) s -= a[i * ld + k] * x[k * ld + c];
+      x[i * ld + c] = s * (1.0 / re(a[i * ld + i]));
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * nb; e += nt) {
+    int i = e / nb, j = e % nb;
+    Dinv[(size_t)i * ldD + j] = x[i * ld + j];
+  }
+}
+
+// One CTA per batch item: A11' = Dinv A11 Dinv^H for the diagonal block at (k0, k0)
+// (A11 read from its lower triangle).  Writes the lower triangle back into A and the
+// full Hermitian block into F (ldF).
+template <typename T>
+__global__ void hegst_diag_kernel(T* A, int lda, long long sA, int k0, int nb, const T* Dinv, int ldD,
+                                  long long sD, T* F, int ldF, long long sF) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* a = reinterpret_cast<T*>(smem_raw);
+  T* x = a + nb * (nb + 1);
+  T* w = x + nb * (nb + 1);
+  const int z = blockIdx.x, ld = nb + 1, tid = threadIdx.x, nt = blockDim.x;
+  A += z * sA;
+  Dinv += z * sD;
+  F += z * sF;
+  for (int e = tid; e < nb * nb; e += nt) {
+    int i = e / nb, j = e % nb;
+    T v = (j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j] : conjg(A[(size_t)(k0 + j) * lda + k0 + i]);
+    if (i == j) v = from_real<T>(re(v));
+    a[i * ld + j] = v;
+    x[i * ld + j] = Dinv[(size_t)i * ldD + j];
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * nb; e += nt) {           // w = x a  (x lower)
+    int i = e / nb, j = e % nb;
+    T s = zero<T>();
+    for (int k = 0; k <= i; k++) mac(s, x[i * ld + k], a[k * ld + j]);
+    w[i * ld + j] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * nb; e += nt) {           // a = w x^H
+    int i = e / nb, j = e % nb;
+    T s = zero<T>();
+    for (int k = 0; k <= j; k++) mac(s, w[i * ld + k], conjg(x[j * ld + k]));
+    a[i * ld + j] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * nb; e += nt) {           // exact Hermitian symmetry from the lower part
+    int i = e / nb, j = e % nb;
+    T v = (j <= i) ? a[i * ld + j] : conjg(a[j * ld + i]);
+    if (i == j) v = from_real<T>(re(v));
+    F[(size_t)i * ldF + j] = v;
+    if (j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = v;
+  }
+}
+
+// Compact WY T factor for H_1 H_2 ... H_k = I - V T V^H with H_i = I - tau_i v_i v_i^H:
+// T upper triangular, T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] (V^H V)[0:i, i].
+// G = V^H V (k x k, ldG) precomputed; one CTA per batch item.
+template <typename T>
+__global__ void larft_kernel(const T* G, int ldG, long long sG, const double* tau, long long stau, int k,
+                             T* Tm, int ldT, long long sT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* t = reinterpret_cast<T*>(smem_raw);
+  T* tmp = t + k * k;
+  const int z = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  G += z * sG;
+  tau += z * stau;
+  Tm += z * sT;
+  for (int e = tid; e < k * k; e += nt) t[e] = zero<T>();
+  __syncthreads();
+  for (int i = 0; i < k; i++) {
+    const double ti = tau[i];
+    for (int r = tid; r < i; r += nt) {
+      T s = zero<T>();
+      for (int c = r; c < i; c++) mac(s, t[r * k + c], G[(size_t)c * ldG + i]);
+      tmp[r] = s;
+    }
+    __syncthreads();
+    for (int r = tid; r < i; r += nt) t[r * k + i] = (-ti) * tmp[r];
+    if (tid == 0) t[i * k + i] = from_real<T>(ti);
+    __syncthreads();
+  }
+  for (int e = tid; e < k * k; e += nt) Tm[(size_t)(e / k) * ldT + (e % k)] = t[e];
+}
+
+// X[b][i][c] = ph[b][i] * Z[b][i][c]  (Z real, X of type T)
+template <typename T>
+__global__ void apply_phase_kernel(T* X, int ldx, long long sX, const double* Z, int ldz, long long sZ,
+                                   const T* ph, long long sph, int n) {
+  const int z = blockIdx.z;
+  X += z * sX;
+  Z += z * sZ;
+  ph += z * sph;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    T p = ph[i];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+      X[(size_t)i * ldx + c] = p * Z[(size_t)i * ldz + c];
+  }
+}
+
+// Upper triangle <- conj(lower triangle); diagonal made real.
+template <typename T>
+__global__ void mirror_lower_kernel(T* A, int lda, long long sA, int n) {
+  const int z = blockIdx.z;
+  A += z * sA;
+  for (int i = blockIdx.y; i < n; i += gridDim.y)
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i; j += gridDim.x * blockDim.x) {
+      T v = A[(size_t)i * lda + j];
+      if (j == i) A[(size_t)i * lda + i] = from_real<T>(re(v));
+      else A[(size_t)j * lda + i] = conjg(v);
+    }
+}
+
+// Column phase convention: the entry of largest modulus (lowest row on ties) becomes
+// real and positive.  One warp per column.
+template <typename T>
+__global__ void column_phase_kernel(T* C, int ldc, long long sC, int rows, int cols) {
+  const int z = blockIdx.y;
+  C += z * sC;
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= cols) return;
+  double best = -1.0;
+  int bi = 0;
+  for (int i = lane; i < rows; i += 32) {
+    double a = abs2(C[(size_t)i * ldc + col]);
+    if (a > best) { best = a; bi = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  T p = C[(size_t)bi * ldc + col];
+  double mag = sqrt(abs2(p));
+  if (!(mag > 0.0)) return;
+  T f = conjg(p) * (1.0 / mag);
+  for (int i = lane; i < rows; i += 32) C[(size_t)i * ldc + col] = C[(size_t)i * ldc + col] * f;
+}
+
+// Fill dst (2n x 2n) with diag(S, S) from the n x n S (lower triangle valid).
+template <typename T>
+__global__ void spinor_overlap_kernel(T* dst, long long sd, const T* S, int lds, long long ss, int n) {
+  const int z = blockIdx.z;
+  dst += z * sd;
+  S += z * ss;
+  const int m = 2 * n;
+  for (int i = blockIdx.y; i < m; i += gridDim.y)
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+      T v = zero<T>();
+      if ((i < n) == (j < n)) {
+        int a = i % n, b = j % n;
+        v = (b <= a) ? S[(size_t)a * lds + b] : conjg(S[(size_t)b * lds + a]);
+      }
+      dst[(size_t)i * m + j] = v;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+static dim3 grid2d(int rows, int cols, int count) {
+  int gx = (cols + 255) / 256;
+  if (gx > 16) gx = 16;
+  if (gx < 1) gx = 1;
+  int gy = rows < 2048 ? (rows > 0 ? rows : 1) : 2048;
+  return dim3(gx, gy, count);
+}
+
+template <typename T>
+void potf2_inv(T* A, int lda, long long sA, int k0, int nb, T* Dinv, int ldD, long long sD, DevStatus* st,
+               int count, cudaStream_t s) {
+  size_t sm = 2 * sizeof(T) * nb * (nb + 1);
+  cudaFuncSetAttribute(potf2_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  potf2_inv_kernel<T><<<count, 256, sm, s>>>(A, lda, sA, k0, nb, Dinv, ldD, sD, st);
+}
+
+template <typename T>
+void hegst_diag(T* A, int lda, long long sA, int k0, int nb, const T* Dinv, int ldD, long long sD, T* F,
+                int ldF, long long sF, int count, cudaStream_t s) {
+  size_t sm = 3 * sizeof(T) * nb * (nb + 1);
+  cudaFuncSetAttribute(hegst_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  hegst_diag_kernel<T><<<count, 256, sm, s>>>(A, lda, sA, k0, nb, Dinv, ldD, sD, F, ldF, sF);
+}
+
+template <typename T>
+void larft(const T* G, int ldG, long long sG, const double* tau, long long stau, int k, T* Tm, int ldT,
+           long long sT, int count, cudaStream_t s) {
+  size_t sm = sizeof(T) * (k * k + k);
+  cudaFuncSetAttribute(larft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  larft_kernel<T><<<count, 128, sm, s>>>(G, ldG, sG, tau, stau, k, Tm, ldT, sT);
+}
+
+template <typename T>
+void apply_phase(T* X, int ldx, long long sX, const double* Z, int ldz, long long sZ, const T* ph, long long sph,
+                 int n, int count, cudaStream_t s) {
+  apply_phase_kernel<T><<<grid2d(n, n, count), 256, 0, s>>>(X, ldx, sX, Z, ldz, sZ, ph, sph, n);
+}
+
+template <typename T>
+void mirror_lower(T* A, int lda, long long sA, int n, int count, cudaStream_t s) {
+  mirror_lower_kernel<T><<<grid2d(n, n, count), 256, 0, s>>>(A, lda, sA, n);
+}
+
+template <typename T>
+void column_phase(T* C, int ldc, long long sC, int rows, int cols, int count, cudaStream_t s) {
+  dim3 grid((cols + 7) / 8, count);
+  column_phase_kernel<T><<<grid, 256, 0, s>>>(C, ldc, sC, rows, cols);
+}
+
+template <typename T>
+void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int n, int count, cudaStream_t s) {
+  spinor_overlap_kernel<T><<<grid2d(2 * n, 2 * n, count), 256, 0, s>>>(dst, sd, S, lds, ss, n);
+}
+
+#define INST(T)                                                                                         \
+  template void potf2_inv<T>(T*, int, long long, int, int, T*, int, long long, DevStatus*, int,          \
+                             cudaStream_t);                                                             \
+  template void hegst_diag<T>(T*, int, long long, int, int, const T*, int, long long, T*, int, long long, \
+                              int, cudaStream_t);                                                       \
+  template void larft<T>(const T*, int, long long, const double*, long long, int, T*, int, long long,    \
+                         int, cudaStream_t);                                                            \
+  template void apply_phase<T>(T*, int, long long, const double*, int, long long, const T*, long long,   \
+                               int, int, cudaStream_t);                                                 \
+  template void mirror_lower<T>(T*, int, long long, int, int, cudaStream_t);                            \
+  template void column_phase<T>(T*, int, long long, int, int, int, cudaStream_t);                      \
+  template void spinor_overlap<T>(T*, long long, const T*, int, long long, int, int, cudaStream_t);
+INST(double)
+INST(zc)
+
+}  // namespace gks

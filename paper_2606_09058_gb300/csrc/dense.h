@@ -1,0 +1,55 @@
+// Launchers for the small dense kernels (dense.cu), the Householder reduction
+// (hetrd.cu), the divide-and-conquer tridiagonal solver (stedc.cu) and occupations
+// (occ.cu).
+#pragma once
+#include "launch.h"
+
+namespace gks {
+
+template <typename T>
+void potf2_inv(T* A, int lda, long long sA, int k0, int nb, T* Dinv, int ldD, long long sD, DevStatus* st,
+               int count, cudaStream_t s);
+template <typename T>
+void hegst_diag(T* A, int lda, long long sA, int k0, int nb, const T* Dinv, int ldD, long long sD, T* F,
+                int ldF, long long sF, int count, cudaStream_t s);
+template <typename T>
+void larft(const T* G, int ldG, long long sG, const double* tau, long long stau, int k, T* Tm, int ldT,
+           long long sT, int count, cudaStream_t s);
+template <typename T>
+void apply_phase(T* X, int ldx, long long sX, const double* Z, int ldz, long long sZ, const T* ph, long long sph,
+                 int n, int count, cudaStream_t s);
+template <typename T>
+void mirror_lower(T* A, int lda, long long sA, int n, int count, cudaStream_t s);
+template <typename T>
+void column_phase(T* C, int ldc, long long sC, int rows, int cols, int count, cudaStream_t s);
+template <typename T>
+void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int n, int count, cudaStream_t s);
+
+// ---- Householder tridiagonalization (hetrd.cu) ----
+// Workspace per batch item: u (m), p (m), q (m) vectors, tau (m).
+template <typename T>
+void hetrd_step(T* A, int lda, long long sA, int j, T* u, T* p, long long sv, double* tau, long long stau,
+                int count, cudaStream_t s);
+template <typename T>
+void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e, long long sde, T* ph,
+                  long long sph, int count, cudaStream_t s);
+// Gather reflectors j0..j1 (descending) into Vblk (rows x (j1-j0+1)) and their taus.
+template <typename T>
+void gather_reflectors(const T* A, int lda, long long sA, const double* tau, long long stau, int j0, int j1,
+                       T* V, int ldv, long long sV, double* tb, long long stb, int count, cudaStream_t s);
+
+// ---- divide and conquer (stedc.cu) ----
+struct DcPlan;
+DcPlan* dc_plan_create(int m, int count);
+void dc_plan_destroy(DcPlan* p);
+size_t dc_workspace_bytes(const DcPlan* p);
+// d (m), e (m-1) per item (stride sde); Z out (m x m, ld m, stride sZ); lam out (stride sde).
+void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, double* Z, long long sZ, void* work,
+              DevStatus* st, cudaStream_t s);
+
+// ---- occupations (occ.cu) ----
+void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,
+              double f_cut, double* occ, double* kscale, double* mu, double* e_band, int* nrho, DevStatus* st,
+              int nsys, cudaStream_t s);
+
+}  // namespace gks

@@ -1,0 +1,212 @@
+"""Python binding of the C ABI in include/gks.h (argument marshalling only).
+
+Every step of the path runs in libgks.so; PyTorch supplies device memory and the CUDA
+stream.  The binding refuses to run without the compiled library or a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+GKS_OK, GKS_EINVAL, GKS_ENOTSPD, GKS_ENOCONV, GKS_ENOMEM, GKS_ECUDA, GKS_ETIMEOUT, GKS_ENOTIMPL = range(8)
+GKS_R64, GKS_C128 = 0, 1
+GKS_COLLINEAR, GKS_NONCOLLINEAR = 0, 1
+_NAMES = {0: "GKS_OK", 1: "GKS_EINVAL", 2: "GKS_ENOTSPD", 3: "GKS_ENOCONV", 4: "GKS_ENOMEM", 5: "GKS_ECUDA",
+          6: "GKS_ETIMEOUT", 7: "GKS_ENOTIMPL"}
+
+_lib = None
+
+
+class GKSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
+                ("f_cut", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libgks.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I64, D, I, U = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_uint
+    lib.gks_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_Opts)]
+    lib.gks_destroy.argtypes = [P]
+    lib.gks_last_error.argtypes = [P]
+    lib.gks_last_error.restype = ctypes.c_char_p
+    lib.gks_solve.argtypes = [P, P, P, I64, I64, I, I, D, D, P, U, P, P, P, P, P]
+    lib.gks_sync.argtypes = [P]
+    lib.gks_potrf.argtypes = [P, P, I64, I64, I]
+    lib.gks_reduce.argtypes = [P, P, P, I64, I64, I]
+    lib.gks_stedc.argtypes = [P, P, P, I64, I64, P, P]
+    for f in ("gks_create", "gks_destroy", "gks_solve", "gks_sync", "gks_potrf", "gks_reduce", "gks_stedc"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check_tensor(t: torch.Tensor, name: str, dtypes):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} has dtype {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+@dataclass
+class Solution:
+    eps: torch.Tensor      # (nk, M) float64, ascending
+    C: torch.Tensor        # (nk, M, M)
+    mu: torch.Tensor       # (1,) float64
+    rho: torch.Tensor      # (nk, M, M)
+    e_band: torch.Tensor   # (1,) float64
+
+
+class Context:
+    """A gks context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None, f_cut: float = 1e-16):
+        if not torch.cuda.is_available():
+            raise RuntimeError("gks needs a CUDA device")
+        lib = load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), 0, f_cut)
+        h = ctypes.c_void_p()
+        rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
+        if rc:
+            raise GKSError(rc, "gks_create failed")
+        self._h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gks_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, rc):
+        if rc:
+            raise GKSError(rc, self._lib.gks_last_error(self._h).decode())
+
+    def sync(self):
+        self._raise(self._lib.gks_sync(self._h))
+
+    # ------------------------------------------------------------------ full path
+    def solve_into(self, H, S, kT, n_elec, spin="collinear", kweights=None, *, eps, C, mu, rho, e_band=None,
+                   sync=True):
+        """gks_solve on caller-provided output tensors (no allocation)."""
+        nk, M = H.shape[0], H.shape[1]
+        nc = spin == "noncollinear"
+        n = S.shape[1]
+        dt = GKS_C128 if H.is_complex() else GKS_R64
+        rc = self._lib.gks_solve(self._h, _ptr(H), _ptr(S), n, nk, dt, GKS_NONCOLLINEAR if nc else GKS_COLLINEAR,
+                                 float(kT), float(n_elec), _ptr(kweights), 0, _ptr(eps), _ptr(C), _ptr(mu), _ptr(rho),
+                                 _ptr(e_band))
+        self._raise(rc)
+        if sync:
+            self.sync()
+
+    def solve(self, H: torch.Tensor, S: torch.Tensor, kT: float, n_elec: float, spin: str = "collinear",
+              kweights: torch.Tensor | None = None, sync: bool = True) -> Solution:
+        """eps, C, mu, rho, E_band for nk pencils sharing one chemical potential.
+
+        H: (nk, M, M), S: (nk, n, n) (noncollinear: M = 2n, S the n x n overlap)."""
+        if H.dim() == 2:
+            H, S = H[None], S[None]
+        cd = (torch.float64, torch.complex128)
+        _check_tensor(H, "H", cd)
+        _check_tensor(S, "S", cd)
+        if S.dtype != H.dtype:
+            raise ValueError("H and S must share a dtype")
+        nk, M = H.shape[0], H.shape[1]
+        if kweights is not None:
+            _check_tensor(kweights, "kweights", (torch.float64,))
+        dev = H.device
+        eps = torch.empty(nk, M, dtype=torch.float64, device=dev)
+        C = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
+        rho = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
+        mu = torch.empty(1, dtype=torch.float64, device=dev)
+        eb = torch.empty(1, dtype=torch.float64, device=dev)
+        self.solve_into(H, S, kT, n_elec, spin, kweights, eps=eps, C=C, mu=mu, rho=rho, e_band=eb, sync=sync)
+        return Solution(eps, C, mu, rho, eb)
+
+    # ------------------------------------------------------------------ stages
+    def potrf(self, A: torch.Tensor) -> torch.Tensor:
+        """In place lower Cholesky factor of each (count, m, m) matrix."""
+        if A.dim() == 2:
+            A = A[None]
+        _check_tensor(A, "A", (torch.float64, torch.complex128))
+        rc = self._lib.gks_potrf(self._h, _ptr(A), A.shape[1], A.shape[0], GKS_C128 if A.is_complex() else GKS_R64)
+        self._raise(rc)
+        self.sync()
+        return A
+
+    def reduce(self, H: torch.Tensor, S: torch.Tensor):
+        """In place: S <- L, lower(H) <- lower(L^-1 H L^-H)."""
+        if H.dim() == 2:
+            H, S = H[None], S[None]
+        for t, nm in ((H, "H"), (S, "S")):
+            _check_tensor(t, nm, (torch.float64, torch.complex128))
+        rc = self._lib.gks_reduce(self._h, _ptr(H), _ptr(S), H.shape[1], H.shape[0],
+                                  GKS_C128 if H.is_complex() else GKS_R64)
+        self._raise(rc)
+        self.sync()
+        return H, S
+
+    def stedc(self, d: torch.Tensor, e: torch.Tensor):
+        """Divide-and-conquer eigensolve of real tridiagonals d (count, m), e (count, m)."""
+        if d.dim() == 1:
+            d, e = d[None], e[None]
+        _check_tensor(d, "d", (torch.float64,))
+        _check_tensor(e, "e", (torch.float64,))
+        count, m = d.shape
+        lam = torch.empty(count, m, dtype=torch.float64, device=d.device)
+        Z = torch.empty(count, m, m, dtype=torch.float64, device=d.device)
+        rc = self._lib.gks_stedc(self._h, _ptr(d), _ptr(e), m, count, _ptr(lam), _ptr(Z))
+        self._raise(rc)
+        self.sync()
+        return lam, Z
+
+
+_default: dict = {}
+
+
+def context(device: int | None = None) -> Context:
+    """A cached context for the current device and stream."""
+    dev = torch.cuda.current_device() if device is None else device
+    key = (dev, torch.cuda.current_stream(dev).cuda_stream)
+    if key not in _default:
+        _default[key] = Context(dev)
+    return _default[key]
+
+
+def solve(H, S, kT, n_elec, spin="collinear", kweights=None) -> Solution:
+    return context(H.device.index).solve(H, S, kT, n_elec, spin, kweights)
