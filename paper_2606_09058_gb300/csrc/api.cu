@@ -35,9 +35,8 @@ struct gks_ctx {
   DcPlan* dc = nullptr;
   DevStatus* st = nullptr;
   // offsets (bytes) of per-item arrays; each holds nk items
-  size_t oA, oL, oDinv, oF, oP, oQ, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho,
-      ow, oeb, odc;
-  long long sMM, sDinv, sF, sP, sQ, sV, sG, sT, sY, sVec;
+  size_t oA, oL, oF, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc;
+  long long sMM, sF, sV, sG, sT, sY, sVec;
 };
 
 namespace {
@@ -69,12 +68,8 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc) return GKS_OK;
   release_ws(c);
   const size_t MM = (size_t)m * m;
-  const int nblk = (m + NB - 1) / NB;
   c->sMM = (long long)MM;
-  c->sDinv = (long long)nblk * NB * NB;
   c->sF = NB * NB;
-  c->sP = (long long)m * NB;
-  c->sQ = (long long)NB * m;
   c->sV = (long long)m * NB;
   c->sG = NB * NB;
   c->sT = NB * NB;
@@ -84,10 +79,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   auto elems = [&](long long per) { return (size_t)per * nk * es; };
   c->oA = a.take<char>(elems(c->sMM));
   c->oL = a.take<char>(elems(c->sMM));
-  c->oDinv = a.take<char>(elems(c->sDinv));
   c->oF = a.take<char>(elems(c->sF));
-  c->oP = a.take<char>(elems(c->sP));
-  c->oQ = a.take<char>(elems(c->sQ));
   c->oV = a.take<char>(elems(c->sV));
   c->oG = a.take<char>(elems(c->sG));
   c->oT = a.take<char>(elems(c->sT));
@@ -159,56 +151,51 @@ void gm(cudaStream_t s, int count, int opA, int opB, int M, int N, int K, double
   gemm<T>(g, M, N, s);
 }
 
-// Blocked right-looking Cholesky of L (in place, lower) with the inverse diagonal blocks.
+// Blocked right-looking Cholesky of L (in place, lower): diagonal block, panel solve
+// L21 = A21 L11^-H by substitution, trailing Hermitian rank-kb update.
 template <typename T>
 void potrf_run(gks_ctx* c, T* L, int M, int nk) {
   cudaStream_t s = c->stream;
-  T* Dinv = at<T>(c, c->oDinv);
-  T* P = at<T>(c, c->oP);
   for (int k0 = 0; k0 < M; k0 += NB) {
-    const int kb = std::min(NB, M - k0), blk = k0 / NB;
-    T* Db = Dinv + (size_t)blk * NB * NB;
-    potf2_inv<T>(L, M, c->sMM, k0, kb, Db, NB, c->sDinv, c->st, nk, s);
+    const int kb = std::min(NB, M - k0);
+    potf2<T>(L, M, c->sMM, k0, kb, c->st, nk, s);
     const int rows = M - k0 - kb;
     if (rows <= 0) continue;
+    T* L11 = L + (size_t)k0 * M + k0;
     T* L21 = L + (size_t)(k0 + kb) * M + k0;
-    gm<T>(s, nk, OP_N, OP_C, rows, kb, kb, 1.0, L21, M, c->sMM, Db, NB, c->sDinv, 0.0, P, NB, c->sP);
-    copy2d<T>(L21, M, c->sMM, P, NB, c->sP, rows, kb, nk, s);
-    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, P, NB, c->sP, P, NB, c->sP, 1.0, L21 + kb, M, c->sMM, 1);
+    trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, L21, M, c->sMM, kb, rows, nk, s);
+    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, L21, M, c->sMM, 1.0, L21 + kb, M, c->sMM, 1);
   }
 }
 
-// Two-sided blocked reduction A <- L^-1 A L^-H (lower triangle), then the deferred
-// block-triangular solve of the strictly lower block part.
+// Two-sided blocked reduction A <- L^-1 A L^-H (lower triangle).  Per panel:
+//   A11 <- L11^-1 A11 L11^-H (in-block recurrence),  W = A21 L11^-H,
+//   V = W - L21 A11'/2,  A22 -= L21 V^H + V L21^H,  R = V - L21 A11'/2,
+// and finally the block-strictly-lower part G = [R_0 R_1 ...] becomes L^-1 G by block
+// forward substitution (diagonal blocks by substitution, the rest GEMM updates).
 template <typename T>
 void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
   cudaStream_t s = c->stream;
-  T* Dinv = at<T>(c, c->oDinv);
   T* F = at<T>(c, c->oF);
-  T* P = at<T>(c, c->oP);
-  T* Q = at<T>(c, c->oQ);
   for (int k0 = 0; k0 < M; k0 += NB) {
-    const int kb = std::min(NB, M - k0), blk = k0 / NB;
-    const T* Db = Dinv + (size_t)blk * NB * NB;
-    hegst_diag<T>(A, M, c->sMM, k0, kb, Db, NB, c->sDinv, F, NB, c->sF, nk, s);
+    const int kb = std::min(NB, M - k0);
+    hegst_diag<T>(A, M, c->sMM, L, M, c->sMM, k0, kb, F, NB, c->sF, nk, s);
     const int rows = M - k0 - kb;
     if (rows <= 0) continue;
+    const T* L11 = L + (size_t)k0 * M + k0;
     const T* L21 = L + (size_t)(k0 + kb) * M + k0;
     T* A21 = A + (size_t)(k0 + kb) * M + k0;
     T* A22 = A21 + kb;
-    gm<T>(s, nk, OP_N, OP_C, rows, kb, kb, 1.0, A21, M, c->sMM, Db, NB, c->sDinv, 0.0, P, NB, c->sP);
-    gm<T>(s, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, P, NB, c->sP);
-    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, P, NB, c->sP, 1.0, A22, M, c->sMM, 1);
-    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, P, NB, c->sP, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
-    gm<T>(s, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, P, NB, c->sP);
-    copy2d<T>(A21, M, c->sMM, P, NB, c->sP, rows, kb, nk, s);
+    trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, A21, M, c->sMM, kb, rows, nk, s);
+    gm<T>(s, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
+    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, A21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, M, c->sMM, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gm<T>(s, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
   }
   for (int r0 = NB; r0 < M; r0 += NB) {
-    const int rb = std::min(NB, M - r0), blk = r0 / NB;
-    const T* Db = Dinv + (size_t)blk * NB * NB;
+    const int rb = std::min(NB, M - r0);
     T* Ai = A + (size_t)r0 * M;
-    copy2d<T>(Q, M, c->sQ, Ai, M, c->sMM, rb, r0, nk, s);
-    gm<T>(s, nk, OP_N, OP_N, rb, r0, rb, 1.0, Db, NB, c->sDinv, Q, M, c->sQ, 0.0, Ai, M, c->sMM);
+    trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * M + r0, M, c->sMM, Ai, M, c->sMM, rb, r0, nk, s);
     const int below = M - r0 - rb;
     if (below > 0)
       gm<T>(s, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM, 1.0,
@@ -238,19 +225,15 @@ void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
   }
 }
 
-// X <- L^-H X by block back substitution with the inverse diagonal blocks.
+// X <- L^-H X by block back substitution (diagonal blocks by substitution).
 template <typename T>
 void unreduce_run(gks_ctx* c, const T* L, T* X, int M, int nk) {
   cudaStream_t s = c->stream;
-  T* Dinv = at<T>(c, c->oDinv);
-  T* Q = at<T>(c, c->oQ);
   const int nblk = (M + NB - 1) / NB;
   for (int blk = nblk - 1; blk >= 0; blk--) {
     const int r0 = blk * NB, rb = std::min(NB, M - r0);
-    const T* Db = Dinv + (size_t)blk * NB * NB;
     T* Xi = X + (size_t)r0 * M;
-    copy2d<T>(Q, M, c->sQ, Xi, M, c->sMM, rb, M, nk, s);
-    gm<T>(s, nk, OP_C, OP_N, rb, M, rb, 1.0, Db, NB, c->sDinv, Q, M, c->sQ, 0.0, Xi, M, c->sMM);
+    trsm_block<T>(TRSM_LEFT_CONJ, L + (size_t)r0 * M + r0, M, c->sMM, Xi, M, c->sMM, rb, M, nk, s);
     if (r0 > 0)
       gm<T>(s, nk, OP_C, OP_N, r0, M, rb, -1.0, L + (size_t)r0 * M, M, c->sMM, Xi, M, c->sMM, 1.0, X, M, c->sMM);
   }

@@ -1,23 +1,21 @@
-// Small dense kernels around the GEMM core: diagonal-block Cholesky with triangular
-// inverse, the two-sided reduction of a diagonal block, the compact-WY T factor, and
-// elementwise helpers (phase application, Hermitian mirror, eigenvector phase).
+// Small dense kernels around the GEMM core: diagonal-block Cholesky, triangular solves
+// against a diagonal block, the two-sided reduction of a diagonal block, the compact-WY
+// T factor, and elementwise helpers (phase application, Hermitian mirror, eigenvector
+// phase, spinor overlap).
 #include "dense.h"
 
 namespace gks {
 
 // One CTA per batch item: factor the nb x nb diagonal block of A at (k0, k0) in place
-// (lower, A = L L^H) and write inv(L11) (lower) to Dinv.  A non-positive pivot records
-// GKS_ENOTSPD with the global column and leaves the rest of the block untouched.
+// (lower, A = L L^H).  A non-positive or non-finite pivot records GKS_ENOTSPD with the
+// global column and leaves the block untouched.
 template <typename T>
-__global__ void potf2_inv_kernel(T* A, int lda, long long sA, int k0, int nb, T* Dinv, int ldD,
-                                 long long sD, DevStatus* st) {
+__global__ void potf2_kernel(T* A, int lda, long long sA, int k0, int nb, DevStatus* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* a = reinterpret_cast<T*>(smem_raw);
-  T* x = a + nb * (nb + 1);
   __shared__ int fail;
   const int z = blockIdx.x, ld = nb + 1, tid = threadIdx.x, nt = blockDim.x;
   A += z * sA;
-  Dinv += z * sD;
   for (int e = tid; e < nb * nb; e += nt) {
     int i = e / nb, j = e % nb;
     a[i * ld + j] = (j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j] : zero<T>();
@@ -50,59 +48,138 @@ __global__ void potf2_inv_kernel(T* A, int lda, long long sA, int k0, int nb, T*
     int i = e / nb, j = e % nb;
     if (j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = a[i * ld + j];
   }
-  // inverse of the lower-triangular factor, one column per thread
-  for (int c = tid; c < nb; c += nt) {
-    for (int i = 0; i < c; i++) x[i * ld + c] = zero<T>();
-    for (int i = c; i < nb; i++) {
-      T s = (i == c) ? from_real<T>(1.0) : zero<T>();
-      for (int k = c; k < i; k++) s -= a[i * ld + k] * x[k * ld + c];
-      x[i * ld + c] = s * (1.0 / re(a[i * ld + i]));
+}
+
+// Triangular solves against one nb x nb lower-triangular block L (ldl), by substitution
+// (no explicit inverse: the diagonal blocks of the Cholesky factor of an overcomplete
+// basis have condition numbers near 1e5).  Each CTA takes 64 right-hand sides into
+// shared memory, one thread per right-hand side.
+//   TRSM_RIGHT_CONJ : B (nrhs x nb rows)  <- B L^-H
+//   TRSM_LEFT       : B (nb x nrhs cols)  <- L^-1 B
+//   TRSM_LEFT_CONJ  : B (nb x nrhs cols)  <- L^-H B
+template <typename T, int MODE>
+__global__ void __launch_bounds__(64) trsm_block_kernel(const T* L, int ldl, long long sL, T* B, int ldb, long long sB,
+                                                        int nb, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* x = reinterpret_cast<T*>(smem_raw);  // MODE 0: [64][nb+1] (row per rhs); else [nb][65]
+  const int z = blockIdx.y, tid = threadIdx.x, r0 = blockIdx.x * 64;
+  L += z * sL;
+  B += z * sB;
+  const int nr = min(64, nrhs - r0);
+  if (MODE == TRSM_RIGHT_CONJ) {
+    const int ld = nb + 1;
+    for (int e = tid; e < nr * nb; e += 64) {
+      int r = e / nb, c = e % nb;
+      x[r * ld + c] = B[(size_t)(r0 + r) * ldb + c];
+    }
+    __syncthreads();
+    if (tid < nr) {
+      T* xr = x + tid * ld;
+      for (int j = 0; j < nb; j++) {  // x L^H = b  <=>  x_j = (b_j - sum_{k<j} x_k conj(L_jk)) / L_jj
+        const T* lj = L + (size_t)j * ldl;
+        T s0 = xr[j], s1 = zero<T>();
+        int k = 0;
+        for (; k + 1 < j; k += 2) {
+          s0 -= xr[k] * conjg(lj[k]);
+          s1 -= xr[k + 1] * conjg(lj[k + 1]);
+        }
+        if (k < j) s0 -= xr[k] * conjg(lj[k]);
+        xr[j] = (s0 + s1) * (1.0 / re(lj[j]));
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * nb; e += 64) {
+      int r = e / nb, c = e % nb;
+      B[(size_t)(r0 + r) * ldb + c] = x[r * ld + c];
+    }
+  } else {
+    const int ld = 65;
+    for (int e = tid; e < nb * 64; e += 64) {
+      int i = e / 64, c = e % 64;
+      if (c < nr) x[i * ld + c] = B[(size_t)i * ldb + r0 + c];
+    }
+    __syncthreads();
+    if (tid < nr) {
+      T* xc = x + tid;
+      if (MODE == TRSM_LEFT) {
+        for (int i = 0; i < nb; i++) {  // x_i = (b_i - sum_{k<i} L_ik x_k) / L_ii
+          const T* li = L + (size_t)i * ldl;
+          T s0 = xc[i * ld], s1 = zero<T>();
+          int k = 0;
+          for (; k + 1 < i; k += 2) {
+            s0 -= li[k] * xc[k * ld];
+            s1 -= li[k + 1] * xc[(k + 1) * ld];
+          }
+          if (k < i) s0 -= li[k] * xc[k * ld];
+          xc[i * ld] = (s0 + s1) * (1.0 / re(li[i]));
+        }
+      } else {
+        for (int i = nb - 1; i >= 0; i--) {  // x_i = (b_i - sum_{k>i} conj(L_ki) x_k) / L_ii
+          T s0 = xc[i * ld], s1 = zero<T>();
+          int k = i + 1;
+          for (; k + 1 < nb; k += 2) {
+            s0 -= conjg(L[(size_t)k * ldl + i]) * xc[k * ld];
+            s1 -= conjg(L[(size_t)(k + 1) * ldl + i]) * xc[(k + 1) * ld];
+          }
+          if (k < nb) s0 -= conjg(L[(size_t)k * ldl + i]) * xc[k * ld];
+          xc[i * ld] = (s0 + s1) * (1.0 / re(L[(size_t)i * ldl + i]));
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * 64; e += 64) {
+      int i = e / 64, c = e % 64;
+      if (c < nr) B[(size_t)i * ldb + r0 + c] = x[i * ld + c];
+    }
+  }
+}
+
+// One CTA per batch item: the diagonal block A11 <- L11^-1 A11 L11^-H (A11 read from its
+// lower triangle) by the two-sided column recurrence
+//   alpha_k = a_kk / l_kk^2,  v = a(k+1:, k)/l_kk - (alpha_k/2) l(k+1:, k),
+//   A(k+1:, k+1:) -= l v^H + v l^H,  r_k = v - (alpha_k/2) l(k+1:, k),
+// followed by the deferred in-block solve X = L11^-1 [r_0 r_1 ...] (strictly lower part).
+// Writes the lower triangle back into A and the full Hermitian block into F (ldF).
+template <typename T>
+__global__ void hegst_diag_kernel(T* A, int lda, long long sA, const T* L, int ldl, long long sL, int k0, int nb,
+                                  T* F, int ldF, long long sF) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* a = reinterpret_cast<T*>(smem_raw);
+  T* l = a + nb * (nb + 1);
+  const int z = blockIdx.x, ld = nb + 1, tid = threadIdx.x, nt = blockDim.x;
+  A += z * sA;
+  L += z * sL;
+  F += z * sF;
+  for (int e = tid; e < nb * nb; e += nt) {
+    int i = e / nb, j = e % nb;
+    a[i * ld + j] = (j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j] : zero<T>();
+    l[i * ld + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : zero<T>();
+  }
+  __syncthreads();
+  for (int k = 0; k < nb; k++) {
+    const double lkk = re(l[k * ld + k]);
+    const double alpha = re(a[k * ld + k]) / (lkk * lkk);
+    for (int i = k + 1 + tid; i < nb; i += nt) a[i * ld + k] = a[i * ld + k] * (1.0 / lkk) - (0.5 * alpha) * l[i * ld + k];
+    __syncthreads();
+    const int m = nb - k - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) a[i * ld + j] -= l[i * ld + k] * conjg(a[j * ld + k]) + a[i * ld + k] * conjg(l[j * ld + k]);
+    }
+    __syncthreads();
+    for (int i = k + 1 + tid; i < nb; i += nt) a[i * ld + k] = a[i * ld + k] - (0.5 * alpha) * l[i * ld + k];
+    if (tid == 0) a[k * ld + k] = from_real<T>(alpha);
+    __syncthreads();
+  }
+  for (int c = tid; c < nb; c += nt) {  // column c: rows i > c, forward substitution with L11
+    for (int i = c + 1; i < nb; i++) {
+      T s = a[i * ld + c];
+      for (int k = c + 1; k < i; k++) s -= l[i * ld + k] * a[k * ld + c];
+      a[i * ld + c] = s * (1.0 / re(l[i * ld + i]));
     }
   }
   __syncthreads();
   for (int e = tid; e < nb * nb; e += nt) {
-    int i = e / nb, j = e % nb;
-    Dinv[(size_t)i * ldD + j] = x[i * ld + j];
-  }
-}
-
-// One CTA per batch item: A11' = Dinv A11 Dinv^H for the diagonal block at (k0, k0)
-// (A11 read from its lower triangle).  Writes the lower triangle back into A and the
-// full Hermitian block into F (ldF).
-template <typename T>
-__global__ void hegst_diag_kernel(T* A, int lda, long long sA, int k0, int nb, const T* Dinv, int ldD,
-                                  long long sD, T* F, int ldF, long long sF) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* a = reinterpret_cast<T*>(smem_raw);
-  T* x = a + nb * (nb + 1);
-  T* w = x + nb * (nb + 1);
-  const int z = blockIdx.x, ld = nb + 1, tid = threadIdx.x, nt = blockDim.x;
-  A += z * sA;
-  Dinv += z * sD;
-  F += z * sF;
-  for (int e = tid; e < nb * nb; e += nt) {
-    int i = e / nb, j = e % nb;
-    T v = (j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j] : conjg(A[(size_t)(k0 + j) * lda + k0 + i]);
-    if (i == j) v = from_real<T>(re(v));
-    a[i * ld + j] = v;
-    x[i * ld + j] = Dinv[(size_t)i * ldD + j];
-  }
-  __syncthreads();
-  for (int e = tid; e < nb * nb; e += nt) {           // w = x a  (x lower)
-    int i = e / nb, j = e % nb;
-    T s = zero<T>();
-    for (int k = 0; k <= i; k++) mac(s, x[i * ld + k], a[k * ld + j]);
-    w[i * ld + j] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < nb * nb; e += nt) {           // a = w x^H
-    int i = e / nb, j = e % nb;
-    T s = zero<T>();
-    for (int k = 0; k <= j; k++) mac(s, w[i * ld + k], conjg(x[j * ld + k]));
-    a[i * ld + j] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < nb * nb; e += nt) {           // exact Hermitian symmetry from the lower part
     int i = e / nb, j = e % nb;
     T v = (j <= i) ? a[i * ld + j] : conjg(a[j * ld + i]);
     if (i == j) v = from_real<T>(re(v));
@@ -225,19 +302,38 @@ static dim3 grid2d(int rows, int cols, int count) {
 }
 
 template <typename T>
-void potf2_inv(T* A, int lda, long long sA, int k0, int nb, T* Dinv, int ldD, long long sD, DevStatus* st,
-               int count, cudaStream_t s) {
-  size_t sm = 2 * sizeof(T) * nb * (nb + 1);
-  cudaFuncSetAttribute(potf2_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  potf2_inv_kernel<T><<<count, 256, sm, s>>>(A, lda, sA, k0, nb, Dinv, ldD, sD, st);
+void potf2(T* A, int lda, long long sA, int k0, int nb, DevStatus* st, int count, cudaStream_t s) {
+  size_t sm = sizeof(T) * nb * (nb + 1);
+  cudaFuncSetAttribute(potf2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  potf2_kernel<T><<<count, 256, sm, s>>>(A, lda, sA, k0, nb, st);
 }
 
 template <typename T>
-void hegst_diag(T* A, int lda, long long sA, int k0, int nb, const T* Dinv, int ldD, long long sD, T* F,
-                int ldF, long long sF, int count, cudaStream_t s) {
-  size_t sm = 3 * sizeof(T) * nb * (nb + 1);
+void trsm_block(int mode, const T* L, int ldl, long long sL, T* B, int ldb, long long sB, int nb, int nrhs,
+                int count, cudaStream_t s) {
+  if (nrhs <= 0 || nb <= 0 || count <= 0) return;
+  dim3 grid((nrhs + 63) / 64, count);
+  if (mode == TRSM_RIGHT_CONJ) {
+    size_t sm = sizeof(T) * 64 * (nb + 1);
+    cudaFuncSetAttribute(trsm_block_kernel<T, TRSM_RIGHT_CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    trsm_block_kernel<T, TRSM_RIGHT_CONJ><<<grid, 64, sm, s>>>(L, ldl, sL, B, ldb, sB, nb, nrhs);
+  } else if (mode == TRSM_LEFT) {
+    size_t sm = sizeof(T) * nb * 65;
+    cudaFuncSetAttribute(trsm_block_kernel<T, TRSM_LEFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    trsm_block_kernel<T, TRSM_LEFT><<<grid, 64, sm, s>>>(L, ldl, sL, B, ldb, sB, nb, nrhs);
+  } else {
+    size_t sm = sizeof(T) * nb * 65;
+    cudaFuncSetAttribute(trsm_block_kernel<T, TRSM_LEFT_CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    trsm_block_kernel<T, TRSM_LEFT_CONJ><<<grid, 64, sm, s>>>(L, ldl, sL, B, ldb, sB, nb, nrhs);
+  }
+}
+
+template <typename T>
+void hegst_diag(T* A, int lda, long long sA, const T* L, int ldl, long long sL, int k0, int nb, T* F, int ldF,
+                long long sF, int count, cudaStream_t s) {
+  size_t sm = 2 * sizeof(T) * nb * (nb + 1);
   cudaFuncSetAttribute(hegst_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  hegst_diag_kernel<T><<<count, 256, sm, s>>>(A, lda, sA, k0, nb, Dinv, ldD, sD, F, ldF, sF);
+  hegst_diag_kernel<T><<<count, 256, sm, s>>>(A, lda, sA, L, ldl, sL, k0, nb, F, ldF, sF);
 }
 
 template <typename T>
@@ -271,9 +367,10 @@ void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int
 }
 
 #define INST(T)                                                                                         \
-  template void potf2_inv<T>(T*, int, long long, int, int, T*, int, long long, DevStatus*, int,          \
-                             cudaStream_t);                                                             \
-  template void hegst_diag<T>(T*, int, long long, int, int, const T*, int, long long, T*, int, long long, \
+  template void potf2<T>(T*, int, long long, int, int, DevStatus*, int, cudaStream_t);                   \
+  template void trsm_block<T>(int, const T*, int, long long, T*, int, long long, int, int, int,         \
+                              cudaStream_t);                                                            \
+  template void hegst_diag<T>(T*, int, long long, const T*, int, long long, int, int, T*, int, long long, \
                               int, cudaStream_t);                                                       \
   template void larft<T>(const T*, int, long long, const double*, long long, int, T*, int, long long,    \
                          int, cudaStream_t);                                                            \

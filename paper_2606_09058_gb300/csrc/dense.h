@@ -6,12 +6,15 @@
 
 namespace gks {
 
+enum { TRSM_RIGHT_CONJ = 0, TRSM_LEFT = 1, TRSM_LEFT_CONJ = 2 };
 template <typename T>
-void potf2_inv(T* A, int lda, long long sA, int k0, int nb, T* Dinv, int ldD, long long sD, DevStatus* st,
-               int count, cudaStream_t s);
+void potf2(T* A, int lda, long long sA, int k0, int nb, DevStatus* st, int count, cudaStream_t s);
 template <typename T>
-void hegst_diag(T* A, int lda, long long sA, int k0, int nb, const T* Dinv, int ldD, long long sD, T* F,
-                int ldF, long long sF, int count, cudaStream_t s);
+void trsm_block(int mode, const T* L, int ldl, long long sL, T* B, int ldb, long long sB, int nb, int nrhs,
+                int count, cudaStream_t s);
+template <typename T>
+void hegst_diag(T* A, int lda, long long sA, const T* L, int ldl, long long sL, int k0, int nb, T* F, int ldF,
+                long long sF, int count, cudaStream_t s);
 template <typename T>
 void larft(const T* G, int ldG, long long sG, const double* tau, long long stau, int k, T* Tm, int ldT,
            long long sT, int count, cudaStream_t s);
