@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the generalized Kohn-Sham eigensolve + density matrix on one GB300.
+
+Workload (default "kbatch512"): the 512-atom Si supercell (4x4x4 conventional cells,
+N = 13 * 512 = 6656 s-Gaussians), complex128 Bloch-summed H(k), S(k) at the 8
+Monkhorst-Pack k-points, kT = 0.01 Ha, n_elec = 2048, one chemical potential shared by
+all k-points, FP64 throughout.  One step = one gks_solve of the whole k-batch
+(Cholesky, reduction, tridiagonalization, divide and conquer, back-transformation,
+occupations and mu, density matrix).
+
+Metric: TFLOP/s of the fixed nominal count (36 M^3 per complex k-point + 4 M^2 n_rho for
+the density matrix; 9 M^3 + M^2 n_rho for real problems), whole job over all ranks.
+Inputs (8 x 709 MB per matrix) are far larger than L2, so no flush is needed.
+
+--impl reference times the CPU oracle (the deliberately plain FP64 reference of this
+project) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "kbatch512": dict(desc="512-atom Si supercell, N=6656, 8 k-points, complex128, shared mu", tiling=(4, 4, 4)),
+    "gamma64": dict(desc="64-atom Si cluster, N=832, Gamma, real", tiling=(2, 2, 2)),
+    "nc384": dict(desc="384-atom Si cluster, noncollinear 2N=9984, complex128", tiling=(4, 4, 3)),
+    "adjoint216": dict(desc="216-atom Si cluster, N=2808, Gamma, real", tiling=(3, 3, 3)),
+}
+FP64_PEAK_TFLOPS = 1956.3 * 1.25 / 2250.0   # measured bf16 dense x nominal FP64/bf16 ratio
+
+
+def nominal_flops(M: int, complex_: bool, nrho) -> float:
+    c = 36.0 if complex_ else 9.0
+    r = 4.0 if complex_ else 1.0
+    return sum(c * M ** 3 + r * M * M * float(n) for n in nrho)
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+SAMPLE_OF = {
+    # the same construction at 64 atoms, timed on one pencil
+    "kbatch512": ("periodic (2,2,2) cells, k-point 0", "periodic", (2, 2, 2)),
+    "gamma64": ("the full 64-atom cluster", "cluster", (2, 2, 2)),
+    "adjoint216": ("64-atom (2,2,2) cluster", "cluster", (2, 2, 2)),
+    "nc384": ("16-atom (2,1,1) noncollinear cluster", "nc", (2, 1, 1)),
+}
+
+
+def oracle_sample(workload: str, seconds_cap: float = 600.0) -> dict:
+    """Time the CPU oracle (one thread) on one pencil of the same construction at a size
+    it finishes in seconds; returns the nominal flops and seconds of that solve."""
+    desc, kind, tiling = SAMPLE_OF[workload]
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np, torch
+torch.set_num_threads(1)
+from oracle import oracle as O
+from paper_2606_09058_gb300 import inputs as I
+kind, tiling = {kind!r}, {tiling!r}
+if kind == "periodic":
+    p = I.periodic(tiling, 1, 0.01)
+elif kind == "nc":
+    p = I.noncollinear(tiling, 2, 0.01)
+else:
+    p = I.collinear_gamma(tiling, 0, 0.01)
+H = p.H[:1].numpy(); S = p.S[:1].numpy()
+t = time.perf_counter()
+r = O.solve(H, S, p.kT, p.n_elec, p.spin)
+dt = time.perf_counter() - t
+M = H.shape[1]; cplx = bool(np.iscomplexobj(H))
+fl = (36.0 if cplx else 9.0) * M ** 3 + (4.0 if cplx else 1.0) * M * M * float(r.n_rho[0])
+print(json.dumps(dict(seconds=dt, flops=fl, n=M, complex=cplx)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=seconds_cap)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    res["desc"] = desc
+    return res
+
+
+def _sample_text(workload, smp):
+    return (f"one {smp['n']}x{smp['n']} {'complex' if smp['complex'] else 'real'} pencil of the same construction "
+            f"({smp['desc']}) solved by the single-threaded unblocked FP64 oracle in {smp['seconds']:.1f} s, "
+            f"rate of the nominal FP64 count")
+
+
+def reference_arm(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    samples = []
+    for _ in range(args.warmup + args.steps):
+        samples.append(oracle_sample(args.workload))
+    timed = samples[args.warmup:]
+    secs = sum(s["seconds"] for s in timed)
+    fl = sum(s["flops"] for s in timed)
+    val = fl / secs / 1e12
+    s0 = timed[0]
+    cpu = {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": _sample_text(args.workload, s0)}
+    line = {"impl": "reference", "metric": "GKS eigensolve+rho throughput (nominal FP64 TFLOP/s)", "value": val,
+            "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / len(timed), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample_n": s0["n"]},
+            "cpu_baseline": cpu, "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def make_problem(workload: str, device: str):
+    from paper_2606_09058_gb300 import inputs as I
+    return I.workload(workload, device=device)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="kbatch512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-json", default=None, help="write the per-class/per-stage event profile here")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        from paper_2606_09058_gb300 import build as B
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2606_09058_gb300 import gks
+
+    # Each rank solves its own independent copy of the workload (weak scaling: the
+    # k-batch of one system is the unit; ranks share nothing on the data path).
+    prob = make_problem(args.workload, str(dev))
+    H, S = prob.H.contiguous(), prob.S.contiguous()
+    nk, M = H.shape[0], H.shape[1]
+    spin = prob.spin
+    kw = torch.as_tensor(np.asarray(prob.kweights, float), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gks.Context(local, stream, profile=True)
+    eps = torch.empty(nk, M, dtype=torch.float64, device=dev)
+    C = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
+    rho = torch.empty_like(C)
+    mu = torch.empty(1, dtype=torch.float64, device=dev)
+    eb = torch.empty(1, dtype=torch.float64, device=dev)
+
+    def step(Hd, Sd, sync=False):
+        ctx.solve_into(Hd, Sd, prob.kT, prob.n_elec, spin, kw, eps=eps, C=C, mu=mu, rho=rho, e_band=eb, sync=sync)
+
+    for _ in range(args.warmup):
+        step(H, S, sync=True)
+    ctx.profile()  # drop warm-up records
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = gks.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(H, S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = gks.launch_count() - l0
+    clk = clocks.stop()
+    ctx.sync()
+    prof = ctx.profile()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+
+    eps_h = eps.cpu().numpy()
+    mu_h = float(mu.item())
+    from math import exp
+
+    def fermi(x):
+        return exp(-x) / (1 + exp(-x)) if x > 0 else 1 / (1 + exp(x))
+    nrho = [int(sum(1 for v in eps_h[k] if fermi((v - mu_h) / prob.kT) >= 1e-16)) for k in range(nk)]
+    fl_step = nominal_flops(M, H.is_complex(), nrho)
+    value = fl_step * world / (ms / 1e3) / 1e12
+
+    # roofline: dominant kernel class over the timed region
+    kern = [p for p in prof if not p["name"].startswith("stage:")]
+    dom = max(kern, key=lambda p: p["ms"]) if kern else None
+    roof = None
+    if dom:
+        per = args.steps
+        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12 if dom["ms"] > 0 else 0.0
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom["name"],
+                "kernel_ms_per_step": dom["ms"] / per, "kernel_share": dom["ms"] / (ms * per),
+                "peak_basis": "FP64 DFMA pipe: measured bf16 dense 1956.3 TFLOP/s x nominal FP64/bf16 ratio 1.25/2250"}
+    stages = {p["name"][6:]: round(p["ms"] / args.steps, 3) for p in prof if p["name"].startswith("stage:")}
+    classes = {p["name"]: {"ms": round(p["ms"] / args.steps, 3),
+                           "tflops": round(p["flops"] / (p["ms"] / 1e3) / 1e12, 4) if p["ms"] > 0 and p["flops"] > 0
+                           else None} for p in kern}
+    if args.profile_json and rank == 0:
+        with open(args.profile_json, "w") as fh:
+            json.dump({"ms_per_step": ms, "profile": prof, "steps": args.steps}, fh, indent=1)
+
+    # end to end through the C ABI with host buffers (pinned), H2D and D2H inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Hh = torch.empty(H.shape, dtype=H.dtype, pin_memory=True)
+        Sh = torch.empty(S.shape, dtype=S.dtype, pin_memory=True)
+        Hh.copy_(H)
+        Sh.copy_(S)
+        eps_out = torch.empty(eps.shape, dtype=eps.dtype, pin_memory=True)
+        mu_out = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        eb_out = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        Hd = torch.empty_like(H)
+        Sd = torch.empty_like(S)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            Hd.copy_(Hh, non_blocking=True)
+            Sd.copy_(Sh, non_blocking=True)
+            step(Hd, Sd)
+            eps_out.copy_(eps, non_blocking=True)
+            mu_out.copy_(mu, non_blocking=True)
+            eb_out.copy_(eb, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ctx.sync()
+        ctx.profile()
+        ems = f0.elapsed_time(f1) / args.steps
+        t = torch.tensor([ems], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+        e2e = {"value": fl_step * world / (ems / 1e3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(Hh.numel() * Hh.element_size() + Sh.numel() * Sh.element_size()),
+               "d2h_bytes_per_step": int(eps_out.numel() * 8 + 16), "ms_per_step": ems}
+        del Hh, Sh, Hd, Sd
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            del C, rho
+            torch.cuda.empty_cache()
+            smp = oracle_sample(args.workload)
+            cpu = {"value": smp["flops"] / smp["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                   "sample": _sample_text(args.workload, smp)}
+        except Exception as ex:  # the CPU leg must not hide the GPU result
+            cpu = {"value": None, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+
+    if rank == 0:
+        line = {"metric": "GKS eigensolve+rho throughput (nominal FP64 TFLOP/s)", "value": value, "unit": "TFLOP/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "M": M, "nk": nk,
+                           "spin": spin, "precision": "fp64", "l2": "inputs larger than L2 (no flush needed)",
+                           "nominal_tflop_per_step": fl_step / 1e12, "n_rho": nrho},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+                "stages_ms": stages, "kernels": classes}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -48,7 +48,19 @@ typedef struct {
   void* cuda_stream;   /* cudaStream_t to enqueue on (NULL = legacy default stream) */
   int precision;       /* gks_prec */
   double f_cut;        /* occupations below f_cut are left out of rho (default 1e-16) */
+  int profile;         /* 1: record CUDA events around every launch group (see gks_profile) */
 } gks_opts;
+
+/* One row of the event profile: a kernel class ("gemm", "hetrd_hemv", ...) or a stage
+ * ("stage:potrf", ...), with its algorithmic FP64 flops and bytes (inputs read plus
+ * outputs written once) summed over the recorded launch groups. */
+typedef struct {
+  char name[32];
+  int groups;          /* recorded launch groups */
+  double ms;           /* summed device time (CUDA events on the context's stream) */
+  double flops;        /* algorithmic flops (complex multiply-add = 8) */
+  double bytes;        /* algorithmic bytes */
+} gks_prof_entry;
 
 /* Create a context bound to opts->device and opts->cuda_stream.  opts may be NULL
  * (device 0, default stream).  On success *ctx is set; release with gks_destroy. */
@@ -94,6 +106,14 @@ gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int6
  * enqueued since the previous gks_sync (GKS_ENOTSPD with the failing column and
  * k-point, GKS_ENOCONV, GKS_EINVAL for occupation parameters found invalid). */
 gks_status gks_sync(gks_ctx* ctx);
+
+/* Wait for the stream and return the event profile of everything enqueued since the
+ * previous gks_profile call (requires opts->profile = 1): up to `max` entries are written
+ * to `out`; the return value is the number of entries (0 when profiling is off). */
+int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max);
+
+/* Number of kernel launches this library has issued in the calling process. */
+long long gks_launch_count(void);
 
 /* Stage entry points (same conventions; `count` independent matrices of order m,
  * stride m*m elements).  Used to check each stage on its own. */

@@ -23,7 +23,54 @@ struct Arena {
 };
 }  // namespace
 
+namespace {
+const char* kClassNames[PC_NCLASS] = {"gemm", "potf2", "trsm_block", "hegst_diag", "hetrd_hemv", "hetrd_rank2",
+                                      "hetrd_vec", "dc_leaf", "dc_secular", "dc_gemm", "backtr_aux",
+                                      "occupations", "misc"};
+const char* kStageNames[PS_NSTAGE] = {"stage:copy", "stage:potrf", "stage:hegst", "stage:hetrd", "stage:stedc",
+                                      "stage:backtransform", "stage:unreduce", "stage:occupations", "stage:rho"};
+
+struct EventProf : Prof {
+  cudaStream_t stream = nullptr;
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec {
+    int cls, e0, e1;
+    double flops, bytes;
+  };
+  std::vector<Rec> recs;
+  // deferred flops of the density-matrix GEMM (its K is the device-side n_rho)
+  const int* nrho_dev = nullptr;
+  int rho_m = 0, rho_nk = 0, rho_es = 8;
+  int ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return (int)used++;
+  }
+  int begin() override {
+    if (!on) return -1;
+    int e = ev();
+    cudaEventRecord(pool[e], stream);
+    return e;
+  }
+  void end(int tok, int cls, double flops, double bytes) override {
+    if (tok < 0) return;
+    int e = ev();
+    cudaEventRecord(pool[e], stream);
+    recs.push_back({cls, tok, e, flops, bytes});
+  }
+  ~EventProf() override {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+}  // namespace
+
 struct gks_ctx {
+  EventProf prof;
   int device = 0;
   cudaStream_t stream = nullptr;
   double f_cut = 1e-16;
@@ -129,6 +176,15 @@ X* at(gks_ctx* c, size_t off) {
   return reinterpret_cast<X*>(c->ws + off);
 }
 
+double gemm_flops(int es, int M, int N, int K, int lower, int count) {
+  double mn = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
+  return (es == 16 ? 8.0 : 2.0) * mn * K * count;
+}
+double gemm_bytes(int es, int M, int N, int K, int lower, int count, bool beta) {
+  double mn = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
+  return (double)es * ((double)M * K + (double)K * N + mn * (beta ? 2.0 : 1.0)) * count;
+}
+
 template <typename T>
 void gm(cudaStream_t s, int count, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda,
         long long sA, const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC, int lower = 0,
@@ -151,20 +207,58 @@ void gm(cudaStream_t s, int count, int opA, int opB, int M, int N, int K, double
   gemm<T>(g, M, N, s);
 }
 
+// gm with a profiler record (class PC_GEMM)
+template <typename T>
+void gmp(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA,
+         const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC, int lower = 0) {
+  if (M <= 0 || N <= 0) return;
+  int tok = c->prof.begin();
+  gm<T>(c->stream, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
+  c->prof.end(tok, PC_GEMM, gemm_flops(sizeof(T), M, N, K, lower, count),
+              gemm_bytes(sizeof(T), M, N, K, lower, count, beta != 0.0));
+}
+
+// Profiler record around one launch group.
+struct Rec {
+  gks_ctx* c;
+  int tok, cls;
+  double flops, bytes;
+  Rec(gks_ctx* c_, int cls_, double fl = 0.0, double by = 0.0) : c(c_), cls(cls_), flops(fl), bytes(by) {
+    tok = c->prof.begin();
+  }
+  ~Rec() { c->prof.end(tok, cls, flops, bytes); }
+};
+// Stage bracket (recorded as class PC_NCLASS + stage).
+struct StageRec {
+  gks_ctx* c;
+  int tok, st;
+  StageRec(gks_ctx* c_, int st_) : c(c_), st(st_) { tok = c->prof.begin(); }
+  ~StageRec() { c->prof.end(tok, PC_NCLASS + st, 0.0, 0.0); }
+};
+
+double cmul(int es) { return es == 16 ? 8.0 : 2.0; }
+
 // Blocked right-looking Cholesky of L (in place, lower): diagonal block, panel solve
 // L21 = A21 L11^-H by substitution, trailing Hermitian rank-kb update.
 template <typename T>
 void potrf_run(gks_ctx* c, T* L, int M, int nk) {
   cudaStream_t s = c->stream;
+  const int es = sizeof(T);
   for (int k0 = 0; k0 < M; k0 += NB) {
     const int kb = std::min(NB, M - k0);
-    potf2<T>(L, M, c->sMM, k0, kb, c->st, nk, s);
+    {
+      Rec r(c, PC_POTF2, cmul(es) * kb * kb * kb / 6.0 * nk, 2.0 * es * kb * kb * nk);
+      potf2<T>(L, M, c->sMM, k0, kb, c->st, nk, s);
+    }
     const int rows = M - k0 - kb;
     if (rows <= 0) continue;
     T* L11 = L + (size_t)k0 * M + k0;
     T* L21 = L + (size_t)(k0 + kb) * M + k0;
-    trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, L21, M, c->sMM, kb, rows, nk, s);
-    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, L21, M, c->sMM, 1.0, L21 + kb, M, c->sMM, 1);
+    {
+      Rec r(c, PC_TRSM, cmul(es) * 0.5 * kb * kb * rows * nk, (2.0 * rows * kb + 0.5 * kb * kb) * es * nk);
+      trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, L21, M, c->sMM, kb, rows, nk, s);
+    }
+    gmp<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, L21, M, c->sMM, 1.0, L21 + kb, M, c->sMM, 1);
   }
 }
 
@@ -176,30 +270,69 @@ void potrf_run(gks_ctx* c, T* L, int M, int nk) {
 template <typename T>
 void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
   cudaStream_t s = c->stream;
+  const int es = sizeof(T);
   T* F = at<T>(c, c->oF);
   for (int k0 = 0; k0 < M; k0 += NB) {
     const int kb = std::min(NB, M - k0);
-    hegst_diag<T>(A, M, c->sMM, L, M, c->sMM, k0, kb, F, NB, c->sF, nk, s);
+    {
+      Rec r(c, PC_HEGST_DIAG, cmul(es) * kb * kb * kb * nk, 3.0 * es * kb * kb * nk);
+      hegst_diag<T>(A, M, c->sMM, L, M, c->sMM, k0, kb, F, NB, c->sF, nk, s);
+    }
     const int rows = M - k0 - kb;
     if (rows <= 0) continue;
     const T* L11 = L + (size_t)k0 * M + k0;
     const T* L21 = L + (size_t)(k0 + kb) * M + k0;
     T* A21 = A + (size_t)(k0 + kb) * M + k0;
     T* A22 = A21 + kb;
-    trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, A21, M, c->sMM, kb, rows, nk, s);
-    gm<T>(s, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
-    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, A21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
-    gm<T>(s, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, M, c->sMM, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
-    gm<T>(s, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
+    {
+      Rec r(c, PC_TRSM, cmul(es) * 0.5 * kb * kb * rows * nk, (2.0 * rows * kb + 0.5 * kb * kb) * es * nk);
+      trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, A21, M, c->sMM, kb, rows, nk, s);
+    }
+    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
+    gmp<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, A21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gmp<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, M, c->sMM, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
   }
   for (int r0 = NB; r0 < M; r0 += NB) {
     const int rb = std::min(NB, M - r0);
     T* Ai = A + (size_t)r0 * M;
-    trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * M + r0, M, c->sMM, Ai, M, c->sMM, rb, r0, nk, s);
+    {
+      Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * r0 * nk, (2.0 * r0 * rb + 0.5 * rb * rb) * es * nk);
+      trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * M + r0, M, c->sMM, Ai, M, c->sMM, rb, r0, nk, s);
+    }
     const int below = M - r0 - rb;
     if (below > 0)
-      gm<T>(s, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM, 1.0,
-            A + (size_t)(r0 + rb) * M, M, c->sMM);
+      gmp<T>(c, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM, 1.0,
+             A + (size_t)(r0 + rb) * M, M, c->sMM);
+  }
+}
+
+// One-stage Householder tridiagonalization, steps j = M-1 .. 2.
+template <typename T>
+void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
+  cudaStream_t s = c->stream;
+  const int es = sizeof(T);
+  T* u = at<T>(c, c->ou);
+  T* p = at<T>(c, c->op);
+  double* tau = at<double>(c, c->otau);
+  for (int j = M - 1; j >= 2; j--) {
+    const double jj = (double)j * j;
+    {
+      Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * es * j * nk);
+      hetrd_reflector<T>(A, M, c->sMM, j, u, c->sVec, tau, M, nk, s);
+    }
+    {
+      Rec r(c, PC_HETRD_HEMV, cmul(es) * jj * nk, (0.5 * jj + 2.0 * j) * es * nk);
+      hetrd_hemv<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, nk, s);
+    }
+    {
+      Rec r(c, PC_HETRD_VEC, 0.0, 3.0 * es * j * nk);
+      hetrd_dot<T>(u, p, c->sVec, tau, M, j, nk, s);
+    }
+    {
+      Rec r(c, PC_HETRD_RANK2, cmul(es) * jj * nk, jj * es * nk);
+      hetrd_rank2<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, nk, s);
+    }
   }
 }
 
@@ -216,12 +349,18 @@ void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
   double* tb = at<double>(c, c->otb);
   for (int j0 = 2; j0 <= M - 1; j0 += NB) {
     const int j1 = std::min(j0 + NB - 1, M - 1), nbb = j1 - j0 + 1;
-    gather_reflectors<T>(A, M, c->sMM, tau, M, j0, j1, V, NB, c->sV, tb, NB, nk, s);
-    gm<T>(s, nk, OP_C, OP_N, nbb, nbb, j1, 1.0, V, NB, c->sV, V, NB, c->sV, 0.0, G, NB, c->sG);
-    larft<T>(G, NB, c->sG, tb, NB, nbb, Tm, NB, c->sT, nk, s);
-    gm<T>(s, nk, OP_C, OP_N, nbb, M, j1, 1.0, V, NB, c->sV, X, M, c->sMM, 0.0, Y, M, c->sY);
-    gm<T>(s, nk, OP_N, OP_N, nbb, M, nbb, 1.0, Tm, NB, c->sT, Y, M, c->sY, 0.0, Y2, M, c->sY);
-    gm<T>(s, nk, OP_N, OP_N, j1, M, nbb, -1.0, V, NB, c->sV, Y2, M, c->sY, 1.0, X, M, c->sMM);
+    {
+      Rec r(c, PC_BACKTR_AUX);
+      gather_reflectors<T>(A, M, c->sMM, tau, M, j0, j1, V, NB, c->sV, tb, NB, nk, s);
+    }
+    gmp<T>(c, nk, OP_C, OP_N, nbb, nbb, j1, 1.0, V, NB, c->sV, V, NB, c->sV, 0.0, G, NB, c->sG);
+    {
+      Rec r(c, PC_BACKTR_AUX);
+      larft<T>(G, NB, c->sG, tb, NB, nbb, Tm, NB, c->sT, nk, s);
+    }
+    gmp<T>(c, nk, OP_C, OP_N, nbb, M, j1, 1.0, V, NB, c->sV, X, M, c->sMM, 0.0, Y, M, c->sY);
+    gmp<T>(c, nk, OP_N, OP_N, nbb, M, nbb, 1.0, Tm, NB, c->sT, Y, M, c->sY, 0.0, Y2, M, c->sY);
+    gmp<T>(c, nk, OP_N, OP_N, j1, M, nbb, -1.0, V, NB, c->sV, Y2, M, c->sY, 1.0, X, M, c->sMM);
   }
 }
 
@@ -229,13 +368,17 @@ void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
 template <typename T>
 void unreduce_run(gks_ctx* c, const T* L, T* X, int M, int nk) {
   cudaStream_t s = c->stream;
+  const int es = sizeof(T);
   const int nblk = (M + NB - 1) / NB;
   for (int blk = nblk - 1; blk >= 0; blk--) {
     const int r0 = blk * NB, rb = std::min(NB, M - r0);
     T* Xi = X + (size_t)r0 * M;
-    trsm_block<T>(TRSM_LEFT_CONJ, L + (size_t)r0 * M + r0, M, c->sMM, Xi, M, c->sMM, rb, M, nk, s);
+    {
+      Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * M * nk, (2.0 * M * rb + 0.5 * rb * rb) * es * nk);
+      trsm_block<T>(TRSM_LEFT_CONJ, L + (size_t)r0 * M + r0, M, c->sMM, Xi, M, c->sMM, rb, M, nk, s);
+    }
     if (r0 > 0)
-      gm<T>(s, nk, OP_C, OP_N, r0, M, rb, -1.0, L + (size_t)r0 * M, M, c->sMM, Xi, M, c->sMM, 1.0, X, M, c->sMM);
+      gmp<T>(c, nk, OP_C, OP_N, r0, M, rb, -1.0, L + (size_t)r0 * M, M, c->sMM, Xi, M, c->sMM, 1.0, X, M, c->sMM);
   }
 }
 
@@ -243,57 +386,97 @@ template <typename T>
 gks_status solve_t(gks_ctx* c, const T* H, const T* S, int n, int nk, bool nc, double kT, double n_elec,
                    const double* kw, double* eps, T* C, double* mu, T* rho, double* e_band) {
   const int M = nc ? 2 * n : n;
-  gks_status rc = ensure_ws(c, M, n, nk, (int)sizeof(T), nc ? 1 : 0);
+  const int es = sizeof(T);
+  gks_status rc = ensure_ws(c, M, n, nk, es, nc ? 1 : 0);
   if (rc) return rc;
   cudaStream_t s = c->stream;
   T* A = at<T>(c, c->oA);
   T* L = at<T>(c, c->oL);
-  cudaMemsetAsync(c->st, 0, sizeof(DevStatus) * nk, s);
-  copy2d<T>(A, M, c->sMM, H, M, (long long)M * M, M, M, nk, s);
-  if (nc) spinor_overlap<T>(L, c->sMM, S, n, (long long)n * n, n, nk, s);
-  else copy2d<T>(L, M, c->sMM, S, n, (long long)n * n, n, n, nk, s);
+  {
+    StageRec sr(c, PS_COPY);
+    Rec r(c, PC_MISC);
+    cudaMemsetAsync(c->st, 0, sizeof(DevStatus) * nk, s);
+    copy2d<T>(A, M, c->sMM, H, M, (long long)M * M, M, M, nk, s);
+    if (nc) spinor_overlap<T>(L, c->sMM, S, n, (long long)n * n, n, nk, s);
+    else copy2d<T>(L, M, c->sMM, S, n, (long long)n * n, n, n, nk, s);
+  }
   // (a1) Cholesky of S, (a2) reduction to the standard problem
-  potrf_run<T>(c, L, M, nk);
-  hegst_run<T>(c, A, L, M, nk);
+  {
+    StageRec sr(c, PS_POTRF);
+    potrf_run<T>(c, L, M, nk);
+  }
+  {
+    StageRec sr(c, PS_HEGST);
+    hegst_run<T>(c, A, L, M, nk);
+  }
   // (a3-a4) Householder tridiagonalization with a real-making phase
-  T* u = at<T>(c, c->ou);
-  T* p = at<T>(c, c->op);
-  double* tau = at<double>(c, c->otau);
-  for (int j = M - 1; j >= 2; j--) hetrd_step<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, nk, s);
   double* d = at<double>(c, c->od);
   double* e = at<double>(c, c->oe);
   T* ph = at<T>(c, c->oph);
-  hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, nk, s);
+  {
+    StageRec sr(c, PS_HETRD);
+    hetrd_run<T>(c, A, M, nk);
+    Rec r(c, PC_HETRD_VEC);
+    hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, nk, s);
+  }
   // (a5) divide and conquer on the real tridiagonal
   double* Z = at<double>(c, c->oZ);
-  dc_solve(c->dc, d, e, M, eps, Z, c->sMM, c->ws + c->odc, c->st, s);
+  {
+    StageRec sr(c, PS_STEDC);
+    dc_solve(c->dc, d, e, M, eps, Z, c->sMM, c->ws + c->odc, c->st, s, &c->prof);
+  }
   // (a6) X = Q D Z, C = L^-H X
-  apply_phase<T>(C, M, c->sMM, Z, M, c->sMM, ph, M, M, nk, s);
-  backtransform_run<T>(c, A, C, M, nk);
-  unreduce_run<T>(c, L, C, M, nk);
-  column_phase<T>(C, M, c->sMM, M, M, nk, s);
+  {
+    StageRec sr(c, PS_BACKTR);
+    {
+      Rec r(c, PC_MISC);
+      apply_phase<T>(C, M, c->sMM, Z, M, c->sMM, ph, M, M, nk, s);
+    }
+    backtransform_run<T>(c, A, C, M, nk);
+  }
+  {
+    StageRec sr(c, PS_UNREDUCE);
+    unreduce_run<T>(c, L, C, M, nk);
+    Rec r(c, PC_MISC);
+    column_phase<T>(C, M, c->sMM, M, M, nk, s);
+  }
   // (a8) occupations and chemical potential, (a9) density matrix
   double* occ = at<double>(c, c->oocc);
   double* ks = at<double>(c, c->oks);
   int* nrho = at<int>(c, c->onrho);
   const double* w = kw ? kw : at<double>(c, c->ow);
   double* eb = e_band ? e_band : at<double>(c, c->oeb);
-  fermi_mu(eps, M, nk, w, nc ? 1.0 : 2.0, kT, n_elec, c->f_cut, occ, ks, mu, eb, nrho, c->st, 1, s);
-  GemmBatch g{};
-  g.base = GemmDesc{C, C, rho, ks, M, M, M, M, M, M};
-  g.sA = c->sMM;
-  g.sB = c->sMM;
-  g.sC = c->sMM;
-  g.sK = M;
-  g.kdev = nrho;
-  g.count = nk;
-  g.opA = OP_N;
-  g.opB = OP_C;
-  g.lower = 1;
-  g.alpha = 1.0;
-  g.beta = 0.0;
-  gemm<T>(g, M, M, s);
-  mirror_lower<T>(rho, M, c->sMM, M, nk, s);
+  {
+    StageRec sr(c, PS_OCC);
+    Rec r(c, PC_OCC);
+    fermi_mu(eps, M, nk, w, nc ? 1.0 : 2.0, kT, n_elec, c->f_cut, occ, ks, mu, eb, nrho, c->st, 1, s);
+  }
+  {
+    StageRec sr(c, PS_RHO);
+    GemmBatch g{};
+    g.base = GemmDesc{C, C, rho, ks, M, M, M, M, M, M};
+    g.sA = c->sMM;
+    g.sB = c->sMM;
+    g.sC = c->sMM;
+    g.sK = M;
+    g.kdev = nrho;
+    g.count = nk;
+    g.opA = OP_N;
+    g.opB = OP_C;
+    g.lower = 1;
+    g.alpha = 1.0;
+    g.beta = 0.0;
+    {
+      Rec r(c, PC_GEMM, -1.0, -1.0);  // flops resolved from n_rho when the profile is read
+      c->prof.nrho_dev = nrho;
+      c->prof.rho_m = M;
+      c->prof.rho_nk = nk;
+      c->prof.rho_es = es;
+      gemm<T>(g, M, M, s);
+    }
+    Rec r(c, PC_MISC);
+    mirror_lower<T>(rho, M, c->sMM, M, nk, s);
+  }
   return cuda_check(c, "gks_solve launch");
 }
 
@@ -308,6 +491,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     c->device = opts->device;
     c->stream = static_cast<cudaStream_t>(opts->cuda_stream);
     if (opts->f_cut > 0.0) c->f_cut = opts->f_cut;
+    c->prof.on = opts->profile != 0;
     if (opts->precision != GKS_FP64) {
       delete c;
       return GKS_ENOTIMPL;
@@ -318,6 +502,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     delete c;
     return GKS_ECUDA;
   }
+  c->prof.stream = c->stream;
   *ctx = c;
   return GKS_OK;
 }
@@ -381,6 +566,48 @@ gks_status gks_sync(gks_ctx* ctx) {
   return GKS_OK;
 }
 
+long long gks_launch_count(void) { return launches_issued(); }
+
+int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max) {
+  if (!ctx || !ctx->prof.on) return 0;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  EventProf& P = ctx->prof;
+  double rho_fl = 0.0, rho_by = 0.0;
+  if (P.nrho_dev && ctx->ws) {
+    std::vector<int> nr(P.rho_nk);
+    cudaMemcpy(nr.data(), P.nrho_dev, sizeof(int) * P.rho_nk, cudaMemcpyDeviceToHost);
+    const double m = P.rho_m;
+    for (int k = 0; k < P.rho_nk; k++) {
+      rho_fl += cmul(P.rho_es) * 0.5 * m * (m + 1) * nr[k];
+      rho_by += (double)P.rho_es * (2.0 * m * nr[k] + 0.5 * m * (m + 1));
+    }
+  }
+  const int nent = PC_NCLASS + PS_NSTAGE;
+  std::vector<gks_prof_entry> acc(nent);
+  for (int i = 0; i < nent; i++) {
+    std::memset(&acc[i], 0, sizeof(gks_prof_entry));
+    std::snprintf(acc[i].name, sizeof(acc[i].name), "%s", i < PC_NCLASS ? kClassNames[i] : kStageNames[i - PC_NCLASS]);
+  }
+  for (auto& r : P.recs) {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, P.pool[r.e0], P.pool[r.e1]);
+    gks_prof_entry& e = acc[r.cls];
+    e.groups++;
+    e.ms += ms;
+    e.flops += r.flops < 0 ? rho_fl : r.flops;
+    e.bytes += r.bytes < 0 ? rho_by : r.bytes;
+  }
+  P.recs.clear();
+  P.used = 0;
+  int k = 0;
+  for (int i = 0; i < nent && k < max; i++)
+    if (acc[i].groups > 0) out[k++] = acc[i];
+  cudaGetLastError();
+  return k;
+}
+
 gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype) {
   if (!ctx || !A || m < 1 || count < 1 || m > 46340) return fail(ctx, GKS_EINVAL, "bad arguments");
   cudaSetDevice(ctx->device);
@@ -433,7 +660,7 @@ gks_status gks_stedc(gks_ctx* ctx, const double* d, const double* e, int64_t m, 
   double* ew = at<double>(ctx, ctx->oe);
   copy2d<double>(dw, (int)m, m, d, (int)m, m, 1, (int)m, (int)count, s);
   copy2d<double>(ew, (int)m, m, e, (int)m, m, 1, (int)m, (int)count, s);
-  dc_solve(ctx->dc, dw, ew, m, lam, Z, m * m, ctx->ws + ctx->odc, ctx->st, s);
+  dc_solve(ctx->dc, dw, ew, m, lam, Z, m * m, ctx->ws + ctx->odc, ctx->st, s, &ctx->prof);
   return cuda_check(ctx, "gks_stedc");
 }
 

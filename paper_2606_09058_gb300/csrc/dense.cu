@@ -305,6 +305,7 @@ template <typename T>
 void potf2(T* A, int lda, long long sA, int k0, int nb, DevStatus* st, int count, cudaStream_t s) {
   size_t sm = sizeof(T) * nb * (nb + 1);
   cudaFuncSetAttribute(potf2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  count_launch();
   potf2_kernel<T><<<count, 256, sm, s>>>(A, lda, sA, k0, nb, st);
 }
 
@@ -316,14 +317,17 @@ void trsm_block(int mode, const T* L, int ldl, long long sL, T* B, int ldb, long
   if (mode == TRSM_RIGHT_CONJ) {
     size_t sm = sizeof(T) * 64 * (nb + 1);
     cudaFuncSetAttribute(trsm_block_kernel<T, TRSM_RIGHT_CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
     trsm_block_kernel<T, TRSM_RIGHT_CONJ><<<grid, 64, sm, s>>>(L, ldl, sL, B, ldb, sB, nb, nrhs);
   } else if (mode == TRSM_LEFT) {
     size_t sm = sizeof(T) * nb * 65;
     cudaFuncSetAttribute(trsm_block_kernel<T, TRSM_LEFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
     trsm_block_kernel<T, TRSM_LEFT><<<grid, 64, sm, s>>>(L, ldl, sL, B, ldb, sB, nb, nrhs);
   } else {
     size_t sm = sizeof(T) * nb * 65;
     cudaFuncSetAttribute(trsm_block_kernel<T, TRSM_LEFT_CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
     trsm_block_kernel<T, TRSM_LEFT_CONJ><<<grid, 64, sm, s>>>(L, ldl, sL, B, ldb, sB, nb, nrhs);
   }
 }
@@ -333,6 +337,7 @@ void hegst_diag(T* A, int lda, long long sA, const T* L, int ldl, long long sL, 
                 long long sF, int count, cudaStream_t s) {
   size_t sm = 2 * sizeof(T) * nb * (nb + 1);
   cudaFuncSetAttribute(hegst_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  count_launch();
   hegst_diag_kernel<T><<<count, 256, sm, s>>>(A, lda, sA, L, ldl, sL, k0, nb, F, ldF, sF);
 }
 
@@ -341,28 +346,33 @@ void larft(const T* G, int ldG, long long sG, const double* tau, long long stau,
            long long sT, int count, cudaStream_t s) {
   size_t sm = sizeof(T) * (k * k + k);
   cudaFuncSetAttribute(larft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  count_launch();
   larft_kernel<T><<<count, 128, sm, s>>>(G, ldG, sG, tau, stau, k, Tm, ldT, sT);
 }
 
 template <typename T>
 void apply_phase(T* X, int ldx, long long sX, const double* Z, int ldz, long long sZ, const T* ph, long long sph,
                  int n, int count, cudaStream_t s) {
+  count_launch();
   apply_phase_kernel<T><<<grid2d(n, n, count), 256, 0, s>>>(X, ldx, sX, Z, ldz, sZ, ph, sph, n);
 }
 
 template <typename T>
 void mirror_lower(T* A, int lda, long long sA, int n, int count, cudaStream_t s) {
+  count_launch();
   mirror_lower_kernel<T><<<grid2d(n, n, count), 256, 0, s>>>(A, lda, sA, n);
 }
 
 template <typename T>
 void column_phase(T* C, int ldc, long long sC, int rows, int cols, int count, cudaStream_t s) {
   dim3 grid((cols + 7) / 8, count);
+  count_launch();
   column_phase_kernel<T><<<grid, 256, 0, s>>>(C, ldc, sC, rows, cols);
 }
 
 template <typename T>
 void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int n, int count, cudaStream_t s) {
+  count_launch();
   spinor_overlap_kernel<T><<<grid2d(2 * n, 2 * n, count), 256, 0, s>>>(dst, sd, S, lds, ss, n);
 }
 

@@ -29,10 +29,18 @@ template <typename T>
 void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int n, int count, cudaStream_t s);
 
 // ---- Householder tridiagonalization (hetrd.cu) ----
-// Workspace per batch item: u (m), p (m), q (m) vectors, tau (m).
+// Workspace per batch item: u (m), p (m) vectors, tau (m).  One step j = four launches.
 template <typename T>
-void hetrd_step(T* A, int lda, long long sA, int j, T* u, T* p, long long sv, double* tau, long long stau,
-                int count, cudaStream_t s);
+void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau, long long stau, int count,
+                     cudaStream_t s);
+template <typename T>
+void hetrd_hemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
+                long long stau, int count, cudaStream_t s);
+template <typename T>
+void hetrd_dot(const T* u, T* p, long long sv, const double* tau, long long stau, int j, int count, cudaStream_t s);
+template <typename T>
+void hetrd_rank2(T* A, int lda, long long sA, int j, const T* u, const T* q, long long sv, const double* tau,
+                 long long stau, int count, cudaStream_t s);
 template <typename T>
 void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e, long long sde, T* ph,
                   long long sph, int count, cudaStream_t s);
@@ -48,7 +56,7 @@ void dc_plan_destroy(DcPlan* p);
 size_t dc_workspace_bytes(const DcPlan* p);
 // d (m), e (m-1) per item (stride sde); Z out (m x m, ld m, stride sZ); lam out (stride sde).
 void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, double* Z, long long sZ, void* work,
-              DevStatus* st, cudaStream_t s);
+              DevStatus* st, cudaStream_t s, Prof* prof);
 
 // ---- occupations (occ.cu) ----
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,

@@ -5,11 +5,16 @@
 // little memory bandwidth: a 64 x 64 register-tiled CTA at K-step 16 asks for under one
 // byte of shared memory per DFMA.  The kernel therefore favours many independent CTAs
 // (grouped problems of different shapes in one launch) over deep software pipelining.
+#include <atomic>
 #include <cstdio>
 
 #include "launch.h"
 
 namespace gks {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_issued() { return g_launches.load(std::memory_order_relaxed); }
 
 template <typename T> struct GemmTile;
 template <> struct GemmTile<double> {
@@ -121,6 +126,7 @@ void gemm(const GemmBatch& b, int maxM, int maxN, cudaStream_t s) {
   constexpr int BM = 16 * GemmTile<T>::TM, BN = 16 * GemmTile<T>::TN;
   if (maxM <= 0 || maxN <= 0 || b.count <= 0) return;
   dim3 grid((maxN + BN - 1) / BN, (maxM + BM - 1) / BM, b.count);
+  count_launch();
   gemm_kernel<T><<<grid, 256, 0, s>>>(b);
 }
 
@@ -140,6 +146,7 @@ void copy2d(T* dst, int ldd, long long sd, const T* src, int lds, long long ss, 
             int count, cudaStream_t s) {
   if (rows <= 0 || cols <= 0 || count <= 0) return;
   dim3 grid((cols + 255) / 256 < 8 ? (cols + 255) / 256 : 8, rows < 1024 ? rows : 1024, count);
+  count_launch();
   copy2d_kernel<T><<<grid, 256, 0, s>>>(dst, ldd, sd, src, lds, ss, rows, cols);
 }
 

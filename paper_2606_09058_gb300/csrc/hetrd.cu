@@ -177,17 +177,36 @@ __global__ void gather_reflectors_kernel(const T* A, int lda, long long sA, cons
 }
 
 template <typename T>
-void hetrd_step(T* A, int lda, long long sA, int j, T* u, T* p, long long sv, double* tau, long long stau,
-                int count, cudaStream_t s) {
+void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau, long long stau, int count,
+                     cudaStream_t s) {
+  count_launch();
   hetrd_reflector_kernel<T><<<count, 256, 0, s>>>(A, lda, sA, j, u, sv, tau, stau);
+}
+
+template <typename T>
+void hetrd_hemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
+                long long stau, int count, cudaStream_t s) {
+  count_launch();
   hetrd_hemv_kernel<T><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau);
+}
+
+template <typename T>
+void hetrd_dot(const T* u, T* p, long long sv, const double* tau, long long stau, int j, int count, cudaStream_t s) {
+  count_launch();
   hetrd_dot_kernel<T><<<count, 256, 0, s>>>(u, p, sv, tau, stau, j);
-  hetrd_rank2_kernel<T><<<dim3(j, count), 128, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau);
+}
+
+template <typename T>
+void hetrd_rank2(T* A, int lda, long long sA, int j, const T* u, const T* q, long long sv, const double* tau,
+                 long long stau, int count, cudaStream_t s) {
+  count_launch();
+  hetrd_rank2_kernel<T><<<dim3(j, count), 128, 0, s>>>(A, lda, sA, j, u, q, sv, tau, stau);
 }
 
 template <typename T>
 void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e, long long sde, T* ph,
                   long long sph, int count, cudaStream_t s) {
+  count_launch();
   hetrd_finish_kernel<T><<<count, 256, 0, s>>>(A, lda, sA, m, d, e, sde, ph, sph);
 }
 
@@ -195,12 +214,18 @@ template <typename T>
 void gather_reflectors(const T* A, int lda, long long sA, const double* tau, long long stau, int j0, int j1,
                        T* V, int ldv, long long sV, double* tb, long long stb, int count, cudaStream_t s) {
   dim3 grid(1, j1 < 2048 ? j1 : 2048, count);
+  count_launch();
   gather_reflectors_kernel<T><<<grid, 64, 0, s>>>(A, lda, sA, tau, stau, j0, j1, V, ldv, sV, tb, stb);
 }
 
 #define INST(T)                                                                                            \
-  template void hetrd_step<T>(T*, int, long long, int, T*, T*, long long, double*, long long, int,          \
-                              cudaStream_t);                                                               \
+  template void hetrd_reflector<T>(T*, int, long long, int, T*, long long, double*, long long, int,         \
+                                   cudaStream_t);                                                          \
+  template void hetrd_hemv<T>(const T*, int, long long, int, const T*, T*, long long, const double*,         \
+                              long long, int, cudaStream_t);                                               \
+  template void hetrd_dot<T>(const T*, T*, long long, const double*, long long, int, int, cudaStream_t);     \
+  template void hetrd_rank2<T>(T*, int, long long, int, const T*, const T*, long long, const double*,        \
+                               long long, int, cudaStream_t);                                              \
   template void hetrd_finish<T>(const T*, int, long long, int, double*, double*, long long, T*, long long,   \
                                 int, cudaStream_t);                                                        \
   template void gather_reflectors<T>(const T*, int, long long, const double*, long long, int, int, T*, int, \

@@ -35,6 +35,25 @@ struct GemmBatch {
 
 template <typename T> void gemm(const GemmBatch& b, int maxM, int maxN, cudaStream_t s);
 
+// Number of kernel launches issued by this library (process-wide).
+void count_launch(int n = 1);
+long long launches_issued();
+
+// Kernel classes and stages for the optional event profiler.
+enum ProfClass : int {
+  PC_GEMM = 0, PC_POTF2, PC_TRSM, PC_HEGST_DIAG, PC_HETRD_HEMV, PC_HETRD_RANK2, PC_HETRD_VEC, PC_DC_LEAF,
+  PC_DC_SECULAR, PC_DC_GEMM, PC_BACKTR_AUX, PC_OCC, PC_MISC, PC_NCLASS
+};
+enum ProfStage : int {
+  PS_COPY = 0, PS_POTRF, PS_HEGST, PS_HETRD, PS_STEDC, PS_BACKTR, PS_UNREDUCE, PS_OCC, PS_RHO, PS_NSTAGE
+};
+// Records CUDA events around launch groups (no-op when profiling is off).
+struct Prof {
+  virtual ~Prof() {}
+  virtual int begin() = 0;
+  virtual void end(int tok, int cls, double flops, double bytes) = 0;
+};
+
 // 2D strided copy with batch: dst[b][i][j] = src[b][i][j] (rows x cols).
 template <typename T>
 void copy2d(T* dst, int ldd, long long sd, const T* src, int lds, long long ss, int rows, int cols,

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(1024) fermi_mu_kernel(const double* eps, int m
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec, double f_cut,
               double* occ, double* kscale, double* mu, double* e_band, int* nrho, DevStatus* st, int nsys,
               cudaStream_t s) {
+  count_launch();
   fermi_mu_kernel<<<nsys, 1024, 0, s>>>(eps, m, nk, w, gs, kT, n_elec, f_cut, occ, kscale, mu, e_band, nrho, st);
 }
 

@@ -496,7 +496,7 @@ static void build_gemm_lists(DcPlan* p, double* Z, long long sZ, void* work) {
 }
 
 void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, double* Z, long long sZ, void* work,
-              DevStatus* st, cudaStream_t s) {
+              DevStatus* st, cudaStream_t s, Prof* prof) {
   const int m = p->m, cnt = p->count;
   if (p->zbound != Z || p->wbound != work || p->sZbound != sZ) build_gemm_lists(p, Z, sZ, work);
   const size_t item = dc_item_bytes(m);
@@ -506,10 +506,14 @@ void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, doubl
   double* lamBuf[2] = {w0.lamA, w0.lamB};
   double* zbuf0 = (p->depth % 2 == 0) ? Z : w0.Zb;
   const long long sZ0 = (p->depth % 2 == 0) ? sZ : slam;
+  int tok = prof->begin();
+  count_launch();
   dc_tear_kernel<<<cnt, 32, 0, s>>>(d, e, sde, p->d_splits, (int)p->splits.size());
   const int nleaves = (int)p->leaves.size() / 2;
+  count_launch();
   dc_leaf_kernel<<<dim3((nleaves + 3) / 4, cnt), 128, 0, s>>>(d, e, sde, lamBuf[0], slam, zbuf0, sZ0, m,
                                                               p->d_leaves, nleaves, st);
+  prof->end(tok, PC_DC_LEAF, 0.0, 0.0);
   for (int t = 0; t < p->depth; t++) {
     DcLevel& L = p->levels[t];
     const int nn = (int)L.nodes.size();
@@ -525,12 +529,26 @@ void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, doubl
     const bool in_is_Z = ((t % 2) == (p->depth % 2));
     a.Zc = in_is_Z ? Z : w0.Zb;
     a.sZ = in_is_Z ? sZ : slam;
+    tok = prof->begin();
+    count_launch();
     dc_merge_prep_kernel<<<dim3(nn, cnt), 256, 0, s>>>(a, L.d_nodes);
     dim3 g1((L.maxn + 127) / 128, nn, cnt);
+    count_launch();
     dc_secular_kernel<<<g1, 128, 0, s>>>(a, L.d_nodes, st);
+    count_launch();
     dc_zhat_kernel<<<g1, 128, 0, s>>>(a, L.d_nodes);
+    count_launch();
     dc_colmap_kernel<<<g1, 128, 0, s>>>(a, L.d_nodes);
+    count_launch();
     dc_buildw_kernel<<<dim3((L.maxn + 7) / 8, nn, cnt), 256, 0, s>>>(a, L.d_nodes);
+    prof->end(tok, PC_DC_SECULAR, 0.0, 0.0);
+    double gfl = 0.0, gby = 0.0;
+    for (auto& nd : L.nodes) {
+      const double nn1 = nd.n1, nn2 = nd.n2, n = nn1 + nn2;
+      gfl += 2.0 * (nn1 * nn1 + nn2 * nn2) * n;
+      gby += 8.0 * (nn1 * nn1 + nn2 * nn2 + 2.0 * n * n);
+    }
+    tok = prof->begin();
     GemmBatch gb{};
     gb.list = L.d_gemm;
     gb.count = 2 * nn * cnt;
@@ -539,6 +557,7 @@ void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, doubl
     gb.alpha = 1.0;
     gb.beta = 0.0;
     gemm<double>(gb, L.maxhalf, L.maxn, s);
+    prof->end(tok, PC_DC_GEMM, gfl * cnt, gby * cnt);
   }
   // final eigenvalues
   double* lamFinal = lamBuf[p->depth % 2];

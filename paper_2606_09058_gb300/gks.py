@@ -30,7 +30,12 @@ class GKSError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
-                ("f_cut", ctypes.c_double)]
+                ("f_cut", ctypes.c_double), ("profile", ctypes.c_int)]
+
+
+class _ProfEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("groups", ctypes.c_int), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 def library_path() -> str:
@@ -56,6 +61,10 @@ def load() -> ctypes.CDLL:
     lib.gks_potrf.argtypes = [P, P, I64, I64, I]
     lib.gks_reduce.argtypes = [P, P, P, I64, I64, I]
     lib.gks_stedc.argtypes = [P, P, P, I64, I64, P, P]
+    lib.gks_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I]
+    lib.gks_profile.restype = I
+    lib.gks_launch_count.argtypes = []
+    lib.gks_launch_count.restype = ctypes.c_longlong
     for f in ("gks_create", "gks_destroy", "gks_solve", "gks_sync", "gks_potrf", "gks_reduce", "gks_stedc"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
@@ -87,13 +96,14 @@ class Solution:
 class Context:
     """A gks context bound to one device and one CUDA stream."""
 
-    def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None, f_cut: float = 1e-16):
+    def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None, f_cut: float = 1e-16,
+                 profile: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("gks needs a CUDA device")
         lib = load()
         self.device = torch.cuda.current_device() if device is None else int(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), 0, f_cut)
+        opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), 0, f_cut, 1 if profile else 0)
         h = ctypes.c_void_p()
         rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
         if rc:
@@ -118,6 +128,14 @@ class Context:
 
     def sync(self):
         self._raise(self._lib.gks_sync(self._h))
+
+    def profile(self) -> list[dict]:
+        """Event profile since the previous call: kernel classes and stages with device
+        time (ms) and algorithmic flops/bytes (empty unless created with profile=True)."""
+        buf = (_ProfEntry * 64)()
+        n = self._lib.gks_profile(self._h, buf, 64)
+        return [dict(name=buf[i].name.decode(), groups=buf[i].groups, ms=buf[i].ms, flops=buf[i].flops,
+                     bytes=buf[i].bytes) for i in range(n)]
 
     # ------------------------------------------------------------------ full path
     def solve_into(self, H, S, kT, n_elec, spin="collinear", kweights=None, *, eps, C, mu, rho, e_band=None,
@@ -194,6 +212,11 @@ class Context:
         self._raise(rc)
         self.sync()
         return lam, Z
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libgks.so in this process."""
+    return int(load().gks_launch_count())
 
 
 _default: dict = {}

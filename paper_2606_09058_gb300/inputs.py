@@ -94,6 +94,16 @@ def _sym_uniform(rng, n, dev):
     return 0.5 * (a + a.T)
 
 
+def _sus(S: torch.Tensor, U: torch.Tensor) -> torch.Tensor:
+    """S U S for complex S and real symmetric U with real GEMMs (S U: two products;
+    (S U) S: three products, (a+ib)(c+id) = ac - bd + i((a+b)(c+d) - ac - bd))."""
+    a, b = S.real.contiguous(), S.imag.contiguous()
+    pa, pb = a @ U, b @ U
+    ac, bd = pa @ a, pb @ b
+    mix = (pa + pb) @ (a + b)
+    return torch.complex(ac - bd, mix - ac - bd)
+
+
 def _hermitize(x: torch.Tensor) -> torch.Tensor:
     return 0.5 * (x + x.transpose(-1, -2).conj())
 
@@ -197,11 +207,11 @@ def periodic(tiling, index: int, kT: float, n_elec: float | None = None, device=
         b = _well_overlaps(c, a, pos, shift, device)
         Bk += phase[:, None, None] * b[None]
         del b
-    U = _sym_uniform(rng, n, device).to(torch.complex128)
+    U = _sym_uniform(rng, n, device)
     for ik in range(nk):
         Sk[ik] = _hermitize(Sk[ik])
         Hk[ik] += -Z_WELL * (Bk[ik] @ Bk[ik].conj().T)
-        Hk[ik] += PERTURB * (Sk[ik] @ U @ Sk[ik])
+        Hk[ik] += PERTURB * _sus(Sk[ik], U)
         Hk[ik] = _hermitize(Hk[ik])
     natoms = pos.shape[0]
     ne = 4.0 * natoms if n_elec is None else n_elec
