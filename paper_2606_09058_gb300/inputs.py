@@ -315,6 +315,8 @@ def workload(name: str, device="cpu") -> Problem:
     """The named workloads (atom counts and N = 13 * atoms bind; see tiling notes)."""
     if name == "gamma64":       # 64 atoms, N = 832, real, kT 0.01, n_elec 256
         return collinear_gamma((2, 2, 2), 0, 0.01, 256.0, device)
+    if name == "kbatch64":      # 64-atom supercell, N = 832, 8 k-points (small case of the same construction)
+        return periodic((2, 2, 2), 1, 0.01, 256.0, device)
     if name == "kbatch512":     # 512 atoms, N = 6656, 8 k-points, complex, n_elec 2048
         return periodic((4, 4, 4), 1, 0.01, 2048.0, device)
     if name == "nc384":         # 384 atoms, N = 4992, 2N = 9984 spinor
