@@ -82,7 +82,8 @@ struct gks_ctx {
   DcPlan* dc = nullptr;
   DevStatus* st = nullptr;
   // offsets (bytes) of per-item arrays; each holds nk items
-  size_t oA, oL, oF, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc;
+  size_t oA, oL, oF, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
+      oticket;
   long long sMM, sF, sV, sG, sT, sY, sVec;
 };
 
@@ -145,6 +146,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->onrho = a.take<int>((size_t)nk);
   c->ow = a.take<double>((size_t)nk);
   c->oeb = a.take<double>(4);
+  c->oticket = a.take<int>((size_t)2 * nk);
   c->dc = dc_plan_create(m, nk);
   c->odc = a.take<char>(dc_workspace_bytes(c->dc));
   c->ws_bytes = a.off;
@@ -307,7 +309,7 @@ void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
   }
 }
 
-// One-stage Householder tridiagonalization, steps j = M-1 .. 2.
+// One-stage Householder tridiagonalization, steps j = M-1 .. 2 (two launches per step).
 template <typename T>
 void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   cudaStream_t s = c->stream;
@@ -315,23 +317,22 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   T* u = at<T>(c, c->ou);
   T* p = at<T>(c, c->op);
   double* tau = at<double>(c, c->otau);
+  int* tk = at<int>(c, c->oticket);
+  if (M < 3) return;
+  cudaMemsetAsync(tk, 0, sizeof(int) * 2 * nk, s);
+  {
+    Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * es * (M - 1) * nk);
+    hetrd_reflector<T>(A, M, c->sMM, M - 1, u, c->sVec, tau, M, nk, s);
+  }
   for (int j = M - 1; j >= 2; j--) {
     const double jj = (double)j * j;
     {
-      Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * es * j * nk);
-      hetrd_reflector<T>(A, M, c->sMM, j, u, c->sVec, tau, M, nk, s);
+      Rec r(c, PC_HETRD_HEMV, cmul(es) * jj * nk, (0.5 * jj + 4.0 * j) * es * nk);
+      hetrd_hemv<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, tk, nk, s);
     }
     {
-      Rec r(c, PC_HETRD_HEMV, cmul(es) * jj * nk, (0.5 * jj + 2.0 * j) * es * nk);
-      hetrd_hemv<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, nk, s);
-    }
-    {
-      Rec r(c, PC_HETRD_VEC, 0.0, 3.0 * es * j * nk);
-      hetrd_dot<T>(u, p, c->sVec, tau, M, j, nk, s);
-    }
-    {
-      Rec r(c, PC_HETRD_RANK2, cmul(es) * jj * nk, jj * es * nk);
-      hetrd_rank2<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, nk, s);
+      Rec r(c, PC_HETRD_RANK2, cmul(es) * jj * nk, (jj + 2.0 * j) * es * nk);
+      hetrd_rank2<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, tk + nk, nk, s);
     }
   }
 }

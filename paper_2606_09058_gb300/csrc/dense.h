@@ -29,18 +29,18 @@ template <typename T>
 void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int n, int count, cudaStream_t s);
 
 // ---- Householder tridiagonalization (hetrd.cu) ----
-// Workspace per batch item: u (m), p (m) vectors, tau (m).  One step j = four launches.
+// Workspace per batch item: u (m), p (m) vectors, tau (m), two zeroed tickets.  Step j is
+// hetrd_hemv (ending in the q update) and hetrd_rank2 (ending in the reflector of step
+// j-1); hetrd_reflector starts the sweep at j = m-1.
 template <typename T>
 void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau, long long stau, int count,
                      cudaStream_t s);
 template <typename T>
 void hetrd_hemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
-                long long stau, int count, cudaStream_t s);
+                long long stau, int* ticket, int count, cudaStream_t s);
 template <typename T>
-void hetrd_dot(const T* u, T* p, long long sv, const double* tau, long long stau, int j, int count, cudaStream_t s);
-template <typename T>
-void hetrd_rank2(T* A, int lda, long long sA, int j, const T* u, const T* q, long long sv, const double* tau,
-                 long long stau, int count, cudaStream_t s);
+void hetrd_rank2(T* A, int lda, long long sA, int j, T* u, const T* q, long long sv, double* tau, long long stau,
+                 int* ticket, int count, cudaStream_t s);
 template <typename T>
 void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e, long long sde, T* ph,
                   long long sph, int count, cudaStream_t s);

@@ -45,6 +45,14 @@ __host__ __device__ __forceinline__ zc operator/(zc a, zc b) {
   return zc{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
 }
 
+// Load through L2 only (bypassing L1): used to read data other CTAs of the same grid
+// wrote before a fence.
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ zc ldcg(const zc* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return zc{v.x, v.y};
+}
+
 // acc += a * b (fused where the type allows)
 __device__ __forceinline__ void mac(double& acc, double a, double b) { acc = fma(a, b, acc); }
 __device__ __forceinline__ void mac(zc& acc, zc a, zc b) {

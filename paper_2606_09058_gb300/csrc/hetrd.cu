@@ -17,25 +17,21 @@
 
 namespace gks {
 
+// Reflector for step j (one CTA): reads row j left of the diagonal (through L2: in the
+// fused form other CTAs have just written it), writes u', tau[j] and the sub-diagonal.
 template <typename T>
-__global__ void hetrd_reflector_kernel(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau,
-                                       long long stau) {
-  __shared__ T red[32];
+__device__ void reflector_body(T* A, int lda, int j, T* u, double* tau) {
   __shared__ double redd[32];
-  const int z = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  A += z * sA;
-  u += z * sv;
-  tau += z * stau;
+  const int tid = threadIdx.x, nt = blockDim.x;
   T* row = A + (size_t)j * lda;
   double s2 = 0.0;
-  for (int i = tid; i < j; i += nt) s2 += abs2(row[i]);
+  for (int i = tid; i < j; i += nt) s2 += abs2(ldcg(row + i));
   const double xnorm2 = block_sum(s2, redd);
-  const T alpha = conjg(row[j - 1]);
+  const T alpha = conjg(ldcg(row + j - 1));
   const double tail = xnorm2 - abs2(alpha);
   if (!(tail > 0.0)) {  // nothing to annihilate: P_j = I
     for (int i = tid; i < j; i += nt) u[i] = (i == j - 1) ? from_real<T>(1.0) : zero<T>();
     if (tid == 0) tau[j] = 0.0;
-    (void)red;
     return;
   }
   const double xn = sqrt(xnorm2);
@@ -46,7 +42,7 @@ __global__ void hetrd_reflector_kernel(T* A, int lda, long long sA, int j, T* u,
   const T inv = conjg(upiv) * (1.0 / abs2(upiv));       // 1 / upiv
   __syncthreads();
   for (int i = tid; i < j - 1; i += nt) {
-    T v = conjg(row[i]) * inv;                         // u'_i = a_i / u_{j-1}
+    T v = conjg(ldcg(row + i)) * inv;                 // u'_i = a_i / u_{j-1}
     u[i] = v;
     row[i] = v;
   }
@@ -57,14 +53,26 @@ __global__ void hetrd_reflector_kernel(T* A, int lda, long long sA, int j, T* u,
   }
 }
 
+template <typename T>
+__global__ void hetrd_reflector_kernel(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau,
+                                       long long stau) {
+  const int z = blockIdx.x;
+  reflector_body<T>(A + z * sA, lda, j, u + z * sv, tau + z * stau);
+}
+
 // p = tau * A[0:j,0:j] u  (Hermitian, lower storage).  CTA b owns rows/columns
 // [64b, 64b+64): its own row panel left of the diagonal plus its column panel below,
 // so every CTA reads the same number of elements and no cross-CTA reduction is needed.
+// The last CTA to finish (atomic ticket after a fence; nothing waits) then forms
+// q = p - (tau/2)(u^H p) u in place of p.
 template <typename T>
 __global__ void __launch_bounds__(256) hetrd_hemv_kernel(const T* A, int lda, long long sA, int j, const T* u,
-                                                         T* p, long long sv, const double* tau, long long stau) {
+                                                         T* p, long long sv, const double* tau, long long stau,
+                                                         int* ticket) {
   __shared__ T part[4][64];
   __shared__ T rowacc[64];
+  __shared__ T red[32];
+  __shared__ int last;
   const int z = blockIdx.y, tid = threadIdx.x;
   A += z * sA;
   u += z * sv;
@@ -95,39 +103,48 @@ __global__ void __launch_bounds__(256) hetrd_hemv_kernel(const T* A, int lda, lo
     T y = rowacc[tid] + part[0][tid] + part[1][tid] + part[2][tid] + part[3][tid];
     p[c0 + tid] = t * y;
   }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(ticket + z, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  if (tid == 0) ticket[z] = 0;
+  T d = zero<T>();
+  for (int i = tid; i < j; i += blockDim.x) macc(d, u[i], ldcg(p + i));
+  d = block_sum(d, red);
+  const T K = (0.5 * t) * d;
+  for (int i = tid; i < j; i += blockDim.x) p[i] = ldcg(p + i) - K * u[i];
 }
 
-// q = p - (tau/2)(u^H p) u, in place of p.
+// A[0:j,0:j] (lower) -= u q^H + q u^H, one CTA per row; the last CTA of each batch item
+// then computes the reflector of step j-1 from the freshly updated row j-1.
 template <typename T>
-__global__ void hetrd_dot_kernel(const T* u, T* p, long long sv, const double* tau, long long stau, int j) {
-  __shared__ T red[32];
-  const int z = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  u += z * sv;
-  p += z * sv;
-  const double t = tau[z * stau + j];
-  T s = zero<T>();
-  for (int i = tid; i < j; i += nt) macc(s, u[i], p[i]);
-  s = block_sum(s, red);
-  const T K = (0.5 * t) * s;
-  for (int i = tid; i < j; i += nt) p[i] = p[i] - K * u[i];
-}
-
-// A[0:j,0:j] (lower) -= u q^H + q u^H ; one CTA per row.
-template <typename T>
-__global__ void hetrd_rank2_kernel(T* A, int lda, long long sA, int j, const T* u, const T* q, long long sv,
-                                   const double* tau, long long stau) {
+__global__ void hetrd_rank2_kernel(T* A, int lda, long long sA, int j, T* u, const T* q, long long sv,
+                                   double* tau, long long stau, int* ticket) {
+  __shared__ int last;
   const int z = blockIdx.y, r = blockIdx.x;
-  if (tau[z * stau + j] == 0.0) return;
   A += z * sA;
   u += z * sv;
   q += z * sv;
-  const T ur = u[r], qr = q[r];
-  T* ar = A + (size_t)r * lda;
-  for (int c = threadIdx.x; c <= r; c += blockDim.x) {
-    T v = ar[c];
-    v -= ur * conjg(q[c]) + qr * conjg(u[c]);
-    ar[c] = v;
+  tau += z * stau;
+  if (tau[j] != 0.0) {
+    const T ur = u[r], qr = q[r];
+    T* ar = A + (size_t)r * lda;
+    for (int c = threadIdx.x; c <= r; c += blockDim.x) {
+      T v = ar[c];
+      v -= ur * conjg(q[c]) + qr * conjg(u[c]);
+      ar[c] = v;
+    }
   }
+  if (j - 1 < 2) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket + z, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  if (threadIdx.x == 0) ticket[z] = 0;
+  __syncthreads();
+  reflector_body<T>(A, lda, j - 1, u, tau);
 }
 
 // d_i = Re A_ii, e_i = |A_{i+1,i}|, ph_0 = 1, ph_{i+1} = ph_i A_{i+1,i}/|A_{i+1,i}|.
@@ -185,22 +202,16 @@ void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, dou
 
 template <typename T>
 void hetrd_hemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
-                long long stau, int count, cudaStream_t s) {
+                long long stau, int* ticket, int count, cudaStream_t s) {
   count_launch();
-  hetrd_hemv_kernel<T><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau);
+  hetrd_hemv_kernel<T><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, ticket);
 }
 
 template <typename T>
-void hetrd_dot(const T* u, T* p, long long sv, const double* tau, long long stau, int j, int count, cudaStream_t s) {
+void hetrd_rank2(T* A, int lda, long long sA, int j, T* u, const T* q, long long sv, double* tau, long long stau,
+                 int* ticket, int count, cudaStream_t s) {
   count_launch();
-  hetrd_dot_kernel<T><<<count, 256, 0, s>>>(u, p, sv, tau, stau, j);
-}
-
-template <typename T>
-void hetrd_rank2(T* A, int lda, long long sA, int j, const T* u, const T* q, long long sv, const double* tau,
-                 long long stau, int count, cudaStream_t s) {
-  count_launch();
-  hetrd_rank2_kernel<T><<<dim3(j, count), 128, 0, s>>>(A, lda, sA, j, u, q, sv, tau, stau);
+  hetrd_rank2_kernel<T><<<dim3(j, count), 256, 0, s>>>(A, lda, sA, j, u, q, sv, tau, stau, ticket);
 }
 
 template <typename T>
@@ -222,10 +233,9 @@ void gather_reflectors(const T* A, int lda, long long sA, const double* tau, lon
   template void hetrd_reflector<T>(T*, int, long long, int, T*, long long, double*, long long, int,         \
                                    cudaStream_t);                                                          \
   template void hetrd_hemv<T>(const T*, int, long long, int, const T*, T*, long long, const double*,         \
-                              long long, int, cudaStream_t);                                               \
-  template void hetrd_dot<T>(const T*, T*, long long, const double*, long long, int, int, cudaStream_t);     \
-  template void hetrd_rank2<T>(T*, int, long long, int, const T*, const T*, long long, const double*,        \
-                               long long, int, cudaStream_t);                                              \
+                              long long, int*, int, cudaStream_t);                                         \
+  template void hetrd_rank2<T>(T*, int, long long, int, T*, const T*, long long, double*, long long, int*,   \
+                               int, cudaStream_t);                                                         \
   template void hetrd_finish<T>(const T*, int, long long, int, double*, double*, long long, T*, long long,   \
                                 int, cudaStream_t);                                                        \
   template void gather_reflectors<T>(const T*, int, long long, const double*, long long, int, int, T*, int, \

@@ -273,14 +273,23 @@ __global__ void dc_merge_prep_kernel(DcArgs a, const DcNode* nodes) {
   w.cnt[3 * off + 2] = nrot;
 }
 
-// Secular roots by bisection in tau, one thread per root.
+// Secular roots, one warp per root.  With origin pole d_o and tau = lam - d_o the function
+//   f(tau) = 1 + rho' sum_i z_i^2 / (delta_i - tau),  delta_i = d_i - d_o,
+// is increasing between its poles.  Each iteration evaluates psi (poles left of the root),
+// phi (poles right of it) and their derivatives (lanes split the K terms), models each
+// part by one pole plus a constant matched in value and slope,
+//   psi ~ p + q/(delta_j - tau),  phi ~ s + t/(delta_{j+1} - tau),
+// and takes the root of the model (a quadratic in u = delta_j - tau) when it falls inside
+// the current sign bracket; otherwise it bisects.  Stops when f is below its rounding
+// level or the bracket is at the working precision of tau.
 __global__ void dc_secular_kernel(DcArgs a, const DcNode* nodes, DevStatus* st) {
   const DcNode nd = nodes[blockIdx.y];
   const int z = blockIdx.z;
   DcWs w = item_ws(a, z);
   const int off = nd.off, s = off + nd.n1;
   const int K = w.cnt[3 * off];
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= K) return;
   const double rho2 = 2.0 * fabs(a.e[z * a.sde + s - 1]);
   const double* dK = w.dK + off;
@@ -290,29 +299,77 @@ __global__ void dc_secular_kernel(DcArgs a, const DcNode* nodes, DevStatus* st) 
   if (j < K - 1) {
     const double gap = dK[j + 1] - dK[j];
     const double mid = 0.5 * gap;
-    double f = 1.0;
-    for (int i = 0; i < K; i++) f += rho2 * zK[i] * zK[i] / ((dK[i] - dK[j]) - mid);
+    double f = 0.0;
+    for (int i = lane; i < K; i += 32) f += zK[i] * zK[i] / ((dK[i] - dK[j]) - mid);
+    f = 1.0 + rho2 * warp_sum(f);
     if (f >= 0.0) { o = j; lo = 0.0; hi = mid; }
     else { o = j + 1; lo = -mid; hi = 0.0; }
   } else {
     double zz = 0.0;
-    for (int i = 0; i < K; i++) zz += zK[i] * zK[i];
+    for (int i = lane; i < K; i += 32) zz += zK[i] * zK[i];
+    zz = warp_sum(zz);
     o = j; lo = 0.0; hi = rho2 * zz * (1.0 + 4.0 * DC_U) + 4.0 * DC_U * fabs(dK[j]);
   }
   const double d0 = dK[o];
+  // poles bracketing the root, relative to the origin: left = delta_j, right = delta_{j+1}
+  const double dl = dK[j] - d0;
+  const bool last = (j == K - 1);
+  const double dr = last ? 0.0 : dK[j + 1] - d0;
+  double tau = 0.5 * (lo + hi);
   int it = 0;
-  for (; it < 400; it++) {
-    double mid = 0.5 * (lo + hi);
-    if (!(hi - lo > 2.0 * DC_U * fmax(fabs(lo), fabs(hi))) || mid == lo || mid == hi) break;
-    double f = 1.0;
-    for (int i = 0; i < K; i++) f += rho2 * zK[i] * zK[i] / ((dK[i] - d0) - mid);
-    if (f < 0.0) lo = mid; else hi = mid;
+  for (; it < 100; it++) {
+    double ps = 0.0, psd = 0.0, fs = 0.0, fsd = 0.0, absum = 0.0;
+    for (int i = lane; i < K; i += 32) {
+      double den = (dK[i] - d0) - tau;
+      double t = zK[i] / den;
+      double term = zK[i] * t;          // z_i^2 / den
+      double dterm = t * t;             // z_i^2 / den^2
+      if (i <= j) { ps += term; psd += dterm; }
+      else { fs += term; fsd += dterm; }
+      absum += fabs(term);
+    }
+    ps = warp_sum(ps); psd = warp_sum(psd); fs = warp_sum(fs); fsd = warp_sum(fsd); absum = warp_sum(absum);
+    const double f = 1.0 + rho2 * (ps + fs);
+    if (f < 0.0) lo = tau; else hi = tau;
+    if (fabs(f) <= 8.0 * DC_U * (1.0 + rho2 * absum)) break;
+    if (!(hi - lo > 2.0 * DC_U * fmax(fabs(lo), fabs(hi)))) break;
+    // two-pole model
+    const double ul = dl - tau;                        // delta_j - tau
+    const double qa = rho2 * psd * ul * ul;            // rho' q
+    const double c0 = 1.0 + rho2 * (ps - psd * ul);    // 1 + rho' p
+    double cand;
+    if (last) {
+      double c = c0 + rho2 * fs;                       // no pole on the right
+      cand = (c > 0.0) ? dl + qa / c : 0.5 * (lo + hi);   // c + qa/(dl - x) = 0
+    } else {
+      const double ur = dr - tau;
+      const double ta = rho2 * fsd * ur * ur;            // rho' t
+      const double c = c0 + rho2 * (fs - fsd * ur);      // 1 + rho'(p + s)
+      const double D = dr - dl;
+      // c u^2 + (c D + qa + ta) u + qa D = 0, u = dl - x in (-D, 0)
+      const double B = c * D + qa + ta, C = qa * D;
+      double u;
+      if (c == 0.0) {
+        u = -C / B;
+      } else {
+        double disc = B * B - 4.0 * c * C;
+        disc = disc > 0.0 ? sqrt(disc) : 0.0;
+        // roots: (-B -+ disc)/(2c); stable form picks the root in (-D, 0)
+        double r1 = (B > 0.0) ? (-B - disc) / (2.0 * c) : (2.0 * C) / (-B + disc);
+        double r2 = (B > 0.0) ? (2.0 * C) / (-B - disc) : (-B + disc) / (2.0 * c);
+        u = (r1 < 0.0 && r1 > -D) ? r1 : r2;
+      }
+      cand = dl - u;
+    }
+    if (!(cand > lo && cand < hi)) cand = 0.5 * (lo + hi);
+    tau = cand;
   }
-  if (it >= 400) set_status(st ? st + z : nullptr, ST_ENOCONV, off + j);
-  const double tau = 0.5 * (lo + hi);
-  w.orig[off + j] = o;
-  w.tauK[off + j] = tau;
-  w.lamK[off + j] = d0 + tau;
+  if (it >= 100 && lane == 0) set_status(st ? st + z : nullptr, ST_ENOCONV, off + j);
+  if (lane == 0) {
+    w.orig[off + j] = o;
+    w.tauK[off + j] = tau;
+    w.lamK[off + j] = d0 + tau;
+  }
 }
 
 // Gu-Eisenstat: z_hat_i^2 = (lam_i - d_i)/rho' * prod_{j != i} (lam_j - d_i)/(d_j - d_i).
@@ -534,7 +591,7 @@ void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, doubl
     dc_merge_prep_kernel<<<dim3(nn, cnt), 256, 0, s>>>(a, L.d_nodes);
     dim3 g1((L.maxn + 127) / 128, nn, cnt);
     count_launch();
-    dc_secular_kernel<<<g1, 128, 0, s>>>(a, L.d_nodes, st);
+    dc_secular_kernel<<<dim3((L.maxn + 7) / 8, nn, cnt), 256, 0, s>>>(a, L.d_nodes, st);
     count_launch();
     dc_zhat_kernel<<<g1, 128, 0, s>>>(a, L.d_nodes);
     count_launch();
