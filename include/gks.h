@@ -102,6 +102,23 @@ gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int6
                      double kT, double n_elec, const double* kweights, unsigned flags, double* eps, void* C,
                      double* mu, void* rho, double* e_band);
 
+/* Vector-Jacobian product of a real loss L(rho, eps, E_band) through gks_solve, with
+ * n_elec fixed (mu moves with H and S).  First-order perturbation of H C = S C eps,
+ * C^H S C = I gives d eps_i = c_i^H (dH - eps_i dS) c_i and, at fixed mu,
+ * d rho = g_s C [G o (C^H dH C) - G' o (C^H dS C)] C^H with
+ * G_ij = (f_i - f_j)/(eps_i - eps_j), G'_ij = (f_i eps_i - f_j eps_j)/(eps_i - eps_j)
+ * (limits f'_i and f_i + eps_i f'_i on equal eigenvalues); the returned gradients satisfy
+ * dL = Re tr(H_bar^H dH) + Re tr(S_bar^H dS) for Hermitian dH, dS.
+ * Inputs: C, eps, mu as returned by gks_solve for the same (n, nk, dtype, spin, kT,
+ * kweights); rho_bar (nk, M, M) = dL/d rho (its Hermitian part is used; NULL = 0);
+ * eps_bar (nk, M) = explicit dL/d eps (NULL = 0); e_band_bar = dL/dE_band.
+ * Outputs: H_bar (nk, M, M) and S_bar (nk, n, n), full Hermitian storage (noncollinear:
+ * S_bar is the sum of the two diagonal spin blocks, since S_NC = diag(S, S)).
+ * The context keeps a separate workspace (3 M^2 elements per k-point) for this call. */
+gks_status gks_adjoint(gks_ctx* ctx, const void* C, const double* eps, const double* mu, int64_t n, int64_t nk,
+                       int dtype, int spin_mode, double kT, const double* kweights, const void* rho_bar,
+                       const double* eps_bar, double e_band_bar, void* H_bar, void* S_bar);
+
 /* Wait for the context's stream and report the first device-side failure of the work
  * enqueued since the previous gks_sync (GKS_ENOTSPD with the failing column and
  * k-point, GKS_ENOCONV, GKS_EINVAL for occupation parameters found invalid). */

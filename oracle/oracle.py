@@ -273,3 +273,68 @@ def eig_condition(H, S, eps, C):
     ns = np.linalg.norm(S, 2)
     cn = np.sum(np.abs(C) ** 2, axis=0)
     return U_ROUND * (nh + np.abs(eps) * ns) * cn
+
+
+# ----------------------------- adjoint (vector-Jacobian product) -----------------------------
+
+def fermi_prime(eps, mu, kT):
+    """df/d eps = -f (1 - f) / kT."""
+    f = fermi((eps - mu) / kT)
+    return -f * (1.0 - f) / kT
+
+
+def adjoint(res: Result, kT: float, spin: str = "collinear", kweights=None, rho_bar=None, eps_bar=None,
+            e_band_bar: float = 0.0):
+    """Gradients of L(rho, eps, E_band) with respect to H and S (Hermitian), n_elec fixed.
+
+    First-order perturbation of H C = S C eps with C^H S C = I: for M = C^H dH C and
+    N = C^H dS C, d eps_i = M_ii - eps_i N_ii and, at fixed mu,
+        d rho = g_s C [G o M - G' o N] C^H,
+        G_ij  = (f_i - f_j)/(eps_i - eps_j)              (f'_i when eps_i = eps_j),
+        G'_ij = (f_i eps_i - f_j eps_j)/(eps_i - eps_j)  (f_i + eps_i f'_i when equal).
+    The electron count fixes d mu = sum w f' d eps / sum w f'.  Collecting the terms with
+    W = C^H rho_bar C (rho_bar made Hermitian):
+        H_bar = C [g_s G o W + diag(e)] C^H,   S_bar = -C [g_s G' o W + diag(eps e)] C^H,
+        e_i = eps_bar_i + E_bar g_s w (f_i + eps_i f'_i) + A w f'_i / sum w f',
+        A = -g_s sum_k sum_i f'_ki Re W_k,ii - E_bar g_s sum_k w_k sum_i f'_ki eps_ki.
+    Noncollinear: S_NC = diag(S, S), so S_bar is the sum of the two diagonal spin blocks.
+    Returns (H_bar (nk, M, M), S_bar (nk, N, N))."""
+    eps, C, mu = res.eps, res.C, res.mu
+    nk, M = eps.shape
+    gs = 2.0 if spin == "collinear" else 1.0
+    w = np.full(nk, 1.0 / nk) if kweights is None else np.asarray(kweights, float)
+    f = np.stack([fermi((eps[k] - mu) / kT) for k in range(nk)])
+    fp = np.stack([fermi_prime(eps[k], mu, kT) for k in range(nk)])
+    Ws = []
+    for k in range(nk):
+        if rho_bar is None:
+            Ws.append(np.zeros((M, M), dtype=C.dtype))
+        else:
+            rb = 0.5 * (rho_bar[k] + rho_bar[k].conj().T)
+            Ws.append(C[k].conj().T @ rb @ C[k])
+    wfp = sum(w[k] * fp[k].sum() for k in range(nk))
+    A = -gs * sum(np.sum(fp[k] * Ws[k].diagonal().real) for k in range(nk))
+    A -= e_band_bar * gs * sum(w[k] * np.sum(fp[k] * eps[k]) for k in range(nk))
+    Hb, Sb = [], []
+    for k in range(nk):
+        e = np.zeros(M) if eps_bar is None else np.array(eps_bar[k], float)
+        e = e + e_band_bar * gs * w[k] * (f[k] + eps[k] * fp[k])
+        if wfp != 0.0:
+            e = e + A * w[k] * fp[k] / wfp
+        d = eps[k][:, None] - eps[k][None, :]
+        close = np.abs(d) <= 1e-12 * np.maximum(1.0, np.abs(eps[k]))[:, None]
+        dsafe = np.where(close, 1.0, d)
+        G = np.where(close, fp[k][:, None], (f[k][:, None] - f[k][None, :]) / dsafe)
+        fe = f[k] * eps[k]
+        Gp = np.where(close, (f[k] + eps[k] * fp[k])[:, None], (fe[:, None] - fe[None, :]) / dsafe)
+        BH = gs * G * Ws[k] + np.diag(e)
+        BS = -(gs * Gp * Ws[k] + np.diag(eps[k] * e))
+        hb = C[k] @ BH @ C[k].conj().T
+        sb = C[k] @ BS @ C[k].conj().T
+        Hb.append(0.5 * (hb + hb.conj().T))
+        sb = 0.5 * (sb + sb.conj().T)
+        if spin == "noncollinear":
+            n = M // 2
+            sb = sb[:n, :n] + sb[n:, n:]
+        Sb.append(sb)
+    return np.stack(Hb), np.stack(Sb)

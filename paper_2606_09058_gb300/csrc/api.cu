@@ -28,7 +28,8 @@ const char* kClassNames[PC_NCLASS] = {"gemm", "potf2", "trsm_block", "hegst_diag
                                       "hetrd_vec", "dc_leaf", "dc_secular", "dc_gemm", "backtr_aux",
                                       "occupations", "misc"};
 const char* kStageNames[PS_NSTAGE] = {"stage:copy", "stage:potrf", "stage:hegst", "stage:hetrd", "stage:stedc",
-                                      "stage:backtransform", "stage:unreduce", "stage:occupations", "stage:rho"};
+                                      "stage:backtransform", "stage:unreduce", "stage:occupations", "stage:rho",
+                                      "stage:adjoint"};
 
 struct EventProf : Prof {
   cudaStream_t stream = nullptr;
@@ -81,6 +82,10 @@ struct gks_ctx {
   int m = -1, n = -1, nk = -1, es = -1, nc = -1;
   DcPlan* dc = nullptr;
   DevStatus* st = nullptr;
+  // adjoint workspace (separate arena, sized for the last adjoint shape)
+  char* aws = nullptr;
+  size_t aws_bytes = 0;
+  int am = -1, ank = -1, aes = -1;
   // offsets (bytes) of per-item arrays; each holds nk items
   size_t oA, oL, oF, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
       oticket;
@@ -98,6 +103,13 @@ gks_status cuda_check(gks_ctx* c, const char* where) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, GKS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
   return GKS_OK;
+}
+
+void release_aws(gks_ctx* c) {
+  if (c->aws) cudaFree(c->aws);
+  c->aws = nullptr;
+  c->aws_bytes = 0;
+  c->am = -1;
 }
 
 void release_ws(gks_ctx* c) {
@@ -481,6 +493,83 @@ gks_status solve_t(gks_ctx* c, const T* H, const T* S, int n, int nk, bool nc, d
   return cuda_check(c, "gks_solve launch");
 }
 
+// Adjoint: W = C^H rho_bar C; weights; BH, BS; H_bar = C BH C^H, S_bar = C BS C^H.
+template <typename T>
+gks_status adjoint_t(gks_ctx* c, const T* C, const double* eps, const double* mu, int n, int nk, bool nc, double kT,
+                     const double* kw, const T* rho_bar, const double* eps_bar, double e_band_bar, T* H_bar,
+                     T* S_bar) {
+  const int M = nc ? 2 * n : n;
+  const int es = sizeof(T);
+  const long long MM = (long long)M * M;
+  if (!(c->aws && c->am == M && c->ank == nk && c->aes == es)) {
+    release_aws(c);
+    size_t bytes = (size_t)3 * MM * nk * es + (size_t)4 * M * nk * sizeof(double) + 4096;
+    if (cudaMalloc(&c->aws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->aws = nullptr;
+      return fail(c, GKS_ENOMEM, "adjoint workspace allocation failed");
+    }
+    c->aws_bytes = bytes;
+    c->am = M;
+    c->ank = nk;
+    c->aes = es;
+  }
+  cudaStream_t s = c->stream;
+  T* R = reinterpret_cast<T*>(c->aws);          // rho_bar (Hermitian part), later BH
+  T* W = R + MM * nk;                            // C^H rho_bar C, later BS
+  T* T1 = W + MM * nk;                           // GEMM temporary
+  double* f = reinterpret_cast<double*>(T1 + MM * nk);
+  double* fp = f + (size_t)M * nk;
+  double* e = fp + (size_t)M * nk;
+  double* wdef = e + (size_t)M * nk;
+  const double gs = nc ? 1.0 : 2.0;
+  StageRec sr(c, PS_ADJOINT);
+  const double* w = kw;
+  if (!w) {
+    std::vector<double> h(nk, 1.0 / nk);
+    cudaMemcpyAsync(wdef, h.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    w = wdef;
+  }
+  {
+    Rec r(c, PC_MISC);
+    adj_occ(eps, mu, kT, (long long)nk * M, f, fp, s);
+  }
+  const int have_w = rho_bar ? 1 : 0;
+  if (have_w) {
+    {
+      Rec r(c, PC_MISC);
+      herm_part<T>(R, rho_bar, MM, MM, M, nk, s);
+    }
+    gmp<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, R, M, MM, C, M, MM, 0.0, T1, M, MM);
+    gmp<T>(c, nk, OP_C, OP_N, M, M, M, 1.0, C, M, MM, T1, M, MM, 0.0, W, M, MM);
+  }
+  {
+    Rec r(c, PC_MISC);
+    adj_weights<T>(eps, f, fp, w, W, MM, M, nk, gs, eps_bar, e_band_bar, have_w, e, s);
+    adj_build<T>(W, R, MM, M, eps, f, e, mu, kT, gs, have_w, nk, s);
+  }
+  // H_bar = C BH C^H
+  gmp<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, C, M, MM, R, M, MM, 0.0, T1, M, MM);
+  gmp<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, H_bar, M, MM);
+  {
+    Rec r(c, PC_MISC);
+    herm_part<T>(H_bar, H_bar, MM, MM, M, nk, s);
+  }
+  // S_bar = C BS C^H (noncollinear: the two diagonal spin blocks summed)
+  gmp<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, C, M, MM, W, M, MM, 0.0, T1, M, MM);
+  if (nc) {
+    gmp<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, R, M, MM);
+    Rec r(c, PC_MISC);
+    spin_block_sum<T>(S_bar, (long long)n * n, R, MM, n, nk, s);
+  } else {
+    gmp<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, S_bar, M, MM);
+    Rec r(c, PC_MISC);
+    herm_part<T>(S_bar, S_bar, MM, MM, M, nk, s);
+  }
+  return cuda_check(c, "gks_adjoint launch");
+}
+
 }  // namespace
 
 extern "C" {
@@ -514,6 +603,7 @@ gks_status gks_destroy(gks_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   release_ws(ctx);
+  release_aws(ctx);
   delete ctx;
   return GKS_OK;
 }
@@ -543,6 +633,28 @@ gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int6
                            n_elec, kweights, eps, static_cast<double*>(C), mu, static_cast<double*>(rho), e_band);
   return solve_t<zc>(ctx, static_cast<const zc*>(H), static_cast<const zc*>(S), (int)n, (int)nk, nc, kT, n_elec,
                      kweights, eps, static_cast<zc*>(C), mu, static_cast<zc*>(rho), e_band);
+}
+
+gks_status gks_adjoint(gks_ctx* ctx, const void* C, const double* eps, const double* mu, int64_t n, int64_t nk,
+                       int dtype, int spin_mode, double kT, const double* kweights, const void* rho_bar,
+                       const double* eps_bar, double e_band_bar, void* H_bar, void* S_bar) {
+  if (!ctx) return GKS_EINVAL;
+  ctx->err.clear();
+  if (!C || !eps || !mu || !H_bar || !S_bar) return fail(ctx, GKS_EINVAL, "null array argument");
+  if (n < 1 || nk < 1 || n > 46340 || nk > 65535) return fail(ctx, GKS_EINVAL, "n or nk out of range");
+  if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
+  const bool nc = spin_mode == GKS_NONCOLLINEAR;
+  if (spin_mode != GKS_COLLINEAR && !nc) return fail(ctx, GKS_EINVAL, "unknown spin mode");
+  if (nc && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
+  if (!(kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
+  cudaSetDevice(ctx->device);
+  if (dtype == GKS_R64)
+    return adjoint_t<double>(ctx, static_cast<const double*>(C), eps, mu, (int)n, (int)nk, nc, kT, kweights,
+                             static_cast<const double*>(rho_bar), eps_bar, e_band_bar, static_cast<double*>(H_bar),
+                             static_cast<double*>(S_bar));
+  return adjoint_t<zc>(ctx, static_cast<const zc*>(C), eps, mu, (int)n, (int)nk, nc, kT, kweights,
+                       static_cast<const zc*>(rho_bar), eps_bar, e_band_bar, static_cast<zc*>(H_bar),
+                       static_cast<zc*>(S_bar));
 }
 
 gks_status gks_sync(gks_ctx* ctx) {

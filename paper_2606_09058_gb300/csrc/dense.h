@@ -58,6 +58,20 @@ size_t dc_workspace_bytes(const DcPlan* p);
 void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, double* Z, long long sZ, void* work,
               DevStatus* st, cudaStream_t s, Prof* prof);
 
+// ---- adjoint (adjoint.cu) ----
+void adj_occ(const double* eps, const double* mu, double kT, long long tot, double* f, double* fp, cudaStream_t s);
+template <typename T>
+void adj_weights(const double* eps, const double* f, const double* fp, const double* w, const T* W, long long sW,
+                 int M, int nk, double gs, const double* eps_bar, double e_band_bar, int have_w, double* e,
+                 cudaStream_t s);
+template <typename T>
+void adj_build(T* W, T* BH, long long sW, int M, const double* eps, const double* f, const double* e,
+               const double* mu, double kT, double gs, int have_w, int nk, cudaStream_t s);
+template <typename T>
+void herm_part(T* dst, const T* src, long long sd, long long ss, int M, int nk, cudaStream_t s);
+template <typename T>
+void spin_block_sum(T* dst, long long sd, const T* src, long long ss, int n, int nk, cudaStream_t s);
+
 // ---- occupations (occ.cu) ----
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,
               double f_cut, double* occ, double* kscale, double* mu, double* e_band, int* nrho, DevStatus* st,

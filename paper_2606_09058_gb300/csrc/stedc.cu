@@ -280,8 +280,9 @@ __global__ void dc_merge_prep_kernel(DcArgs a, const DcNode* nodes) {
 // part by one pole plus a constant matched in value and slope,
 //   psi ~ p + q/(delta_j - tau),  phi ~ s + t/(delta_{j+1} - tau),
 // and takes the root of the model (a quadratic in u = delta_j - tau) when it falls inside
-// the current sign bracket; otherwise it bisects.  Stops when f is below its rounding
-// level or the bracket is at the working precision of tau.
+// the current sign bracket; otherwise it bisects, and it also bisects whenever two steps
+// failed to halve the bracket.  Stops when f is below its rounding level or the bracket
+// is at the working precision of tau.
 __global__ void dc_secular_kernel(DcArgs a, const DcNode* nodes, DevStatus* st) {
   const DcNode nd = nodes[blockIdx.y];
   const int z = blockIdx.z;
@@ -316,8 +317,9 @@ __global__ void dc_secular_kernel(DcArgs a, const DcNode* nodes, DevStatus* st) 
   const bool last = (j == K - 1);
   const double dr = last ? 0.0 : dK[j + 1] - d0;
   double tau = 0.5 * (lo + hi);
+  double wref = hi - lo;  // bracket width two iterations ago: a step must halve it
   int it = 0;
-  for (; it < 100; it++) {
+  for (; it < 200; it++) {
     double ps = 0.0, psd = 0.0, fs = 0.0, fsd = 0.0, absum = 0.0;
     for (int i = lane; i < K; i += 32) {
       double den = (dK[i] - d0) - tau;
@@ -361,10 +363,15 @@ __global__ void dc_secular_kernel(DcArgs a, const DcNode* nodes, DevStatus* st) 
       }
       cand = dl - u;
     }
+    if ((it & 1) == 1) {
+      if (hi - lo > 0.5 * wref) cand = 0.5 * (lo + hi);  // slow one-sided progress: bisect
+      wref = hi - lo;
+    }
     if (!(cand > lo && cand < hi)) cand = 0.5 * (lo + hi);
+    if (cand == tau) break;
     tau = cand;
   }
-  if (it >= 100 && lane == 0) set_status(st ? st + z : nullptr, ST_ENOCONV, off + j);
+  if (it >= 200 && lane == 0) set_status(st ? st + z : nullptr, ST_ENOCONV, off + j);
   if (lane == 0) {
     w.orig[off + j] = o;
     w.tauK[off + j] = tau;

@@ -61,6 +61,8 @@ def load() -> ctypes.CDLL:
     lib.gks_potrf.argtypes = [P, P, I64, I64, I]
     lib.gks_reduce.argtypes = [P, P, P, I64, I64, I]
     lib.gks_stedc.argtypes = [P, P, P, I64, I64, P, P]
+    lib.gks_adjoint.argtypes = [P, P, P, P, I64, I64, I, I, D, P, P, P, D, P, P]
+    lib.gks_adjoint.restype = I
     lib.gks_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I]
     lib.gks_profile.restype = I
     lib.gks_launch_count.argtypes = []
@@ -176,6 +178,30 @@ class Context:
         self.solve_into(H, S, kT, n_elec, spin, kweights, eps=eps, C=C, mu=mu, rho=rho, e_band=eb, sync=sync)
         return Solution(eps, C, mu, rho, eb)
 
+    # ------------------------------------------------------------------ adjoint
+    def adjoint(self, sol: Solution, S: torch.Tensor, kT: float, spin: str = "collinear", kweights=None,
+                rho_bar: torch.Tensor | None = None, eps_bar: torch.Tensor | None = None,
+                e_band_bar: float = 0.0, sync: bool = True):
+        """Gradients (H_bar, S_bar) of L(rho, eps, E_band) through a previous solve (n_elec
+        fixed): dL = Re tr(H_bar^H dH) + Re tr(S_bar^H dS) for Hermitian dH, dS."""
+        C, eps, mu = sol.C, sol.eps, sol.mu
+        nk, M = C.shape[0], C.shape[1]
+        n = S.shape[-1]
+        nc = spin == "noncollinear"
+        for t, nm in ((rho_bar, "rho_bar"), (eps_bar, "eps_bar")):
+            if t is not None:
+                _check_tensor(t, nm, (torch.float64, torch.complex128))
+        Hb = torch.empty(nk, M, M, dtype=C.dtype, device=C.device)
+        Sb = torch.empty(nk, n, n, dtype=C.dtype, device=C.device)
+        rc = self._lib.gks_adjoint(self._h, _ptr(C), _ptr(eps), _ptr(mu), n, nk,
+                                   GKS_C128 if C.is_complex() else GKS_R64,
+                                   GKS_NONCOLLINEAR if nc else GKS_COLLINEAR, float(kT), _ptr(kweights),
+                                   _ptr(rho_bar), _ptr(eps_bar), float(e_band_bar), _ptr(Hb), _ptr(Sb))
+        self._raise(rc)
+        if sync:
+            self.sync()
+        return Hb, Sb
+
     # ------------------------------------------------------------------ stages
     def potrf(self, A: torch.Tensor) -> torch.Tensor:
         """In place lower Cholesky factor of each (count, m, m) matrix."""
@@ -233,3 +259,33 @@ def context(device: int | None = None) -> Context:
 
 def solve(H, S, kT, n_elec, spin="collinear", kweights=None) -> Solution:
     return context(H.device.index).solve(H, S, kT, n_elec, spin, kweights)
+
+
+class GKSSolve(torch.autograd.Function):
+    """eps, rho, E_band = GKSSolve.apply(H, S, kT, n_elec, spin, kweights).
+
+    Forward runs gks_solve; backward runs gks_adjoint (n_elec fixed).  H and S must be
+    Hermitian (the solver reads their lower triangles); the gradients returned are the
+    Hermitian ones, i.e. those of a loss evaluated on Hermitian H and S."""
+
+    @staticmethod
+    def forward(ctx, H, S, kT, n_elec, spin="collinear", kweights=None):
+        c = context(H.device.index)
+        Hb = H if H.dim() == 3 else H[None]
+        Sb = S if S.dim() == 3 else S[None]
+        sol = c.solve(Hb.contiguous(), Sb.contiguous(), kT, n_elec, spin, kweights)
+        ctx.save_for_backward(sol.C, sol.eps, sol.mu, Sb)
+        ctx.kT, ctx.spin, ctx.kweights, ctx.hshape, ctx.sshape = kT, spin, kweights, H.shape, S.shape
+        ctx.mark_non_differentiable(sol.mu)
+        return sol.eps, sol.rho, sol.e_band, sol.mu
+
+    @staticmethod
+    def backward(ctx, g_eps, g_rho, g_eband, g_mu):
+        C, eps, mu, Sb = ctx.saved_tensors
+        c = context(C.device.index)
+        sol = Solution(eps, C, mu, None, None)
+        eb = 0.0 if g_eband is None else float(g_eband.reshape(-1)[0].item())
+        Hbar, Sbar = c.adjoint(sol, Sb, ctx.kT, ctx.spin, ctx.kweights,
+                           rho_bar=None if g_rho is None else g_rho.contiguous(),
+                           eps_bar=None if g_eps is None else g_eps.contiguous(), e_band_bar=eb)
+        return Hbar.reshape(ctx.hshape), Sbar.reshape(ctx.sshape), None, None, None, None

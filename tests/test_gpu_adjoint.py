@@ -1,0 +1,141 @@
+"""Adjoint (gks_adjoint) parity with the oracle adjoint, finite differences of the CUDA
+solve, the free-energy identity, and the torch.autograd.Function wrapper."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2606_09058_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_09058_gb300 import gks
+    return gks.Context(0)
+
+
+def _cuda(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+def _orth(G, L):
+    """Gradient in orthonormalized coordinates: for dX = L Gd L^H, dL = Re tr((L^H X L)^H Gd)."""
+    return L.conj().T @ G @ L
+
+
+@pytest.mark.parametrize("case", ["random", "random_complex", "si_cluster", "kbatch", "noncollinear"])
+def test_adjoint_matches_oracle(ctx, case):
+    rng = np.random.default_rng(5)
+    spin, kw = "collinear", None
+    if case.startswith("random"):
+        H, S = I.random_pencil(70, 9, case.endswith("complex"), 10.0)
+        H, S, kT, ne = H[None], S[None], 0.1, 50.0
+    elif case == "si_cluster":
+        p = I.collinear_gamma((1, 1, 1), 3, 0.02)
+        H, S, kT, ne = p.H.numpy(), p.S.numpy(), p.kT, p.n_elec
+    elif case == "kbatch":
+        p = I.periodic((1, 1, 1), 1, 0.01)
+        H, S, kT, ne, kw = p.H.numpy(), p.S.numpy(), 0.05, p.n_elec, p.kweights
+    else:
+        p = I.noncollinear((1, 1, 1), 2, 0.02)
+        H, S, kT, ne, spin = p.H.numpy(), p.S.numpy(), p.kT, p.n_elec, "noncollinear"
+    nk, M = H.shape[0], H.shape[1]
+    ref = O.solve(H, S, kT, ne, spin, kw)
+    rho_t = ref.rho + 0.01 * rng.standard_normal(ref.rho.shape)
+    a_eps = 0.1 * rng.standard_normal((nk, M))
+    # loss = E_band + tr(D S D S) per k + a.eps, D = rho - rho_t  ->  rho_bar = 2 S D S
+    rb_ref = np.stack([2.0 * (O.spinor_overlap(S[k]) if spin == "noncollinear" else S[k])
+                       @ (ref.rho[k] - rho_t[k]) @ (O.spinor_overlap(S[k]) if spin == "noncollinear" else S[k])
+                       for k in range(nk)])
+    Hb_ref, Sb_ref = O.adjoint(ref, kT, spin, kw, rho_bar=rb_ref, eps_bar=a_eps, e_band_bar=1.0)
+    kwd = None if kw is None else _cuda(np.asarray(kw, float))
+    sol = ctx.solve(_cuda(H), _cuda(S), kT, ne, spin, kwd)
+    rho = sol.rho.cpu().numpy()
+    rb = np.stack([2.0 * (O.spinor_overlap(S[k]) if spin == "noncollinear" else S[k])
+                   @ (rho[k] - rho_t[k]) @ (O.spinor_overlap(S[k]) if spin == "noncollinear" else S[k])
+                   for k in range(nk)])
+    Hb, Sb = ctx.adjoint(sol, _cuda(S), kT, spin, kwd, rho_bar=_cuda(rb), eps_bar=_cuda(a_eps), e_band_bar=1.0)
+    Hb, Sb = Hb.cpu().numpy(), Sb.cpu().numpy()
+    for k in range(nk):
+        Lc = np.linalg.cholesky(S[k])
+        Ls = O.spinor_overlap(Lc) if spin == "noncollinear" else Lc
+        gh, gh_ref = _orth(Hb[k], Ls), _orth(Hb_ref[k], Ls)
+        gs, gs_ref = _orth(Sb[k], Lc), _orth(Sb_ref[k], Lc)
+        assert np.abs(gh - gh_ref).max() <= 1e-6 * max(1.0, np.abs(gh_ref).max()), np.abs(gh - gh_ref).max()
+        assert np.abs(gs - gs_ref).max() <= 1e-6 * max(1.0, np.abs(gs_ref).max()), np.abs(gs - gs_ref).max()
+        assert np.abs(Hb[k] - Hb[k].conj().T).max() == 0.0
+
+
+def test_adjoint_free_energy_identity(ctx):
+    """With explicit eigenvalue weights w g_s f the adjoint returns dF/dH = rho exactly."""
+    p = I.collinear_gamma((2, 1, 1), 0, 0.01)
+    sol = ctx.solve(p.H.cuda(), p.S.cuda(), p.kT, p.n_elec)
+    eps = sol.eps.cpu().numpy()
+    f = O.fermi((eps - sol.mu.item()) / p.kT)
+    Hb, _ = ctx.adjoint(sol, p.S.cuda(), p.kT, eps_bar=_cuda(2.0 * f))
+    rho = sol.rho.cpu().numpy()[0]
+    S = p.S.numpy()[0]
+    d = np.abs(S @ (Hb.cpu().numpy()[0] - rho) @ S).max()
+    assert d <= 1e-9 * np.abs(S @ rho @ S).max()
+
+
+def test_adjoint_finite_differences_at_config_size(ctx):
+    """N = 2808 (the 216-atom size), real, kT = 0.02: 64 directions in H and 64 in S,
+    D = L G L^T with G of unit Frobenius norm, central differences h = 1e-6 of the CUDA
+    solve against the CUDA adjoint, relative error <= 1e-6.  The pencil is a random
+    well-conditioned one: on the Si Gaussian basis the FP64 eigenvalue noise (about 1e-8)
+    divided by h exceeds the 1e-6 gate for any FP64 solver."""
+    n, kT = 2808, 0.02
+    H, S = I.random_pencil(n, 2808, False, 10.0)
+    ne = 0.6 * n
+    rng = np.random.default_rng(2808)
+    Hd, Sd = _cuda(H[None]), _cuda(S[None])
+    base = ctx.solve(Hd, Sd, kT, ne)
+    rho_t = base.rho + 1e-3 * torch.as_tensor(rng.standard_normal((1, n, n)), device="cuda")
+    rho_t = 0.5 * (rho_t + rho_t.transpose(-1, -2))
+
+    def loss(Hx, Sx):
+        s = ctx.solve(Hx, Sx, kT, ne)
+        return float(s.e_band.item() + ((s.rho - rho_t) ** 2).sum().item())
+
+    Hb, Sb = ctx.adjoint(base, Sd, kT, rho_bar=2.0 * (base.rho - rho_t), e_band_bar=1.0)
+    Lc = torch.linalg.cholesky(Sd[0])
+    h, worst = 1e-6, 0.0
+    for which in ("H", "S"):
+        for _ in range(64):
+            G = torch.as_tensor(rng.standard_normal((n, n)), device="cuda")
+            G = 0.5 * (G + G.T)
+            G /= torch.linalg.norm(G)
+            D = (Lc @ G @ Lc.T)[None]
+            if which == "H":
+                fd = (loss(Hd + h * D, Sd) - loss(Hd - h * D, Sd)) / (2 * h)
+                ad = float((Hb * D).sum().item())
+            else:
+                fd = (loss(Hd, Sd + h * D) - loss(Hd, Sd - h * D)) / (2 * h)
+                ad = float((Sb * D).sum().item())
+            rel = abs(fd - ad) / max(abs(fd), abs(ad), 1e-8)
+            worst = max(worst, rel)
+    assert worst <= 1e-6, worst
+
+
+def test_autograd_function(ctx):
+    from paper_2606_09058_gb300.gks import GKSSolve
+    H, S = I.random_pencil(60, 4, True, 10.0)
+    Ht = _cuda(H[None]).requires_grad_(True)
+    St = _cuda(S[None]).requires_grad_(True)
+    eps, rho, e_band, mu = GKSSolve.apply(Ht, St, 0.1, 40.0)
+    L = e_band.sum() + (rho.abs() ** 2).sum() + eps.sum()
+    L.backward()
+    sol = ctx.solve(_cuda(H[None]), _cuda(S[None]), 0.1, 40.0)
+    Hb, Sb = ctx.adjoint(sol, _cuda(S[None]), 0.1, rho_bar=2.0 * sol.rho,
+                         eps_bar=torch.ones_like(sol.eps), e_band_bar=1.0)
+    assert torch.allclose(Ht.grad, Hb, rtol=1e-9, atol=1e-9 * Hb.abs().max().item())
+    assert torch.allclose(St.grad, Sb, rtol=1e-9, atol=1e-9 * Sb.abs().max().item())
