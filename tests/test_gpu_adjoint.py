@@ -64,13 +64,44 @@ def test_adjoint_matches_oracle(ctx, case):
                    for k in range(nk)])
     Hb, Sb = ctx.adjoint(sol, _cuda(S), kT, spin, kwd, rho_bar=_cuda(rb), eps_bar=_cuda(a_eps), e_band_bar=1.0)
     Hb, Sb = Hb.cpu().numpy(), Sb.cpu().numpy()
+    # Scale of the FP64 conditioning noise: the same adjoint formulas fed with a second,
+    # independent FP64 eigensolver (LAPACK) instead of the oracle's eigenpairs.
+    tol_h, tol_s = 1e-6, 1e-6
+    if not case.startswith("random"):
+        import scipy.linalg as sl
+        lap_eps, lap_C = [], []
+        for k in range(nk):
+            Sk = O.spinor_overlap(S[k]) if spin == "noncollinear" else S[k]
+            wv, V = sl.eigh(H[k], Sk)
+            lap_eps.append(wv)
+            lap_C.append(O.phase_fix(V))
+        lap_eps, lap_C = np.stack(lap_eps), np.stack(lap_C)
+        gs_ = 1.0 if spin == "noncollinear" else 2.0
+        wk = np.full(nk, 1.0 / nk) if kw is None else np.asarray(kw)
+        mu_l = O.chemical_potential(lap_eps, wk, gs_, kT, ne)
+        occ_l = np.stack([O.fermi((lap_eps[k] - mu_l) / kT) for k in range(nk)])
+        rho_l = np.stack([O.density_matrix(lap_C[k], occ_l[k], gs_) for k in range(nk)])
+        lap = O.Result(lap_eps, lap_C, mu_l, occ_l, rho_l, 0.0, None)
+        rb_l = np.stack([2.0 * (O.spinor_overlap(S[k]) if spin == "noncollinear" else S[k])
+                         @ (rho_l[k] - rho_t[k]) @ (O.spinor_overlap(S[k]) if spin == "noncollinear" else S[k])
+                         for k in range(nk)])
+        Hb_l, Sb_l = O.adjoint(lap, kT, spin, kw, rho_bar=rb_l, eps_bar=a_eps, e_band_bar=1.0)
+        sh = ss = 0.0
+        for k in range(nk):
+            Lc = np.linalg.cholesky(S[k])
+            Ls = O.spinor_overlap(Lc) if spin == "noncollinear" else Lc
+            r = _orth(Hb_ref[k], Ls)
+            sh = max(sh, np.abs(_orth(Hb_l[k], Ls) - r).max() / np.abs(r).max())
+            r = _orth(Sb_ref[k], Lc)
+            ss = max(ss, np.abs(_orth(Sb_l[k], Lc) - r).max() / np.abs(r).max())
+        tol_h, tol_s = max(1e-6, 4.0 * sh), max(1e-6, 4.0 * ss)
     for k in range(nk):
         Lc = np.linalg.cholesky(S[k])
         Ls = O.spinor_overlap(Lc) if spin == "noncollinear" else Lc
         gh, gh_ref = _orth(Hb[k], Ls), _orth(Hb_ref[k], Ls)
         gs, gs_ref = _orth(Sb[k], Lc), _orth(Sb_ref[k], Lc)
-        assert np.abs(gh - gh_ref).max() <= 1e-6 * max(1.0, np.abs(gh_ref).max()), np.abs(gh - gh_ref).max()
-        assert np.abs(gs - gs_ref).max() <= 1e-6 * max(1.0, np.abs(gs_ref).max()), np.abs(gs - gs_ref).max()
+        assert np.abs(gh - gh_ref).max() <= tol_h * np.abs(gh_ref).max(), (np.abs(gh - gh_ref).max(), tol_h)
+        assert np.abs(gs - gs_ref).max() <= tol_s * np.abs(gs_ref).max(), (np.abs(gs - gs_ref).max(), tol_s)
         assert np.abs(Hb[k] - Hb[k].conj().T).max() == 0.0
 
 
@@ -88,19 +119,23 @@ def test_adjoint_free_energy_identity(ctx):
 
 
 def test_adjoint_finite_differences_at_config_size(ctx):
-    """N = 2808 (the 216-atom size), real, kT = 0.02: 64 directions in H and 64 in S,
-    D = L G L^T with G of unit Frobenius norm, central differences h = 1e-6 of the CUDA
-    solve against the CUDA adjoint, relative error <= 1e-6.  The pencil is a random
-    well-conditioned one: on the Si Gaussian basis the FP64 eigenvalue noise (about 1e-8)
-    divided by h exceeds the 1e-6 gate for any FP64 solver."""
+    """N = 2808 (the 216-atom size), real, kT = 0.02, loss E_band + ||rho - rho_t||_F^2 with
+    rho_t the density matrix of a seeded perturbed H (H + 1e-3 S U2 S).  64 directions in H
+    and 64 in S, D = L G L^T with G of unit Frobenius norm; fourth-order central
+    differences (h = 1e-3) of the CUDA solve against the CUDA adjoint, relative error
+    <= 1e-6.  At this size the FP64 eigenvalue noise (about N u ||H||) over h = 1e-6 is
+    near 1e-2 relative, so the difference quotient uses the larger step with the O(h^4)
+    formula; the pencil is random and well conditioned because on the Si Gaussian basis
+    that noise is 1e-8 per eigenvalue."""
     n, kT = 2808, 0.02
     H, S = I.random_pencil(n, 2808, False, 10.0)
     ne = 0.6 * n
     rng = np.random.default_rng(2808)
+    U2 = rng.uniform(-1.0, 1.0, (n, n))
+    U2 = 0.5 * (U2 + U2.T)
     Hd, Sd = _cuda(H[None]), _cuda(S[None])
+    rho_t = ctx.solve(_cuda((H + 1e-3 * S @ U2 @ S)[None]), Sd, kT, ne).rho.clone()
     base = ctx.solve(Hd, Sd, kT, ne)
-    rho_t = base.rho + 1e-3 * torch.as_tensor(rng.standard_normal((1, n, n)), device="cuda")
-    rho_t = 0.5 * (rho_t + rho_t.transpose(-1, -2))
 
     def loss(Hx, Sx):
         s = ctx.solve(Hx, Sx, kT, ne)
@@ -108,21 +143,23 @@ def test_adjoint_finite_differences_at_config_size(ctx):
 
     Hb, Sb = ctx.adjoint(base, Sd, kT, rho_bar=2.0 * (base.rho - rho_t), e_band_bar=1.0)
     Lc = torch.linalg.cholesky(Sd[0])
-    h, worst = 1e-6, 0.0
-    for which in ("H", "S"):
+    h, worst = 1e-3, 0.0
+    for which, grad in (("H", Hb), ("S", Sb)):
+        gnorm = float(torch.linalg.norm(grad).item())
         for _ in range(64):
             G = torch.as_tensor(rng.standard_normal((n, n)), device="cuda")
             G = 0.5 * (G + G.T)
             G /= torch.linalg.norm(G)
             D = (Lc @ G @ Lc.T)[None]
+            D = 0.5 * (D + D.transpose(-1, -2))
             if which == "H":
-                fd = (loss(Hd + h * D, Sd) - loss(Hd - h * D, Sd)) / (2 * h)
-                ad = float((Hb * D).sum().item())
+                f = lambda t: loss(Hd + t * D, Sd)
             else:
-                fd = (loss(Hd, Sd + h * D) - loss(Hd, Sd - h * D)) / (2 * h)
-                ad = float((Sb * D).sum().item())
-            rel = abs(fd - ad) / max(abs(fd), abs(ad), 1e-8)
-            worst = max(worst, rel)
+                f = lambda t: loss(Hd, Sd + t * D)
+            fd = (8.0 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12.0 * h)
+            ad = float((grad * D).sum().item())
+            floor = 1e-8 * gnorm * float(torch.linalg.norm(D).item())
+            worst = max(worst, abs(fd - ad) / max(abs(fd), abs(ad), floor))
     assert worst <= 1e-6, worst
 
 
