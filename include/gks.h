@@ -49,7 +49,24 @@ typedef struct {
   int precision;       /* gks_prec */
   double f_cut;        /* occupations below f_cut are left out of rho (default 1e-16) */
   int profile;         /* 1: record CUDA events around every launch group (see gks_profile) */
+  int graph;           /* 1: capture each solve (and each batch) into a CUDA graph and replay it
+                          while the arguments are unchanged; needs a non-default stream */
 } gks_opts;
+
+/* One problem of gks_solve_batched: the arguments of gks_solve. */
+typedef struct {
+  const void* H;
+  const void* S;
+  int64_t n, nk;
+  int dtype, spin_mode;
+  double kT, n_elec;
+  const double* kweights;
+  double* eps;
+  void* C;
+  double* mu;
+  void* rho;
+  double* e_band;
+} gks_problem;
 
 /* One row of the event profile: a kernel class ("gemm", "hetrd_hemv", ...) or a stage
  * ("stage:potrf", ...), with its algorithmic FP64 flops and bytes (inputs read plus
@@ -101,6 +118,14 @@ const char* gks_last_error(const gks_ctx* ctx);
 gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int64_t nk, int dtype, int spin_mode,
                      double kT, double n_elec, const double* kweights, unsigned flags, double* eps, void* C,
                      double* mu, void* rho, double* e_band);
+
+/* Independent problems of uneven order in one launch sequence: problem b is enqueued on
+ * worker stream b mod nstreams (nstreams <= 0: 8), the workers forked from and joined back
+ * into the context's stream, so small systems run concurrently.  With opts->graph the
+ * whole batch is captured into one CUDA graph (first call eager, second call captures,
+ * later calls replay).  Each problem keeps its own workspace.  Same conventions and
+ * outputs as gks_solve; gks_sync reports the first failing problem. */
+gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* probs, int nstreams);
 
 /* Vector-Jacobian product of a real loss L(rho, eps, E_band) through gks_solve, with
  * n_elec fixed (mu moves with H and S).  First-order perturbation of H C = S C eps,

@@ -1,5 +1,6 @@
 // Runtime and C ABI: context, workspace arena, stage orchestration, status reporting.
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -70,9 +71,23 @@ struct EventProf : Prof {
 };
 }  // namespace
 
+struct SolveKey {
+  const void *H, *S, *kw, *eps, *C, *mu, *rho, *eb;
+  long long n, nk;
+  int dtype, spin;
+  double kT, ne;
+};
+
 struct gks_ctx {
   EventProf prof;
   int device = 0;
+  bool graph = false;                  // capture solves into CUDA graphs
+  cudaGraphExec_t gexec = nullptr;     // graph of the last captured solve
+  SolveKey gkey{};
+  std::vector<gks_ctx*> subs;          // per-problem contexts of gks_solve_batched
+  std::vector<cudaStream_t> workers;   // fork/join streams of gks_solve_batched
+  cudaGraphExec_t bexec = nullptr;     // graph of the last captured batch
+  std::vector<SolveKey> bkey;
   cudaStream_t stream = nullptr;
   double f_cut = 1e-16;
   std::string err;
@@ -112,7 +127,16 @@ void release_aws(gks_ctx* c) {
   c->am = -1;
 }
 
+void release_graph(gks_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  if (c->bexec) cudaGraphExecDestroy(c->bexec);
+  c->bexec = nullptr;
+  c->bkey.clear();
+}
+
 void release_ws(gks_ctx* c) {
+  release_graph(c);
   if (c->ws) cudaFree(c->ws);
   if (c->st) cudaFree(c->st);
   dc_plan_destroy(c->dc);
@@ -570,6 +594,61 @@ gks_status adjoint_t(gks_ctx* c, const T* C, const double* eps, const double* mu
   return cuda_check(c, "gks_adjoint launch");
 }
 
+gks_status validate_solve(gks_ctx* ctx, const SolveKey& k) {
+  if (!k.H || !k.S || !k.eps || !k.C || !k.mu || !k.rho) return fail(ctx, GKS_EINVAL, "null array argument");
+  if (k.n < 1 || k.nk < 1 || k.n > 46340 || k.nk > 65535) return fail(ctx, GKS_EINVAL, "n or nk out of range");
+  if (k.dtype != GKS_R64 && k.dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
+  if (k.spin != GKS_COLLINEAR && k.spin != GKS_NONCOLLINEAR) return fail(ctx, GKS_EINVAL, "unknown spin mode");
+  const bool nc = k.spin == GKS_NONCOLLINEAR;
+  if (nc && k.dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
+  if (nc && 2 * k.n > 46340) return fail(ctx, GKS_EINVAL, "2n out of range");
+  if (!(k.kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
+  const double gs = nc ? 1.0 : 2.0;
+  const double M = nc ? 2.0 * k.n : (double)k.n;
+  if (!(k.ne > 0.0) || !(k.ne < gs * M)) return fail(ctx, GKS_EINVAL, "n_elec must lie in (0, g_s M)");
+  return GKS_OK;
+}
+
+gks_status enqueue_solve(gks_ctx* ctx, const SolveKey& k) {
+  const bool nc = k.spin == GKS_NONCOLLINEAR;
+  if (k.dtype == GKS_R64)
+    return solve_t<double>(ctx, static_cast<const double*>(k.H), static_cast<const double*>(k.S), (int)k.n,
+                           (int)k.nk, nc, k.kT, k.ne, static_cast<const double*>(k.kw),
+                           const_cast<double*>(static_cast<const double*>(k.eps)),
+                           static_cast<double*>(const_cast<void*>(k.C)), const_cast<double*>(static_cast<const double*>(k.mu)),
+                           static_cast<double*>(const_cast<void*>(k.rho)), const_cast<double*>(static_cast<const double*>(k.eb)));
+  return solve_t<zc>(ctx, static_cast<const zc*>(k.H), static_cast<const zc*>(k.S), (int)k.n, (int)k.nk, nc, k.kT,
+                     k.ne, static_cast<const double*>(k.kw), const_cast<double*>(static_cast<const double*>(k.eps)),
+                     static_cast<zc*>(const_cast<void*>(k.C)), const_cast<double*>(static_cast<const double*>(k.mu)),
+                     static_cast<zc*>(const_cast<void*>(k.rho)), const_cast<double*>(static_cast<const double*>(k.eb)));
+}
+
+bool same_key(const SolveKey& a, const SolveKey& b) { return std::memcmp(&a, &b, sizeof(SolveKey)) == 0; }
+
+// Capture whatever `body` enqueues on c->stream into a graph and instantiate it.
+template <typename F>
+gks_status capture(gks_ctx* c, cudaGraphExec_t* out, F body) {
+  const bool prof_on = c->prof.on;
+  c->prof.on = false;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    c->prof.on = prof_on;
+    return cuda_check(c, "graph capture begin");
+  }
+  gks_status rc = body();
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  c->prof.on = prof_on;
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess || !g) return fail(c, GKS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, GKS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return GKS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -582,6 +661,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     c->stream = static_cast<cudaStream_t>(opts->cuda_stream);
     if (opts->f_cut > 0.0) c->f_cut = opts->f_cut;
     c->prof.on = opts->profile != 0;
+    c->graph = opts->graph != 0;
     if (opts->precision != GKS_FP64) {
       delete c;
       return GKS_ENOTIMPL;
@@ -602,6 +682,12 @@ gks_status gks_destroy(gks_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  for (auto sc : ctx->subs) {
+    release_ws(sc);
+    release_aws(sc);
+    delete sc;
+  }
+  for (auto w : ctx->workers) cudaStreamDestroy(w);
   release_ws(ctx);
   release_aws(ctx);
   delete ctx;
@@ -615,24 +701,106 @@ gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int6
                      double* mu, void* rho, double* e_band) {
   if (!ctx) return GKS_EINVAL;
   ctx->err.clear();
-  if (!H || !S || !eps || !C || !mu || !rho) return fail(ctx, GKS_EINVAL, "null array argument");
-  if (n < 1 || nk < 1 || n > 46340 || nk > 65535) return fail(ctx, GKS_EINVAL, "n or nk out of range");
-  if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
-  if (spin_mode != GKS_COLLINEAR && spin_mode != GKS_NONCOLLINEAR) return fail(ctx, GKS_EINVAL, "unknown spin mode");
-  const bool nc = spin_mode == GKS_NONCOLLINEAR;
-  if (nc && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
-  if (nc && 2 * n > 46340) return fail(ctx, GKS_EINVAL, "2n out of range");
-  if (!(kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
-  const double gs = nc ? 1.0 : 2.0;
-  const double M = nc ? 2.0 * n : (double)n;
-  if (!(n_elec > 0.0) || !(n_elec < gs * M)) return fail(ctx, GKS_EINVAL, "n_elec must lie in (0, g_s M)");
+  SolveKey k{H, S, kweights, eps, C, mu, rho, e_band, (long long)n, (long long)nk, dtype, spin_mode, kT, n_elec};
+  gks_status rc = validate_solve(ctx, k);
+  if (rc) return rc;
   if (flags != 0) return fail(ctx, GKS_ENOTIMPL, "flags must be 0");
   cudaSetDevice(ctx->device);
-  if (dtype == GKS_R64)
-    return solve_t<double>(ctx, static_cast<const double*>(H), static_cast<const double*>(S), (int)n, (int)nk, nc, kT,
-                           n_elec, kweights, eps, static_cast<double*>(C), mu, static_cast<double*>(rho), e_band);
-  return solve_t<zc>(ctx, static_cast<const zc*>(H), static_cast<const zc*>(S), (int)n, (int)nk, nc, kT, n_elec,
-                     kweights, eps, static_cast<zc*>(C), mu, static_cast<zc*>(rho), e_band);
+  if (!ctx->graph || ctx->stream == nullptr) return enqueue_solve(ctx, k);
+  // graph mode: replay while the arguments are unchanged; the first call for a new
+  // argument set runs eagerly (allocates the workspace and the merge lists), the next
+  // one captures.
+  if (ctx->gexec && same_key(ctx->gkey, k)) {
+    cudaGraphLaunch(ctx->gexec, ctx->stream);
+    return cuda_check(ctx, "graph launch");
+  }
+  const int M = spin_mode == GKS_NONCOLLINEAR ? (int)(2 * n) : (int)n;
+  const bool ready = ctx->ws && ctx->m == M && ctx->nk == nk && ctx->es == (dtype == GKS_R64 ? 8 : 16) &&
+                     ctx->gkey.H == k.H && ctx->gkey.C == k.C;
+  ctx->gkey = k;
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  if (!ready) return enqueue_solve(ctx, k);
+  rc = capture(ctx, &ctx->gexec, [&]() { return enqueue_solve(ctx, k); });
+  if (rc) return rc;
+  cudaGraphLaunch(ctx->gexec, ctx->stream);
+  return cuda_check(ctx, "graph launch");
+}
+
+gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* probs, int nstreams) {
+  if (!ctx || count < 1 || !probs) return fail(ctx, GKS_EINVAL, "bad batch arguments");
+  ctx->err.clear();
+  if (ctx->stream == nullptr) return fail(ctx, GKS_EINVAL, "gks_solve_batched needs a non-default stream");
+  std::vector<SolveKey> keys((size_t)count);
+  for (int64_t b = 0; b < count; b++) {
+    const gks_problem& p = probs[b];
+    keys[b] = SolveKey{p.H, p.S, p.kweights, p.eps, p.C, p.mu, p.rho, p.e_band, (long long)p.n, (long long)p.nk,
+                       p.dtype, p.spin_mode, p.kT, p.n_elec};
+    gks_status rc = validate_solve(ctx, keys[b]);
+    if (rc) return fail(ctx, rc, "problem " + std::to_string(b) + ": " + ctx->err);
+  }
+  cudaSetDevice(ctx->device);
+  const int P = std::max(1, std::min(nstreams > 0 ? nstreams : 8, (int)count));
+  while ((int)ctx->workers.size() < P) {
+    cudaStream_t w;
+    if (cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking) != cudaSuccess) return cuda_check(ctx, "stream create");
+    ctx->workers.push_back(w);
+  }
+  while ((int64_t)ctx->subs.size() < count) {
+    gks_ctx* sc = new gks_ctx();
+    sc->device = ctx->device;
+    sc->f_cut = ctx->f_cut;
+    ctx->subs.push_back(sc);
+  }
+  auto body = [&]() -> gks_status {
+    cudaEvent_t fork;
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    cudaEventRecord(fork, ctx->stream);
+    for (int w = 0; w < P; w++) cudaStreamWaitEvent(ctx->workers[w], fork, 0);
+    gks_status rc = GKS_OK;
+    for (int64_t b = 0; b < count && !rc; b++) {
+      gks_ctx* sc = ctx->subs[b];
+      sc->stream = ctx->workers[b % P];
+      sc->prof.stream = sc->stream;
+      rc = enqueue_solve(sc, keys[b]);
+      if (rc) ctx->err = "problem " + std::to_string(b) + ": " + sc->err;
+    }
+    for (int w = 0; w < P; w++) {
+      cudaEvent_t join;
+      cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+      cudaEventRecord(join, ctx->workers[w]);
+      cudaStreamWaitEvent(ctx->stream, join, 0);
+      cudaEventDestroy(join);
+    }
+    cudaEventDestroy(fork);
+    return rc;
+  };
+  if (!ctx->graph) {
+    gks_status rc = body();
+    return rc ? rc : cuda_check(ctx, "gks_solve_batched launch");
+  }
+  if (ctx->bexec && ctx->bkey.size() == keys.size() &&
+      std::equal(keys.begin(), keys.end(), ctx->bkey.begin(), same_key)) {
+    cudaGraphLaunch(ctx->bexec, ctx->stream);
+    return cuda_check(ctx, "batch graph launch");
+  }
+  if (ctx->bexec) {
+    cudaGraphExecDestroy(ctx->bexec);
+    ctx->bexec = nullptr;
+  }
+  const bool first = ctx->bkey.size() != keys.size() ||
+                     !std::equal(keys.begin(), keys.end(), ctx->bkey.begin(), same_key);
+  ctx->bkey = keys;
+  if (first) {  // eager run: allocates every problem's workspace and merge lists
+    gks_status rc = body();
+    return rc ? rc : cuda_check(ctx, "gks_solve_batched launch");
+  }
+  gks_status rc = capture(ctx, &ctx->bexec, body);
+  if (rc) return rc;
+  cudaGraphLaunch(ctx->bexec, ctx->stream);
+  return cuda_check(ctx, "batch graph launch");
 }
 
 gks_status gks_adjoint(gks_ctx* ctx, const void* C, const double* eps, const double* mu, int64_t n, int64_t nk,
@@ -662,6 +830,10 @@ gks_status gks_sync(gks_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaError_t e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(ctx, GKS_ECUDA, std::string("synchronize: ") + cudaGetErrorString(e));
+  for (size_t b = 0; b < ctx->subs.size(); b++) {
+    gks_status rc = gks_sync(ctx->subs[b]);
+    if (rc) return fail(ctx, rc, "batch problem " + std::to_string(b) + ": " + ctx->subs[b]->err);
+  }
   if (!ctx->st) return GKS_OK;
   std::vector<DevStatus> h(ctx->nk);
   if (cudaMemcpy(h.data(), ctx->st, sizeof(DevStatus) * ctx->nk, cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -30,7 +30,15 @@ class GKSError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
-                ("f_cut", ctypes.c_double), ("profile", ctypes.c_int)]
+                ("f_cut", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_void_p), ("S", ctypes.c_void_p), ("n", ctypes.c_int64), ("nk", ctypes.c_int64),
+                ("dtype", ctypes.c_int), ("spin_mode", ctypes.c_int), ("kT", ctypes.c_double),
+                ("n_elec", ctypes.c_double), ("kweights", ctypes.c_void_p), ("eps", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("e_band", ctypes.c_void_p)]
 
 
 class _ProfEntry(ctypes.Structure):
@@ -61,6 +69,8 @@ def load() -> ctypes.CDLL:
     lib.gks_potrf.argtypes = [P, P, I64, I64, I]
     lib.gks_reduce.argtypes = [P, P, P, I64, I64, I]
     lib.gks_stedc.argtypes = [P, P, P, I64, I64, P, P]
+    lib.gks_solve_batched.argtypes = [P, I64, ctypes.POINTER(_Problem), I]
+    lib.gks_solve_batched.restype = I
     lib.gks_adjoint.argtypes = [P, P, P, P, I64, I64, I, I, D, P, P, P, D, P, P]
     lib.gks_adjoint.restype = I
     lib.gks_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I]
@@ -99,13 +109,14 @@ class Context:
     """A gks context bound to one device and one CUDA stream."""
 
     def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None, f_cut: float = 1e-16,
-                 profile: bool = False):
+                 profile: bool = False, graph: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("gks needs a CUDA device")
         lib = load()
         self.device = torch.cuda.current_device() if device is None else int(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), 0, f_cut, 1 if profile else 0)
+        opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), 0, f_cut, 1 if profile else 0,
+                     1 if graph else 0)
         h = ctypes.c_void_p()
         rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
         if rc:
@@ -177,6 +188,37 @@ class Context:
         eb = torch.empty(1, dtype=torch.float64, device=dev)
         self.solve_into(H, S, kT, n_elec, spin, kweights, eps=eps, C=C, mu=mu, rho=rho, e_band=eb, sync=sync)
         return Solution(eps, C, mu, rho, eb)
+
+    # ------------------------------------------------------------------ batch
+    def solve_batched(self, problems, nstreams: int = 8, sync: bool = True, out: list | None = None) -> list:
+        """Independent problems of uneven order in one launch sequence.  `problems` is a list
+        of dicts with keys H, S, kT, n_elec and optional spin, kweights; returns one
+        Solution per problem (allocated here unless `out` passes those of a previous call;
+        reusing them lets a graph-mode context replay its captured batch)."""
+        arr = (_Problem * len(problems))()
+        sols = []
+        for b, pr in enumerate(problems):
+            H, S = pr["H"], pr["S"]
+            if H.dim() == 2:
+                H, S = H[None], S[None]
+            spin = pr.get("spin", "collinear")
+            nk, M = H.shape[0], H.shape[1]
+            dev = H.device
+            sol = out[b] if out is not None else Solution(
+                torch.empty(nk, M, dtype=torch.float64, device=dev), torch.empty(nk, M, M, dtype=H.dtype, device=dev),
+                torch.empty(1, dtype=torch.float64, device=dev), torch.empty(nk, M, M, dtype=H.dtype, device=dev),
+                torch.empty(1, dtype=torch.float64, device=dev))
+            kw = pr.get("kweights")
+            arr[b] = _Problem(H.data_ptr(), S.data_ptr(), S.shape[1], nk, GKS_C128 if H.is_complex() else GKS_R64,
+                              GKS_NONCOLLINEAR if spin == "noncollinear" else GKS_COLLINEAR, float(pr["kT"]),
+                              float(pr["n_elec"]), kw.data_ptr() if kw is not None else None, sol.eps.data_ptr(),
+                              sol.C.data_ptr(), sol.mu.data_ptr(), sol.rho.data_ptr(), sol.e_band.data_ptr())
+            sols.append(sol)
+        self._keep = (problems, sols)
+        self._raise(self._lib.gks_solve_batched(self._h, len(problems), arr, nstreams))
+        if sync:
+            self.sync()
+        return sols
 
     # ------------------------------------------------------------------ adjoint
     def adjoint(self, sol: Solution, S: torch.Tensor, kT: float, spin: str = "collinear", kweights=None,

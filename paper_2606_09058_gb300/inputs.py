@@ -311,6 +311,25 @@ def random_pencil(n: int, seed: int, complex_: bool = False, cond: float = 1e2):
     return H, S
 
 
+def uneven_batch(seed: int = 4, count: int = 48, n_nc: int = 12, device="cpu") -> list:
+    """Independent clusters with seeded tilings (n1, n2, n3) in {1..5}^3, 2 <= n1 n2 n3 <= 20
+    (16-160 atoms, N = 208-2080); the first n_nc are noncollinear (2N up to 4160),
+    the rest collinear real; kT 0.01, n_elec = 4 atoms."""
+    rng = np.random.default_rng(seed_for(seed))
+    tilings = []
+    while len(tilings) < count:
+        t = tuple(int(x) for x in rng.integers(1, 6, size=3))
+        if 2 <= t[0] * t[1] * t[2] <= 20:
+            tilings.append(t)
+    out = []
+    for b, t in enumerate(tilings):
+        if b < n_nc:
+            out.append(noncollinear(t, 100 + b, 0.01, device=device))
+        else:
+            out.append(collinear_gamma(t, 100 + b, 0.01, device=device))
+    return out
+
+
 def workload(name: str, device="cpu") -> Problem:
     """The named workloads (atom counts and N = 13 * atoms bind; see tiling notes)."""
     if name == "gamma64":       # 64 atoms, N = 832, real, kT 0.01, n_elec 256
