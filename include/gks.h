@@ -51,6 +51,10 @@ typedef struct {
   int profile;         /* 1: record CUDA events around every launch group (see gks_profile) */
   int graph;           /* 1: capture each solve (and each batch) into a CUDA graph and replay it
                           while the arguments are unchanged; needs a non-default stream */
+  int gemm;            /* FP64 products: 0 = large ones as exact split-bf16 tensor-core products
+                          with FP64 accumulation, small ones on the FP64 pipe (default);
+                          1 = FP64 pipe only; 2 = split products for every product */
+  int slices;          /* 6-bit digits per operand in split products (4..12, 0 = 9) */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */
@@ -156,6 +160,14 @@ int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max);
 
 /* Number of kernel launches this library has issued in the calling process. */
 long long gks_launch_count(void);
+
+/* C = alpha op(A) op(B) + beta C for one product (row-major, op 0 = N, 1 = T, 2 = conjugate
+ * transpose; op(A) is M x K, op(B) K x N).  mode 1: the FP64 pipe; mode 2: exact split-
+ * bf16 tensor-core products with FP64 accumulation (the path large products of gks_solve
+ * take).  Exposed to check the product kernels on their own. */
+gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha,
+                    const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
+                    int mode);
 
 /* Stage entry points (same conventions; `count` independent matrices of order m,
  * stride m*m elements).  Used to check each stage on its own. */

@@ -27,7 +27,7 @@ struct Arena {
 namespace {
 const char* kClassNames[PC_NCLASS] = {"gemm", "potf2", "trsm_block", "hegst_diag", "hetrd_hemv", "hetrd_rank2",
                                       "hetrd_vec", "dc_leaf", "dc_secular", "dc_gemm", "backtr_aux",
-                                      "occupations", "misc"};
+                                      "occupations", "misc", "split_gemm"};
 const char* kStageNames[PS_NSTAGE] = {"stage:copy", "stage:potrf", "stage:hegst", "stage:hetrd", "stage:stedc",
                                       "stage:backtransform", "stage:unreduce", "stage:occupations", "stage:rho",
                                       "stage:adjoint"};
@@ -82,6 +82,10 @@ struct gks_ctx {
   EventProf prof;
   int device = 0;
   bool graph = false;                  // capture solves into CUDA graphs
+  int gemm_mode = 0;                   // 0 auto, 1 DFMA only, 2 split products always
+  int slices = 9;                      // 6-bit digits per operand in split products
+  void* oz = nullptr;                  // digit workspace of the split-product GEMM
+  size_t oz_bytes = 0;
   cudaGraphExec_t gexec = nullptr;     // graph of the last captured solve
   SolveKey gkey{};
   std::vector<gks_ctx*> subs;          // per-problem contexts of gks_solve_batched
@@ -133,6 +137,12 @@ void release_graph(gks_ctx* c) {
   if (c->bexec) cudaGraphExecDestroy(c->bexec);
   c->bexec = nullptr;
   c->bkey.clear();
+}
+
+void release_oz(gks_ctx* c) {
+  if (c->oz) cudaFree(c->oz);
+  c->oz = nullptr;
+  c->oz_bytes = 0;
 }
 
 void release_ws(gks_ctx* c) {
@@ -276,6 +286,37 @@ struct StageRec {
 
 double cmul(int es) { return es == 16 ? 8.0 : 2.0; }
 
+// GEMM dispatch: large products go through exact split-bf16 products with FP64
+// accumulation (ozaki.cu), one batch item at a time; small ones stay on the DFMA kernel.
+template <typename T>
+void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA,
+         const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC, int lower = 0) {
+  if (M <= 0 || N <= 0) return;
+  const int es = sizeof(T);
+  const double fl = gemm_flops(es, M, N, K, lower, count);
+  const bool split = c->gemm_mode == 2 || (c->gemm_mode == 0 && fl >= 5e8 * count && M >= 32 && N >= 32 && K >= 16);
+  if (!split) {
+    gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
+    return;
+  }
+  const size_t need = ozaki_workspace_bytes(M, N, K, es == 16, c->slices);
+  if (need > c->oz_bytes) {
+    cudaStreamSynchronize(c->stream);
+    release_oz(c);
+    if (cudaMalloc(&c->oz, need) != cudaSuccess) {
+      cudaGetLastError();
+      c->oz = nullptr;
+      gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
+      return;
+    }
+    c->oz_bytes = need;
+  }
+  Rec r(c, PC_OZAKI, fl, gemm_bytes(es, M, N, K, lower, count, beta != 0.0));
+  for (int z = 0; z < count; z++)
+    ozaki_gemm<T>(opA, opB, M, N, K, alpha, A + z * sA, lda, B + z * sB, ldb, beta, C + z * sC, ldc, lower, c->slices,
+                  c->oz, c->stream);
+}
+
 // Blocked right-looking Cholesky of L (in place, lower): diagonal block, panel solve
 // L21 = A21 L11^-H by substitution, trailing Hermitian rank-kb update.
 template <typename T>
@@ -296,7 +337,7 @@ void potrf_run(gks_ctx* c, T* L, int M, int nk) {
       Rec r(c, PC_TRSM, cmul(es) * 0.5 * kb * kb * rows * nk, (2.0 * rows * kb + 0.5 * kb * kb) * es * nk);
       trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, L21, M, c->sMM, kb, rows, nk, s);
     }
-    gmp<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, L21, M, c->sMM, 1.0, L21 + kb, M, c->sMM, 1);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, L21, M, c->sMM, 1.0, L21 + kb, M, c->sMM, 1);
   }
 }
 
@@ -327,8 +368,8 @@ void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
       trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, A21, M, c->sMM, kb, rows, nk, s);
     }
     gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
-    gmp<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, A21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
-    gmp<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, M, c->sMM, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, A21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, M, c->sMM, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
     gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
   }
   for (int r0 = NB; r0 < M; r0 += NB) {
@@ -340,7 +381,7 @@ void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
     }
     const int below = M - r0 - rb;
     if (below > 0)
-      gmp<T>(c, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM, 1.0,
+      gmx<T>(c, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM, 1.0,
              A + (size_t)(r0 + rb) * M, M, c->sMM);
   }
 }
@@ -395,9 +436,9 @@ void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
       Rec r(c, PC_BACKTR_AUX);
       larft<T>(G, NB, c->sG, tb, NB, nbb, Tm, NB, c->sT, nk, s);
     }
-    gmp<T>(c, nk, OP_C, OP_N, nbb, M, j1, 1.0, V, NB, c->sV, X, M, c->sMM, 0.0, Y, M, c->sY);
+    gmx<T>(c, nk, OP_C, OP_N, nbb, M, j1, 1.0, V, NB, c->sV, X, M, c->sMM, 0.0, Y, M, c->sY);
     gmp<T>(c, nk, OP_N, OP_N, nbb, M, nbb, 1.0, Tm, NB, c->sT, Y, M, c->sY, 0.0, Y2, M, c->sY);
-    gmp<T>(c, nk, OP_N, OP_N, j1, M, nbb, -1.0, V, NB, c->sV, Y2, M, c->sY, 1.0, X, M, c->sMM);
+    gmx<T>(c, nk, OP_N, OP_N, j1, M, nbb, -1.0, V, NB, c->sV, Y2, M, c->sY, 1.0, X, M, c->sMM);
   }
 }
 
@@ -415,7 +456,7 @@ void unreduce_run(gks_ctx* c, const T* L, T* X, int M, int nk) {
       trsm_block<T>(TRSM_LEFT_CONJ, L + (size_t)r0 * M + r0, M, c->sMM, Xi, M, c->sMM, rb, M, nk, s);
     }
     if (r0 > 0)
-      gmp<T>(c, nk, OP_C, OP_N, r0, M, rb, -1.0, L + (size_t)r0 * M, M, c->sMM, Xi, M, c->sMM, 1.0, X, M, c->sMM);
+      gmx<T>(c, nk, OP_C, OP_N, r0, M, rb, -1.0, L + (size_t)r0 * M, M, c->sMM, Xi, M, c->sMM, 1.0, X, M, c->sMM);
   }
 }
 
@@ -565,8 +606,8 @@ gks_status adjoint_t(gks_ctx* c, const T* C, const double* eps, const double* mu
       Rec r(c, PC_MISC);
       herm_part<T>(R, rho_bar, MM, MM, M, nk, s);
     }
-    gmp<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, R, M, MM, C, M, MM, 0.0, T1, M, MM);
-    gmp<T>(c, nk, OP_C, OP_N, M, M, M, 1.0, C, M, MM, T1, M, MM, 0.0, W, M, MM);
+    gmx<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, R, M, MM, C, M, MM, 0.0, T1, M, MM);
+    gmx<T>(c, nk, OP_C, OP_N, M, M, M, 1.0, C, M, MM, T1, M, MM, 0.0, W, M, MM);
   }
   {
     Rec r(c, PC_MISC);
@@ -574,20 +615,20 @@ gks_status adjoint_t(gks_ctx* c, const T* C, const double* eps, const double* mu
     adj_build<T>(W, R, MM, M, eps, f, e, mu, kT, gs, have_w, nk, s);
   }
   // H_bar = C BH C^H
-  gmp<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, C, M, MM, R, M, MM, 0.0, T1, M, MM);
-  gmp<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, H_bar, M, MM);
+  gmx<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, C, M, MM, R, M, MM, 0.0, T1, M, MM);
+  gmx<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, H_bar, M, MM);
   {
     Rec r(c, PC_MISC);
     herm_part<T>(H_bar, H_bar, MM, MM, M, nk, s);
   }
   // S_bar = C BS C^H (noncollinear: the two diagonal spin blocks summed)
-  gmp<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, C, M, MM, W, M, MM, 0.0, T1, M, MM);
+  gmx<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, C, M, MM, W, M, MM, 0.0, T1, M, MM);
   if (nc) {
-    gmp<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, R, M, MM);
+    gmx<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, R, M, MM);
     Rec r(c, PC_MISC);
     spin_block_sum<T>(S_bar, (long long)n * n, R, MM, n, nk, s);
   } else {
-    gmp<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, S_bar, M, MM);
+    gmx<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, S_bar, M, MM);
     Rec r(c, PC_MISC);
     herm_part<T>(S_bar, S_bar, MM, MM, M, nk, s);
   }
@@ -662,6 +703,12 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     if (opts->f_cut > 0.0) c->f_cut = opts->f_cut;
     c->prof.on = opts->profile != 0;
     c->graph = opts->graph != 0;
+    c->gemm_mode = opts->gemm;
+    if (opts->slices > 0) c->slices = opts->slices;
+    if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 12) {
+      delete c;
+      return GKS_EINVAL;
+    }
     if (opts->precision != GKS_FP64) {
       delete c;
       return GKS_ENOTIMPL;
@@ -685,11 +732,13 @@ gks_status gks_destroy(gks_ctx* ctx) {
   for (auto sc : ctx->subs) {
     release_ws(sc);
     release_aws(sc);
+    release_oz(sc);
     delete sc;
   }
   for (auto w : ctx->workers) cudaStreamDestroy(w);
   release_ws(ctx);
   release_aws(ctx);
+  release_oz(ctx);
   delete ctx;
   return GKS_OK;
 }
@@ -752,6 +801,8 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     gks_ctx* sc = new gks_ctx();
     sc->device = ctx->device;
     sc->f_cut = ctx->f_cut;
+    sc->gemm_mode = ctx->gemm_mode;
+    sc->slices = ctx->slices;
     ctx->subs.push_back(sc);
   }
   auto body = [&]() -> gks_status {
@@ -891,6 +942,29 @@ int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max) {
     if (acc[i].groups > 0) out[k++] = acc[i];
   cudaGetLastError();
   return k;
+}
+
+gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha,
+                    const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
+                    int mode) {
+  if (!ctx || !A || !B || !C || M < 0 || N < 0 || K < 0) return fail(ctx, GKS_EINVAL, "bad arguments");
+  if (opA < 0 || opA > 2 || opB < 0 || opB > 2 || mode < 1 || mode > 2) return fail(ctx, GKS_EINVAL, "bad op or mode");
+  if (M > 46340 || N > 46340 || K > 46340) return fail(ctx, GKS_EINVAL, "dimension too large");
+  cudaSetDevice(ctx->device);
+  const int saved = ctx->gemm_mode;
+  ctx->gemm_mode = mode;
+  if (dtype == GKS_R64)
+    gmx<double>(ctx, 1, opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const double*>(A), (int)lda, 0,
+                static_cast<const double*>(B), (int)ldb, 0, beta, static_cast<double*>(C), (int)ldc, 0);
+  else if (dtype == GKS_C128)
+    gmx<zc>(ctx, 1, opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const zc*>(A), (int)lda, 0,
+            static_cast<const zc*>(B), (int)ldb, 0, beta, static_cast<zc*>(C), (int)ldc, 0);
+  else {
+    ctx->gemm_mode = saved;
+    return fail(ctx, GKS_EINVAL, "unknown dtype");
+  }
+  ctx->gemm_mode = saved;
+  return cuda_check(ctx, "gks_gemm");
 }
 
 gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype) {

@@ -72,6 +72,12 @@ void herm_part(T* dst, const T* src, long long sd, long long ss, int M, int nk, 
 template <typename T>
 void spin_block_sum(T* dst, long long sd, const T* src, long long ss, int n, int nk, cudaStream_t s);
 
+// ---- FP64-accurate GEMM from exact bf16 digit products (ozaki.cu) ----
+size_t ozaki_workspace_bytes(int M, int N, int K, bool cplx, int S);
+template <typename T>
+void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, const T* B, int ldb,
+                double beta, T* C, int ldc, int lower, int S, void* work, cudaStream_t s);
+
 // ---- occupations (occ.cu) ----
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,
               double f_cut, double* occ, double* kscale, double* mu, double* e_band, int* nrho, DevStatus* st,

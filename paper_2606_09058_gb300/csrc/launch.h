@@ -42,7 +42,7 @@ long long launches_issued();
 // Kernel classes and stages for the optional event profiler.
 enum ProfClass : int {
   PC_GEMM = 0, PC_POTF2, PC_TRSM, PC_HEGST_DIAG, PC_HETRD_HEMV, PC_HETRD_RANK2, PC_HETRD_VEC, PC_DC_LEAF,
-  PC_DC_SECULAR, PC_DC_GEMM, PC_BACKTR_AUX, PC_OCC, PC_MISC, PC_NCLASS
+  PC_DC_SECULAR, PC_DC_GEMM, PC_BACKTR_AUX, PC_OCC, PC_MISC, PC_OZAKI, PC_NCLASS
 };
 enum ProfStage : int {
   PS_COPY = 0, PS_POTRF, PS_HEGST, PS_HETRD, PS_STEDC, PS_BACKTR, PS_UNREDUCE, PS_OCC, PS_RHO, PS_ADJOINT, PS_NSTAGE

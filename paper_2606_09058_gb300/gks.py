@@ -30,7 +30,8 @@ class GKSError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
-                ("f_cut", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("f_cut", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int),
+                ("gemm", ctypes.c_int), ("slices", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -69,6 +70,8 @@ def load() -> ctypes.CDLL:
     lib.gks_potrf.argtypes = [P, P, I64, I64, I]
     lib.gks_reduce.argtypes = [P, P, P, I64, I64, I]
     lib.gks_stedc.argtypes = [P, P, P, I64, I64, P, P]
+    lib.gks_gemm.argtypes = [P, I, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64, I]
+    lib.gks_gemm.restype = I
     lib.gks_solve_batched.argtypes = [P, I64, ctypes.POINTER(_Problem), I]
     lib.gks_solve_batched.restype = I
     lib.gks_adjoint.argtypes = [P, P, P, P, I64, I64, I, I, D, P, P, P, D, P, P]
@@ -109,14 +112,15 @@ class Context:
     """A gks context bound to one device and one CUDA stream."""
 
     def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None, f_cut: float = 1e-16,
-                 profile: bool = False, graph: bool = False):
+                 profile: bool = False, graph: bool = False, gemm: str = "auto", slices: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("gks needs a CUDA device")
         lib = load()
         self.device = torch.cuda.current_device() if device is None else int(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        gm = {"auto": 0, "fp64": 1, "split": 2}[gemm]
         opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), 0, f_cut, 1 if profile else 0,
-                     1 if graph else 0)
+                     1 if graph else 0, gm, int(slices))
         h = ctypes.c_void_p()
         rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
         if rc:
@@ -245,6 +249,18 @@ class Context:
         return Hb, Sb
 
     # ------------------------------------------------------------------ stages
+    def gemm(self, A, B, C, opA="N", opB="N", alpha=1.0, beta=0.0, mode="split"):
+        """C = alpha op(A) op(B) + beta C through gks_gemm (mode "fp64" or "split")."""
+        ops = {"N": 0, "T": 1, "C": 2}
+        M, N = C.shape
+        K = A.shape[1] if opA == "N" else A.shape[0]
+        rc = self._lib.gks_gemm(self._h, GKS_C128 if C.is_complex() else GKS_R64, ops[opA], ops[opB], M, N, K,
+                                float(alpha), _ptr(A), A.shape[1], _ptr(B), B.shape[1], float(beta), _ptr(C),
+                                C.shape[1], 1 if mode == "fp64" else 2)
+        self._raise(rc)
+        self.sync()
+        return C
+
     def potrf(self, A: torch.Tensor) -> torch.Tensor:
         """In place lower Cholesky factor of each (count, m, m) matrix."""
         if A.dim() == 2:

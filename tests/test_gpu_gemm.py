@@ -1,0 +1,96 @@
+"""The split-bf16 FP64 product (gks_gemm mode 2) against numpy's FP64 product and the
+FP64-pipe kernel, within the error bound of the splitting: 54-bit digits relative to each
+row's and column's largest entry, plus the FP64 rounding of K accumulated terms."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_09058_gb300 import gks
+    return gks.Context(0)
+
+
+def _op(X, op):
+    return X if op == "N" else (X.T if op == "T" else X.conj().T)
+
+
+def _bound(A, B, K):
+    aA, aB = np.abs(A), np.abs(B)
+    rowmax, colmax = aA.max(axis=1, keepdims=True), aB.max(axis=0, keepdims=True)
+    split = 2.0 ** -54 * (rowmax * aB.sum(axis=0, keepdims=True) + aA.sum(axis=1, keepdims=True) * colmax)
+    return 4.0 * (split + 2 * K * U * (aA @ aB))
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("ops", [("N", "N"), ("N", "C"), ("C", "N"), ("T", "T")])
+@pytest.mark.parametrize("shape", [(200, 150, 300), (129, 257, 64), (64, 70, 5000), (1, 33, 7)])
+@pytest.mark.parametrize("scaling", ["plain", "ill"])
+def test_split_gemm_accuracy(ctx, cplx, ops, shape, scaling):
+    M, N, K = shape
+    rng = np.random.default_rng(M * 7 + N + K + cplx)
+    def rnd(r, c):
+        x = rng.standard_normal((r, c))
+        if cplx:
+            x = x + 1j * rng.standard_normal((r, c))
+        return x
+    A = rnd(*((M, K) if ops[0] == "N" else (K, M)))
+    B = rnd(*((K, N) if ops[1] == "N" else (N, K)))
+    if scaling == "ill":   # rows and columns scaled over 16 decades, entries over 6 decades
+        A = A * 10.0 ** rng.uniform(-8, 8, (A.shape[0], 1)) * 10.0 ** rng.uniform(-3, 3, A.shape)
+        B = B * 10.0 ** rng.uniform(-8, 8, (1, B.shape[1])) * 10.0 ** rng.uniform(-3, 3, B.shape)
+    C0 = rnd(M, N)
+    opA, opB = _op(A, ops[0]), _op(B, ops[1])
+    ref = 0.7 * (opA @ opB) - 0.3 * C0
+    dt = torch.complex128 if cplx else torch.float64
+    Ad = torch.as_tensor(A, dtype=dt).cuda()
+    Bd = torch.as_tensor(B, dtype=dt).cuda()
+    Cs = torch.as_tensor(C0, dtype=dt).cuda()
+    Cf = Cs.clone()
+    ctx.gemm(Ad, Bd, Cs, ops[0], ops[1], 0.7, -0.3, "split")
+    ctx.gemm(Ad, Bd, Cf, ops[0], ops[1], 0.7, -0.3, "fp64")
+    bound = 0.7 * _bound(opA, opB, K) + 0.3 * U * np.abs(C0) * 4
+    es = np.abs(Cs.cpu().numpy() - ref)
+    ef = np.abs(Cf.cpu().numpy() - ref)
+    assert np.all(es <= bound), (es / bound).max()
+    assert np.all(ef <= bound), (ef / bound).max()
+
+
+def test_split_gemm_is_exact_on_small_integers(ctx):
+    """Integer operands below 2^6 are single digits: the product is exact."""
+    rng = np.random.default_rng(0)
+    A = rng.integers(-63, 64, (300, 700)).astype(float)
+    B = rng.integers(-63, 64, (700, 250)).astype(float)
+    C = torch.zeros(300, 250, dtype=torch.float64, device="cuda")
+    ctx.gemm(torch.as_tensor(A).cuda(), torch.as_tensor(B).cuda(), C, mode="split")
+    assert np.array_equal(C.cpu().numpy(), A @ B)
+
+
+def test_solve_with_split_products_matches_oracle(ctx):
+    """Full path with every product forced through split products, on the Si cluster."""
+    from oracle import oracle as O
+    from paper_2606_09058_gb300 import gks, inputs as I
+    c2 = gks.Context(0, gemm="split")
+    for p in (I.collinear_gamma((2, 1, 1), 0, 0.01), I.periodic((1, 1, 1), 1, 0.01)):
+        sol = c2.solve(p.H.cuda(), p.S.cuda(), p.kT, p.n_elec, kweights=torch.as_tensor(p.kweights).cuda())
+        ref = O.solve(p.H.numpy(), p.S.numpy(), p.kT, p.n_elec, kweights=p.kweights)
+        for k in range(p.nk):
+            H, S = p.H[k].numpy(), p.S[k].numpy()
+            beta = O.eig_condition(H, S, ref.eps[k], ref.C[k])
+            assert np.all(np.abs(sol.eps.cpu().numpy()[k] - ref.eps[k]) <= np.maximum(1e-10, 8 * beta))
+            C = sol.C.cpu().numpy()[k]
+            cn = np.linalg.norm(C, axis=0)
+            R = H @ C - (S @ C) * sol.eps.cpu().numpy()[k]
+            bwd = (np.linalg.norm(R, axis=0) / ((np.linalg.norm(H, 2) + np.abs(ref.eps[k]) * np.linalg.norm(S, 2)) * cn)).max()
+            assert bwd <= 1e-12 * np.sqrt(H.shape[0])
+            d = np.abs(S @ (sol.rho.cpu().numpy()[k] - ref.rho[k]) @ S).max()
+            assert d <= 1e-9 * max(1.0, beta.max() / 1e-10)
