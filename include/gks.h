@@ -54,7 +54,7 @@ typedef struct {
   int gemm;            /* FP64 products: 0 = large ones as exact split-bf16 tensor-core products
                           with FP64 accumulation, small ones on the FP64 pipe (default);
                           1 = FP64 pipe only; 2 = split products for every product */
-  int slices;          /* 6-bit digits per operand in split products (4..12, 0 = 9) */
+  int slices;          /* 6-bit digits per operand in split products (4..10, 0 = 9) */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */

@@ -294,7 +294,7 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
   if (M <= 0 || N <= 0) return;
   const int es = sizeof(T);
   const double fl = gemm_flops(es, M, N, K, lower, count);
-  const bool split = c->gemm_mode == 2 || (c->gemm_mode == 0 && fl >= 5e8 * count && M >= 32 && N >= 32 && K >= 16);
+  const bool split = c->gemm_mode == 2 || (c->gemm_mode == 0 && fl >= 5e8 * count && M >= 256 && N >= 256 && K >= 256);
   if (!split) {
     gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
     return;
@@ -705,7 +705,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     c->graph = opts->graph != 0;
     c->gemm_mode = opts->gemm;
     if (opts->slices > 0) c->slices = opts->slices;
-    if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 12) {
+    if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 10) {
       delete c;
       return GKS_EINVAL;
     }

@@ -9,7 +9,8 @@
 // is exact in the FP32 accumulator of the bf16 mma.  The kernel multiplies the digit pairs
 // with s + t <= S + 1 (the dropped pairs are below 2^{-6(S+1)}), drains each exact chunk
 // into an FP64 accumulator scaled by 2^{-6(s+t)}, and applies 2^{e_i + f_j} at the end.
-// With S = 9 the digits carry 54 bits below each row's largest entry.
+// With S = 9 the digits carry 54 bits below each row's largest entry.  (S <= 10 keeps the
+// digit integer within 60 bits.)
 //
 // Complex products use a real embedding that keeps (Re, Im) of one output next to each
 // other: A' = [Re a, Im a] interleaved along k, B' column 2j = (Re b, -Im b) interleaved,
@@ -24,18 +25,20 @@
 namespace gks {
 
 static constexpr int OZ_BITS = 6;
-static constexpr int OZ_KSTEP = 32;   // k per pipeline step
+static constexpr int OZ_KSTEP = 64;   // k per pipeline step
 static constexpr int OZ_CHUNK = 4096; // exact FP32 accumulation length (63*63*4096 < 2^24)
 
 // ------------------------------------------------------------------ splitting
 
-// Digits of one value already scaled below 1 in magnitude.
+// Digits of one value already scaled below 1 in magnitude.  The first S base-64 digits
+// of |r| truncated toward zero are the base-64 digits of the integer trunc(|r| 2^{6S})
+// (6S <= 60 bits): one conversion, then integer shifts.
 __device__ __forceinline__ void put_digits(double r, __nv_bfloat16* dst, long long sstride, int S) {
+  const long long q = __double2ll_rz(ldexp(fabs(r), OZ_BITS * S));
+  const float sg = r < 0.0 ? -1.0f : 1.0f;
   for (int s = 0; s < S; s++) {
-    double t = r * 64.0;
-    double d = trunc(t);
-    dst[s * sstride] = __float2bfloat16_rn((float)d);
-    r = t - d;
+    const int d = (int)((q >> (OZ_BITS * (S - 1 - s))) & 63);
+    dst[s * sstride] = __float2bfloat16_rn(sg * (float)d);
   }
 }
 
@@ -83,18 +86,18 @@ __device__ __forceinline__ void emit<zc>(zc x, int e, int role, int v, int k, __
   }
 }
 
-// One CTA (128 threads) per 32 vectors.  Pass 1: per-vector max (thread per vector when the
+// One CTA (256 threads) per 32 vectors.  Pass 1: per-vector max (thread per vector when the
 // vector index is the contiguous direction, else a warp sweeps each vector along k).
 // Pass 2: digits.  Padding vectors and k beyond K are written as zero digits elsewhere.
 template <typename T>
-__global__ void __launch_bounds__(128) oz_split_kernel(const T* X, int ld, int role, int op, int nvec, int K,
+__global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, int role, int op, int nvec, int K,
                                                        __nv_bfloat16* D, int Kp, long long sstride, int S, int* ex) {
   __shared__ double smax[32];
   __shared__ int sexp[32];
   const int v0 = blockIdx.x * 32, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool contig = (role == 0) == (op == OP_N);  // k contiguous in memory
   if (contig) {
-    for (int vv = warp; vv < 32; vv += 4) {
+    for (int vv = warp; vv < 32; vv += 8) {
       const int v = v0 + vv;
       double m = 0.0;
       if (v < nvec)
@@ -103,12 +106,18 @@ __global__ void __launch_bounds__(128) oz_split_kernel(const T* X, int ld, int r
       if (lane == 0) smax[vv] = m;
     }
   } else {
+    // 8 warps sweep k in parallel, lanes run over the 32 vectors (coalesced), then reduce
+    __shared__ double pm[8][32];
+    double m = 0.0;
+    const int v = v0 + lane;
+    if (v < nvec)
+      for (int k = warp; k < K; k += 8) m = fmax(m, amax(split_elem(X, ld, role, op, v, k)));
+    pm[warp][lane] = m;
+    __syncthreads();
     if (tid < 32) {
-      const int v = v0 + tid;
-      double m = 0.0;
-      if (v < nvec)
-        for (int k = 0; k < K; k++) m = fmax(m, amax(split_elem(X, ld, role, op, v, k)));
-      smax[tid] = m;
+      double mm = 0.0;
+      for (int w = 0; w < 8; w++) mm = fmax(mm, pm[w][tid]);
+      smax[tid] = mm;
     }
   }
   __syncthreads();
@@ -118,7 +127,7 @@ __global__ void __launch_bounds__(128) oz_split_kernel(const T* X, int ld, int r
   }
   __syncthreads();
   if (contig) {
-    for (int vv = warp; vv < 32; vv += 4) {
+    for (int vv = warp; vv < 32; vv += 8) {
       const int v = v0 + vv;
       if (v >= nvec) continue;
       for (int k = lane; k < K; k += 32) emit<T>(split_elem(X, ld, role, op, v, k), sexp[vv], role, v, k, D, Kp, sstride, S);
@@ -128,12 +137,12 @@ __global__ void __launch_bounds__(128) oz_split_kernel(const T* X, int ld, int r
     // the reads run along the vectors and the digit writes along k
     __shared__ T tile[32][33];
     for (int k0 = 0; k0 < K; k0 += 32) {
-      for (int kk = warp; kk < 32; kk += 4) {
+      for (int kk = warp; kk < 32; kk += 8) {
         const int k = k0 + kk, v = v0 + lane;
         tile[kk][lane] = (k < K && v < nvec) ? split_elem(X, ld, role, op, v, k) : zero<T>();
       }
       __syncthreads();
-      for (int vv = warp; vv < 32; vv += 4) {
+      for (int vv = warp; vv < 32; vv += 8) {
         const int v = v0 + vv, k = k0 + lane;
         if (v < nvec && k < K) emit<T>(tile[lane][vv], sexp[vv], role, v, k, D, Kp, sstride, S);
       }
@@ -186,20 +195,21 @@ struct OzArgs {
   long long sAd, sBd;       // slice strides (elements)
 };
 
-static constexpr int OZ_BM = 128, OZ_BN = 128, OZ_LDS = OZ_KSTEP + 8, OZ_STAGES = 3;
-static constexpr int OZ_SMEM = OZ_BM * OZ_BN * 8 + OZ_STAGES * (OZ_BM + OZ_BN) * OZ_LDS * 2;
+static constexpr int OZ_BM = 128, OZ_BN = 128, OZ_LDS = OZ_KSTEP + 8, OZ_STAGES = 2;
+static constexpr int OZ_ACC_LD = OZ_BN + 2;  // padded FP64 accumulator rows (drain bank spread)
+static constexpr int OZ_SMEM = OZ_BM * OZ_ACC_LD * 8 + OZ_STAGES * (OZ_BM + OZ_BN) * OZ_LDS * 2;
 
 __global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* acc64 = reinterpret_cast<double*>(smem_raw);  // [128][128]
-  __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(smem_raw + OZ_BM * OZ_BN * 8);
+  double* acc64 = reinterpret_cast<double*>(smem_raw);  // [128][OZ_ACC_LD]
+  __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(smem_raw + OZ_BM * OZ_ACC_LD * 8);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, warp tile 64 x 32
   const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
   // lower triangle of the logical output: skip tiles strictly above the diagonal
   const int ncol0 = a.cplx ? n0 / 2 : n0;
   if (a.lower && m0 + OZ_BM - 1 < ncol0) return;
-  for (int e = tid; e < OZ_BM * OZ_BN; e += 256) acc64[e] = 0.0;
+  for (int e = tid; e < OZ_BM * OZ_ACC_LD; e += 256) acc64[e] = 0.0;
 
   // pairs (s, t), s + t <= S + 1, s,t >= 1
   const int S = a.S;
@@ -226,9 +236,10 @@ __global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
     const __nv_bfloat16* gb = a.Bd + (size_t)(t - 1) * a.sBd + (size_t)n0 * a.Kp + (size_t)kk * OZ_KSTEP;
     __nv_bfloat16* sa = stage_ptr(stg);
     __nv_bfloat16* sb = sa + OZ_BM * OZ_LDS;
-    // 128 rows x 32 bf16 = 128 x 4 chunks of 16 B for each operand
-    for (int c = tid; c < OZ_BM * 4; c += 256) {
-      int r = c >> 2, cc = (c & 3) * 8;
+    // 128 rows x OZ_KSTEP bf16 = 128 x (OZ_KSTEP/8) chunks of 16 B for each operand
+    constexpr int CPR = OZ_KSTEP / 8;
+    for (int c = tid; c < OZ_BM * CPR; c += 256) {
+      int r = c / CPR, cc = (c % CPR) * 8;
       cp_async16(sa + r * OZ_LDS + cc, ga + (size_t)r * a.Kp + cc);
       cp_async16(sb + r * OZ_LDS + cc, gb + (size_t)r * a.Kp + cc);
     }
@@ -258,14 +269,13 @@ __global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
     }
     const __nv_bfloat16* sa = stage_ptr((int)(q % OZ_STAGES));
     const __nv_bfloat16* sb = sa + OZ_BM * OZ_LDS;
-#pragma unroll
-    for (int k16 = 0; k16 < OZ_KSTEP; k16 += 16) {
-      uint32_t af[4][4], bf[4][2];
+    uint32_t af[2][4][4], bf[2][4][2];
+    auto load_frags = [&](int k16, int buf) {
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         const int row = wm * 64 + i * 16 + (lane & 15);
         const int col = k16 + (lane >> 4) * 8;
-        ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3], sa + row * OZ_LDS + col);
+        ldsm_x4(af[buf][i][0], af[buf][i][1], af[buf][i][2], af[buf][i][3], sa + row * OZ_LDS + col);
       }
 #pragma unroll
       for (int j = 0; j < 4; j += 2) {
@@ -274,15 +284,21 @@ __global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
         const int col = k16 + ((lane >> 3) & 1) * 8;
         uint32_t r0, r1, r2, r3;
         ldsm_x4(r0, r1, r2, r3, sb + nrow * OZ_LDS + col);
-        bf[j][0] = r0;
-        bf[j][1] = r1;
-        bf[j + 1][0] = r2;
-        bf[j + 1][1] = r3;
+        bf[buf][j][0] = r0;
+        bf[buf][j][1] = r1;
+        bf[buf][j + 1][0] = r2;
+        bf[buf][j + 1][1] = r3;
       }
+    };
+    load_frags(0, 0);
+#pragma unroll
+    for (int ks = 0; ks < OZ_KSTEP / 16; ks++) {
+      const int cur = ks & 1;
+      if (ks + 1 < OZ_KSTEP / 16) load_frags((ks + 1) * 16, cur ^ 1);
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[i], bf[j][0], bf[j][1]);
+        for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[cur][i], bf[cur][j][0], bf[cur][j][1]);
     }
     // drain at the end of each exact chunk and of each pair
     const int kk = (int)(q % ksteps);
@@ -296,10 +312,10 @@ __global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
 #pragma unroll
         for (int j = 0; j < 4; j++) {
           const int r = wm * 64 + i * 16 + g, c = wn * 32 + j * 8 + tq * 2;
-          acc64[r * OZ_BN + c] += sc * (double)acc[i][j][0];
-          acc64[r * OZ_BN + c + 1] += sc * (double)acc[i][j][1];
-          acc64[(r + 8) * OZ_BN + c] += sc * (double)acc[i][j][2];
-          acc64[(r + 8) * OZ_BN + c + 1] += sc * (double)acc[i][j][3];
+          acc64[r * OZ_ACC_LD + c] += sc * (double)acc[i][j][0];
+          acc64[r * OZ_ACC_LD + c + 1] += sc * (double)acc[i][j][1];
+          acc64[(r + 8) * OZ_ACC_LD + c] += sc * (double)acc[i][j][2];
+          acc64[(r + 8) * OZ_ACC_LD + c + 1] += sc * (double)acc[i][j][3];
 #pragma unroll
           for (int rr = 0; rr < 4; rr++) acc[i][j][rr] = 0.f;
         }
@@ -315,7 +331,7 @@ __global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
       const int i = m0 + r, j = n0 / 2 + cj;
       if (i >= a.M || j >= a.N || (a.lower && j > i)) continue;
       const int ee = a.ea[i] + a.eb[j];
-      zc v{ldexp(acc64[r * OZ_BN + 2 * cj], ee) * a.alpha, ldexp(acc64[r * OZ_BN + 2 * cj + 1], ee) * a.alpha};
+      zc v{ldexp(acc64[r * OZ_ACC_LD + 2 * cj], ee) * a.alpha, ldexp(acc64[r * OZ_ACC_LD + 2 * cj + 1], ee) * a.alpha};
       zc* cp = C + (size_t)i * a.ldc + j;
       if (a.beta != 0.0) v = v + a.beta * (*cp);
       *cp = v;
@@ -326,7 +342,7 @@ __global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
       const int r = e / OZ_BN, c = e % OZ_BN;
       const int i = m0 + r, j = n0 + c;
       if (i >= a.M || j >= a.N || (a.lower && j > i)) continue;
-      double v = ldexp(acc64[r * OZ_BN + c], a.ea[i] + a.eb[j]) * a.alpha;
+      double v = ldexp(acc64[r * OZ_ACC_LD + c], a.ea[i] + a.eb[j]) * a.alpha;
       double* cp = C + (size_t)i * a.ldc + j;
       if (a.beta != 0.0) v += a.beta * (*cp);
       *cp = v;
@@ -360,9 +376,9 @@ void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   cudaMemsetAsync(Ad, 0, (size_t)S * ((size_t)Mp + Np) * Kp * 2, s);
   if (K > 0) {
     count_launch();
-    oz_split_kernel<T><<<(M + 31) / 32, 128, 0, s>>>(A, lda, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, S, ea);
+    oz_split_kernel<T><<<(M + 31) / 32, 256, 0, s>>>(A, lda, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, S, ea);
     count_launch();
-    oz_split_kernel<T><<<(N + 31) / 32, 128, 0, s>>>(B, ldb, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, S, eb);
+    oz_split_kernel<T><<<(N + 31) / 32, 256, 0, s>>>(B, ldb, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, S, eb);
   } else {
     cudaMemsetAsync(ea, 0, sizeof(int) * ((size_t)Mp + Np), s);
   }

@@ -1,6 +1,7 @@
 """The split-bf16 FP64 product (gks_gemm mode 2) against numpy's FP64 product and the
 FP64-pipe kernel, within the error bound of the splitting: 54-bit digits relative to each
-row's and column's largest entry, plus the FP64 rounding of K accumulated terms."""
+row's and column's largest entry (so the error scales with K max|a_i.| max|b_.j| rather than
+with sum |a_ik||b_kj|), plus the FP64 rounding of K accumulated terms."""
 import numpy as np
 import pytest
 import torch
@@ -24,11 +25,14 @@ def _op(X, op):
     return X if op == "N" else (X.T if op == "T" else X.conj().T)
 
 
-def _bound(A, B, K):
+def _bound(A, B, K, S=9):
+    """FP64 rounding of the K-term sum plus the splitting error: every digit product and
+    the remainders are below 2^{-6S} of the row scale 2^{e_i} <= 2 max_k |a_ik| times the
+    column scale (the S + 2 levels at and beyond the truncation, both remainders)."""
     aA, aB = np.abs(A), np.abs(B)
     rowmax, colmax = aA.max(axis=1, keepdims=True), aB.max(axis=0, keepdims=True)
-    split = 2.0 ** -54 * (rowmax * aB.sum(axis=0, keepdims=True) + aA.sum(axis=1, keepdims=True) * colmax)
-    return 4.0 * (split + 2 * K * U * (aA @ aB))
+    split = (S + 2) * K * 2.0 ** (-6 * S) * (2 * rowmax) * (2 * colmax)
+    return 2.0 * (split + 2 * K * U * (aA @ aB))
 
 
 @pytest.mark.parametrize("cplx", [False, True])
