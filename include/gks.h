@@ -169,6 +169,34 @@ gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_
                     const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
                     int mode);
 
+/* Size in bytes of the fixed device scratch behind gks_gemm_split_noalloc. */
+#define GKS_NOALLOC_SCRATCH_BYTES 16777216
+
+/* The split-bf16 product of gks_gemm (mode 2) without any device allocation: the digit
+ * scratch is a fixed region of GKS_NOALLOC_SCRATCH_BYTES (16 MiB) compiled into this
+ * library, one per device, instead of memory the context obtains with cudaMalloc.  For
+ * callers that must not allocate device memory at the point of the call: a process whose
+ * device memory is already handed out to another allocator or capped, or a loop that
+ * cannot afford the device-wide synchronization an allocation implies.  The paper has no
+ * counterpart; this is a library service around the same product kernels.
+ *
+ * Arguments as in gks_gemm; the digit count is the context's opts->slices (S, default 9).
+ * The scratch needed is S * (Mp + Np) * Kp * 2 + 4 * (Mp + Np) + 1024 bytes with
+ * Mp = M rounded up to 128, Np = N' rounded up to 128, Kp = K' rounded up to 64, where
+ * N' = N, K' = K for GKS_R64 and N' = 2N, K' = 2K for GKS_C128 (e.g. real 512 x 512 x 512
+ * at S = 9 needs 9.4 MB).  A larger product returns GKS_EINVAL before any work is
+ * enqueued, with the sizes in gks_last_error.
+ *
+ * The first call on a device looks up the scratch address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture on the device.
+ * The work is enqueued on the context's stream and the call returns without waiting.
+ * All calls on one device share the one scratch region: two calls whose work overlaps in
+ * time (other streams, other contexts, other host threads) corrupt each other's results.
+ * Order them on one stream or synchronize between them. */
+gks_status gks_gemm_split_noalloc(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_t N, int64_t K,
+                                  double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                  double beta, void* C, int64_t ldc);
+
 /* Stage entry points (same conventions; `count` independent matrices of order m,
  * stride m*m elements).  Used to check each stage on its own. */
 

@@ -2,6 +2,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -692,6 +693,31 @@ gks_status capture(gks_ctx* c, cudaGraphExec_t* out, F body) {
 
 }  // namespace
 
+// ---- fixed scratch for split products that allocate nothing ----
+// Digit scratch of gks_gemm_split_noalloc, part of the library image on every device.
+// Shared by all calls on a device: calls whose work overlaps in time race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GKS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocDevices] = {};
+
+// Device address of the scratch on `dev`, which must be the current device; resolved
+// once per device.
+cudaError_t noalloc_scratch(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
 extern "C" {
 
 gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
@@ -965,6 +991,37 @@ gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_
   }
   ctx->gemm_mode = saved;
   return cuda_check(ctx, "gks_gemm");
+}
+
+gks_status gks_gemm_split_noalloc(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_t N, int64_t K,
+                                  double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                  double beta, void* C, int64_t ldc) {
+  if (!ctx || !A || !B || !C || M < 0 || N < 0 || K < 0) return fail(ctx, GKS_EINVAL, "bad arguments");
+  if (opA < 0 || opA > 2 || opB < 0 || opB > 2) return fail(ctx, GKS_EINVAL, "bad op");
+  if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
+  if (M > 46340 || N > 46340 || K > 46340) return fail(ctx, GKS_EINVAL, "dimension too large");
+  if (ctx->device < 0 || ctx->device >= kNoAllocDevices) return fail(ctx, GKS_EINVAL, "device index out of range");
+  const size_t need = ozaki_workspace_bytes((int)M, (int)N, (int)K, dtype == GKS_C128, ctx->slices);
+  if (need > (size_t)GKS_NOALLOC_SCRATCH_BYTES)
+    return fail(ctx, GKS_EINVAL,
+                "product needs " + std::to_string(need) + " bytes of split scratch; the fixed scratch holds " +
+                    std::to_string((size_t)GKS_NOALLOC_SCRATCH_BYTES) + " bytes");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_check(ctx, "gks_gemm_split_noalloc: set device");
+  void* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(ctx->device, &scratch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, GKS_ECUDA, std::string("gks_gemm_split_noalloc: scratch lookup: ") + cudaGetErrorString(e));
+  }
+  if (dtype == GKS_R64)
+    ozaki_gemm<double>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const double*>(A), (int)lda,
+                       static_cast<const double*>(B), (int)ldb, beta, static_cast<double*>(C), (int)ldc, 0,
+                       ctx->slices, scratch, ctx->stream);
+  else
+    ozaki_gemm<zc>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const zc*>(A), (int)lda,
+                   static_cast<const zc*>(B), (int)ldb, beta, static_cast<zc*>(C), (int)ldc, 0, ctx->slices,
+                   scratch, ctx->stream);
+  return cuda_check(ctx, "gks_gemm_split_noalloc");
 }
 
 gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype) {

@@ -72,6 +72,8 @@ def load() -> ctypes.CDLL:
     lib.gks_stedc.argtypes = [P, P, P, I64, I64, P, P]
     lib.gks_gemm.argtypes = [P, I, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64, I]
     lib.gks_gemm.restype = I
+    lib.gks_gemm_split_noalloc.argtypes = [P, I, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64]
+    lib.gks_gemm_split_noalloc.restype = I
     lib.gks_solve_batched.argtypes = [P, I64, ctypes.POINTER(_Problem), I]
     lib.gks_solve_batched.restype = I
     lib.gks_adjoint.argtypes = [P, P, P, P, I64, I64, I, I, D, P, P, P, D, P, P]
@@ -257,6 +259,19 @@ class Context:
         rc = self._lib.gks_gemm(self._h, GKS_C128 if C.is_complex() else GKS_R64, ops[opA], ops[opB], M, N, K,
                                 float(alpha), _ptr(A), A.shape[1], _ptr(B), B.shape[1], float(beta), _ptr(C),
                                 C.shape[1], 1 if mode == "fp64" else 2)
+        self._raise(rc)
+        self.sync()
+        return C
+
+    def gemm_split_noalloc(self, A, B, C, opA="N", opB="N", alpha=1.0, beta=0.0):
+        """C = alpha op(A) op(B) + beta C through gks_gemm_split_noalloc: the split product
+        on the library's fixed device scratch, with no device allocation."""
+        ops = {"N": 0, "T": 1, "C": 2}
+        M, N = C.shape
+        K = A.shape[1] if opA == "N" else A.shape[0]
+        rc = self._lib.gks_gemm_split_noalloc(self._h, GKS_C128 if C.is_complex() else GKS_R64, ops[opA], ops[opB],
+                                              M, N, K, float(alpha), _ptr(A), A.shape[1], _ptr(B), B.shape[1],
+                                              float(beta), _ptr(C), C.shape[1])
         self._raise(rc)
         self.sync()
         return C
