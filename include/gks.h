@@ -55,6 +55,8 @@ typedef struct {
                           with FP64 accumulation, small ones on the FP64 pipe (default);
                           1 = FP64 pipe only; 2 = split products for every product */
   int slices;          /* 6-bit digits per operand in split products (4..10, 0 = 9) */
+  int block;           /* outer block width of the two-level blocked Cholesky, reduction and
+                          back-transforms: a multiple of 64 in 64..1024, 0 = 256 */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */

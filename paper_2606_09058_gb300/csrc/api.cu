@@ -85,6 +85,7 @@ struct gks_ctx {
   bool graph = false;                  // capture solves into CUDA graphs
   int gemm_mode = 0;                   // 0 auto, 1 DFMA only, 2 split products always
   int slices = 9;                      // 6-bit digits per operand in split products
+  int nbb = 256;                       // outer block of the two-level blocked stages
   void* oz = nullptr;                  // digit workspace of the split-product GEMM
   size_t oz_bytes = 0;
   cudaGraphExec_t gexec = nullptr;     // graph of the last captured solve
@@ -107,9 +108,9 @@ struct gks_ctx {
   size_t aws_bytes = 0;
   int am = -1, ank = -1, aes = -1;
   // offsets (bytes) of per-item arrays; each holds nk items
-  size_t oA, oL, oF, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
+  size_t oA, oL, oF, oFB, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
       oticket;
-  long long sMM, sF, sV, sG, sT, sY, sVec;
+  long long sMM, sF, sFB, sV, sG, sT, sY, sVec;
 };
 
 namespace {
@@ -164,17 +165,20 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   release_ws(c);
   const size_t MM = (size_t)m * m;
   c->sMM = (long long)MM;
+  const int nbb = c->nbb;
   c->sF = NB * NB;
-  c->sV = (long long)m * NB;
-  c->sG = NB * NB;
-  c->sT = NB * NB;
-  c->sY = (long long)NB * m;
+  c->sFB = (long long)nbb * nbb;
+  c->sV = (long long)m * nbb;
+  c->sG = (long long)nbb * nbb;
+  c->sT = (long long)nbb * nbb;
+  c->sY = (long long)nbb * m;
   c->sVec = m;
   Arena a;
   auto elems = [&](long long per) { return (size_t)per * nk * es; };
   c->oA = a.take<char>(elems(c->sMM));
   c->oL = a.take<char>(elems(c->sMM));
   c->oF = a.take<char>(elems(c->sF));
+  c->oFB = a.take<char>(elems(c->sFB));
   c->oV = a.take<char>(elems(c->sV));
   c->oG = a.take<char>(elems(c->sG));
   c->oT = a.take<char>(elems(c->sT));
@@ -184,7 +188,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->op = a.take<char>(elems(m));
   c->oph = a.take<char>(elems(m));
   c->otau = a.take<double>((size_t)m * nk);
-  c->otb = a.take<double>((size_t)NB * nk);
+  c->otb = a.take<double>((size_t)nbb * nk);
   c->od = a.take<double>((size_t)m * nk);
   c->oe = a.take<double>((size_t)m * nk);
   c->oZ = a.take<double>(MM * nk);
@@ -288,19 +292,28 @@ struct StageRec {
 double cmul(int es) { return es == 16 ? 8.0 : 2.0; }
 
 // GEMM dispatch: large products go through exact split-bf16 products with FP64
-// accumulation (ozaki.cu), one batch item at a time; small ones stay on the DFMA kernel.
+// accumulation (ozaki.cu) when M, N, K >= 256 and the batch fills at least one wave of
+// 128 x 128 output tiles; the rest stays on the DFMA kernel.  Batch items are split into
+// launches whose digit workspace stays within kOzCap bytes.
+constexpr size_t kOzCap = (size_t)12 << 30;
+
 template <typename T>
 void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA,
          const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC, int lower = 0) {
   if (M <= 0 || N <= 0) return;
   const int es = sizeof(T);
   const double fl = gemm_flops(es, M, N, K, lower, count);
-  const bool split = c->gemm_mode == 2 || (c->gemm_mode == 0 && fl >= 5e8 * count && M >= 256 && N >= 256 && K >= 256);
+  const bool big = fl >= 5e8 * count && M >= 256 && N >= 256 && K >= 256 &&
+                   (long long)ozaki_tiles(M, N, es == 16) * count >= 152;
+  const bool split = c->gemm_mode == 2 || (c->gemm_mode == 0 && big);
   if (!split) {
     gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
     return;
   }
-  const size_t need = ozaki_workspace_bytes(M, N, K, es == 16, c->slices);
+  const size_t item = ozaki_workspace_bytes(M, N, K, es == 16, c->slices);
+  const int maxper = (int)std::max<size_t>(1, std::min<size_t>((size_t)count, kOzCap / item));
+  const int nch = (count + maxper - 1) / maxper, per = (count + nch - 1) / nch;
+  const size_t need = item * per;
   if (need > c->oz_bytes) {
     cudaStreamSynchronize(c->stream);
     release_oz(c);
@@ -313,77 +326,159 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
     c->oz_bytes = need;
   }
   Rec r(c, PC_OZAKI, fl, gemm_bytes(es, M, N, K, lower, count, beta != 0.0));
-  for (int z = 0; z < count; z++)
-    ozaki_gemm<T>(opA, opB, M, N, K, alpha, A + z * sA, lda, B + z * sB, ldb, beta, C + z * sC, ldc, lower, c->slices,
-                  c->oz, c->stream);
+  for (int z0 = 0; z0 < count; z0 += per) {
+    const int cnt = std::min(per, count - z0);
+    ozaki_gemm<T>(opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc, sC,
+                  cnt, lower, c->slices, c->oz, c->stream);
+  }
 }
 
-// Blocked right-looking Cholesky of L (in place, lower): diagonal block, panel solve
-// L21 = A21 L11^-H by substitution, trailing Hermitian rank-kb update.
+// Blocked right-looking Cholesky of L (in place, lower), two levels.  Outer panels of
+// nbb columns: inside a panel, 64-wide steps (diagonal block in shared memory, L21 =
+// A21 L11^-H by substitution, rank-64 update of the rest of the panel only); after the
+// panel, one rank-nbb update of the trailing matrix (the product that dominates, now with
+// K = nbb).
 template <typename T>
 void potrf_run(gks_ctx* c, T* L, int M, int nk) {
   cudaStream_t s = c->stream;
   const int es = sizeof(T);
-  for (int k0 = 0; k0 < M; k0 += NB) {
-    const int kb = std::min(NB, M - k0);
-    {
-      Rec r(c, PC_POTF2, cmul(es) * kb * kb * kb / 6.0 * nk, 2.0 * es * kb * kb * nk);
-      potf2<T>(L, M, c->sMM, k0, kb, c->st, nk, s);
+  const int nbb = c->nbb;
+  for (int K0 = 0; K0 < M; K0 += nbb) {
+    const int KB = std::min(nbb, M - K0);
+    for (int k0 = K0; k0 < K0 + KB; k0 += NB) {
+      const int kb = std::min(NB, K0 + KB - k0);
+      {
+        Rec r(c, PC_POTF2, cmul(es) * kb * kb * kb / 6.0 * nk, 2.0 * es * kb * kb * nk);
+        potf2<T>(L, M, c->sMM, k0, kb, c->st, nk, s);
+      }
+      const int rows = M - k0 - kb;
+      if (rows <= 0) continue;
+      T* L11 = L + (size_t)k0 * M + k0;
+      T* L21 = L + (size_t)(k0 + kb) * M + k0;
+      {
+        Rec r(c, PC_TRSM, cmul(es) * 0.5 * kb * kb * rows * nk, (2.0 * rows * kb + 0.5 * kb * kb) * es * nk);
+        trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, L21, M, c->sMM, kb, rows, nk, s);
+      }
+      const int w = K0 + KB - (k0 + kb);  // panel columns right of this step
+      if (w > 0)
+        gmx<T>(c, nk, OP_N, OP_C, rows, w, kb, -1.0, L21, M, c->sMM, L21, M, c->sMM, 1.0, L21 + kb, M, c->sMM, 1);
     }
-    const int rows = M - k0 - kb;
-    if (rows <= 0) continue;
-    T* L11 = L + (size_t)k0 * M + k0;
-    T* L21 = L + (size_t)(k0 + kb) * M + k0;
-    {
-      Rec r(c, PC_TRSM, cmul(es) * 0.5 * kb * kb * rows * nk, (2.0 * rows * kb + 0.5 * kb * kb) * es * nk);
-      trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, L21, M, c->sMM, kb, rows, nk, s);
+    const int rows2 = M - K0 - KB;
+    if (rows2 > 0) {
+      T* P = L + (size_t)(K0 + KB) * M + K0;
+      gmx<T>(c, nk, OP_N, OP_C, rows2, rows2, KB, -1.0, P, M, c->sMM, P, M, c->sMM, 1.0, P + KB, M, c->sMM, 1);
     }
-    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, L21, M, c->sMM, 1.0, L21 + kb, M, c->sMM, 1);
   }
 }
 
-// Two-sided blocked reduction A <- L^-1 A L^-H (lower triangle).  Per panel:
+// Two-sided blocked reduction A <- L^-1 A L^-H (lower triangle) of the order-n block at
+// A, L (leading dimension ld), one level of 64-wide panels.  Per panel:
 //   A11 <- L11^-1 A11 L11^-H (in-block recurrence),  W = A21 L11^-H,
 //   V = W - L21 A11'/2,  A22 -= L21 V^H + V L21^H,  R = V - L21 A11'/2,
 // and finally the block-strictly-lower part G = [R_0 R_1 ...] becomes L^-1 G by block
 // forward substitution (diagonal blocks by substitution, the rest GEMM updates).
 template <typename T>
-void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
+void hegst_level(gks_ctx* c, T* A, const T* L, int n, int ld, int nk) {
   cudaStream_t s = c->stream;
   const int es = sizeof(T);
   T* F = at<T>(c, c->oF);
-  for (int k0 = 0; k0 < M; k0 += NB) {
-    const int kb = std::min(NB, M - k0);
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
     {
       Rec r(c, PC_HEGST_DIAG, cmul(es) * kb * kb * kb * nk, 3.0 * es * kb * kb * nk);
-      hegst_diag<T>(A, M, c->sMM, L, M, c->sMM, k0, kb, F, NB, c->sF, nk, s);
+      hegst_diag<T>(A, ld, c->sMM, L, ld, c->sMM, k0, kb, F, NB, c->sF, nk, s);
     }
-    const int rows = M - k0 - kb;
+    const int rows = n - k0 - kb;
     if (rows <= 0) continue;
-    const T* L11 = L + (size_t)k0 * M + k0;
-    const T* L21 = L + (size_t)(k0 + kb) * M + k0;
-    T* A21 = A + (size_t)(k0 + kb) * M + k0;
+    const T* L11 = L + (size_t)k0 * ld + k0;
+    const T* L21 = L + (size_t)(k0 + kb) * ld + k0;
+    T* A21 = A + (size_t)(k0 + kb) * ld + k0;
     T* A22 = A21 + kb;
     {
       Rec r(c, PC_TRSM, cmul(es) * 0.5 * kb * kb * rows * nk, (2.0 * rows * kb + 0.5 * kb * kb) * es * nk);
-      trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, A21, M, c->sMM, kb, rows, nk, s);
+      trsm_block<T>(TRSM_RIGHT_CONJ, L11, ld, c->sMM, A21, ld, c->sMM, kb, rows, nk, s);
     }
-    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
-    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, M, c->sMM, A21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
-    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, M, c->sMM, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
-    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, M, c->sMM, F, NB, c->sF, 1.0, A21, M, c->sMM);
+    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, ld, c->sMM, F, NB, c->sF, 1.0, A21, ld, c->sMM);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, ld, c->sMM, A21, ld, c->sMM, 1.0, A22, ld, c->sMM, 1);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, ld, c->sMM, L21, ld, c->sMM, 1.0, A22, ld, c->sMM, 1);
+    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, ld, c->sMM, F, NB, c->sF, 1.0, A21, ld, c->sMM);
   }
-  for (int r0 = NB; r0 < M; r0 += NB) {
-    const int rb = std::min(NB, M - r0);
-    T* Ai = A + (size_t)r0 * M;
+  for (int r0 = NB; r0 < n; r0 += NB) {
+    const int rb = std::min(NB, n - r0);
+    T* Ai = A + (size_t)r0 * ld;
     {
       Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * r0 * nk, (2.0 * r0 * rb + 0.5 * rb * rb) * es * nk);
-      trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * M + r0, M, c->sMM, Ai, M, c->sMM, rb, r0, nk, s);
+      trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * ld + r0, ld, c->sMM, Ai, ld, c->sMM, rb, r0, nk, s);
     }
-    const int below = M - r0 - rb;
+    const int below = n - r0 - rb;
     if (below > 0)
-      gmx<T>(c, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM, 1.0,
-             A + (size_t)(r0 + rb) * M, M, c->sMM);
+      gmx<T>(c, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * ld + r0, ld, c->sMM, Ai, ld, c->sMM,
+             1.0, A + (size_t)(r0 + rb) * ld, ld, c->sMM);
+  }
+}
+
+// The same reduction with outer panels of nbb columns: the diagonal nbb block by
+// hegst_level, then the panel steps with K = nbb products (A21 L11^-H by 64-wide block
+// substitution, the Hermitian A11' as a full copy for the two half-updates, the rank-2nbb
+// trailing update), and the deferred substitution L^-1 [R_0 R_1 ...] blocked the same way.
+template <typename T>
+void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
+  cudaStream_t s = c->stream;
+  const int es = sizeof(T);
+  const int nbb = c->nbb;
+  if (M <= nbb || nbb <= NB) {
+    hegst_level<T>(c, A, L, M, M, nk);
+    return;
+  }
+  T* FB = at<T>(c, c->oFB);
+  for (int K0 = 0; K0 < M; K0 += nbb) {
+    const int KB = std::min(nbb, M - K0);
+    T* A11 = A + (size_t)K0 * M + K0;
+    const T* L11 = L + (size_t)K0 * M + K0;
+    hegst_level<T>(c, A11, L11, KB, M, nk);
+    const int rows = M - K0 - KB;
+    if (rows <= 0) continue;
+    const T* L21 = L + (size_t)(K0 + KB) * M + K0;
+    T* A21 = A + (size_t)(K0 + KB) * M + K0;
+    T* A22 = A21 + KB;
+    // A21 <- A21 L11^-H: column blocks left to right, X_j = (A_j - X_<j L11[j,<j]^H) L11[j,j]^-H
+    for (int j0 = 0; j0 < KB; j0 += NB) {
+      const int jb = std::min(NB, KB - j0);
+      if (j0 > 0)
+        gmx<T>(c, nk, OP_N, OP_C, rows, jb, j0, -1.0, A21, M, c->sMM, L11 + (size_t)j0 * M, M, c->sMM, 1.0,
+               A21 + j0, M, c->sMM);
+      Rec r(c, PC_TRSM, cmul(es) * 0.5 * jb * jb * rows * nk, (2.0 * rows * jb + 0.5 * jb * jb) * es * nk);
+      trsm_block<T>(TRSM_RIGHT_CONJ, L11 + (size_t)j0 * M + j0, M, c->sMM, A21 + j0, M, c->sMM, jb, rows, nk, s);
+    }
+    {
+      Rec r(c, PC_MISC);
+      copy2d<T>(FB, nbb, c->sFB, A11, M, c->sMM, KB, KB, nk, s);
+      mirror_lower<T>(FB, nbb, c->sFB, KB, nk, s);
+    }
+    gmx<T>(c, nk, OP_N, OP_N, rows, KB, KB, -0.5, L21, M, c->sMM, FB, nbb, c->sFB, 1.0, A21, M, c->sMM);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, KB, -1.0, L21, M, c->sMM, A21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, KB, -1.0, A21, M, c->sMM, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
+    gmx<T>(c, nk, OP_N, OP_N, rows, KB, KB, -0.5, L21, M, c->sMM, FB, nbb, c->sFB, 1.0, A21, M, c->sMM);
+  }
+  // deferred substitution over the outer-block-strictly-lower part
+  for (int R0 = nbb; R0 < M; R0 += nbb) {
+    const int RB = std::min(nbb, M - R0);
+    for (int r0 = R0; r0 < R0 + RB; r0 += NB) {
+      const int rb = std::min(NB, R0 + RB - r0);
+      T* Ai = A + (size_t)r0 * M;
+      {
+        Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * R0 * nk, (2.0 * R0 * rb + 0.5 * rb * rb) * es * nk);
+        trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * M + r0, M, c->sMM, Ai, M, c->sMM, rb, R0, nk, s);
+      }
+      const int below = R0 + RB - r0 - rb;
+      if (below > 0)
+        gmx<T>(c, nk, OP_N, OP_N, below, R0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM,
+               1.0, A + (size_t)(r0 + rb) * M, M, c->sMM);
+    }
+    const int below = M - R0 - RB;
+    if (below > 0)
+      gmx<T>(c, nk, OP_N, OP_N, below, R0, RB, -1.0, L + (size_t)(R0 + RB) * M + R0, M, c->sMM, A + (size_t)R0 * M,
+             M, c->sMM, 1.0, A + (size_t)(R0 + RB) * M, M, c->sMM);
   }
 }
 
@@ -415,10 +510,14 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   }
 }
 
-// X <- Q X with Q = P_{M-1} ... P_2 (reflectors stored by the reduction), blocked WY.
+// X <- Q X with Q = P_{M-1} ... P_2 (reflectors stored by the reduction), compact WY in
+// blocks of nbb reflectors: B = I - V T V^H.  T (upper triangular) is assembled from the
+// 64-wide diagonal blocks (larft on G = V^H V) by the merge
+//   T[:s, s:s+k] = -T[:s, :s] G[:s, s:s+k] T[s:s+k, s:s+k].
 template <typename T>
 void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
   cudaStream_t s = c->stream;
+  const int nbb = c->nbb;
   T* V = at<T>(c, c->oV);
   T* G = at<T>(c, c->oG);
   T* Tm = at<T>(c, c->oT);
@@ -426,38 +525,61 @@ void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
   T* Y2 = at<T>(c, c->oY2);
   double* tau = at<double>(c, c->otau);
   double* tb = at<double>(c, c->otb);
-  for (int j0 = 2; j0 <= M - 1; j0 += NB) {
-    const int j1 = std::min(j0 + NB - 1, M - 1), nbb = j1 - j0 + 1;
+  if (M < 3) return;
+  cudaMemsetAsync(Tm, 0, sizeof(T) * (size_t)c->sT * nk, s);
+  for (int j0 = 2; j0 <= M - 1; j0 += nbb) {
+    const int j1 = std::min(j0 + nbb - 1, M - 1), nbk = j1 - j0 + 1;
     {
       Rec r(c, PC_BACKTR_AUX);
-      gather_reflectors<T>(A, M, c->sMM, tau, M, j0, j1, V, NB, c->sV, tb, NB, nk, s);
+      gather_reflectors<T>(A, M, c->sMM, tau, M, j0, j1, V, nbb, c->sV, tb, nbb, nk, s);
     }
-    gmp<T>(c, nk, OP_C, OP_N, nbb, nbb, j1, 1.0, V, NB, c->sV, V, NB, c->sV, 0.0, G, NB, c->sG);
-    {
-      Rec r(c, PC_BACKTR_AUX);
-      larft<T>(G, NB, c->sG, tb, NB, nbb, Tm, NB, c->sT, nk, s);
+    gmx<T>(c, nk, OP_C, OP_N, nbk, nbk, j1, 1.0, V, nbb, c->sV, V, nbb, c->sV, 0.0, G, nbb, c->sG);
+    for (int s0 = 0; s0 < nbk; s0 += NB) {
+      const int ks = std::min(NB, nbk - s0);
+      {
+        Rec r(c, PC_BACKTR_AUX);
+        larft<T>(G + (size_t)s0 * nbb + s0, nbb, c->sG, tb + s0, nbb, ks, Tm + (size_t)s0 * nbb + s0, nbb, c->sT,
+                 nk, s);
+      }
+      if (s0 > 0) {
+        // P = G[:s0, s0:s0+ks] T_ss (P in Y2, ld NB), then T[:s0, s0:s0+ks] = -T[:s0, :s0] P
+        gmp<T>(c, nk, OP_N, OP_N, s0, ks, ks, 1.0, G + s0, nbb, c->sG, Tm + (size_t)s0 * nbb + s0, nbb, c->sT, 0.0,
+               Y2, NB, c->sY);
+        gmp<T>(c, nk, OP_N, OP_N, s0, ks, s0, -1.0, Tm, nbb, c->sT, Y2, NB, c->sY, 0.0, Tm + s0, nbb, c->sT);
+      }
     }
-    gmx<T>(c, nk, OP_C, OP_N, nbb, M, j1, 1.0, V, NB, c->sV, X, M, c->sMM, 0.0, Y, M, c->sY);
-    gmp<T>(c, nk, OP_N, OP_N, nbb, M, nbb, 1.0, Tm, NB, c->sT, Y, M, c->sY, 0.0, Y2, M, c->sY);
-    gmx<T>(c, nk, OP_N, OP_N, j1, M, nbb, -1.0, V, NB, c->sV, Y2, M, c->sY, 1.0, X, M, c->sMM);
+    gmx<T>(c, nk, OP_C, OP_N, nbk, M, j1, 1.0, V, nbb, c->sV, X, M, c->sMM, 0.0, Y, M, c->sY);
+    gmx<T>(c, nk, OP_N, OP_N, nbk, M, nbk, 1.0, Tm, nbb, c->sT, Y, M, c->sY, 0.0, Y2, M, c->sY);
+    gmx<T>(c, nk, OP_N, OP_N, j1, M, nbk, -1.0, V, nbb, c->sV, Y2, M, c->sY, 1.0, X, M, c->sMM);
   }
 }
 
-// X <- L^-H X by block back substitution (diagonal blocks by substitution).
+// X <- L^-H X by block back substitution, two levels: within an outer block of nbb rows,
+// 64-row diagonal blocks by substitution and updates of the rows of that outer block
+// only; then one K = nbb update of all rows above it.
 template <typename T>
 void unreduce_run(gks_ctx* c, const T* L, T* X, int M, int nk) {
   cudaStream_t s = c->stream;
   const int es = sizeof(T);
-  const int nblk = (M + NB - 1) / NB;
-  for (int blk = nblk - 1; blk >= 0; blk--) {
-    const int r0 = blk * NB, rb = std::min(NB, M - r0);
-    T* Xi = X + (size_t)r0 * M;
-    {
-      Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * M * nk, (2.0 * M * rb + 0.5 * rb * rb) * es * nk);
-      trsm_block<T>(TRSM_LEFT_CONJ, L + (size_t)r0 * M + r0, M, c->sMM, Xi, M, c->sMM, rb, M, nk, s);
+  const int nbb = c->nbb;
+  const int nob = (M + nbb - 1) / nbb;
+  for (int ob = nob - 1; ob >= 0; ob--) {
+    const int R0 = ob * nbb, RB = std::min(nbb, M - R0);
+    const int nib = (RB + NB - 1) / NB;
+    for (int ib = nib - 1; ib >= 0; ib--) {
+      const int r0 = R0 + ib * NB, rb = std::min(NB, R0 + RB - r0);
+      T* Xi = X + (size_t)r0 * M;
+      {
+        Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * M * nk, (2.0 * M * rb + 0.5 * rb * rb) * es * nk);
+        trsm_block<T>(TRSM_LEFT_CONJ, L + (size_t)r0 * M + r0, M, c->sMM, Xi, M, c->sMM, rb, M, nk, s);
+      }
+      if (r0 > R0)
+        gmx<T>(c, nk, OP_C, OP_N, r0 - R0, M, rb, -1.0, L + (size_t)r0 * M + R0, M, c->sMM, Xi, M, c->sMM, 1.0,
+               X + (size_t)R0 * M, M, c->sMM);
     }
-    if (r0 > 0)
-      gmx<T>(c, nk, OP_C, OP_N, r0, M, rb, -1.0, L + (size_t)r0 * M, M, c->sMM, Xi, M, c->sMM, 1.0, X, M, c->sMM);
+    if (R0 > 0)
+      gmx<T>(c, nk, OP_C, OP_N, R0, M, RB, -1.0, L + (size_t)R0 * M, M, c->sMM, X + (size_t)R0 * M, M, c->sMM, 1.0,
+             X, M, c->sMM);
   }
 }
 
@@ -731,7 +853,9 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     c->graph = opts->graph != 0;
     c->gemm_mode = opts->gemm;
     if (opts->slices > 0) c->slices = opts->slices;
-    if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 10) {
+    if (opts->block > 0) c->nbb = opts->block;
+    if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 10 || c->nbb < NB || c->nbb > 1024 ||
+        c->nbb % NB) {
       delete c;
       return GKS_EINVAL;
     }
@@ -829,6 +953,7 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     sc->f_cut = ctx->f_cut;
     sc->gemm_mode = ctx->gemm_mode;
     sc->slices = ctx->slices;
+    sc->nbb = ctx->nbb;
     ctx->subs.push_back(sc);
   }
   auto body = [&]() -> gks_status {
@@ -1014,13 +1139,13 @@ gks_status gks_gemm_split_noalloc(gks_ctx* ctx, int dtype, int opA, int opB, int
     return fail(ctx, GKS_ECUDA, std::string("gks_gemm_split_noalloc: scratch lookup: ") + cudaGetErrorString(e));
   }
   if (dtype == GKS_R64)
-    ozaki_gemm<double>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const double*>(A), (int)lda,
-                       static_cast<const double*>(B), (int)ldb, beta, static_cast<double*>(C), (int)ldc, 0,
+    ozaki_gemm<double>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const double*>(A), (int)lda, 0,
+                       static_cast<const double*>(B), (int)ldb, 0, beta, static_cast<double*>(C), (int)ldc, 0, 1, 0,
                        ctx->slices, scratch, ctx->stream);
   else
-    ozaki_gemm<zc>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const zc*>(A), (int)lda,
-                   static_cast<const zc*>(B), (int)ldb, beta, static_cast<zc*>(C), (int)ldc, 0, ctx->slices,
-                   scratch, ctx->stream);
+    ozaki_gemm<zc>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const zc*>(A), (int)lda, 0,
+                   static_cast<const zc*>(B), (int)ldb, 0, beta, static_cast<zc*>(C), (int)ldc, 0, 1, 0,
+                   ctx->slices, scratch, ctx->stream);
   return cuda_check(ctx, "gks_gemm_split_noalloc");
 }
 

@@ -73,10 +73,13 @@ template <typename T>
 void spin_block_sum(T* dst, long long sd, const T* src, long long ss, int n, int nk, cudaStream_t s);
 
 // ---- FP64-accurate GEMM from exact bf16 digit products (ozaki.cu) ----
+// Workspace bytes per batch item (a multiple of 256), and output tiles per item.
 size_t ozaki_workspace_bytes(int M, int N, int K, bool cplx, int S);
+int ozaki_tiles(int M, int N, bool cplx);
 template <typename T>
-void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, const T* B, int ldb,
-                double beta, T* C, int ldc, int lower, int S, void* work, cudaStream_t s);
+void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
+                int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
+                void* work, cudaStream_t s);
 
 // ---- occupations (occ.cu) ----
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,

@@ -89,12 +89,17 @@ __device__ __forceinline__ void emit<zc>(zc x, int e, int role, int v, int k, __
 // One CTA (256 threads) per 32 vectors.  Pass 1: per-vector max (thread per vector when the
 // vector index is the contiguous direction, else a warp sweeps each vector along k).
 // Pass 2: digits.  Padding vectors and k beyond K are written as zero digits elsewhere.
+// blockIdx.y runs over the batch items (strides sX, sD, sE).
 template <typename T>
-__global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, int role, int op, int nvec, int K,
-                                                       __nv_bfloat16* D, int Kp, long long sstride, int S, int* ex) {
+__global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long long sX, int role, int op, int nvec,
+                                                       int K, __nv_bfloat16* D, int Kp, long long sstride,
+                                                       long long sD, int S, int* ex, long long sE) {
   __shared__ double smax[32];
   __shared__ int sexp[32];
   const int v0 = blockIdx.x * 32, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  X += blockIdx.y * sX;
+  D += blockIdx.y * sD;
+  ex += blockIdx.y * sE;
   const bool contig = (role == 0) == (op == OP_N);  // k contiguous in memory
   if (contig) {
     for (int vv = warp; vv < 32; vv += 8) {
@@ -193,6 +198,7 @@ struct OzArgs {
   int cplx, lower;
   double alpha, beta;
   long long sAd, sBd;       // slice strides (elements)
+  long long zAd, zBd, zE, zC;  // batch item strides of the digits, exponents and C
 };
 
 static constexpr int OZ_BM = 128, OZ_BN = 128, OZ_LDS = OZ_KSTEP + 8, OZ_STAGES = 2;
@@ -206,6 +212,14 @@ __global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, warp tile 64 x 32
   const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
+  {
+    const long long z = blockIdx.z;
+    a.Ad += z * a.zAd;
+    a.Bd += z * a.zBd;
+    a.ea += z * a.zE;
+    a.eb += z * a.zE;
+    a.C = static_cast<char*>(a.C) + z * a.zC * (a.cplx ? 16 : 8);
+  }
   // lower triangle of the logical output: skip tiles strictly above the diagonal
   const int ncol0 = a.cplx ? n0 / 2 : n0;
   if (a.lower && m0 + OZ_BM - 1 < ncol0) return;
@@ -357,30 +371,41 @@ static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 size_t ozaki_workspace_bytes(int M, int N, int K, bool cplx, int S) {
   const int Kp = round_up(cplx ? 2 * K : K, OZ_KSTEP);
   const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
-  return (size_t)S * ((size_t)Mp + Np) * Kp * 2 + sizeof(int) * ((size_t)Mp + Np) + 1024;
+  const size_t b = (size_t)S * ((size_t)Mp + Np) * Kp * 2 + sizeof(int) * ((size_t)Mp + Np) + 1024;
+  return (b + 255) & ~size_t(255);
 }
 
+int ozaki_tiles(int M, int N, bool cplx) {
+  return (round_up(M, OZ_BM) / OZ_BM) * (round_up(cplx ? 2 * N : N, OZ_BN) / OZ_BN);
+}
+
+// count items, item z at A + z sA, B + z sB, C + z sC; work holds count workspaces of
+// ozaki_workspace_bytes each.
 template <typename T>
-void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, const T* B, int ldb,
-                double beta, T* C, int ldc, int lower, int S, void* work, cudaStream_t s) {
-  if (M <= 0 || N <= 0) return;
+void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
+                int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
+                void* work, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || count <= 0) return;
   const bool cplx = sizeof(T) == 16;
   const int Ke = cplx ? 2 * K : K;
   const int Kp = round_up(Ke > 0 ? Ke : 1, OZ_KSTEP);
   const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
+  const size_t item = ozaki_workspace_bytes(M, N, K, cplx, S);
+  // per item: A digits [S][Mp][Kp], B digits [S][Np][Kp], then Mp + Np exponents
   __nv_bfloat16* Ad = static_cast<__nv_bfloat16*>(work);
   __nv_bfloat16* Bd = Ad + (size_t)S * Mp * Kp;
   int* ea = reinterpret_cast<int*>(Bd + (size_t)S * Np * Kp);
   int* eb = ea + Mp;
-  // zero digits (padding rows/columns and k beyond K stay zero)
-  cudaMemsetAsync(Ad, 0, (size_t)S * ((size_t)Mp + Np) * Kp * 2, s);
+  const long long zD = (long long)(item / 2), zE = (long long)(item / sizeof(int));
+  // zero digits and exponents (padding rows/columns and k beyond K stay zero)
+  cudaMemsetAsync(work, 0, item * count, s);
   if (K > 0) {
     count_launch();
-    oz_split_kernel<T><<<(M + 31) / 32, 256, 0, s>>>(A, lda, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, S, ea);
+    oz_split_kernel<T><<<dim3((M + 31) / 32, count), 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp,
+                                                                   (long long)Mp * Kp, zD, S, ea, zE);
     count_launch();
-    oz_split_kernel<T><<<(N + 31) / 32, 256, 0, s>>>(B, ldb, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, S, eb);
-  } else {
-    cudaMemsetAsync(ea, 0, sizeof(int) * ((size_t)Mp + Np), s);
+    oz_split_kernel<T><<<dim3((N + 31) / 32, count), 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp,
+                                                                   (long long)Np * Kp, zD, S, eb, zE);
   }
   OzArgs oa;
   oa.Ad = Ad;
@@ -401,15 +426,19 @@ void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   oa.beta = beta;
   oa.sAd = (long long)Mp * Kp;
   oa.sBd = (long long)Np * Kp;
+  oa.zAd = zD;
+  oa.zBd = zD;
+  oa.zE = zE;
+  oa.zC = sC;
   cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-  dim3 grid(Np / OZ_BN, Mp / OZ_BM);
+  dim3 grid(Np / OZ_BN, Mp / OZ_BM, count);
   count_launch();
   oz_gemm_kernel<<<grid, 256, OZ_SMEM, s>>>(oa);
 }
 
-template void ozaki_gemm<double>(int, int, int, int, int, double, const double*, int, const double*, int, double,
-                                 double*, int, int, int, void*, cudaStream_t);
-template void ozaki_gemm<zc>(int, int, int, int, int, double, const zc*, int, const zc*, int, double, zc*, int, int,
-                             int, void*, cudaStream_t);
+template void ozaki_gemm<double>(int, int, int, int, int, double, const double*, int, long long, const double*, int,
+                                 long long, double, double*, int, long long, int, int, int, void*, cudaStream_t);
+template void ozaki_gemm<zc>(int, int, int, int, int, double, const zc*, int, long long, const zc*, int, long long,
+                             double, zc*, int, long long, int, int, int, void*, cudaStream_t);
 
 }  // namespace gks

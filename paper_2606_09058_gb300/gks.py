@@ -31,7 +31,7 @@ class GKSError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("f_cut", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int),
-                ("gemm", ctypes.c_int), ("slices", ctypes.c_int)]
+                ("gemm", ctypes.c_int), ("slices", ctypes.c_int), ("block", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -114,7 +114,8 @@ class Context:
     """A gks context bound to one device and one CUDA stream."""
 
     def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None, f_cut: float = 1e-16,
-                 profile: bool = False, graph: bool = False, gemm: str = "auto", slices: int = 0):
+                 profile: bool = False, graph: bool = False, gemm: str = "auto", slices: int = 0,
+                 block: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("gks needs a CUDA device")
         lib = load()
@@ -122,7 +123,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         gm = {"auto": 0, "fp64": 1, "split": 2}[gemm]
         opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), 0, f_cut, 1 if profile else 0,
-                     1 if graph else 0, gm, int(slices))
+                     1 if graph else 0, gm, int(slices), int(block))
         h = ctypes.c_void_p()
         rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
         if rc:

@@ -226,3 +226,32 @@ def test_solve_reports_not_positive_definite(ctx):
     # the context stays usable
     H2, S2 = I.chain(80, 0.0, -1.0)
     ctx.solve(_cuda(H2), _cuda(S2), 0.01, 10.0)
+
+
+# ------------------------------------------------------------------ outer block widths
+
+@pytest.fixture(scope="module", params=[64, 128, 192, 512])
+def ctx_block(request, ctx):
+    from paper_2606_09058_gb300 import gks
+    return gks.Context(0, block=request.param)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_blocked_potrf_and_reduce_outer_widths(ctx_block, cplx):
+    """Two-level Cholesky and reduction with several outer panels and a ragged tail."""
+    m = 461
+    H, S = I.random_pencil(m, 500 + cplx, cplx, cond=1e3)
+    L = ctx_block.potrf(_cuda(S)).cpu().numpy()[0]
+    Lr = O.cholesky(S)
+    assert np.abs(np.tril(L) - Lr).max() <= 1e-11 * max(1.0, np.abs(Lr).max())
+    Hd, _ = ctx_block.reduce(_cuda(H), _cuda(S))
+    ref = O.reduce_standard(Lr, H)
+    assert np.abs(np.tril(Hd.cpu().numpy()[0]) - np.tril(ref)).max() <= 1e-12 * m * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_blocked_solve_outer_widths(ctx_block, cplx):
+    """Full solve (two-level back-transforms included) for each outer width."""
+    m = 389
+    H, S = I.random_pencil(m, 600 + cplx, cplx, cond=1e2)
+    _compare(ctx_block, H[None], S[None], 0.1, 0.6 * m, raw=True)
