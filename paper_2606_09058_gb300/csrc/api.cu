@@ -26,7 +26,7 @@ struct Arena {
 }  // namespace
 
 namespace {
-const char* kClassNames[PC_NCLASS] = {"gemm", "potf2", "trsm_block", "hegst_diag", "hetrd_hemv", "hetrd_rank2",
+const char* kClassNames[PC_NCLASS] = {"gemm", "potf2", "trsm_block", "hegst_diag", "hetrd_hemv", "hetrd_update",
                                       "hetrd_vec", "dc_leaf", "dc_secular", "dc_gemm", "backtr_aux",
                                       "occupations", "misc", "split_gemm"};
 const char* kStageNames[PS_NSTAGE] = {"stage:copy", "stage:potrf", "stage:hegst", "stage:hetrd", "stage:stedc",
@@ -108,9 +108,9 @@ struct gks_ctx {
   size_t aws_bytes = 0;
   int am = -1, ank = -1, aes = -1;
   // offsets (bytes) of per-item arrays; each holds nk items
-  size_t oA, oL, oF, oFB, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
+  size_t oA, oL, oF, oFB, oU, oQ, opart, oy, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
       oticket;
-  long long sMM, sF, sFB, sV, sG, sT, sY, sVec;
+  long long sMM, sF, sFB, sU, spart, sy, sV, sG, sT, sY, sVec;
 };
 
 namespace {
@@ -172,6 +172,9 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->sG = (long long)nbb * nbb;
   c->sT = (long long)nbb * nbb;
   c->sY = (long long)nbb * m;
+  c->sU = (long long)m * nbb;
+  c->spart = (long long)((m + 63) / 64) * (2 * nbb + 2);
+  c->sy = 2 * nbb + 2;
   c->sVec = m;
   Arena a;
   auto elems = [&](long long per) { return (size_t)per * nk * es; };
@@ -179,6 +182,10 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->oL = a.take<char>(elems(c->sMM));
   c->oF = a.take<char>(elems(c->sF));
   c->oFB = a.take<char>(elems(c->sFB));
+  c->oU = a.take<char>(elems(c->sU));
+  c->oQ = a.take<char>(elems(c->sU));
+  c->opart = a.take<char>(elems(c->spart));
+  c->oy = a.take<char>(elems(c->sy));
   c->oV = a.take<char>(elems(c->sV));
   c->oG = a.take<char>(elems(c->sG));
   c->oT = a.take<char>(elems(c->sT));
@@ -482,31 +489,51 @@ void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
   }
 }
 
-// One-stage Householder tridiagonalization, steps j = M-1 .. 2 (two launches per step).
+// One-stage Householder tridiagonalization, steps j = M-1 .. 2, in panels of nbb steps.
+// Each step is two launches (the Hermitian product over the stale trailing block with the
+// panel's corrections, then q, the panel buffers and the next row); each panel ends with
+// the deferred update A[0:j,0:j] -= U Q^H + Q U^H as two lower-triangle GEMMs with K = the
+// panel's step count.
 template <typename T>
 void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   cudaStream_t s = c->stream;
   const int es = sizeof(T);
+  const int ldu = c->nbb;
   T* u = at<T>(c, c->ou);
   T* p = at<T>(c, c->op);
+  T* U = at<T>(c, c->oU);
+  T* Q = at<T>(c, c->oQ);
+  T* part = at<T>(c, c->opart);
+  T* y = at<T>(c, c->oy);
   double* tau = at<double>(c, c->otau);
   int* tk = at<int>(c, c->oticket);
   if (M < 3) return;
   cudaMemsetAsync(tk, 0, sizeof(int) * 2 * nk, s);
-  {
-    Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * es * (M - 1) * nk);
-    hetrd_reflector<T>(A, M, c->sMM, M - 1, u, c->sVec, tau, M, nk, s);
-  }
-  for (int j = M - 1; j >= 2; j--) {
-    const double jj = (double)j * j;
+  for (int jh = M - 1; jh >= 2; jh -= ldu) {
+    const int jl = std::max(2, jh - ldu + 1);  // steps jh .. jl in this panel
     {
-      Rec r(c, PC_HETRD_HEMV, cmul(es) * jj * nk, (0.5 * jj + 4.0 * j) * es * nk);
-      hetrd_hemv<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, tk, nk, s);
+      Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * es * jh * nk);
+      hetrd_reflector<T>(A, M, c->sMM, jh, u, c->sVec, tau, M, nk, s);
     }
-    {
-      Rec r(c, PC_HETRD_RANK2, cmul(es) * jj * nk, (jj + 2.0 * j) * es * nk);
-      hetrd_rank2<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, tk + nk, nk, s);
+    for (int j = jh; j >= jl; j--) {
+      const int k = jh - j;  // panel steps already taken
+      const double jj = (double)j * j;
+      {
+        Rec r(c, PC_HETRD_HEMV, cmul(es) * (jj + 2.0 * j * k) * nk, (0.5 * jj + 2.0 * j * k + 4.0 * j) * es * nk);
+        hetrd_phemv<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, U, Q, ldu, c->sU, k, part, c->spart, y, c->sy, tk,
+                       nk, s);
+      }
+      const int rowupd = (j > jl) ? 1 : 0;
+      {
+        Rec r(c, PC_HETRD_RANK2, cmul(es) * 2.0 * j * (k + 1) * (1 + rowupd) * nk, (2.0 * j * (k + 1) + 4.0 * j) * es * nk);
+        hetrd_pupdate<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, U, Q, ldu, c->sU, k, y, c->sy, rowupd, tk + nk, nk,
+                         s);
+      }
     }
+    // deferred rank-2k update of the trailing block [0:jl, 0:jl]
+    const int kp = jh - jl + 1;
+    gmx<T>(c, nk, OP_N, OP_C, jl, jl, kp, -1.0, U, ldu, c->sU, Q, ldu, c->sU, 1.0, A, M, c->sMM, 1);
+    gmx<T>(c, nk, OP_N, OP_C, jl, jl, kp, -1.0, Q, ldu, c->sU, U, ldu, c->sU, 1.0, A, M, c->sMM, 1);
   }
 }
 

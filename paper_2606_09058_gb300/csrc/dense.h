@@ -29,18 +29,21 @@ template <typename T>
 void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int n, int count, cudaStream_t s);
 
 // ---- Householder tridiagonalization (hetrd.cu) ----
-// Workspace per batch item: u (m), p (m) vectors, tau (m), two zeroed tickets.  Step j is
-// hetrd_hemv (ending in the q update) and hetrd_rank2 (ending in the reflector of step
-// j-1); hetrd_reflector starts the sweep at j = m-1.
+// Workspace per batch item: u (m), p (m) vectors, tau (m), two zeroed tickets, and for the
+// panel form U, Q (m x ldu), per-CTA shares (ceil(m/64) x (2 ldu + 2)) and y (2 ldu + 2).
+// hetrd_reflector starts a panel at step j; step j is hetrd_phemv then hetrd_pupdate (which
+// with rowupd also forms the reflector of step j-1).
 template <typename T>
 void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau, long long stau, int count,
                      cudaStream_t s);
 template <typename T>
-void hetrd_hemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
-                long long stau, int* ticket, int count, cudaStream_t s);
+void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
+                 long long stau, const T* U, const T* Q, int ldu, long long sU, int k, T* part, long long spart,
+                 T* y, long long sy, int* ticket, int count, cudaStream_t s);
 template <typename T>
-void hetrd_rank2(T* A, int lda, long long sA, int j, T* u, const T* q, long long sv, double* tau, long long stau,
-                 int* ticket, int count, cudaStream_t s);
+void hetrd_pupdate(T* A, int lda, long long sA, int j, T* u, const T* p, long long sv, double* tau, long long stau,
+                   T* U, T* Q, int ldu, long long sU, int k, const T* y, long long sy, int rowupd, int* ticket,
+                   int count, cudaStream_t s);
 template <typename T>
 void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e, long long sde, T* ph,
                   long long sph, int count, cudaStream_t s);

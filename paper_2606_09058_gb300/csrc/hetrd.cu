@@ -12,7 +12,9 @@
 //
 // On GB300 the Hermitian matrix-vector product that dominates each step is bound by the
 // FP64 pipe, not by HBM: a complex element read once feeds two complex multiply-adds
-// (16 flops per 16 bytes), above the DFMA pipe's balance point of ~0.15 flop/byte.
+// (16 flops per 16 bytes), above the DFMA pipe's balance point of ~0.15 flop/byte.  The
+// rank-2 updates are therefore deferred over panels of steps and applied as GEMMs (the
+// panel form below), which the product dispatcher can send to the tensor cores.
 #include "dense.h"
 
 namespace gks {
@@ -60,16 +62,28 @@ __global__ void hetrd_reflector_kernel(T* A, int lda, long long sA, int j, T* u,
   reflector_body<T>(A + z * sA, lda, j, u + z * sv, tau + z * stau);
 }
 
-// p = tau * A[0:j,0:j] u  (Hermitian, lower storage).  CTA b owns rows/columns
-// [64b, 64b+64): its own row panel left of the diagonal plus its column panel below,
-// so every CTA reads the same number of elements and no cross-CTA reduction is needed.
-// The last CTA to finish (atomic ticket after a fence; nothing waits) then forms
-// q = p - (tau/2)(u^H p) u in place of p.
+// Panel (blocked) form.  A panel of steps keeps the trailing block A[0:j,0:j] as it was
+// at the panel's start; the panel buffers U and Q (M x ldu per item, row r holds u_s[r]
+// and q_s[r] for the panel's earlier steps s < k) carry what it has not seen yet:
+//   A_true = A - U Q^H - Q U^H   on [0:j, 0:j].
+// The panel ends with that rank-2k update as two GEMMs.
+//
+// Step j, first half: p_raw = A[0:j,0:j] u over the stale block.  CTA b owns rows/columns
+// [64b, 64b+64): its row panel left of the diagonal plus its column panel below, so every
+// CTA reads the same number of elements.  It adds its rows' shares of Q^H u, U^H u and
+// u^H p_raw.  The last CTA (atomic ticket after a fence; nothing waits) sums the shares:
+//   y1 = Q^H u,  y2 = U^H u,  u^H p = tau (u^H p_raw - y2^H y1 - y1^H y2),
+//   kq = (tau/2) u^H p,
+// since p = tau A_true u = tau (p_raw - U y1 - Q y2).
+// y layout per item: y1 at [0, k), y2 at [ldu, ldu + k), u^H p_raw at 2 ldu, kq at 2 ldu + 1;
+// the shares use the same layout per CTA with stride 2 ldu + 2.
 template <typename T>
-__global__ void __launch_bounds__(256) hetrd_hemv_kernel(const T* A, int lda, long long sA, int j, const T* u,
-                                                         T* p, long long sv, const double* tau, long long stau,
-                                                         int* ticket) {
-  __shared__ T part[4][64];
+__global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, long long sA, int j, const T* u,
+                                                          T* p, long long sv, const double* tau, long long stau,
+                                                          const T* U, const T* Q, int ldu, long long sU, int k,
+                                                          T* part, long long spart, T* y, long long sy,
+                                                          int* ticket) {
+  __shared__ T colpart[4][64];
   __shared__ T rowacc[64];
   __shared__ T red[32];
   __shared__ int last;
@@ -77,10 +91,15 @@ __global__ void __launch_bounds__(256) hetrd_hemv_kernel(const T* A, int lda, lo
   A += z * sA;
   u += z * sv;
   p += z * sv;
+  U += z * sU;
+  Q += z * sU;
+  part += z * spart;
+  y += z * sy;
   const double t = tau[z * stau + j];
   const int c0 = blockIdx.x * 64;
   const int cend = min(c0 + 64, j);
-  // row part: rows r in [c0, cend), columns 0..r ; one warp per row
+  const int pst = 2 * ldu + 2;
+  // row part: rows r in [c0, cend), columns 0..r; one warp per row
   const int warp = tid >> 5, lane = tid & 31;
   for (int r = c0 + warp; r < cend; r += 8) {
     const T* ar = A + (size_t)r * lda;
@@ -90,18 +109,35 @@ __global__ void __launch_bounds__(256) hetrd_hemv_kernel(const T* A, int lda, lo
     if (lane == 0) rowacc[r - c0] = s;
   }
   // column part: columns c in [c0, cend), rows r > c
-  const int cc = tid & 63, g = tid >> 6;
-  const int c = c0 + cc;
-  T s = zero<T>();
-  if (c < cend) {
-    for (int r = c0 + g; r < j; r += 4)
-      if (r > c) macc(s, A[(size_t)r * lda + c], u[r]);
+  {
+    const int cc = tid & 63, g = tid >> 6;
+    const int c = c0 + cc;
+    T s = zero<T>();
+    if (c < cend) {
+      for (int r = c0 + g; r < j; r += 4)
+        if (r > c) macc(s, A[(size_t)r * lda + c], u[r]);
+    }
+    colpart[g][cc] = s;
   }
-  part[g][cc] = s;
   __syncthreads();
+  T d0 = zero<T>();
   if (tid < 64 && c0 + tid < cend) {
-    T y = rowacc[tid] + part[0][tid] + part[1][tid] + part[2][tid] + part[3][tid];
-    p[c0 + tid] = t * y;
+    const T pr = rowacc[tid] + colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
+    p[c0 + tid] = pr;
+    macc(d0, u[c0 + tid], pr);
+  }
+  d0 = block_sum(d0, red);
+  T* mine = part + (size_t)blockIdx.x * pst;
+  if (tid == 0) mine[2 * ldu] = d0;
+  for (int s = tid; s < k; s += blockDim.x) {
+    T a1 = zero<T>(), a2 = zero<T>();
+    for (int r = c0; r < cend; r++) {
+      const T ur = u[r];
+      macc(a1, Q[(size_t)r * ldu + s], ur);
+      macc(a2, U[(size_t)r * ldu + s], ur);
+    }
+    mine[s] = a1;
+    mine[ldu + s] = a2;
   }
   __threadfence();
   __syncthreads();
@@ -109,40 +145,119 @@ __global__ void __launch_bounds__(256) hetrd_hemv_kernel(const T* A, int lda, lo
   __syncthreads();
   if (!last) return;
   if (tid == 0) ticket[z] = 0;
-  T d = zero<T>();
-  for (int i = tid; i < j; i += blockDim.x) macc(d, u[i], ldcg(p + i));
-  d = block_sum(d, red);
-  const T K = (0.5 * t) * d;
-  for (int i = tid; i < j; i += blockDim.x) p[i] = ldcg(p + i) - K * u[i];
+  const int nb = gridDim.x;
+  for (int e = tid; e < k; e += blockDim.x) {
+    T a1 = zero<T>(), a2 = zero<T>();
+    for (int b = 0; b < nb; b++) {
+      a1 += ldcg(part + (size_t)b * pst + e);
+      a2 += ldcg(part + (size_t)b * pst + ldu + e);
+    }
+    y[e] = a1;
+    y[ldu + e] = a2;
+  }
+  T tot = zero<T>();
+  if (tid == 0)
+    for (int b = 0; b < nb; b++) tot += ldcg(part + (size_t)b * pst + 2 * ldu);
+  __syncthreads();
+  T w = zero<T>();
+  for (int e = tid; e < k; e += blockDim.x) {
+    macc(w, y[ldu + e], y[e]);
+    macc(w, y[e], y[ldu + e]);
+  }
+  w = block_sum(w, red);
+  if (tid == 0) {
+    const T uhp = t * (tot - w);
+    y[2 * ldu] = tot;
+    y[2 * ldu + 1] = (0.5 * t) * uhp;
+  }
 }
 
-// A[0:j,0:j] (lower) -= u q^H + q u^H, one CTA per row; the last CTA of each batch item
-// then computes the reflector of step j-1 from the freshly updated row j-1.
+// Step j, second half: q = tau (p_raw - U y1 - Q y2) - kq u for the rows of this CTA (64
+// per CTA), stored with u as column k of Q and U.  With rowupd, row j-1 of A (columns
+// 0..j-1) receives the panel's updates so far,
+//   A[j-1][c] -= sum_{s<=k} U[j-1][s] conj(Q[c][s]) + Q[j-1][s] conj(U[c][s]),
+// (each CTA computes the single q_k[j-1] it needs itself), and the last CTA forms the
+// reflector of step j-1 from that row.  Dynamic shared memory: 4 (ldu + 1) elements.
 template <typename T>
-__global__ void hetrd_rank2_kernel(T* A, int lda, long long sA, int j, T* u, const T* q, long long sv,
-                                   double* tau, long long stau, int* ticket) {
+__global__ void __launch_bounds__(256) hetrd_pupdate_kernel(T* A, int lda, long long sA, int j, T* u,
+                                                            const T* p, long long sv, double* tau, long long stau,
+                                                            T* U, T* Q, int ldu, long long sU, int k, const T* y,
+                                                            long long sy, int rowupd, int* ticket) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* y1s = reinterpret_cast<T*>(smem_raw);
+  T* y2s = y1s + (ldu + 1);
+  T* ujs = y2s + (ldu + 1);
+  T* qjs = ujs + (ldu + 1);
   __shared__ int last;
-  const int z = blockIdx.y, r = blockIdx.x;
+  const int z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   A += z * sA;
   u += z * sv;
-  q += z * sv;
+  p += z * sv;
+  U += z * sU;
+  Q += z * sU;
+  y += z * sy;
   tau += z * stau;
-  if (tau[j] != 0.0) {
-    const T ur = u[r], qr = q[r];
-    T* ar = A + (size_t)r * lda;
-    for (int c = threadIdx.x; c <= r; c += blockDim.x) {
-      T v = ar[c];
-      v -= ur * conjg(q[c]) + qr * conjg(u[c]);
-      ar[c] = v;
+  const double t = tau[j];
+  const T kq = y[2 * ldu + 1];
+  for (int s = tid; s < k; s += blockDim.x) {
+    y1s[s] = y[s];
+    y2s[s] = y[ldu + s];
+    if (rowupd) {
+      ujs[s] = U[(size_t)(j - 1) * ldu + s];
+      qjs[s] = Q[(size_t)(j - 1) * ldu + s];
     }
   }
-  if (j - 1 < 2) return;
+  __syncthreads();
+  if (rowupd && warp == 0) {
+    T corr = zero<T>();
+    for (int s = lane; s < k; s += 32) {
+      mac(corr, ujs[s], y1s[s]);
+      mac(corr, qjs[s], y2s[s]);
+    }
+    corr = warp_sum(corr);
+    if (lane == 0) {
+      const T uj = u[j - 1];
+      ujs[k] = uj;
+      qjs[k] = t * (p[j - 1] - corr) - kq * uj;
+    }
+  }
+  __syncthreads();
+  const int c0 = blockIdx.x * 64, cend = min(c0 + 64, j);
+  for (int c = c0 + warp; c < cend; c += 8) {
+    const T* Uc = U + (size_t)c * ldu;
+    const T* Qc = Q + (size_t)c * ldu;
+    T corr = zero<T>(), rs = zero<T>();
+    for (int s = lane; s < k; s += 32) {
+      const T uc = Uc[s], qc = Qc[s];
+      mac(corr, uc, y1s[s]);
+      mac(corr, qc, y2s[s]);
+      if (rowupd) {
+        mac(rs, ujs[s], conjg(qc));
+        mac(rs, qjs[s], conjg(uc));
+      }
+    }
+    corr = warp_sum(corr);
+    if (rowupd) rs = warp_sum(rs);
+    if (lane == 0) {
+      const T uc = u[c];
+      const T qc = t * (p[c] - corr) - kq * uc;
+      U[(size_t)c * ldu + k] = uc;
+      Q[(size_t)c * ldu + k] = qc;
+      if (rowupd) {
+        mac(rs, ujs[k], conjg(qc));
+        mac(rs, qjs[k], conjg(uc));
+        T* a = A + (size_t)(j - 1) * lda + c;
+        *a = *a - rs;
+      }
+    }
+  }
+  if (!rowupd) return;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ticket + z, 1) == (int)gridDim.x - 1);
+  if (tid == 0) last = (atomicAdd(ticket + z, 1) == (int)gridDim.x - 1);
   __syncthreads();
   if (!last) return;
-  if (threadIdx.x == 0) ticket[z] = 0;
+  if (tid == 0) ticket[z] = 0;
   __syncthreads();
   reflector_body<T>(A, lda, j - 1, u, tau);
 }
@@ -201,17 +316,23 @@ void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, dou
 }
 
 template <typename T>
-void hetrd_hemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
-                long long stau, int* ticket, int count, cudaStream_t s) {
+void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
+                 long long stau, const T* U, const T* Q, int ldu, long long sU, int k, T* part, long long spart,
+                 T* y, long long sy, int* ticket, int count, cudaStream_t s) {
   count_launch();
-  hetrd_hemv_kernel<T><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, ticket);
+  hetrd_phemv_kernel<T><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q, ldu,
+                                                                   sU, k, part, spart, y, sy, ticket);
 }
 
 template <typename T>
-void hetrd_rank2(T* A, int lda, long long sA, int j, T* u, const T* q, long long sv, double* tau, long long stau,
-                 int* ticket, int count, cudaStream_t s) {
+void hetrd_pupdate(T* A, int lda, long long sA, int j, T* u, const T* p, long long sv, double* tau, long long stau,
+                   T* U, T* Q, int ldu, long long sU, int k, const T* y, long long sy, int rowupd, int* ticket,
+                   int count, cudaStream_t s) {
+  const int sm = (int)(4 * sizeof(T) * (ldu + 1));
+  if (sm > 48 * 1024) cudaFuncSetAttribute(hetrd_pupdate_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   count_launch();
-  hetrd_rank2_kernel<T><<<dim3(j, count), 256, 0, s>>>(A, lda, sA, j, u, q, sv, tau, stau, ticket);
+  hetrd_pupdate_kernel<T><<<dim3((j + 63) / 64, count), 256, sm, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q, ldu,
+                                                                      sU, k, y, sy, rowupd, ticket);
 }
 
 template <typename T>
@@ -232,10 +353,11 @@ void gather_reflectors(const T* A, int lda, long long sA, const double* tau, lon
 #define INST(T)                                                                                            \
   template void hetrd_reflector<T>(T*, int, long long, int, T*, long long, double*, long long, int,         \
                                    cudaStream_t);                                                          \
-  template void hetrd_hemv<T>(const T*, int, long long, int, const T*, T*, long long, const double*,         \
-                              long long, int*, int, cudaStream_t);                                         \
-  template void hetrd_rank2<T>(T*, int, long long, int, T*, const T*, long long, double*, long long, int*,   \
-                               int, cudaStream_t);                                                         \
+  template void hetrd_phemv<T>(const T*, int, long long, int, const T*, T*, long long, const double*,        \
+                               long long, const T*, const T*, int, long long, int, T*, long long, T*, long long, \
+                               int*, int, cudaStream_t);                                                   \
+  template void hetrd_pupdate<T>(T*, int, long long, int, T*, const T*, long long, double*, long long, T*,  \
+                                 T*, int, long long, int, const T*, long long, int, int*, int, cudaStream_t); \
   template void hetrd_finish<T>(const T*, int, long long, int, double*, double*, long long, T*, long long,   \
                                 int, cudaStream_t);                                                        \
   template void gather_reflectors<T>(const T*, int, long long, const double*, long long, int, int, T*, int, \
