@@ -304,20 +304,9 @@ double cmul(int es) { return es == 16 ? 8.0 : 2.0; }
 // launches whose digit workspace stays within kOzCap bytes.
 constexpr size_t kOzCap = (size_t)12 << 30;
 
-template <typename T>
-void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA,
-         const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC, int lower = 0) {
-  if (M <= 0 || N <= 0) return;
-  const int es = sizeof(T);
-  const double fl = gemm_flops(es, M, N, K, lower, count);
-  const bool big = fl >= 5e8 * count && M >= 256 && N >= 256 && K >= 256 &&
-                   (long long)ozaki_tiles(M, N, es == 16) * count >= 152;
-  const bool split = c->gemm_mode == 2 || (c->gemm_mode == 0 && big);
-  if (!split) {
-    gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
-    return;
-  }
-  const size_t item = ozaki_workspace_bytes(M, N, K, es == 16, c->slices);
+// Digit workspace for split products of `count` items of `item` bytes each: items per
+// launch (within kOzCap), growing the buffer when needed; 0 if it cannot be allocated.
+int oz_reserve(gks_ctx* c, size_t item, int count) {
   const int maxper = (int)std::max<size_t>(1, std::min<size_t>((size_t)count, kOzCap / item));
   const int nch = (count + maxper - 1) / maxper, per = (count + nch - 1) / nch;
   const size_t need = item * per;
@@ -327,17 +316,75 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
     if (cudaMalloc(&c->oz, need) != cudaSuccess) {
       cudaGetLastError();
       c->oz = nullptr;
-      gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
-      return;
+      return 0;
     }
     c->oz_bytes = need;
+  }
+  return per;
+}
+
+bool split_worth(gks_ctx* c, int count, int M, int N, int K, int es, double fl) {
+  if (c->gemm_mode == 2) return true;
+  return c->gemm_mode == 0 && fl >= 5e8 * count && M >= 128 && N >= 128 && K >= 64 &&
+         (long long)ozaki_tiles(M, N, es == 16) * count >= 152;
+}
+
+template <typename T>
+void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA,
+         const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC, int lower = 0) {
+  if (M <= 0 || N <= 0) return;
+  const int es = sizeof(T);
+  const double fl = gemm_flops(es, M, N, K, lower, count);
+  const int per = split_worth(c, count, M, N, K, es, fl)
+                      ? oz_reserve(c, ozaki_workspace_bytes(M, N, K, es == 16, c->slices), count)
+                      : 0;
+  if (per == 0) {
+    gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
+    return;
   }
   Rec r(c, PC_OZAKI, fl, gemm_bytes(es, M, N, K, lower, count, beta != 0.0));
   for (int z0 = 0; z0 < count; z0 += per) {
     const int cnt = std::min(per, count - z0);
-    ozaki_gemm<T>(opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc, sC,
-                  cnt, lower, c->slices, c->oz, c->stream);
+    if (!ozaki_gemm<T>(opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc,
+                       sC, cnt, lower, c->slices, c->oz, c->st, c->stream))
+      gmp<T>(c, cnt, opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc, sC,
+             lower);
   }
+}
+
+// rho_k = C_k diag(ks_k) C_k^H over the leading n_rho(k) columns (n_rho read on the device),
+// lower triangle.  Split products take K = M with the device count cutting the digits and
+// the k loop; the DFMA kernel reads the same count.
+template <typename T>
+void rho_run(gks_ctx* c, const T* C, T* rho, const double* ks, const int* nrho, int M, int nk) {
+  const int es = sizeof(T);
+  const int per = split_worth(c, nk, M, M, M, es, gemm_flops(es, M, M, M / 4, 1, nk))
+                      ? oz_reserve(c, ozaki_workspace_bytes(M, M, M, es == 16, c->slices), nk)
+                      : 0;
+  int z0 = 0;
+  for (; per > 0 && z0 < nk; z0 += per) {
+    const int cnt = std::min(per, nk - z0);
+    const long long o = (long long)z0 * c->sMM;
+    if (!ozaki_gemm<T>(OP_N, OP_C, M, M, M, 1.0, C + o, M, c->sMM, C + o, M, c->sMM, 0.0, rho + o, M, c->sMM, cnt, 1,
+                       c->slices, c->oz, c->st, c->stream, ks + (size_t)z0 * M, M, nrho + z0))
+      break;  // tensor maps unavailable: the DFMA kernel takes the remaining items
+  }
+  if (z0 >= nk) return;
+  const long long o = (long long)z0 * c->sMM;
+  GemmBatch g{};
+  g.base = GemmDesc{C + o, C + o, rho + o, ks + (size_t)z0 * M, M, M, M, M, M, M};
+  g.sA = c->sMM;
+  g.sB = c->sMM;
+  g.sC = c->sMM;
+  g.sK = M;
+  g.kdev = nrho + z0;
+  g.count = nk - z0;
+  g.opA = OP_N;
+  g.opB = OP_C;
+  g.lower = 1;
+  g.alpha = 1.0;
+  g.beta = 0.0;
+  gemm<T>(g, M, M, c->stream);
 }
 
 // Blocked right-looking Cholesky of L (in place, lower), two levels.  Outer panels of
@@ -651,7 +698,15 @@ gks_status solve_t(gks_ctx* c, const T* H, const T* S, int n, int nk, bool nc, d
   double* Z = at<double>(c, c->oZ);
   {
     StageRec sr(c, PS_STEDC);
-    dc_solve(c->dc, d, e, M, eps, Z, c->sMM, c->ws + c->odc, c->st, s, &c->prof);
+    DcSplit sp{nullptr, 0, c->slices, 512};
+    if (c->gemm_mode != 1 && M >= 1024) {
+      const size_t item = dc_split_item_bytes(c->dc, sp.min_half, c->slices);
+      if (item > 0) {
+        sp.per = oz_reserve(c, item, nk);
+        sp.work = c->oz;
+      }
+    }
+    dc_solve(c->dc, d, e, M, eps, Z, c->sMM, c->ws + c->odc, c->st, s, &c->prof, &sp);
   }
   // (a6) X = Q D Z, C = L^-H X
   {
@@ -681,26 +736,14 @@ gks_status solve_t(gks_ctx* c, const T* H, const T* S, int n, int nk, bool nc, d
   }
   {
     StageRec sr(c, PS_RHO);
-    GemmBatch g{};
-    g.base = GemmDesc{C, C, rho, ks, M, M, M, M, M, M};
-    g.sA = c->sMM;
-    g.sB = c->sMM;
-    g.sC = c->sMM;
-    g.sK = M;
-    g.kdev = nrho;
-    g.count = nk;
-    g.opA = OP_N;
-    g.opB = OP_C;
-    g.lower = 1;
-    g.alpha = 1.0;
-    g.beta = 0.0;
     {
-      Rec r(c, PC_GEMM, -1.0, -1.0);  // flops resolved from n_rho when the profile is read
+      const bool split = split_worth(c, nk, M, M, M, es, gemm_flops(es, M, M, M / 4, 1, nk));
+      Rec r(c, split ? PC_OZAKI : PC_GEMM, -1.0, -1.0);  // flops resolved from n_rho when the profile is read
       c->prof.nrho_dev = nrho;
       c->prof.rho_m = M;
       c->prof.rho_nk = nk;
       c->prof.rho_es = es;
-      gemm<T>(g, M, M, s);
+      rho_run<T>(c, C, rho, ks, nrho, M, nk);
     }
     Rec r(c, PC_MISC);
     mirror_lower<T>(rho, M, c->sMM, M, nk, s);
@@ -1165,14 +1208,16 @@ gks_status gks_gemm_split_noalloc(gks_ctx* ctx, int dtype, int opA, int opB, int
     cudaGetLastError();
     return fail(ctx, GKS_ECUDA, std::string("gks_gemm_split_noalloc: scratch lookup: ") + cudaGetErrorString(e));
   }
+  bool ok;
   if (dtype == GKS_R64)
-    ozaki_gemm<double>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const double*>(A), (int)lda, 0,
+    ok = ozaki_gemm<double>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const double*>(A), (int)lda, 0,
                        static_cast<const double*>(B), (int)ldb, 0, beta, static_cast<double*>(C), (int)ldc, 0, 1, 0,
-                       ctx->slices, scratch, ctx->stream);
+                       ctx->slices, scratch, nullptr, ctx->stream);
   else
-    ozaki_gemm<zc>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const zc*>(A), (int)lda, 0,
+    ok = ozaki_gemm<zc>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const zc*>(A), (int)lda, 0,
                    static_cast<const zc*>(B), (int)ldb, 0, beta, static_cast<zc*>(C), (int)ldc, 0, 1, 0,
-                   ctx->slices, scratch, ctx->stream);
+                   ctx->slices, scratch, nullptr, ctx->stream);
+  if (!ok) return fail(ctx, GKS_ECUDA, "gks_gemm_split_noalloc: TMA tensor map encoding unavailable");
   return cuda_check(ctx, "gks_gemm_split_noalloc");
 }
 

@@ -57,9 +57,16 @@ struct DcPlan;
 DcPlan* dc_plan_create(int m, int count);
 void dc_plan_destroy(DcPlan* p);
 size_t dc_workspace_bytes(const DcPlan* p);
+// Merges whose halves reach min_half rows run as split products on `work` (per items per
+// launch, S digits); the rest use the grouped FP64 kernel.
+struct DcSplit {
+  void* work;
+  int per, S, min_half;
+};
+size_t dc_split_item_bytes(const DcPlan* p, int min_half, int S);
 // d (m), e (m-1) per item (stride sde); Z out (m x m, ld m, stride sZ); lam out (stride sde).
 void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, double* Z, long long sZ, void* work,
-              DevStatus* st, cudaStream_t s, Prof* prof);
+              DevStatus* st, cudaStream_t s, Prof* prof, const DcSplit* sp = nullptr);
 
 // ---- adjoint (adjoint.cu) ----
 void adj_occ(const double* eps, const double* mu, double kT, long long tot, double* f, double* fp, cudaStream_t s);
@@ -79,10 +86,14 @@ void spin_block_sum(T* dst, long long sd, const T* src, long long ss, int n, int
 // Workspace bytes per batch item (a multiple of 256), and output tiles per item.
 size_t ozaki_workspace_bytes(int M, int N, int K, bool cplx, int S);
 int ozaki_tiles(int M, int N, bool cplx);
+// Returns false (nothing enqueued) when the TMA tensor maps cannot be encoded.  Optional:
+// kscale (per item, stride sks) scales column k of op(A) before the product; kdev (per
+// item, device) cuts K to its value.
 template <typename T>
-void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
+bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
                 int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
-                void* work, cudaStream_t s);
+                void* work, DevStatus* status, cudaStream_t s, const double* kscale = nullptr, long long sks = 0,
+                const int* kdev = nullptr);
 
 // ---- occupations (occ.cu) ----
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,

@@ -16,9 +16,14 @@
 // other: A' = [Re a, Im a] interleaved along k, B' column 2j = (Re b, -Im b) interleaved,
 // column 2j+1 = (Im b, Re b); then (A' B')[i][2j] = Re c_ij and [i][2j+1] = Im c_ij.
 //
-// On GB300 the legacy bf16 mma.sync path runs at about 606 TFLOP/s (measured), so the 45
-// digit products of S = 9 still deliver roughly ten times the DFMA rate of an FP64 GEMM.
+// On GB300 the bf16 tensor cores (tcgen05) run the 45 digit products of S = 9 at an
+// FP64-equivalent rate of 13-18 TFLOP/s on large products, against 1.2 TFLOP/s for the
+// FP64 pipe.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "dense.h"
 
@@ -89,24 +94,32 @@ __device__ __forceinline__ void emit<zc>(zc x, int e, int role, int v, int k, __
 // One CTA (256 threads) per 32 vectors.  Pass 1: per-vector max (thread per vector when the
 // vector index is the contiguous direction, else a warp sweeps each vector along k).
 // Pass 2: digits.  Padding vectors and k beyond K are written as zero digits elsewhere.
-// blockIdx.y runs over the batch items (strides sX, sD, sE).
+// blockIdx.y runs over the batch items (strides sX, sD, sE).  Optional per item: kdev
+// (device) cuts K to its value, ksc scales element k by ksc[k] before splitting.
 template <typename T>
 __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long long sX, int role, int op, int nvec,
                                                        int K, __nv_bfloat16* D, int Kp, long long sstride,
-                                                       long long sD, int S, int* ex, long long sE) {
+                                                       long long sD, int S, int* ex, long long sE,
+                                                       const double* ksc, long long sks, const int* kdev) {
   __shared__ double smax[32];
   __shared__ int sexp[32];
   const int v0 = blockIdx.x * 32, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   X += blockIdx.y * sX;
   D += blockIdx.y * sD;
   ex += blockIdx.y * sE;
+  if (kdev) K = min(K, max(0, kdev[blockIdx.y]));
+  if (ksc) ksc += blockIdx.y * sks;
+  auto elem = [&](int v, int k) -> T {
+    T x = split_elem(X, ld, role, op, v, k);
+    return ksc ? x * ksc[k] : x;
+  };
   const bool contig = (role == 0) == (op == OP_N);  // k contiguous in memory
   if (contig) {
     for (int vv = warp; vv < 32; vv += 8) {
       const int v = v0 + vv;
       double m = 0.0;
       if (v < nvec)
-        for (int k = lane; k < K; k += 32) m = fmax(m, amax(split_elem(X, ld, role, op, v, k)));
+        for (int k = lane; k < K; k += 32) m = fmax(m, amax(elem(v, k)));
       for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
       if (lane == 0) smax[vv] = m;
     }
@@ -116,7 +129,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long 
     double m = 0.0;
     const int v = v0 + lane;
     if (v < nvec)
-      for (int k = warp; k < K; k += 8) m = fmax(m, amax(split_elem(X, ld, role, op, v, k)));
+      for (int k = warp; k < K; k += 8) m = fmax(m, amax(elem(v, k)));
     pm[warp][lane] = m;
     __syncthreads();
     if (tid < 32) {
@@ -135,7 +148,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long 
     for (int vv = warp; vv < 32; vv += 8) {
       const int v = v0 + vv;
       if (v >= nvec) continue;
-      for (int k = lane; k < K; k += 32) emit<T>(split_elem(X, ld, role, op, v, k), sexp[vv], role, v, k, D, Kp, sstride, S);
+      for (int k = lane; k < K; k += 32) emit<T>(elem(v, k), sexp[vv], role, v, k, D, Kp, sstride, S);
     }
   } else {
     // k strided in memory: stage 32 (k) x 32 (vectors) tiles through shared memory so that
@@ -144,7 +157,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long 
     for (int k0 = 0; k0 < K; k0 += 32) {
       for (int kk = warp; kk < 32; kk += 8) {
         const int k = k0 + kk, v = v0 + lane;
-        tile[kk][lane] = (k < K && v < nvec) ? split_elem(X, ld, role, op, v, k) : zero<T>();
+        tile[kk][lane] = (k < K && v < nvec) ? elem(v, k) : zero<T>();
       }
       __syncthreads();
       for (int vv = warp; vv < 32; vv += 8) {
@@ -162,28 +175,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sdst)), "l"(gsrc));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
+static constexpr int OZ_BM = 128, OZ_BN = 128;  // output tile of the product kernel
 
 struct OzArgs {
   const __nv_bfloat16* Ad;  // [S][Mp][Kp]
@@ -198,170 +190,357 @@ struct OzArgs {
   int cplx, lower;
   double alpha, beta;
   long long sAd, sBd;       // slice strides (elements)
-  long long zAd, zBd, zE, zC;  // batch item strides of the digits, exponents and C
+  long long zAd, zBd, zEa, zEb, zC;  // batch item strides of the digits, exponents and C
+  const int* kdev;          // optional per-item K read on the device (logical, <= K)
 };
 
-static constexpr int OZ_BM = 128, OZ_BN = 128, OZ_LDS = OZ_KSTEP + 8, OZ_STAGES = 2;
-static constexpr int OZ_ACC_LD = OZ_BN + 2;  // padded FP64 accumulator rows (drain bank spread)
-static constexpr int OZ_SMEM = OZ_BM * OZ_ACC_LD * 8 + OZ_STAGES * (OZ_BM + OZ_BN) * OZ_LDS * 2;
+// ------------------------------------------------------------------ tcgen05 product kernel
+//
+// The same digit products on the 5th-generation tensor cores.  One CTA owns a 128 x 128
+// output tile (of the embedded product) and walks the units in level order: a unit is a
+// level L = s + t and a K chunk short enough that the sum over all pairs of the level,
+// (L - 1) 63^2 chunk, stays within 2^24, so one FP32 accumulation holds every pair of the
+// level exactly and a single drain (scale 2^{-6L}) serves them all.  Warp 0 streams
+// 128 x 64 digit tiles of A slice s and B slice t into a
+// ring of shared-memory stages with TMA (128-byte swizzle), one thread of warp 1 issues
+// tcgen05.mma (M = N = 128, K = 16) into one of two FP32 accumulators in tensor memory,
+// and eight epilogue warps read the finished accumulator with tcgen05.ld, scale it by
+// 2^{-6L} and add it into FP64 registers (thread = one tile row x 64 columns), while
+// the tensor cores fill the other accumulator.  Every wait is bounded: past the limit
+// the CTA raises an abort flag and a timeout status, lets its copies and products land,
+// frees its tensor memory and exits.
+namespace tcg {
+constexpr int BM = 128, BN = 128, BK = 64;           // BK bf16 = 128 bytes = one swizzle row
+constexpr int STAGES = 6;
+constexpr int TILE_BYTES = BM * BK * 2;              // 16 KB per operand tile
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;
+constexpr int TMEM_COLS = 2 * BN;                    // two FP32 accumulators
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int SMEM = STAGES * STAGE_BYTES + 1024;    // + alignment slack
+constexpr long long WAIT_CYCLES = 1ll << 32;         // about two seconds
 
-__global__ void __launch_bounds__(256, 1) oz_gemm_kernel(OzArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* acc64 = reinterpret_cast<double*>(smem_raw);  // [128][OZ_ACC_LD]
-  __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(smem_raw + OZ_BM * OZ_ACC_LD * 8);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, warp tile 64 x 32
-  const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
-  {
-    const long long z = blockIdx.z;
-    a.Ad += z * a.zAd;
-    a.Bd += z * a.zBd;
-    a.ea += z * a.zE;
-    a.eb += z * a.zE;
-    a.C = static_cast<char*>(a.C) + z * a.zC * (a.cplx ? 16 : 8);
+// kind::f16 instruction descriptor: FP32 accumulator, bf16 A and B, both K-major, M x N.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+// k blocks per unit of level L: (L - 1) pairs, digit products up to 63^2.
+__device__ __forceinline__ int level_blocks(int L) {
+  const int cb = (int)((1u << 24) / ((unsigned)(L - 1) * 3969u * (unsigned)BK));
+  return min(cb, OZ_CHUNK / BK);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false on abort or timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *abort = 1;
+      return false;
+    }
   }
-  // lower triangle of the logical output: skip tiles strictly above the diagonal
+  return true;
+}
+// Wait without watching the abort flag (draining after an abort), still bounded.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > WAIT_CYCLES) return;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile of 8-row groups 1024 bytes apart,
+// 128-byte swizzle, descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+}  // namespace tcg
+
+__global__ void __launch_bounds__(tcg::THREADS, 1)
+    oz_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs a,
+                 DevStatus* status) {
+  using namespace tcg;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, z = blockIdx.z;
   const int ncol0 = a.cplx ? n0 / 2 : n0;
-  if (a.lower && m0 + OZ_BM - 1 < ncol0) return;
-  for (int e = tid; e < OZ_BM * OZ_ACC_LD; e += 256) acc64[e] = 0.0;
+  if (a.lower && m0 + BM - 1 < ncol0) return;  // whole tile above the diagonal (uniform)
 
-  // pairs (s, t), s + t <= S + 1, s,t >= 1
   const int S = a.S;
-  const int ksteps = a.Kp / OZ_KSTEP;
-  int npairs = 0;
-  for (int s = 1; s <= S; s++) npairs += (S + 1 - s);
-  const long long total = (long long)npairs * ksteps;
-  const int chunk_steps = OZ_CHUNK / OZ_KSTEP;
-
-  auto pair_of = [&](int p, int& s, int& t) {
-    int q = p;
-    for (s = 1; s <= S; s++) {
-      int cnt = S + 1 - s;
-      if (q < cnt) { t = 1 + q; return; }
-      q -= cnt;
-    }
-  };
-  auto stage_ptr = [&](int stg) { return st + (size_t)stg * (OZ_BM + OZ_BN) * OZ_LDS; };
-  auto load_step = [&](long long q, int stg) {
-    const int p = (int)(q / ksteps), kk = (int)(q % ksteps);
-    int s, t;
-    pair_of(p, s, t);
-    const __nv_bfloat16* ga = a.Ad + (size_t)(s - 1) * a.sAd + (size_t)m0 * a.Kp + (size_t)kk * OZ_KSTEP;
-    const __nv_bfloat16* gb = a.Bd + (size_t)(t - 1) * a.sBd + (size_t)n0 * a.Kp + (size_t)kk * OZ_KSTEP;
-    __nv_bfloat16* sa = stage_ptr(stg);
-    __nv_bfloat16* sb = sa + OZ_BM * OZ_LDS;
-    // 128 rows x OZ_KSTEP bf16 = 128 x (OZ_KSTEP/8) chunks of 16 B for each operand
-    constexpr int CPR = OZ_KSTEP / 8;
-    for (int c = tid; c < OZ_BM * CPR; c += 256) {
-      int r = c / CPR, cc = (c % CPR) * 8;
-      cp_async16(sa + r * OZ_LDS + cc, ga + (size_t)r * a.Kp + cc);
-      cp_async16(sb + r * OZ_LDS + cc, gb + (size_t)r * a.Kp + cc);
-    }
-  };
-
-  float acc[4][4][4];
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++)
-#pragma unroll
-      for (int r = 0; r < 4; r++) acc[i][j][r] = 0.f;
-
-  // prologue
-  for (int stg = 0; stg < OZ_STAGES - 1; stg++) {
-    if (stg < total) load_step(stg, stg);
-    cp_commit();
+  int kblocks = a.Kp / BK;
+  if (a.kdev) {
+    const int ke = min(a.Kp, max(0, a.kdev[z]) * (a.cplx ? 2 : 1));
+    kblocks = (ke + BK - 1) / BK;
   }
+
+  if (tid == 0) {
+    for (int i = 0; i < STAGES; i++) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_WARPS);
+    }
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  tc_fence_before();
   __syncthreads();
-  for (long long q = 0; q < total; q++) {
-    cp_wait<OZ_STAGES - 2>();
-    __syncthreads();
-    {
-      long long nq = q + OZ_STAGES - 1;
-      if (nq < total) load_step(nq, (int)(nq % OZ_STAGES));
-      cp_commit();
-    }
-    const __nv_bfloat16* sa = stage_ptr((int)(q % OZ_STAGES));
-    const __nv_bfloat16* sb = sa + OZ_BM * OZ_LDS;
-    uint32_t af[2][4][4], bf[2][4][2];
-    auto load_frags = [&](int k16, int buf) {
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  volatile int* abort = &abort_flag;
+
+  double acc[64];
 #pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const int row = wm * 64 + i * 16 + (lane & 15);
-        const int col = k16 + (lane >> 4) * 8;
-        ldsm_x4(af[buf][i][0], af[buf][i][1], af[buf][i][2], af[buf][i][3], sa + row * OZ_LDS + col);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j += 2) {
-        // two n8 blocks x two k halves: matrices (n 0-7,k0), (n 0-7,k8), (n 8-15,k0), (n 8-15,k8)
-        const int nrow = wn * 32 + j * 8 + (lane & 7) + ((lane >> 4) << 3);
-        const int col = k16 + ((lane >> 3) & 1) * 8;
-        uint32_t r0, r1, r2, r3;
-        ldsm_x4(r0, r1, r2, r3, sb + nrow * OZ_LDS + col);
-        bf[buf][j][0] = r0;
-        bf[buf][j][1] = r1;
-        bf[buf][j + 1][0] = r2;
-        bf[buf][j + 1][1] = r3;
-      }
-    };
-    load_frags(0, 0);
-#pragma unroll
-    for (int ks = 0; ks < OZ_KSTEP / 16; ks++) {
-      const int cur = ks & 1;
-      if (ks + 1 < OZ_KSTEP / 16) load_frags((ks + 1) * 16, cur ^ 1);
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[cur][i], bf[cur][j][0], bf[cur][j][1]);
-    }
-    // drain at the end of each exact chunk and of each pair
-    const int kk = (int)(q % ksteps);
-    if (kk == ksteps - 1 || (kk + 1) % chunk_steps == 0) {
-      int s, t;
-      pair_of((int)(q / ksteps), s, t);
-      const double sc = ldexp(1.0, -OZ_BITS * (s + t));
-      const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-          const int r = wm * 64 + i * 16 + g, c = wn * 32 + j * 8 + tq * 2;
-          acc64[r * OZ_ACC_LD + c] += sc * (double)acc[i][j][0];
-          acc64[r * OZ_ACC_LD + c + 1] += sc * (double)acc[i][j][1];
-          acc64[(r + 8) * OZ_ACC_LD + c] += sc * (double)acc[i][j][2];
-          acc64[(r + 8) * OZ_ACC_LD + c + 1] += sc * (double)acc[i][j][3];
-#pragma unroll
-          for (int rr = 0; rr < 4; rr++) acc[i][j][rr] = 0.f;
+  for (int i = 0; i < 64; i++) acc[i] = 0.0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: digit tiles of A slice s and B slice t, k block kb, in unit order
+      long long q = 0;
+      for (int L = 2; L <= S + 1 && !*abort; L++) {
+        const int cb = level_blocks(L);
+        for (int c0 = 0; c0 < kblocks && !*abort; c0 += cb) {
+          const int c1 = min(kblocks, c0 + cb);
+          for (int si = 1; si < L && !*abort; si++) {
+            const int ya = (z * S + si - 1) * a.Mp + m0, yb = (z * S + (L - si) - 1) * a.Np + n0;
+            for (int kb = c0; kb < c1; kb++, q++) {
+              const int stg = (int)(q % STAGES);
+              const uint32_t ph = (uint32_t)((q / STAGES) & 1);
+              if (!mbar_wait(&empty[stg], ph ^ 1u, abort)) break;
+              unsigned char* sa = ring + (size_t)stg * STAGE_BYTES;
+              mbar_expect_tx(&full[stg], STAGE_BYTES);
+              tma_load_2d(sa, &mapA, &full[stg], kb * BK, ya);
+              tma_load_2d(sa + TILE_BYTES, &mapB, &full[stg], kb * BK, yb);
+            }
+          }
         }
+      }
+      // let every issued copy land before the CTA can leave
+      for (long long r = (q > STAGES ? q - STAGES : 0); r < q; r++)
+        mbar_drain(&full[r % STAGES], (uint32_t)((r / STAGES) & 1));
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      long long q = 0;
+      int u = 0;
+      bool ok = true;
+      for (int L = 2; L <= S + 1 && ok; L++) {
+        const int cb = level_blocks(L);
+        for (int c0 = 0; c0 < kblocks && ok; c0 += cb, u++) {
+          const int c1 = min(kblocks, c0 + cb);
+          const int b = u & 1;
+          const uint32_t uph = (uint32_t)((u >> 1) & 1);
+          if (!mbar_wait(&tempty[b], uph ^ 1u, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          uint32_t accum = 0;
+          for (int si = 1; si < L && ok; si++) {
+            for (int kb = c0; kb < c1; kb++, q++) {
+              const int stg = (int)(q % STAGES);
+              const uint32_t ph = (uint32_t)((q / STAGES) & 1);
+              if (!mbar_wait(&full[stg], ph, abort)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(ring + (size_t)stg * STAGE_BYTES);
+              const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TILE_BYTES);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; kk++) {
+                umma(tmem + (uint32_t)(b * BN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), accum);
+                accum = 1u;
+              }
+              umma_commit(&empty[stg]);
+            }
+          }
+          if (!ok) break;
+          umma_commit(&tfull[b]);
+        }
+      }
+      // all issued products complete before tensor memory is released
+      umma_commit(&done);
+      mbar_drain(&done, 0);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, column half (w - 2) / 4
+    const int lq = warp & 3, ch = (warp - 2) >> 2;
+    int u = 0;
+    bool ok = true;
+    for (int L = 2; L <= S + 1 && ok; L++) {
+      const int cb = level_blocks(L);
+      const double sc = ldexp(1.0, -OZ_BITS * L);
+      for (int c0 = 0; c0 < kblocks; c0 += cb, u++) {
+        const int b = u & 1;
+        const uint32_t uph = (uint32_t)((u >> 1) & 1);
+        if (!mbar_wait(&tfull[b], uph, abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * BN + ch * 64);
+        float v[32];
+        tmem_ld32(taddr, v);
+#pragma unroll
+        for (int i = 0; i < 32; i++) acc[i] = fma(sc, (double)v[i], acc[i]);
+        tmem_ld32(taddr + 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; i++) acc[32 + i] = fma(sc, (double)v[i], acc[32 + i]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
     }
   }
-  cp_wait<0>();
+  tc_fence_before();
   __syncthreads();
-  // epilogue: C = alpha 2^{e_i + f_j} acc + beta C
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+  if (*abort) {
+    if (tid == 0) set_status(status, ST_ETIMEOUT, -2);
+    return;
+  }
+  if (warp < 2) return;
+  // C = alpha 2^{e_i + f_j} acc + beta C for this thread's row and 64 embedded columns
+  const int lq = warp & 3, ch = (warp - 2) >> 2;
+  const int i = m0 + lq * 32 + lane;
+  if (i >= a.M) return;
+  const long long zz = z;
+  const int* ea = a.ea + zz * a.zEa;
+  const int* eb = a.eb + zz * a.zEb;
   if (a.cplx) {
-    zc* C = static_cast<zc*>(a.C);
-    for (int e = tid; e < OZ_BM * (OZ_BN / 2); e += 256) {
-      const int r = e / (OZ_BN / 2), cj = e % (OZ_BN / 2);
-      const int i = m0 + r, j = n0 / 2 + cj;
-      if (i >= a.M || j >= a.N || (a.lower && j > i)) continue;
-      const int ee = a.ea[i] + a.eb[j];
-      zc v{ldexp(acc64[r * OZ_ACC_LD + 2 * cj], ee) * a.alpha, ldexp(acc64[r * OZ_ACC_LD + 2 * cj + 1], ee) * a.alpha};
+    zc* C = static_cast<zc*>(a.C) + zz * a.zC;
+    const int j0 = n0 / 2 + ch * 32;
+#pragma unroll
+    for (int jj = 0; jj < 32; jj++) {
+      const int j = j0 + jj;
+      if (j >= a.N || (a.lower && j > i)) continue;
+      const int ee = ea[i] + eb[j];
+      zc v{ldexp(acc[2 * jj], ee) * a.alpha, ldexp(acc[2 * jj + 1], ee) * a.alpha};
       zc* cp = C + (size_t)i * a.ldc + j;
       if (a.beta != 0.0) v = v + a.beta * (*cp);
       *cp = v;
     }
   } else {
-    double* C = static_cast<double*>(a.C);
-    for (int e = tid; e < OZ_BM * OZ_BN; e += 256) {
-      const int r = e / OZ_BN, c = e % OZ_BN;
-      const int i = m0 + r, j = n0 + c;
-      if (i >= a.M || j >= a.N || (a.lower && j > i)) continue;
-      double v = ldexp(acc64[r * OZ_ACC_LD + c], a.ea[i] + a.eb[j]) * a.alpha;
+    double* C = static_cast<double*>(a.C) + zz * a.zC;
+    const int j0 = n0 + ch * 64;
+#pragma unroll
+    for (int jj = 0; jj < 64; jj++) {
+      const int j = j0 + jj;
+      if (j >= a.N || (a.lower && j > i)) continue;
+      double v = ldexp(acc[jj], ea[i] + eb[j]) * a.alpha;
       double* cp = C + (size_t)i * a.ldc + j;
       if (a.beta != 0.0) v += a.beta * (*cp);
       *cp = v;
     }
   }
+}
+
+// ---- tensor maps (driver entry point looked up once through the runtime)
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2-D bf16 map over rows x Kp (row stride Kp), box 64 (k) x 128 (rows), 128-byte swizzle.
+static bool digit_map(CUtensorMap* m, const void* base, long long rows, int Kp) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)tcg::BK, (cuuint32_t)tcg::BM};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // ------------------------------------------------------------------ host
@@ -379,33 +558,35 @@ int ozaki_tiles(int M, int N, bool cplx) {
   return (round_up(M, OZ_BM) / OZ_BM) * (round_up(cplx ? 2 * N : N, OZ_BN) / OZ_BN);
 }
 
-// count items, item z at A + z sA, B + z sB, C + z sC; work holds count workspaces of
-// ozaki_workspace_bytes each.
+// count items, item z at A + z sA, B + z sB, C + z sC.  work holds, for all items, the A
+// digits [count][S][Mp][Kp], then the B digits [count][S][Np][Kp], then the exponents
+// [count][Mp] and [count][Np] (within count * ozaki_workspace_bytes).
 template <typename T>
-void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
+bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
                 int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
-                void* work, cudaStream_t s) {
-  if (M <= 0 || N <= 0 || count <= 0) return;
+                void* work, DevStatus* status, cudaStream_t s, const double* kscale, long long sks,
+                const int* kdev) {
+  if (M <= 0 || N <= 0 || count <= 0) return true;
   const bool cplx = sizeof(T) == 16;
   const int Ke = cplx ? 2 * K : K;
   const int Kp = round_up(Ke > 0 ? Ke : 1, OZ_KSTEP);
   const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
-  const size_t item = ozaki_workspace_bytes(M, N, K, cplx, S);
-  // per item: A digits [S][Mp][Kp], B digits [S][Np][Kp], then Mp + Np exponents
+  const long long zA = (long long)S * Mp * Kp, zB = (long long)S * Np * Kp;
   __nv_bfloat16* Ad = static_cast<__nv_bfloat16*>(work);
-  __nv_bfloat16* Bd = Ad + (size_t)S * Mp * Kp;
-  int* ea = reinterpret_cast<int*>(Bd + (size_t)S * Np * Kp);
-  int* eb = ea + Mp;
-  const long long zD = (long long)(item / 2), zE = (long long)(item / sizeof(int));
+  __nv_bfloat16* Bd = Ad + zA * count;
+  int* ea = reinterpret_cast<int*>(Bd + zB * count);
+  int* eb = ea + (size_t)Mp * count;
   // zero digits and exponents (padding rows/columns and k beyond K stay zero)
-  cudaMemsetAsync(work, 0, item * count, s);
+  cudaMemsetAsync(work, 0, ((size_t)(zA + zB) * 2 + sizeof(int) * ((size_t)Mp + Np)) * count, s);
   if (K > 0) {
     count_launch();
     oz_split_kernel<T><<<dim3((M + 31) / 32, count), 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp,
-                                                                   (long long)Mp * Kp, zD, S, ea, zE);
+                                                                   (long long)Mp * Kp, zA, S, ea, Mp, kscale, sks,
+                                                                   kdev);
     count_launch();
     oz_split_kernel<T><<<dim3((N + 31) / 32, count), 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp,
-                                                                   (long long)Np * Kp, zD, S, eb, zE);
+                                                                   (long long)Np * Kp, zB, S, eb, Np, nullptr, 0,
+                                                                   kdev);
   }
   OzArgs oa;
   oa.Ad = Ad;
@@ -426,19 +607,27 @@ void ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   oa.beta = beta;
   oa.sAd = (long long)Mp * Kp;
   oa.sBd = (long long)Np * Kp;
-  oa.zAd = zD;
-  oa.zBd = zD;
-  oa.zE = zE;
+  oa.zAd = zA;
+  oa.zBd = zB;
+  oa.zEa = Mp;
+  oa.zEb = Np;
   oa.zC = sC;
-  cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+  oa.kdev = kdev;
   dim3 grid(Np / OZ_BN, Mp / OZ_BM, count);
+  CUtensorMap ma, mb;
+  if (!digit_map(&ma, Ad, (long long)count * S * Mp, Kp) || !digit_map(&mb, Bd, (long long)count * S * Np, Kp))
+    return false;
+  cudaFuncSetAttribute(oz_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM);
   count_launch();
-  oz_gemm_kernel<<<grid, 256, OZ_SMEM, s>>>(oa);
+  oz_tc_kernel<<<grid, tcg::THREADS, tcg::SMEM, s>>>(ma, mb, oa, status);
+  return true;
 }
 
-template void ozaki_gemm<double>(int, int, int, int, int, double, const double*, int, long long, const double*, int,
-                                 long long, double, double*, int, long long, int, int, int, void*, cudaStream_t);
-template void ozaki_gemm<zc>(int, int, int, int, int, double, const zc*, int, long long, const zc*, int, long long,
-                             double, zc*, int, long long, int, int, int, void*, cudaStream_t);
+template bool ozaki_gemm<double>(int, int, int, int, int, double, const double*, int, long long, const double*, int,
+                                 long long, double, double*, int, long long, int, int, int, void*, DevStatus*,
+                                 cudaStream_t, const double*, long long, const int*);
+template bool ozaki_gemm<zc>(int, int, int, int, int, double, const zc*, int, long long, const zc*, int, long long,
+                             double, zc*, int, long long, int, int, int, void*, DevStatus*, cudaStream_t,
+                             const double*, long long, const int*);
 
 }  // namespace gks

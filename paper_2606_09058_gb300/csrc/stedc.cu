@@ -559,8 +559,20 @@ static void build_gemm_lists(DcPlan* p, double* Z, long long sZ, void* work) {
   p->sZbound = sZ;
 }
 
+size_t dc_split_item_bytes(const DcPlan* p, int min_half, int S) {
+  size_t b = 0;
+  for (auto& L : p->levels)
+    if (L.maxhalf >= min_half)
+      for (auto& nd : L.nodes) {
+        const int n = nd.n1 + nd.n2;
+        b = std::max(b, ozaki_workspace_bytes(nd.n1, n, nd.n1, false, S));
+        b = std::max(b, ozaki_workspace_bytes(nd.n2, n, nd.n2, false, S));
+      }
+  return b;
+}
+
 void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, double* Z, long long sZ, void* work,
-              DevStatus* st, cudaStream_t s, Prof* prof) {
+              DevStatus* st, cudaStream_t s, Prof* prof, const DcSplit* sp) {
   const int m = p->m, cnt = p->count;
   if (p->zbound != Z || p->wbound != work || p->sZbound != sZ) build_gemm_lists(p, Z, sZ, work);
   const size_t item = dc_item_bytes(m);
@@ -611,6 +623,30 @@ void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, doubl
       const double nn1 = nd.n1, nn2 = nd.n2, n = nn1 + nn2;
       gfl += 2.0 * (nn1 * nn1 + nn2 * nn2) * n;
       gby += 8.0 * (nn1 * nn1 + nn2 * nn2 + 2.0 * n * n);
+    }
+    if (sp && sp->per > 0 && L.maxhalf >= sp->min_half) {
+      // large merges: per node, exact split-bf16 products batched over the items
+      tok = prof->begin();
+      const long long sin = in_is_Z ? sZ : slam, sout = in_is_Z ? slam : sZ;
+      double* in0 = in_is_Z ? Z : w0.Zb;
+      double* out0 = in_is_Z ? w0.Zb : Z;
+      bool ok = true;
+      for (auto& nd : L.nodes) {
+        const int off = nd.off, n = nd.n1 + nd.n2, sft = off + nd.n1;
+        for (int z0 = 0; z0 < cnt && ok; z0 += sp->per) {
+          const int c = std::min(sp->per, cnt - z0);
+          const DcWs wz = dc_ws(static_cast<char*>(work) + (size_t)z0 * item, m);
+          const long long iz = (long long)z0 * sin, oz = (long long)z0 * sout;
+          ok = ozaki_gemm<double>(OP_N, OP_T, nd.n1, n, nd.n1, 1.0, in0 + iz + (size_t)off * m + off, m, sin,
+                                  wz.W + (size_t)off * m + off, m, slam, 0.0, out0 + oz + (size_t)off * m + off, m,
+                                  sout, c, 0, sp->S, sp->work, st, s) &&
+               ozaki_gemm<double>(OP_N, OP_T, nd.n2, n, nd.n2, 1.0, in0 + iz + (size_t)sft * m + sft, m, sin,
+                                  wz.W + (size_t)off * m + sft, m, slam, 0.0, out0 + oz + (size_t)sft * m + off, m,
+                                  sout, c, 0, sp->S, sp->work, st, s);
+        }
+      }
+      prof->end(tok, PC_OZAKI, gfl * cnt, gby * cnt);
+      if (ok) continue;
     }
     tok = prof->begin();
     GemmBatch gb{};

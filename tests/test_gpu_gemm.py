@@ -79,6 +79,28 @@ def test_split_gemm_is_exact_on_small_integers(ctx):
     assert np.array_equal(C.cpu().numpy(), A @ B)
 
 
+@pytest.mark.parametrize("K", [4096, 4160, 9000])
+@pytest.mark.parametrize("signs", ["positive", "mixed"])
+def test_split_gemm_saturated_digits(ctx, K, signs):
+    """Entries 1 - 2^-52 have (nearly) all 54 digit bits set, so every digit product is
+    63^2 and the exact FP32 partial sums reach their 2^24 limit.  A single lost bit in the
+    leading level would be an error of 2^-12 per element, far above the splitting bound
+    (which the dropped pairs s + t > S + 1 nearly reach here)."""
+    x = 1.0 - 2.0 ** -52
+    rng = np.random.default_rng(K)
+    A = np.full((130, K), x)
+    B = np.full((K, 140), x)
+    if signs == "mixed":
+        A *= rng.choice([-1.0, 1.0], A.shape)
+        B *= rng.choice([-1.0, 1.0], B.shape)
+    C = torch.zeros(130, 140, dtype=torch.float64, device="cuda")
+    ctx.gemm(torch.as_tensor(A).cuda(), torch.as_tensor(B).cuda(), C, mode="split")
+    # exact: (A B)_ij = x^2 * (integer sign sum), x^2 = 1 - 2^-51 + 2^-104
+    ssum = np.sign(A) @ np.sign(B)
+    ref = ssum * x * x
+    assert np.all(np.abs(C.cpu().numpy() - ref) <= _bound(A, B, K))
+
+
 def test_solve_with_split_products_matches_oracle(ctx):
     """Full path with every product forced through split products, on the Si cluster."""
     from oracle import oracle as O

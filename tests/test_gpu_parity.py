@@ -163,6 +163,14 @@ def test_solve_random_pencil(ctx, cplx, m):
     _compare(ctx, H[None], S[None], 0.1, 0.6 * m, raw=True)
 
 
+@pytest.mark.parametrize("cplx,m", [(False, 1100), (True, 1030)])
+def test_solve_random_pencil_large(ctx, cplx, m):
+    """Orders past 1024: the top divide-and-conquer merges and (complex) the density matrix
+    run as split products."""
+    H, S = I.random_pencil(m, 700 + m, cplx, cond=1e2)
+    _compare(ctx, H[None], S[None], 0.1, 0.6 * m, raw=True)
+
+
 @pytest.mark.parametrize("tiling", [(1, 1, 1), (2, 1, 1)])
 def test_solve_si_cluster(ctx, tiling):
     p = I.collinear_gamma(tiling, 0, 0.01)
