@@ -556,8 +556,10 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   int* tk = at<int>(c, c->oticket);
   if (M < 3) return;
   cudaMemsetAsync(tk, 0, sizeof(int) * 2 * nk, s);
-  for (int jh = M - 1; jh >= 2; jh -= ldu) {
-    const int jl = std::max(2, jh - ldu + 1);  // steps jh .. jl in this panel
+  // small orders are latency-bound per step: shorter panels keep the corrections short
+  const int pw = M < 2048 ? std::min(NB, ldu) : ldu;
+  for (int jh = M - 1; jh >= 2; jh -= pw) {
+    const int jl = std::max(2, jh - pw + 1);  // steps jh .. jl in this panel
     {
       Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * es * jh * nk);
       hetrd_reflector<T>(A, M, c->sMM, jh, u, c->sVec, tau, M, nk, s);

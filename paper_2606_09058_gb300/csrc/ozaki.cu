@@ -301,8 +301,17 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// x 2^-s as a double, for x an integer-valued float (the exact unit sums): built from the
+// float's bits with integer operations (sign, exponent shifted by 896 - s, mantissa moved
+// up by 29 bits), so the drain spends one FP64 add per element and no FP64 conversion.
+__device__ __forceinline__ double exact_scaled(uint32_t b, uint32_t s) {
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint32_t hi = (b & 0x80000000u) | ((e + 896u - s) << 20) | ((b & 0x7fffffu) >> 3);
+  const uint32_t lo = b << 29;
+  return e ? __hiloint2double((int)hi, (int)lo) : 0.0;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
       "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
@@ -312,8 +321,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 }  // namespace tcg
 
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
     bool ok = true;
     for (int L = 2; L <= S + 1 && ok; L++) {
       const int cb = level_blocks(L);
-      const double sc = ldexp(1.0, -OZ_BITS * L);
+      const uint32_t sh = (uint32_t)(OZ_BITS * L);
       for (int c0 = 0; c0 < kblocks; c0 += cb, u++) {
         const int b = u & 1;
         const uint32_t uph = (uint32_t)((u >> 1) & 1);
@@ -454,13 +461,13 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
         }
         tc_fence_after();
         const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * BN + ch * 64);
-        float v[32];
+        uint32_t v[32];
         tmem_ld32(taddr, v);
 #pragma unroll
-        for (int i = 0; i < 32; i++) acc[i] = fma(sc, (double)v[i], acc[i]);
+        for (int i = 0; i < 32; i++) acc[i] += exact_scaled(v[i], sh);
         tmem_ld32(taddr + 32, v);
 #pragma unroll
-        for (int i = 0; i < 32; i++) acc[32 + i] = fma(sc, (double)v[i], acc[32 + i]);
+        for (int i = 0; i < 32; i++) acc[32 + i] += exact_scaled(v[i], sh);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
