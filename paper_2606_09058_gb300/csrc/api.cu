@@ -108,7 +108,7 @@ struct gks_ctx {
   size_t aws_bytes = 0;
   int am = -1, ank = -1, aes = -1;
   // offsets (bytes) of per-item arrays; each holds nk items
-  size_t oA, oL, oF, oFB, oU, oQ, opart, oy, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
+  size_t oA, oL, oF, oFB, oU, oQ, opart, oy, ouw, oSg, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
       oticket;
   long long sMM, sF, sFB, sU, spart, sy, sV, sG, sT, sY, sVec;
 };
@@ -186,6 +186,8 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->oQ = a.take<char>(elems(c->sU));
   c->opart = a.take<char>(elems(c->spart));
   c->oy = a.take<char>(elems(c->sy));
+  c->ouw = a.take<double>((size_t)3 * m * nk);
+  c->oSg = es == 16 ? a.take<double>(MM * nk) : 0;
   c->oV = a.take<char>(elems(c->sV));
   c->oG = a.take<char>(elems(c->sG));
   c->oT = a.take<char>(elems(c->sT));
@@ -558,25 +560,30 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   cudaMemsetAsync(tk, 0, sizeof(int) * 2 * nk, s);
   // small orders are latency-bound per step: shorter panels keep the corrections short
   const int pw = M < 2048 ? std::min(NB, ldu) : ldu;
+  // complex: three-multiplication products need Re + Im of the stale block (per panel)
+  double* uw = es == 16 ? at<double>(c, c->ouw) : nullptr;
+  double* Sg = es == 16 ? at<double>(c, c->oSg) : nullptr;
   for (int jh = M - 1; jh >= 2; jh -= pw) {
     const int jl = std::max(2, jh - pw + 1);  // steps jh .. jl in this panel
     {
       Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * es * jh * nk);
-      hetrd_reflector<T>(A, M, c->sMM, jh, u, c->sVec, tau, M, nk, s);
+      if (Sg) hetrd_sums(reinterpret_cast<const zc*>(A), M, c->sMM, jh, Sg, nk, s);
+      hetrd_reflector<T>(A, M, c->sMM, jh, u, c->sVec, tau, M, nk, s, uw);
     }
     for (int j = jh; j >= jl; j--) {
       const int k = jh - j;  // panel steps already taken
       const double jj = (double)j * j;
       {
-        Rec r(c, PC_HETRD_HEMV, cmul(es) * (jj + 2.0 * j * k) * nk, (0.5 * jj + 2.0 * j * k + 4.0 * j) * es * nk);
+        Rec r(c, PC_HETRD_HEMV, cmul(es) * (jj + 2.0 * j * k) * nk,
+              (0.5 * jj * (es == 16 ? 1.5 : 1.0) + 2.0 * j * k + 4.0 * j) * es * nk);
         hetrd_phemv<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, U, Q, ldu, c->sU, k, part, c->spart, y, c->sy, tk,
-                       nk, s);
+                       nk, s, Sg, uw);
       }
       const int rowupd = (j > jl) ? 1 : 0;
       {
         Rec r(c, PC_HETRD_RANK2, cmul(es) * 2.0 * j * (k + 1) * (1 + rowupd) * nk, (2.0 * j * (k + 1) + 4.0 * j) * es * nk);
         hetrd_pupdate<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, U, Q, ldu, c->sU, k, y, c->sy, rowupd, tk + nk, nk,
-                         s);
+                         s, uw);
       }
     }
     // deferred rank-2k update of the trailing block [0:jl, 0:jl]

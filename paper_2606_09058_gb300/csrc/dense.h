@@ -35,15 +35,21 @@ void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int
 // with rowupd also forms the reflector of step j-1).
 template <typename T>
 void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau, long long stau, int count,
-                     cudaStream_t s);
+                     cudaStream_t s, double* uw = nullptr);
+// Complex panel form only: Sg = Re + Im of the stale block (lower, leading n x n, stride sA
+// per item, same indexing as A) and uw = (Re u, Im u - Re u, Re u + Im u) per element (3 sv
+// doubles per item); with both, the matrix-vector step uses three real products per
+// complex product.
+void hetrd_sums(const zc* A, int lda, long long sA, int n, double* Sg, int count, cudaStream_t s);
 template <typename T>
 void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
                  long long stau, const T* U, const T* Q, int ldu, long long sU, int k, T* part, long long spart,
-                 T* y, long long sy, int* ticket, int count, cudaStream_t s);
+                 T* y, long long sy, int* ticket, int count, cudaStream_t s, const double* Sg = nullptr,
+                 const double* uw = nullptr);
 template <typename T>
 void hetrd_pupdate(T* A, int lda, long long sA, int j, T* u, const T* p, long long sv, double* tau, long long stau,
                    T* U, T* Q, int ldu, long long sU, int k, const T* y, long long sy, int rowupd, int* ticket,
-                   int count, cudaStream_t s);
+                   int count, cudaStream_t s, double* uw = nullptr);
 template <typename T>
 void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e, long long sde, T* ph,
                   long long sph, int count, cudaStream_t s);

@@ -21,8 +21,18 @@ namespace gks {
 
 // Reflector for step j (one CTA): reads row j left of the diagonal (through L2: in the
 // fused form other CTAs have just written it), writes u', tau[j] and the sub-diagonal.
+// uw (complex only, nullable): per element (Re u, Im u - Re u, Re u + Im u), the vector form
+// of the three-multiplication complex products of the panel matrix-vector step.
+__device__ __forceinline__ void put_uw(double* uw, int i, double ur, double ui) {
+  if (uw) {
+    uw[3 * i] = ur;
+    uw[3 * i + 1] = ui - ur;
+    uw[3 * i + 2] = ur + ui;
+  }
+}
+
 template <typename T>
-__device__ void reflector_body(T* A, int lda, int j, T* u, double* tau) {
+__device__ void reflector_body(T* A, int lda, int j, T* u, double* tau, double* uw) {
   __shared__ double redd[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   T* row = A + (size_t)j * lda;
@@ -32,7 +42,10 @@ __device__ void reflector_body(T* A, int lda, int j, T* u, double* tau) {
   const T alpha = conjg(ldcg(row + j - 1));
   const double tail = xnorm2 - abs2(alpha);
   if (!(tail > 0.0)) {  // nothing to annihilate: P_j = I
-    for (int i = tid; i < j; i += nt) u[i] = (i == j - 1) ? from_real<T>(1.0) : zero<T>();
+    for (int i = tid; i < j; i += nt) {
+      u[i] = (i == j - 1) ? from_real<T>(1.0) : zero<T>();
+      put_uw(uw, i, i == j - 1 ? 1.0 : 0.0, 0.0);
+    }
     if (tid == 0) tau[j] = 0.0;
     return;
   }
@@ -47,9 +60,11 @@ __device__ void reflector_body(T* A, int lda, int j, T* u, double* tau) {
     T v = conjg(ldcg(row + i)) * inv;                 // u'_i = a_i / u_{j-1}
     u[i] = v;
     row[i] = v;
+    put_uw(uw, i, re(v), im(v));
   }
   if (tid == 0) {
     u[j - 1] = from_real<T>(1.0);
+    put_uw(uw, j - 1, 1.0, 0.0);
     tau[j] = beta * abs2(upiv);
     row[j - 1] = conjg(ph) * (-xn);                     // lower-storage sub-diagonal
   }
@@ -57,9 +72,22 @@ __device__ void reflector_body(T* A, int lda, int j, T* u, double* tau) {
 
 template <typename T>
 __global__ void hetrd_reflector_kernel(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau,
-                                       long long stau) {
+                                       long long stau, double* uw) {
   const int z = blockIdx.x;
-  reflector_body<T>(A + z * sA, lda, j, u + z * sv, tau + z * stau);
+  reflector_body<T>(A + z * sA, lda, j, u + z * sv, tau + z * stau, uw ? uw + z * 3 * sv : nullptr);
+}
+
+// Sg[r][c] = Re A[r][c] + Im A[r][c] over the lower triangle of the leading n x n block
+// (the stale block of a panel), for the three-multiplication products.
+__global__ void hetrd_sums_kernel(const zc* A, int lda, long long sA, int n, double* Sg) {
+  const int z = blockIdx.z;
+  A += z * sA;
+  Sg += z * sA;
+  for (int r = blockIdx.y; r < n; r += gridDim.y)
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= r; c += gridDim.x * blockDim.x) {
+      const zc a = A[(size_t)r * lda + c];
+      Sg[(size_t)r * lda + c] = a.x + a.y;
+    }
 }
 
 // Panel (blocked) form.  A panel of steps keeps the trailing block A[0:j,0:j] as it was
@@ -82,7 +110,7 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
                                                           T* p, long long sv, const double* tau, long long stau,
                                                           const T* U, const T* Q, int ldu, long long sU, int k,
                                                           T* part, long long spart, T* y, long long sy,
-                                                          int* ticket) {
+                                                          int* ticket, const double* Sg, const double* uw) {
   __shared__ T colpart[4][64];
   __shared__ T rowacc[64];
   __shared__ T red[32];
@@ -99,17 +127,57 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
   const int c0 = blockIdx.x * 64;
   const int cend = min(c0 + 64, j);
   const int pst = 2 * ldu + 2;
-  // row part: rows r in [c0, cend), columns 0..r; one warp per row
   const int warp = tid >> 5, lane = tid & 31;
-  for (int r = c0 + warp; r < cend; r += 8) {
-    const T* ar = A + (size_t)r * lda;
-    T s = zero<T>();
-    for (int c = lane; c <= r; c += 32) mac(s, ar[c], u[c]);
-    s = warp_sum(s);
-    if (lane == 0) rowacc[r - c0] = s;
+  bool done = false;
+  if constexpr (sizeof(T) == 16) {
+    if (Sg) {
+      // Three real multiply-adds per complex product (Gauss): with s = Re a + Im a (Sg) and
+      // the vector form (c, d - c, c + d) of u_c = c + i d (uw),
+      //   a u    = (c s - Im a (c + d)) + i (c s + Re a (d - c)),
+      //   a* u   = (c s + Im a (d - c)) + i (Re a (c + d) - c s).
+      Sg += z * sA;
+      uw += z * 3 * sv;
+      for (int r = c0 + warp; r < cend; r += 8) {
+        const zc* ar = reinterpret_cast<const zc*>(A) + (size_t)r * lda;
+        const double* sr = Sg + (size_t)r * lda;
+        double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        for (int c = lane; c <= r; c += 32) {
+          const zc a = ar[c];
+          k1 = fma(uw[3 * c], sr[c], k1);
+          k2 = fma(a.x, uw[3 * c + 1], k2);
+          k3 = fma(a.y, uw[3 * c + 2], k3);
+        }
+        k1 = warp_sum(k1);
+        k2 = warp_sum(k2);
+        k3 = warp_sum(k3);
+        if (lane == 0) rowacc[r - c0] = T{k1 - k3, k1 + k2};
+      }
+      const int cc = tid & 63, g = tid >> 6;
+      const int c = c0 + cc;
+      double l1 = 0.0, l3 = 0.0, l4 = 0.0;
+      if (c < cend) {
+        for (int r = c0 + g; r < j; r += 4)
+          if (r > c) {
+            const zc a = reinterpret_cast<const zc*>(A)[(size_t)r * lda + c];
+            l1 = fma(uw[3 * r], Sg[(size_t)r * lda + c], l1);
+            l3 = fma(a.y, uw[3 * r + 1], l3);
+            l4 = fma(a.x, uw[3 * r + 2], l4);
+          }
+      }
+      colpart[g][cc] = T{l1 + l3, l4 - l1};
+      done = true;
+    }
   }
-  // column part: columns c in [c0, cend), rows r > c
-  {
+  if (!done) {
+    // row part: rows r in [c0, cend), columns 0..r; one warp per row
+    for (int r = c0 + warp; r < cend; r += 8) {
+      const T* ar = A + (size_t)r * lda;
+      T s = zero<T>();
+      for (int c = lane; c <= r; c += 32) mac(s, ar[c], u[c]);
+      s = warp_sum(s);
+      if (lane == 0) rowacc[r - c0] = s;
+    }
+    // column part: columns c in [c0, cend), rows r > c
     const int cc = tid & 63, g = tid >> 6;
     const int c = c0 + cc;
     T s = zero<T>();
@@ -182,7 +250,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) hetrd_pupdate_kernel(T* A, int lda, long long sA, int j, T* u,
                                                             const T* p, long long sv, double* tau, long long stau,
                                                             T* U, T* Q, int ldu, long long sU, int k, const T* y,
-                                                            long long sy, int rowupd, int* ticket) {
+                                                            long long sy, int rowupd, int* ticket, double* uw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y1s = reinterpret_cast<T*>(smem_raw);
   T* y2s = y1s + (ldu + 1);
@@ -197,6 +265,7 @@ __global__ void __launch_bounds__(256) hetrd_pupdate_kernel(T* A, int lda, long 
   Q += z * sU;
   y += z * sy;
   tau += z * stau;
+  if (uw) uw += z * 3 * sv;
   const double t = tau[j];
   const T kq = y[2 * ldu + 1];
   for (int s = tid; s < k; s += blockDim.x) {
@@ -259,7 +328,7 @@ __global__ void __launch_bounds__(256) hetrd_pupdate_kernel(T* A, int lda, long 
   if (!last) return;
   if (tid == 0) ticket[z] = 0;
   __syncthreads();
-  reflector_body<T>(A, lda, j - 1, u, tau);
+  reflector_body<T>(A, lda, j - 1, u, tau, uw);
 }
 
 // d_i = Re A_ii, e_i = |A_{i+1,i}|, ph_0 = 1, ph_{i+1} = ph_i A_{i+1,i}/|A_{i+1,i}|.
@@ -310,29 +379,36 @@ __global__ void gather_reflectors_kernel(const T* A, int lda, long long sA, cons
 
 template <typename T>
 void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau, long long stau, int count,
-                     cudaStream_t s) {
+                     cudaStream_t s, double* uw) {
   count_launch();
-  hetrd_reflector_kernel<T><<<count, 256, 0, s>>>(A, lda, sA, j, u, sv, tau, stau);
+  hetrd_reflector_kernel<T><<<count, 256, 0, s>>>(A, lda, sA, j, u, sv, tau, stau, uw);
+}
+
+void hetrd_sums(const zc* A, int lda, long long sA, int n, double* Sg, int count, cudaStream_t s) {
+  if (n <= 0) return;
+  dim3 grid((n + 255) / 256 < 16 ? (n + 255) / 256 : 16, n < 4096 ? n : 4096, count);
+  count_launch();
+  hetrd_sums_kernel<<<grid, 256, 0, s>>>(A, lda, sA, n, Sg);
 }
 
 template <typename T>
 void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
                  long long stau, const T* U, const T* Q, int ldu, long long sU, int k, T* part, long long spart,
-                 T* y, long long sy, int* ticket, int count, cudaStream_t s) {
+                 T* y, long long sy, int* ticket, int count, cudaStream_t s, const double* Sg, const double* uw) {
   count_launch();
   hetrd_phemv_kernel<T><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q, ldu,
-                                                                   sU, k, part, spart, y, sy, ticket);
+                                                                   sU, k, part, spart, y, sy, ticket, Sg, uw);
 }
 
 template <typename T>
 void hetrd_pupdate(T* A, int lda, long long sA, int j, T* u, const T* p, long long sv, double* tau, long long stau,
                    T* U, T* Q, int ldu, long long sU, int k, const T* y, long long sy, int rowupd, int* ticket,
-                   int count, cudaStream_t s) {
+                   int count, cudaStream_t s, double* uw) {
   const int sm = (int)(4 * sizeof(T) * (ldu + 1));
   if (sm > 48 * 1024) cudaFuncSetAttribute(hetrd_pupdate_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   count_launch();
   hetrd_pupdate_kernel<T><<<dim3((j + 63) / 64, count), 256, sm, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q, ldu,
-                                                                      sU, k, y, sy, rowupd, ticket);
+                                                                      sU, k, y, sy, rowupd, ticket, uw);
 }
 
 template <typename T>
@@ -352,12 +428,13 @@ void gather_reflectors(const T* A, int lda, long long sA, const double* tau, lon
 
 #define INST(T)                                                                                            \
   template void hetrd_reflector<T>(T*, int, long long, int, T*, long long, double*, long long, int,         \
-                                   cudaStream_t);                                                          \
+                                   cudaStream_t, double*);                                                 \
   template void hetrd_phemv<T>(const T*, int, long long, int, const T*, T*, long long, const double*,        \
                                long long, const T*, const T*, int, long long, int, T*, long long, T*, long long, \
-                               int*, int, cudaStream_t);                                                   \
+                               int*, int, cudaStream_t, const double*, const double*);                     \
   template void hetrd_pupdate<T>(T*, int, long long, int, T*, const T*, long long, double*, long long, T*,  \
-                                 T*, int, long long, int, const T*, long long, int, int*, int, cudaStream_t); \
+                                 T*, int, long long, int, const T*, long long, int, int*, int, cudaStream_t, \
+                                 double*);                                                                 \
   template void hetrd_finish<T>(const T*, int, long long, int, double*, double*, long long, T*, long long,   \
                                 int, cudaStream_t);                                                        \
   template void gather_reflectors<T>(const T*, int, long long, const double*, long long, int, int, T*, int, \
