@@ -173,7 +173,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->sT = (long long)nbb * nbb;
   c->sY = (long long)nbb * m;
   c->sU = (long long)m * nbb;
-  c->spart = (long long)((m + 63) / 64) * (2 * nbb + 2);
+  c->spart = (long long)((m + 15) / 16) * (2 * nbb + 2);
   c->sy = 2 * nbb + 2;
   c->sVec = m;
   Arena a;

@@ -30,7 +30,7 @@ void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int
 
 // ---- Householder tridiagonalization (hetrd.cu) ----
 // Workspace per batch item: u (m), p (m) vectors, tau (m), two zeroed tickets, and for the
-// panel form U, Q (m x ldu), per-CTA shares (ceil(m/64) x (2 ldu + 2)) and y (2 ldu + 2).
+// panel form U, Q (m x ldu), per-CTA shares (ceil(m/16) x (2 ldu + 2)) and y (2 ldu + 2).
 // hetrd_reflector starts a panel at step j; step j is hetrd_phemv then hetrd_pupdate (which
 // with rowupd also forms the reflector of step j-1).
 template <typename T>

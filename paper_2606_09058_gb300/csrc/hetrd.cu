@@ -97,7 +97,7 @@ __global__ void hetrd_sums_kernel(const zc* A, int lda, long long sA, int n, dou
 // The panel ends with that rank-2k update as two GEMMs.
 //
 // Step j, first half: p_raw = A[0:j,0:j] u over the stale block.  CTA b owns rows/columns
-// [64b, 64b+64): its row panel left of the diagonal plus its column panel below, so every
+// [RB b, RB b + RB): its row panel left of the diagonal plus its column panel below, so every
 // CTA reads the same number of elements.  It adds its rows' shares of Q^H u, U^H u and
 // u^H p_raw.  The last CTA (atomic ticket after a fence; nothing waits) sums the shares:
 //   y1 = Q^H u,  y2 = U^H u,  u^H p = tau (u^H p_raw - y2^H y1 - y1^H y2),
@@ -105,14 +105,16 @@ __global__ void hetrd_sums_kernel(const zc* A, int lda, long long sA, int n, dou
 // since p = tau A_true u = tau (p_raw - U y1 - Q y2).
 // y layout per item: y1 at [0, k), y2 at [ldu, ldu + k), u^H p_raw at 2 ldu, kq at 2 ldu + 1;
 // the shares use the same layout per CTA with stride 2 ldu + 2.
-template <typename T>
+template <typename T, int RB>
 __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, long long sA, int j, const T* u,
                                                           T* p, long long sv, const double* tau, long long stau,
                                                           const T* U, const T* Q, int ldu, long long sU, int k,
                                                           T* part, long long spart, T* y, long long sy,
                                                           int* ticket, const double* Sg, const double* uw) {
-  __shared__ T colpart[4][64];
-  __shared__ T rowacc[64];
+  // RB rows/columns per CTA (64, or 16 when the grid would not fill the GPU)
+  constexpr int NG = 256 / RB;
+  __shared__ T colpart[NG][RB];
+  __shared__ T rowacc[RB];
   __shared__ T red[32];
   __shared__ int last;
   const int z = blockIdx.y, tid = threadIdx.x;
@@ -124,8 +126,8 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
   part += z * spart;
   y += z * sy;
   const double t = tau[z * stau + j];
-  const int c0 = blockIdx.x * 64;
-  const int cend = min(c0 + 64, j);
+  const int c0 = blockIdx.x * RB;
+  const int cend = min(c0 + RB, j);
   const int pst = 2 * ldu + 2;
   const int warp = tid >> 5, lane = tid & 31;
   bool done = false;
@@ -152,11 +154,11 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
         k3 = warp_sum(k3);
         if (lane == 0) rowacc[r - c0] = T{k1 - k3, k1 + k2};
       }
-      const int cc = tid & 63, g = tid >> 6;
+      const int cc = tid % RB, g = tid / RB;
       const int c = c0 + cc;
       double l1 = 0.0, l3 = 0.0, l4 = 0.0;
       if (c < cend) {
-        for (int r = c0 + g; r < j; r += 4)
+        for (int r = c0 + g; r < j; r += NG)
           if (r > c) {
             const zc a = reinterpret_cast<const zc*>(A)[(size_t)r * lda + c];
             l1 = fma(uw[3 * r], Sg[(size_t)r * lda + c], l1);
@@ -178,19 +180,21 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
       if (lane == 0) rowacc[r - c0] = s;
     }
     // column part: columns c in [c0, cend), rows r > c
-    const int cc = tid & 63, g = tid >> 6;
+    const int cc = tid % RB, g = tid / RB;
     const int c = c0 + cc;
     T s = zero<T>();
     if (c < cend) {
-      for (int r = c0 + g; r < j; r += 4)
+      for (int r = c0 + g; r < j; r += NG)
         if (r > c) macc(s, A[(size_t)r * lda + c], u[r]);
     }
     colpart[g][cc] = s;
   }
   __syncthreads();
   T d0 = zero<T>();
-  if (tid < 64 && c0 + tid < cend) {
-    const T pr = rowacc[tid] + colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
+  if (tid < RB && c0 + tid < cend) {
+    T pr = rowacc[tid];
+#pragma unroll
+    for (int g = 0; g < NG; g++) pr += colpart[g][tid];
     p[c0 + tid] = pr;
     macc(d0, u[c0 + tid], pr);
   }
@@ -239,6 +243,14 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
     y[2 * ldu + 1] = (0.5 * t) * uhp;
   }
 }
+
+// Sum over aligned groups of 8 lanes (every lane of the warp takes part).
+__device__ __forceinline__ double group8_sum(double v) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ zc group8_sum(zc v) { return zc{group8_sum(v.x), group8_sum(v.y)}; }
 
 // Step j, second half: q = tau (p_raw - U y1 - Q y2) - kq u for the rows of this CTA (64
 // per CTA), stored with u as column k of Q and U.  With rowupd, row j-1 of A (columns
@@ -291,23 +303,29 @@ __global__ void __launch_bounds__(256) hetrd_pupdate_kernel(T* A, int lda, long 
     }
   }
   __syncthreads();
+  // 32 groups of 8 lanes, two columns per group (more columns in flight, short reductions)
   const int c0 = blockIdx.x * 64, cend = min(c0 + 64, j);
-  for (int c = c0 + warp; c < cend; c += 8) {
-    const T* Uc = U + (size_t)c * ldu;
-    const T* Qc = Q + (size_t)c * ldu;
+  const int grp = tid >> 3, gl = tid & 7;
+  for (int it = 0; it < 2; it++) {
+    const int c = c0 + grp + 32 * it;
+    const bool ok = c < cend;
     T corr = zero<T>(), rs = zero<T>();
-    for (int s = lane; s < k; s += 32) {
-      const T uc = Uc[s], qc = Qc[s];
-      mac(corr, uc, y1s[s]);
-      mac(corr, qc, y2s[s]);
-      if (rowupd) {
-        mac(rs, ujs[s], conjg(qc));
-        mac(rs, qjs[s], conjg(uc));
+    if (ok) {
+      const T* Uc = U + (size_t)c * ldu;
+      const T* Qc = Q + (size_t)c * ldu;
+      for (int s = gl; s < k; s += 8) {
+        const T uc = Uc[s], qc = Qc[s];
+        mac(corr, uc, y1s[s]);
+        mac(corr, qc, y2s[s]);
+        if (rowupd) {
+          mac(rs, ujs[s], conjg(qc));
+          mac(rs, qjs[s], conjg(uc));
+        }
       }
     }
-    corr = warp_sum(corr);
-    if (rowupd) rs = warp_sum(rs);
-    if (lane == 0) {
+    corr = group8_sum(corr);
+    if (rowupd) rs = group8_sum(rs);
+    if (ok && gl == 0) {
       const T uc = u[c];
       const T qc = t * (p[c] - corr) - kq * uc;
       U[(size_t)c * ldu + k] = uc;
@@ -396,8 +414,14 @@ void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, lon
                  long long stau, const T* U, const T* Q, int ldu, long long sU, int k, T* part, long long spart,
                  T* y, long long sy, int* ticket, int count, cudaStream_t s, const double* Sg, const double* uw) {
   count_launch();
-  hetrd_phemv_kernel<T><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q, ldu,
-                                                                   sU, k, part, spart, y, sy, ticket, Sg, uw);
+  if ((long long)((j + 63) / 64) * count >= 152)
+    hetrd_phemv_kernel<T, 64><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q,
+                                                                         ldu, sU, k, part, spart, y, sy, ticket, Sg,
+                                                                         uw);
+  else
+    hetrd_phemv_kernel<T, 16><<<dim3((j + 15) / 16, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q,
+                                                                         ldu, sU, k, part, spart, y, sy, ticket, Sg,
+                                                                         uw);
 }
 
 template <typename T>

@@ -124,8 +124,9 @@ def _fd_check(ctx, n, ndir, h, gate, seed):
     Directions D = L G L^T (G of unit Frobenius norm), ndir in H and ndir in S; fourth-
     order central differences of the CUDA solve against the CUDA adjoint must agree to
     `gate` relative plus the difference quotient's own noise, 20 sigma/h, with sigma the
-    measured rounding noise of the loss (the plain FP64 oracle itself misses a bare 1e-6
-    gate at n = 400 on its smallest derivatives)."""
+    measured rounding noise of the loss, at least one rounding unit of the loss value (the
+    plain FP64 oracle itself misses a bare 1e-6 gate at n = 400 on its smallest
+    derivatives)."""
     kT = 0.02
     H, S = I.random_pencil(n, seed, False, 10.0)
     ne = 0.6 * n
@@ -147,7 +148,9 @@ def _fd_check(ctx, n, ndir, h, gate, seed):
     for _ in range(5):
         P = torch.as_tensor(rng.standard_normal((n, n)), device="cuda")
         vals.append(loss(Hd + 1e-15 * (0.5 * (P + P.T))[None], Sd))
-    sigma = float(np.std(vals))
+    # no smaller than the rounding of the loss value itself: with |L| ~ 1e4 perturbations at
+    # the last bit of H can leave every sample on the same float, so std() reads 0
+    sigma = max(float(np.std(vals)), 2.0 ** -52 * abs(vals[0]))
     worst = 0.0
     for which, grad in (("H", Hb), ("S", Sb)):
         gnorm = float(torch.linalg.norm(grad).item())
