@@ -36,6 +36,8 @@ WORKLOADS = {
     "gamma64": dict(desc="64-atom Si cluster, N=832, Gamma, real", tiling=(2, 2, 2)),
     "nc384": dict(desc="384-atom Si cluster, noncollinear 2N=9984, complex128", tiling=(4, 4, 3)),
     "adjoint216": dict(desc="216-atom Si cluster, N=2808, Gamma, real", tiling=(3, 3, 3)),
+    "uneven48": dict(desc="48 independent Si clusters of 16-160 atoms (N=208-2080), the first 12 noncollinear "
+                          "(2N up to 4160, complex128), the rest real; one batched launch sequence", tiling=None),
 }
 # FP64 pipe: nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock, i.e. 3.97 flops per
 # clock per SM over 152 SMs; the peak of a run scales with the SM clock sampled during it.
@@ -117,6 +119,7 @@ SAMPLE_OF = {
     "gamma64": ("the full 64-atom cluster", "cluster", (2, 2, 2)),
     "adjoint216": ("64-atom (2,2,2) cluster", "cluster", (2, 2, 2)),
     "nc384": ("16-atom (2,1,1) noncollinear cluster", "nc", (2, 1, 1)),
+    "uneven48": ("the full 64-atom (2,2,2) real cluster", "cluster", (2, 2, 2)),
 }
 
 
@@ -188,6 +191,106 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+def run_uneven(args):
+    """48 independent systems of uneven order in one batched launch sequence per step
+    (gks_solve_batched), after tuning the outer width per shape class (not timed)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from math import exp
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        from paper_2606_09058_gb300 import build as B
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2606_09058_gb300 import gks, inputs as I
+
+    probs = I.uneven_batch(device=str(dev))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(dev)  # the batched solve forks its worker streams from a non-default stream
+    ctx = gks.Context(local, stream, graph=not args.no_graph)
+    tuned = {}
+    if not args.no_tune:
+        seen = set()
+        for p in probs:
+            n, cplx = p.S.shape[-1], p.H.is_complex()
+            M = p.H.shape[-1]
+            b = 1 << max(6, (M - 1).bit_length())
+            key = (b, cplx, p.spin)
+            if key in seen:
+                continue
+            seen.add(key)
+            best, _ = ctx.tune(n, 1, cplx, p.spin, widths=(64, 128, 256))
+            tuned[f"{'nc' if p.spin == 'noncollinear' else ('c' if cplx else 'r')}{b}"] = best
+    items = [dict(H=p.H.contiguous(), S=p.S.contiguous(), kT=p.kT, n_elec=p.n_elec, spin=p.spin) for p in probs]
+    sols = None
+    for _ in range(max(2, args.warmup)):  # eager, then capture (graph mode), then replays
+        sols = ctx.solve_batched(items, nstreams=8, sync=True, out=sols)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = gks.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.solve_batched(items, nstreams=8, sync=False, out=sols)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = gks.launch_count() - l0
+    clk = clocks.stop()
+    ctx.sync()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+
+    def fermi(x):
+        return exp(-x) / (1 + exp(-x)) if x > 0 else 1 / (1 + exp(x))
+    fl = 0.0
+    for p, sol in zip(probs, sols):
+        M = p.H.shape[-1]
+        e = sol.eps.cpu().numpy()[0]
+        m = float(sol.mu.item())
+        nr = sum(1 for v in e if fermi((v - m) / p.kT) >= 1e-16)
+        fl += nominal_flops(M, p.H.is_complex(), [nr])
+    value = fl * world / (ms / 1e3) / 1e12
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            smp = oracle_sample(args.workload)
+            cpu = {"value": smp["flops"] / smp["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                   "sample": _sample_text(args.workload, smp)}
+        except Exception as ex:
+            cpu = {"value": None, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+    if rank == 0:
+        line = {"metric": "GKS eigensolve+rho throughput (nominal FP64 TFLOP/s)", "value": value, "unit": "TFLOP/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "systems": len(probs),
+                           "systems_per_s": len(probs) * world / (ms / 1e3), "precision": "fp64",
+                           "graph": not args.no_graph,
+                           "tuned_widths": tuned, "nominal_tflop_per_step": fl / 1e12,
+                           "l2": "48 systems, 2.4 GB of inputs, larger than L2 (no flush needed)"},
+                "roofline": None, "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(launches),
+                "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def make_problem(workload: str, device: str):
     from paper_2606_09058_gb300 import inputs as I
     return I.workload(workload, device=device)
@@ -203,9 +306,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-json", default=None, help="write the per-class/per-stage event profile here")
+    ap.add_argument("--no-tune", action="store_true", help="uneven48: skip the width tuner")
+    ap.add_argument("--no-graph", action="store_true", help="uneven48: eager launches instead of graph replay")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "uneven48":
+        return run_uneven(args)
 
     import numpy as np
     import torch

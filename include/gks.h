@@ -171,6 +171,24 @@ gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_
                     const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
                     int mode);
 
+/* Width tuner (the outer block of the two-level blocked Cholesky, reduction and
+ * back-transforms, which is also the Householder panel length).  Solves seeded synthetic
+ * pencils of order n (2n noncollinear), nk items, dtype and spin as gks_solve would, twice
+ * per candidate width (multiples of 64 in 64..1024, host array `widths`), and keeps the
+ * fastest for every later solve on this context whose matrix order falls in the same
+ * power-of-two bucket, element type and spin mode.  Host outputs: ms[i] the device time of
+ * the second solve with widths[i]; *best the chosen width.  Allocates and frees its own
+ * test pencils (≈ 3·nk·M² elements); GKS_EINVAL for invalid arguments or pencils above
+ * 64 GB.  Graph capture is off for the tuning solves. */
+gks_status gks_tune(gks_ctx* ctx, int64_t n, int64_t nk, int dtype, int spin_mode, const int* widths, int count,
+                    double* ms, int* best);
+
+/* Set (width > 0) or forget (width = 0) the tuned width of a shape class, e.g. from a
+ * cache the caller keeps between runs; gks_tune_get returns the width solves of order n
+ * would use now (the tuned one, else opts->block). */
+gks_status gks_tune_set(gks_ctx* ctx, int64_t n, int dtype, int spin_mode, int width);
+int gks_tune_get(const gks_ctx* ctx, int64_t n, int dtype, int spin_mode);
+
 /* Size in bytes of the fixed device scratch behind gks_gemm_split_noalloc. */
 #define GKS_NOALLOC_SCRATCH_BYTES 16777216
 

@@ -2,7 +2,9 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -85,7 +87,9 @@ struct gks_ctx {
   bool graph = false;                  // capture solves into CUDA graphs
   int gemm_mode = 0;                   // 0 auto, 1 DFMA only, 2 split products always
   int slices = 9;                      // 6-bit digits per operand in split products
-  int nbb = 256;                       // outer block of the two-level blocked stages
+  int nbb = 256;                       // outer block of the two-level blocked stages (active)
+  int nbb_default = 256;               // opts.block, used for shapes the tuner has not seen
+  std::map<std::tuple<int, int, int>, int> tuned;  // (order bucket, element size, spin) -> width
   void* oz = nullptr;                  // digit workspace of the split-product GEMM
   size_t oz_bytes = 0;
   cudaGraphExec_t gexec = nullptr;     // graph of the last captured solve
@@ -159,10 +163,24 @@ void release_ws(gks_ctx* c) {
   c->m = -1;
 }
 
+// Orders share a tuned width by power-of-two bucket.
+int order_bucket(int m) {
+  int b = 64;
+  while (b < m) b <<= 1;
+  return b;
+}
+
+int pick_width(const gks_ctx* c, int m, int es, int nc) {
+  auto it = c->tuned.find(std::make_tuple(order_bucket(m), es, nc));
+  return it != c->tuned.end() ? it->second : c->nbb_default;
+}
+
 // Workspace for nk problems of order m (element size es, n = basis per spin).
 gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
-  if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc) return GKS_OK;
+  const int want = pick_width(c, m, es, nc);
+  if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc && c->nbb == want) return GKS_OK;
   release_ws(c);
+  c->nbb = want;
   const size_t MM = (size_t)m * m;
   c->sMM = (long long)MM;
   const int nbb = c->nbb;
@@ -933,6 +951,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     c->gemm_mode = opts->gemm;
     if (opts->slices > 0) c->slices = opts->slices;
     if (opts->block > 0) c->nbb = opts->block;
+    c->nbb_default = c->nbb;
     if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 10 || c->nbb < NB || c->nbb > 1024 ||
         c->nbb % NB) {
       delete c;
@@ -1033,8 +1052,10 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     sc->gemm_mode = ctx->gemm_mode;
     sc->slices = ctx->slices;
     sc->nbb = ctx->nbb;
+    sc->nbb_default = ctx->nbb_default;
     ctx->subs.push_back(sc);
   }
+  for (auto* sc : ctx->subs) sc->tuned = ctx->tuned;
   auto body = [&]() -> gks_status {
     cudaEvent_t fork;
     cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
@@ -1228,6 +1249,96 @@ gks_status gks_gemm_split_noalloc(gks_ctx* ctx, int dtype, int opA, int opB, int
                    ctx->slices, scratch, nullptr, ctx->stream);
   if (!ok) return fail(ctx, GKS_ECUDA, "gks_gemm_split_noalloc: TMA tensor map encoding unavailable");
   return cuda_check(ctx, "gks_gemm_split_noalloc");
+}
+
+gks_status gks_tune(gks_ctx* ctx, int64_t n, int64_t nk, int dtype, int spin_mode, const int* widths, int count,
+                    double* ms, int* best) {
+  if (!ctx || n < 1 || nk < 1 || !widths || count < 1 || !ms || !best) return fail(ctx, GKS_EINVAL, "bad arguments");
+  if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
+  if (spin_mode != GKS_COLLINEAR && spin_mode != GKS_NONCOLLINEAR) return fail(ctx, GKS_EINVAL, "unknown spin mode");
+  const bool nc = spin_mode == GKS_NONCOLLINEAR;
+  if (nc && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear requires complex");
+  for (int i = 0; i < count; i++)
+    if (widths[i] < NB || widths[i] > 1024 || widths[i] % NB) return fail(ctx, GKS_EINVAL, "width not a multiple of 64 in 64..1024");
+  const int M = nc ? 2 * (int)n : (int)n;
+  const int es = dtype == GKS_C128 ? 16 : 8;
+  if ((double)M * M * nk * es > 64e9) return fail(ctx, GKS_EINVAL, "tuning problem too large");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_check(ctx, "gks_tune: set device");
+  const size_t bH = (size_t)M * M * nk * es, bS = (size_t)n * n * nk * es;
+  void *H = nullptr, *S = nullptr, *C = nullptr, *rho = nullptr;
+  double *eps = nullptr, *mu = nullptr;
+  auto release = [&]() {
+    cudaFree(H);
+    cudaFree(S);
+    cudaFree(C);
+    cudaFree(rho);
+    cudaFree(eps);
+    cudaFree(mu);
+  };
+  if (cudaMalloc(&H, bH) != cudaSuccess || cudaMalloc(&S, bS) != cudaSuccess || cudaMalloc(&C, bH) != cudaSuccess ||
+      cudaMalloc(&rho, bH) != cudaSuccess || cudaMalloc(&eps, sizeof(double) * M * nk) != cudaSuccess ||
+      cudaMalloc(&mu, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(ctx, GKS_ENOMEM, "gks_tune: allocation of the test pencils failed");
+  }
+  if (es == 16) {
+    tune_pencil<zc>(static_cast<zc*>(H), M, (int)nk, 1, ctx->stream);
+    tune_pencil<zc>(static_cast<zc*>(S), (int)n, (int)nk, 0, ctx->stream);
+  } else {
+    tune_pencil<double>(static_cast<double*>(H), M, (int)nk, 1, ctx->stream);
+    tune_pencil<double>(static_cast<double*>(S), (int)n, (int)nk, 0, ctx->stream);
+  }
+  const auto key = std::make_tuple(order_bucket(M), es, nc ? 1 : 0);
+  const bool graph = ctx->graph;
+  ctx->graph = false;
+  const double gs = nc ? 1.0 : 2.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  gks_status rc = GKS_OK;
+  int bi = 0;
+  for (int i = 0; i < count && rc == GKS_OK; i++) {
+    ctx->tuned[key] = widths[i];
+    for (int rep = 0; rep < 2 && rc == GKS_OK; rep++) {
+      cudaEventRecord(e0, ctx->stream);
+      rc = gks_solve(ctx, H, S, n, nk, dtype, spin_mode, 0.01, 0.5 * gs * M, nullptr, 0, eps, C, mu, rho, nullptr);
+      cudaEventRecord(e1, ctx->stream);
+      if (rc == GKS_OK) rc = gks_sync(ctx);
+    }
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms[i] = t;
+    if (ms[i] < ms[bi]) bi = i;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->graph = graph;
+  release();
+  if (rc != GKS_OK) {
+    ctx->tuned.erase(key);
+    return rc;
+  }
+  ctx->tuned[key] = widths[bi];
+  *best = widths[bi];
+  return cuda_check(ctx, "gks_tune");
+}
+
+gks_status gks_tune_set(gks_ctx* ctx, int64_t n, int dtype, int spin_mode, int width) {
+  if (!ctx || n < 1 || (dtype != GKS_R64 && dtype != GKS_C128)) return fail(ctx, GKS_EINVAL, "bad arguments");
+  if (width != 0 && (width < NB || width > 1024 || width % NB))
+    return fail(ctx, GKS_EINVAL, "width not a multiple of 64 in 64..1024");
+  const bool nc = spin_mode == GKS_NONCOLLINEAR;
+  const auto key = std::make_tuple(order_bucket(nc ? 2 * (int)n : (int)n), dtype == GKS_C128 ? 16 : 8, nc ? 1 : 0);
+  if (width == 0) ctx->tuned.erase(key);
+  else ctx->tuned[key] = width;
+  return GKS_OK;
+}
+
+int gks_tune_get(const gks_ctx* ctx, int64_t n, int dtype, int spin_mode) {
+  if (!ctx || n < 1) return 0;
+  const bool nc = spin_mode == GKS_NONCOLLINEAR;
+  return pick_width(ctx, nc ? 2 * (int)n : (int)n, dtype == GKS_C128 ? 16 : 8, nc ? 1 : 0);
 }
 
 gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype) {

@@ -376,6 +376,39 @@ void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int
   spinor_overlap_kernel<T><<<grid2d(2 * n, 2 * n, count), 256, 0, s>>>(dst, sd, S, lds, ss, n);
 }
 
+// Seeded test pencils for the width tuner (no input data needed): splitmix64 of the
+// element index gives uniform numbers.  hermitian = 1: entries in [-1, 1] (both parts);
+// hermitian = 0: S = I + entries in [-0.5, 0.5]/m off the diagonal (diagonally dominant).
+__device__ __forceinline__ double tune_uniform(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * 0x1.0p-53;
+}
+
+template <typename T>
+__global__ void tune_pencil_kernel(T* A, int m, int hermitian) {
+  const int z = blockIdx.z;
+  A += (size_t)z * m * m;
+  for (int i = blockIdx.y; i < m; i += gridDim.y)
+    for (int jj = blockIdx.x * blockDim.x + threadIdx.x; jj <= i; jj += gridDim.x * blockDim.x) {
+      const unsigned long long id = (((unsigned long long)z * m + i) * m + jj) * 2ull;
+      const double a = 2.0 * tune_uniform(id) - 1.0, b = 2.0 * tune_uniform(id + 1) - 1.0;
+      T v;
+      if constexpr (sizeof(T) == 16) v = zc{a, i == jj ? 0.0 : b};
+      else v = a;
+      if (!hermitian) v = (i == jj) ? from_real<T>(1.0) : (0.5 / m) * v;
+      A[(size_t)i * m + jj] = v;
+    }
+}
+
+template <typename T>
+void tune_pencil(T* A, int m, int count, int hermitian, cudaStream_t s) {
+  count_launch();
+  tune_pencil_kernel<T><<<grid2d(m, m, count), 256, 0, s>>>(A, m, hermitian);
+}
+
 #define INST(T)                                                                                         \
   template void potf2<T>(T*, int, long long, int, int, DevStatus*, int, cudaStream_t);                   \
   template void trsm_block<T>(int, const T*, int, long long, T*, int, long long, int, int, int,         \
@@ -388,7 +421,8 @@ void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int
                                int, int, cudaStream_t);                                                 \
   template void mirror_lower<T>(T*, int, long long, int, int, cudaStream_t);                            \
   template void column_phase<T>(T*, int, long long, int, int, int, cudaStream_t);                      \
-  template void spinor_overlap<T>(T*, long long, const T*, int, long long, int, int, cudaStream_t);
+  template void spinor_overlap<T>(T*, long long, const T*, int, long long, int, int, cudaStream_t);         \
+  template void tune_pencil<T>(T*, int, int, int, cudaStream_t);
 INST(double)
 INST(zc)
 

@@ -27,6 +27,9 @@ template <typename T>
 void column_phase(T* C, int ldc, long long sC, int rows, int cols, int count, cudaStream_t s);
 template <typename T>
 void spinor_overlap(T* dst, long long sd, const T* S, int lds, long long ss, int n, int count, cudaStream_t s);
+// Seeded lower-triangle test pencils for the width tuner (hermitian 1: H, 0: SPD S).
+template <typename T>
+void tune_pencil(T* A, int m, int count, int hermitian, cudaStream_t s);
 
 // ---- Householder tridiagonalization (hetrd.cu) ----
 // Workspace per batch item: u (m), p (m) vectors, tau (m), two zeroed tickets, and for the

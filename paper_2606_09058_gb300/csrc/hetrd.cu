@@ -414,7 +414,7 @@ void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, lon
                  long long stau, const T* U, const T* Q, int ldu, long long sU, int k, T* part, long long spart,
                  T* y, long long sy, int* ticket, int count, cudaStream_t s, const double* Sg, const double* uw) {
   count_launch();
-  if ((long long)((j + 63) / 64) * count >= 152)
+  if ((long long)((j + 63) / 64) * count >= 4 * 152)
     hetrd_phemv_kernel<T, 64><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q,
                                                                          ldu, sU, k, part, spart, y, sy, ticket, Sg,
                                                                          uw);

@@ -74,6 +74,13 @@ def load() -> ctypes.CDLL:
     lib.gks_gemm.restype = I
     lib.gks_gemm_split_noalloc.argtypes = [P, I, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64]
     lib.gks_gemm_split_noalloc.restype = I
+    lib.gks_tune.argtypes = [P, I64, I64, I, I, ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_int)]
+    lib.gks_tune.restype = I
+    lib.gks_tune_set.argtypes = [P, I64, I, I, I]
+    lib.gks_tune_set.restype = I
+    lib.gks_tune_get.argtypes = [P, I64, I, I]
+    lib.gks_tune_get.restype = I
     lib.gks_solve_batched.argtypes = [P, I64, ctypes.POINTER(_Problem), I]
     lib.gks_solve_batched.restype = I
     lib.gks_adjoint.argtypes = [P, P, P, P, I64, I64, I, I, D, P, P, P, D, P, P]
@@ -263,6 +270,26 @@ class Context:
         self._raise(rc)
         self.sync()
         return C
+
+    def tune(self, n: int, nk: int = 1, complex_: bool = False, spin: str = "collinear",
+             widths=(128, 256, 384, 512)) -> tuple[int, dict]:
+        """gks_tune: time the candidate outer widths on seeded pencils of this shape and keep
+        the fastest for the shape class; returns (best width, {width: ms})."""
+        w = (ctypes.c_int * len(widths))(*widths)
+        ms = (ctypes.c_double * len(widths))()
+        best = ctypes.c_int()
+        rc = self._lib.gks_tune(self._h, int(n), int(nk), GKS_C128 if complex_ else GKS_R64,
+                                1 if spin == "noncollinear" else 0, w, len(widths), ms, ctypes.byref(best))
+        self._raise(rc)
+        return best.value, {int(widths[i]): ms[i] for i in range(len(widths))}
+
+    def tune_set(self, n: int, complex_: bool, spin: str, width: int):
+        self._raise(self._lib.gks_tune_set(self._h, int(n), GKS_C128 if complex_ else GKS_R64,
+                                           1 if spin == "noncollinear" else 0, int(width)))
+
+    def tune_get(self, n: int, complex_: bool = False, spin: str = "collinear") -> int:
+        return self._lib.gks_tune_get(self._h, int(n), GKS_C128 if complex_ else GKS_R64,
+                                      1 if spin == "noncollinear" else 0)
 
     def gemm_split_noalloc(self, A, B, C, opA="N", opB="N", alpha=1.0, beta=0.0):
         """C = alpha op(A) op(B) + beta C through gks_gemm_split_noalloc: the split product
