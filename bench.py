@@ -310,6 +310,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="uneven48: eager launches instead of graph replay")
     ap.add_argument("--gemm", default="auto", choices=["auto", "fp64", "split"],
                     help="products: auto (split-bf16 tensor-core products where they pay), fp64 (FP64 pipe only)")
+    ap.add_argument("--block", type=int, default=0, help="outer block width (0 = library default)")
     ap.add_argument("--per-k", action="store_true",
                     help="solve the k-points one call each (nk = 1, shared mu lost) instead of one batched call")
     args = ap.parse_args()
@@ -342,7 +343,7 @@ def main():
     spin = prob.spin
     kw = torch.as_tensor(np.asarray(prob.kweights, float), device=dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = gks.Context(local, stream, profile=True, gemm=args.gemm)
+    ctx = gks.Context(local, stream, profile=True, gemm=args.gemm, block=args.block)
     eps = torch.empty(nk, M, dtype=torch.float64, device=dev)
     C = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
     rho = torch.empty_like(C)
@@ -478,6 +479,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "M": M, "nk": nk,
                            "spin": spin, "precision": "fp64", "products": args.gemm,
+                           "block": args.block or 256,
                            "batching": "one call per k-point" if args.per_k else "all k-points in one call",
                            "l2": "inputs larger than L2 (no flush needed)",
                            "nominal_tflop_per_step": fl_step / 1e12, "n_rho": nrho},

@@ -345,7 +345,8 @@ int oz_reserve(gks_ctx* c, size_t item, int count) {
 
 bool split_worth(gks_ctx* c, int count, int M, int N, int K, int es, double fl) {
   if (c->gemm_mode == 2) return true;
-  return c->gemm_mode == 0 && fl >= 5e8 * count && M >= 128 && N >= 128 && K >= 64 &&
+  const int Ne = es == 16 ? 2 * N : N;  // embedded output columns
+  return c->gemm_mode == 0 && fl >= 2e8 * count && M >= 64 && Ne >= 64 && K >= 64 &&
          (long long)ozaki_tiles(M, N, es == 16) * count >= 152;
 }
 
@@ -576,8 +577,9 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   int* tk = at<int>(c, c->oticket);
   if (M < 3) return;
   cudaMemsetAsync(tk, 0, sizeof(int) * 2 * nk, s);
-  // small orders are latency-bound per step: shorter panels keep the corrections short
-  const int pw = M < 2048 ? std::min(NB, ldu) : ldu;
+  // panels of at most 128 steps: the per-step corrections grow with the panel length, the
+  // deferred update runs fine at K = 128; small orders are latency-bound per step (64)
+  const int pw = M < 2048 ? std::min(NB, ldu) : std::min(2 * NB, ldu);
   // complex: three-multiplication products need Re + Im of the stale block (per panel)
   double* uw = es == 16 ? at<double>(c, c->ouw) : nullptr;
   double* Sg = es == 16 ? at<double>(c, c->oSg) : nullptr;
