@@ -479,7 +479,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "M": M, "nk": nk,
                            "spin": spin, "precision": "fp64", "products": args.gemm,
-                           "block": args.block or 256,
+                           "block": args.block or (512 if M >= 4096 else 256),
                            "batching": "one call per k-point" if args.per_k else "all k-points in one call",
                            "l2": "inputs larger than L2 (no flush needed)",
                            "nominal_tflop_per_step": fl_step / 1e12, "n_rho": nrho},

@@ -56,7 +56,8 @@ typedef struct {
                           1 = FP64 pipe only; 2 = split products for every product */
   int slices;          /* 6-bit digits per operand in split products (4..10, 0 = 9) */
   int block;           /* outer block width of the two-level blocked Cholesky, reduction and
-                          back-transforms: a multiple of 64 in 64..1024, 0 = 256 */
+                          back-transforms: a multiple of 64 in 64..1024; 0 = 512 for orders
+                          from 4096 up and 256 below (gks_tune overrides per shape class) */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */
@@ -185,7 +186,7 @@ gks_status gks_tune(gks_ctx* ctx, int64_t n, int64_t nk, int dtype, int spin_mod
 
 /* Set (width > 0) or forget (width = 0) the tuned width of a shape class, e.g. from a
  * cache the caller keeps between runs; gks_tune_get returns the width solves of order n
- * would use now (the tuned one, else opts->block). */
+ * would use now (the tuned one, else opts->block, else the size default). */
 gks_status gks_tune_set(gks_ctx* ctx, int64_t n, int dtype, int spin_mode, int width);
 int gks_tune_get(const gks_ctx* ctx, int64_t n, int dtype, int spin_mode);
 

@@ -89,6 +89,7 @@ struct gks_ctx {
   int slices = 9;                      // 6-bit digits per operand in split products
   int nbb = 256;                       // outer block of the two-level blocked stages (active)
   int nbb_default = 256;               // opts.block, used for shapes the tuner has not seen
+  bool nbb_fixed = false;              // opts.block given: no size-dependent default
   std::map<std::tuple<int, int, int>, int> tuned;  // (order bucket, element size, spin) -> width
   void* oz = nullptr;                  // digit workspace of the split-product GEMM
   size_t oz_bytes = 0;
@@ -170,9 +171,13 @@ int order_bucket(int m) {
   return b;
 }
 
+// Width for a shape: the tuned one, else opts.block, else 512 from order 4096 up (the WY
+// back-transform gains most from wider blocks there) and 256 below.
 int pick_width(const gks_ctx* c, int m, int es, int nc) {
   auto it = c->tuned.find(std::make_tuple(order_bucket(m), es, nc));
-  return it != c->tuned.end() ? it->second : c->nbb_default;
+  if (it != c->tuned.end()) return it->second;
+  if (c->nbb_fixed) return c->nbb_default;
+  return m >= 4096 ? 512 : 256;
 }
 
 // Workspace for nk problems of order m (element size es, n = basis per spin).
@@ -954,6 +959,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     if (opts->slices > 0) c->slices = opts->slices;
     if (opts->block > 0) c->nbb = opts->block;
     c->nbb_default = c->nbb;
+    c->nbb_fixed = opts->block > 0;
     if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 10 || c->nbb < NB || c->nbb > 1024 ||
         c->nbb % NB) {
       delete c;
@@ -1055,6 +1061,7 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     sc->slices = ctx->slices;
     sc->nbb = ctx->nbb;
     sc->nbb_default = ctx->nbb_default;
+    sc->nbb_fixed = ctx->nbb_fixed;
     ctx->subs.push_back(sc);
   }
   for (auto* sc : ctx->subs) sc->tuned = ctx->tuned;
