@@ -36,6 +36,8 @@ WORKLOADS = {
     "gamma64": dict(desc="64-atom Si cluster, N=832, Gamma, real", tiling=(2, 2, 2)),
     "nc384": dict(desc="384-atom Si cluster, noncollinear 2N=9984, complex128", tiling=(4, 4, 3)),
     "adjoint216": dict(desc="216-atom Si cluster, N=2808, Gamma, real", tiling=(3, 3, 3)),
+    "product4096": dict(desc="one FP64-accurate split-bf16 product, complex 4096 x 4096 x 4096 (the tensor-core "
+                             "kernel of the path on its own)", tiling=None),
     "uneven48": dict(desc="48 independent Si clusters of 16-160 atoms (N=208-2080), the first 12 noncollinear "
                           "(2N up to 4160, complex128), the rest real; one batched launch sequence", tiling=None),
 }
@@ -191,6 +193,78 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+def run_product(args):
+    """One complex 4096^3 product through gks_gemm (split-bf16 digits, FP64 accumulation),
+    with the tensor roofline of the executed bf16 work: per product 2 Mp N'p K'p bf16 flops
+    for each of the 45 digit pairs of S = 9 (N' = 2N, K' = 2K for the real embedding)."""
+    import numpy as np
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2606_09058_gb300 import build as B
+    B.build()
+    from paper_2606_09058_gb300 import gks
+    n = 4096
+    g = torch.Generator(device=dev).manual_seed(9058005)
+    A = torch.randn(n, n, dtype=torch.complex128, device=dev, generator=g)
+    Bm = torch.randn(n, n, dtype=torch.complex128, device=dev, generator=g)
+    C = torch.zeros(n, n, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gks.Context(local, stream)
+    lib, h = ctx._lib, ctx._h
+
+    def prod():
+        rc = lib.gks_gemm(h, gks.GKS_C128, 0, 0, n, n, n, 1.0, A.data_ptr(), n, Bm.data_ptr(), n, 0.0, C.data_ptr(),
+                          n, 2)
+        if rc:
+            raise RuntimeError(f"gks_gemm failed: {rc}")
+    for _ in range(max(3, args.warmup)):
+        prod()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = gks.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    steps = max(args.steps, 5)
+    for _ in range(steps):
+        prod()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = gks.launch_count() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
+    ref_err = None
+    if rank == 0:  # spot check against torch's FP64 product on 64 rows
+        ref = A[:64] @ Bm
+        ref_err = float(((C[:64] - ref).abs().max() / ref.abs().max()).item())
+    fl = 8.0 * n ** 3
+    bf16 = 2.0 * n * (2 * n) * (2 * n) * 45
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    ach = bf16 / (ms / 1e3) / 1e12
+    if rank == 0:
+        line = {"metric": "FP64-accurate complex product throughput (FP64-equivalent TFLOP/s)",
+                "value": fl / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16 digits, fp32 tensor accumulation, fp64 sums", "data": "synthetic",
+                "config": {"workload": "product4096", "desc": WORKLOADS["product4096"]["desc"],
+                           "max_rel_err_vs_fp64_rows0_63": ref_err,
+                           "l2": "operands and digits (1.8 GB) larger than L2 (no flush needed)"},
+                "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+                             "frac": ach / bf16_peak, "traffic": None, "kernel": "oz_tc_kernel + oz_split_kernel",
+                             "peak_basis": "bf16 dense, MEASURED_PEAKS.json burst"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches),
+                "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_uneven(args):
     """48 independent systems of uneven order in one batched launch sequence per step
     (gks_solve_batched), after tuning the outer width per shape class (not timed)."""
@@ -318,6 +392,8 @@ def main():
         return reference_arm(args)
     if args.workload == "uneven48":
         return run_uneven(args)
+    if args.workload == "product4096":
+        return run_product(args)
 
     import numpy as np
     import torch
