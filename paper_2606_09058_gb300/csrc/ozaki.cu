@@ -334,7 +334,18 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
   __shared__ int abort_flag;
   unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, z = blockIdx.z;
+  // grouped tile order: consecutive CTAs walk 8 row tiles of one column tile, then the next
+  // column tile, so the CTAs resident together share both operands' digit tiles in L2
+  int m0, n0;
+  {
+    constexpr int G = 8;
+    const int ntn = gridDim.x, ntm = gridDim.y;
+    const int bid = blockIdx.y * ntn + blockIdx.x, per = G * ntn;
+    const int fm = (bid / per) * G, gs = min(ntm - fm, G), r = bid % per;
+    m0 = (fm + r % gs) * BM;
+    n0 = (r / gs) * BN;
+  }
+  const int z = blockIdx.z;
   const int ncol0 = a.cplx ? n0 / 2 : n0;
   if (a.lower && m0 + BM - 1 < ncol0) return;  // whole tile above the diagonal (uniform)
 
