@@ -77,14 +77,16 @@ __global__ void __launch_bounds__(64) trsm_block_kernel(const T* L, int ldl, lon
       T* xr = x + tid * ld;
       for (int j = 0; j < nb; j++) {  // x L^H = b  <=>  x_j = (b_j - sum_{k<j} x_k conj(L_jk)) / L_jj
         const T* lj = L + (size_t)j * ldl;
-        T s0 = xr[j], s1 = zero<T>();
+        T s0 = xr[j], s1 = zero<T>(), s2 = zero<T>(), s3 = zero<T>();  // four chains (latency)
         int k = 0;
-        for (; k + 1 < j; k += 2) {
+        for (; k + 3 < j; k += 4) {
           s0 -= xr[k] * conjg(lj[k]);
           s1 -= xr[k + 1] * conjg(lj[k + 1]);
+          s2 -= xr[k + 2] * conjg(lj[k + 2]);
+          s3 -= xr[k + 3] * conjg(lj[k + 3]);
         }
-        if (k < j) s0 -= xr[k] * conjg(lj[k]);
-        xr[j] = (s0 + s1) * (1.0 / re(lj[j]));
+        for (; k < j; k++) s0 -= xr[k] * conjg(lj[k]);
+        xr[j] = ((s0 + s1) + (s2 + s3)) * (1.0 / re(lj[j]));
       }
     }
     __syncthreads();
@@ -104,25 +106,29 @@ __global__ void __launch_bounds__(64) trsm_block_kernel(const T* L, int ldl, lon
       if (MODE == TRSM_LEFT) {
         for (int i = 0; i < nb; i++) {  // x_i = (b_i - sum_{k<i} L_ik x_k) / L_ii
           const T* li = L + (size_t)i * ldl;
-          T s0 = xc[i * ld], s1 = zero<T>();
+          T s0 = xc[i * ld], s1 = zero<T>(), s2 = zero<T>(), s3 = zero<T>();
           int k = 0;
-          for (; k + 1 < i; k += 2) {
+          for (; k + 3 < i; k += 4) {
             s0 -= li[k] * xc[k * ld];
             s1 -= li[k + 1] * xc[(k + 1) * ld];
+            s2 -= li[k + 2] * xc[(k + 2) * ld];
+            s3 -= li[k + 3] * xc[(k + 3) * ld];
           }
-          if (k < i) s0 -= li[k] * xc[k * ld];
-          xc[i * ld] = (s0 + s1) * (1.0 / re(li[i]));
+          for (; k < i; k++) s0 -= li[k] * xc[k * ld];
+          xc[i * ld] = ((s0 + s1) + (s2 + s3)) * (1.0 / re(li[i]));
         }
       } else {
         for (int i = nb - 1; i >= 0; i--) {  // x_i = (b_i - sum_{k>i} conj(L_ki) x_k) / L_ii
-          T s0 = xc[i * ld], s1 = zero<T>();
+          T s0 = xc[i * ld], s1 = zero<T>(), s2 = zero<T>(), s3 = zero<T>();
           int k = i + 1;
-          for (; k + 1 < nb; k += 2) {
+          for (; k + 3 < nb; k += 4) {
             s0 -= conjg(L[(size_t)k * ldl + i]) * xc[k * ld];
             s1 -= conjg(L[(size_t)(k + 1) * ldl + i]) * xc[(k + 1) * ld];
+            s2 -= conjg(L[(size_t)(k + 2) * ldl + i]) * xc[(k + 2) * ld];
+            s3 -= conjg(L[(size_t)(k + 3) * ldl + i]) * xc[(k + 3) * ld];
           }
-          if (k < nb) s0 -= conjg(L[(size_t)k * ldl + i]) * xc[k * ld];
-          xc[i * ld] = (s0 + s1) * (1.0 / re(L[(size_t)i * ldl + i]));
+          for (; k < nb; k++) s0 -= conjg(L[(size_t)k * ldl + i]) * xc[k * ld];
+          xc[i * ld] = ((s0 + s1) + (s2 + s3)) * (1.0 / re(L[(size_t)i * ldl + i]));
         }
       }
     }
