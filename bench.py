@@ -60,6 +60,17 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The slowest rank's value (whole-job time); the value itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -322,11 +333,7 @@ def run_uneven(args):
     launches = gks.launch_count() - l0
     clk = clocks.stop()
     ctx.sync()
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
 
     def fermi(x):
         return exp(-x) / (1 + exp(-x)) if x > 0 else 1 / (1 + exp(x))
@@ -455,11 +462,7 @@ def main():
     clk = clocks.stop()
     ctx.sync()
     prof = ctx.profile()
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
 
     eps_h = eps.cpu().numpy()
     mu_h = float(mu.item())
@@ -527,11 +530,7 @@ def main():
         torch.cuda.synchronize()
         ctx.sync()
         ctx.profile()
-        ems = f0.elapsed_time(f1) / args.steps
-        t = torch.tensor([ems], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
+        ems = max_over_ranks(f0.elapsed_time(f1) / args.steps, dev)
         e2e = {"value": fl_step * world / (ems / 1e3) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(Hh.numel() * Hh.element_size() + Sh.numel() * Sh.element_size()),
                "d2h_bytes_per_step": int(eps_out.numel() * 8 + 16), "ms_per_step": ems}
