@@ -263,3 +263,16 @@ def test_blocked_solve_outer_widths(ctx_block, cplx):
     m = 389
     H, S = I.random_pencil(m, 600 + cplx, cplx, cond=1e2)
     _compare(ctx_block, H[None], S[None], 0.1, 0.6 * m, raw=True)
+
+
+# ------------------------------------------------------------------ FP64-pipe-only products
+
+@pytest.mark.parametrize("cplx,m", [(False, 461), (True, 389)])
+def test_solve_fp64_products_only(cplx, m):
+    """Every product on the FP64 pipe (no split products): the plain FP64 form of the path."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_09058_gb300 import gks
+    c64 = gks.Context(0, gemm="fp64", block=128)
+    H, S = I.random_pencil(m, 900 + m, cplx, cond=1e2)
+    _compare(c64, H[None], S[None], 0.1, 0.6 * m, raw=True)
