@@ -1020,7 +1020,11 @@ gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int6
     return cuda_check(ctx, "graph launch");
   }
   const int M = spin_mode == GKS_NONCOLLINEAR ? (int)(2 * n) : (int)n;
-  const bool ready = ctx->ws && ctx->m == M && ctx->nk == nk && ctx->es == (dtype == GKS_R64 ? 8 : 16) &&
+  const int es = dtype == GKS_R64 ? 8 : 16;
+  // capture only when the workspace (order, batch, type and width) is already in place,
+  // so that nothing is allocated or freed while the stream is being captured
+  const bool ready = ctx->ws && ctx->m == M && ctx->nk == nk && ctx->es == es &&
+                     ctx->nbb == pick_width(ctx, M, es, spin_mode == GKS_NONCOLLINEAR ? 1 : 0) &&
                      ctx->gkey.H == k.H && ctx->gkey.C == k.C;
   ctx->gkey = k;
   if (ctx->gexec) {
