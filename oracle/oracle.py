@@ -9,7 +9,9 @@ it.  Everything here is plain FP64:
   gks_oracle.c (Cholesky, explicit substitution, Householder, implicit QL, back
   substitution);
 * occupations, chemical potential, band energy and density matrix (paper Sec. 3.1
-  Parts 3 and 4; Sec. 2 density-matrix definition) are direct numpy sums.
+  Parts 3 and 4; Sec. 2 density-matrix definition) are direct numpy sums;
+* refine_truth: Ogita-Aishima refinement of those eigenpairs with double-double residual
+  products, a reference beyond the FP64 rounding of the eigensolver itself.
 
 Readings where the paper is silent (each listed in the design notes):
 * Fermi-Dirac f(x) = 1/(1+e^x), x = (eps - mu)/kT (the paper names f_i only);
@@ -273,6 +275,108 @@ def eig_condition(H, S, eps, C):
     ns = np.linalg.norm(S, 2)
     cn = np.sum(np.abs(C) ** 2, axis=0)
     return U_ROUND * (nh + np.abs(eps) * ns) * cn
+
+
+# ----------------------------- truth refinement -----------------------------
+#
+# A reference beyond FP64 rounding of the computation: Ogita-Aishima refinement steps
+# (Ogita & Aishima 2018, generalized here with the S inner product) applied to the
+# oracle's eigenpairs of the stored FP64 pencil, with the residual products X^H S X and
+# X^H H X evaluated to about twice FP64 precision.  Those products use error-free
+# splitting (Ozaki, Ogita, Oishi, Rump): every entry is cut into three 21-bit slices
+# relative to its row's (or column's) largest entry, each slice product is then an exact
+# FP64 matrix product (21 + 21 bits per term, at most 2^11 terms), and the slice products
+# are summed in double-double arithmetic (Knuth's TwoSum).
+
+def _two_sum(a, b):
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def _slices(X, axis, nbits=21, count=3):
+    """Real X = 2^e (sum_s D_s 2^{-nbits (s+1)}) + remainder below 2^{e - nbits count},
+    e per row (axis=1) or column (axis=0); D_s integer-valued."""
+    m = np.max(np.abs(X), axis=axis, keepdims=True)
+    e = np.where(m > 0, np.ceil(np.log2(np.where(m > 0, m, 1.0))) + 1, 0.0)
+    r = np.ldexp(X, (-e).astype(int))
+    out = []
+    for _ in range(count):
+        t = np.ldexp(r, nbits)
+        d = np.trunc(t)
+        out.append(d)
+        r = t - d
+    return e, out
+
+
+def _dd_matmul_real(A, B, nbits=21, count=3):
+    """(hi, lo) with hi + lo = A @ B to about 2^-(nbits count) of the row and column scales."""
+    if A.shape[1] > 2 ** (53 - 2 * nbits):
+        raise ValueError("inner dimension too large for exact slice products")
+    ea, As = _slices(A, 1, nbits, count)
+    eb, Bs = _slices(B, 0, nbits, count)
+    hi = np.zeros((A.shape[0], B.shape[1]))
+    lo = np.zeros_like(hi)
+    for s in range(count):
+        for t in range(count):
+            if s + t > count:  # below the kept precision
+                continue
+            P = As[s] @ Bs[t]  # exact: integers below 2^53
+            P = np.ldexp(P, (ea + eb - nbits * (s + t + 2)).astype(int))
+            hi, err = _two_sum(hi, P)
+            lo += err
+    return _two_sum(hi, lo)
+
+
+def dd_matmul(A, B):
+    """A @ B (real or complex) as a double-double pair (hi, lo)."""
+    if not (np.iscomplexobj(A) or np.iscomplexobj(B)):
+        return _dd_matmul_real(np.asarray(A, float), np.asarray(B, float))
+    Ar, Ai = np.real(A).astype(float), np.imag(A).astype(float)
+    Br, Bi = np.real(B).astype(float), np.imag(B).astype(float)
+    parts = []
+    for X, Y, sign in ((Ar, Br, 1), (Ai, Bi, -1), (Ar, Bi, 1), (Ai, Br, 1)):
+        h, l = _dd_matmul_real(X, Y)
+        parts.append((sign * h, sign * l))
+    rh, rl = _two_sum(parts[0][0], parts[1][0])
+    rl = rl + parts[0][1] + parts[1][1]
+    ih, il = _two_sum(parts[2][0], parts[3][0])
+    il = il + parts[2][1] + parts[3][1]
+    return rh + 1j * ih, rl + 1j * il
+
+
+def refine_truth(H, S, eps, C, sweeps: int = 3):
+    """Refined eigenpairs of the stored pencil (H, S): Ogita-Aishima steps with
+    R = I - X^H S X and T = X^H H X in double-double,
+        lambda_i = t_ii / (1 - r_ii),  e_ii = r_ii / 2,
+        e_ij = (t_ij + lambda_j r_ij) / (lambda_j - lambda_i)  (separated pairs),
+        e_ij = r_ij / 2                                         (|lambda_i - lambda_j| <= omega),
+        X <- X + X E,
+    omega = 2 (||T - diag(lambda)||_2 + ||H||_2 ||R||_2) as in the published method.
+    Returns (lambda, X) after `sweeps` steps; lambda carries the double-double residuals'
+    accuracy (not FP64 rounding of the eigensolver)."""
+    X = np.array(C, dtype=np.result_type(C, H, S))
+    nh = np.linalg.norm(H, 2)
+    lam = np.asarray(eps, float).copy()
+    M = X.shape[1]
+    for _ in range(sweeps):
+        SXh, SXl = dd_matmul(S, X)
+        HXh, HXl = dd_matmul(H, X)
+        Xh = X.conj().T
+        Gh, Gl = dd_matmul(Xh, SXh)
+        Gl = Gl + Xh @ SXl
+        Th, Tl = dd_matmul(Xh, HXh)
+        Tl = Tl + Xh @ HXl
+        R = -(Gh - np.eye(M)) - Gl
+        T = Th + Tl
+        lam = np.real(np.diag(T)) / (1.0 - np.real(np.diag(R)))
+        omega = 2.0 * (np.linalg.norm(T - np.diag(lam), 2) + nh * np.linalg.norm(R, 2))
+        D = lam[None, :] - lam[:, None]  # D_ij = lambda_j - lambda_i
+        sep = np.abs(D) > omega
+        E = np.where(sep, (T + lam[None, :] * R) / np.where(sep, D, 1.0), R / 2.0)
+        np.fill_diagonal(E, np.real(np.diag(R)) / 2.0)
+        X = X + X @ E
+    return lam, X
 
 
 # ----------------------------- adjoint (vector-Jacobian product) -----------------------------
