@@ -11,7 +11,8 @@ it.  Everything here is plain FP64:
 * occupations, chemical potential, band energy and density matrix (paper Sec. 3.1
   Parts 3 and 4; Sec. 2 density-matrix definition) are direct numpy sums;
 * refine_truth: Ogita-Aishima refinement of those eigenpairs with double-double residual
-  products, a reference beyond the FP64 rounding of the eigensolver itself.
+  products, a reference beyond the FP64 rounding of the eigensolver itself;
+* band_reduce / bulge_chase: stage references for a two-stage tridiagonalization.
 
 Readings where the paper is silent (each listed in the design notes):
 * Fermi-Dirac f(x) = 1/(1+e^x), x = (eps - mu)/kT (the paper names f_i only);
@@ -114,6 +115,74 @@ def tridiagonalize(A: np.ndarray):
     beta = np.zeros(n)
     getattr(_load(), f"oracle_tridiag_{_sfx(A)}")(n, _ptr(A), _ptr(d), _ptr(sub), _ptr(U), _ptr(beta))
     return d, sub[: max(n - 1, 0)], U, beta
+
+
+# ----------------------------- two-stage reduction (stage references) -----------------------------
+#
+# Dense -> band -> tridiagonal, written as plain full-matrix Householder similarity
+# transforms so that every step can be read against its definition.  Stage references for
+# a two-stage tridiagonalization (the scope's dense-to-band and band-to-tridiagonal rows);
+# the one-stage oracle above remains the reference for the full eigensolve.
+
+def householder(x: np.ndarray):
+    """(v, tau, beta) with v[0] = 1 and (I - tau v v^H)^H x = beta e_1, beta real."""
+    x = np.asarray(x)
+    alpha = x[0]
+    xn = np.linalg.norm(x[1:]) if x.size > 1 else 0.0
+    v = np.zeros_like(x)
+    v[0] = 1.0
+    if xn == 0.0 and np.imag(alpha) == 0.0:
+        return v, 0.0 * alpha, np.real(alpha)
+    beta = -np.copysign(np.sqrt(np.abs(alpha) ** 2 + xn ** 2), np.real(alpha))
+    tau = (beta - alpha) / beta
+    v[1:] = x[1:] / (alpha - beta)
+    return v, tau, beta
+
+
+def _apply_similarity(A, Q, v, tau, r0):
+    """A <- H^H A H, Q <- Q H with H = I - tau v v^H acting on rows/columns r0.."""
+    n = A.shape[0]
+    H = np.eye(n, dtype=A.dtype)
+    k = v.size
+    H[r0:r0 + k, r0:r0 + k] -= tau * np.outer(v, np.conj(v))
+    return H.conj().T @ A @ H, Q @ H
+
+
+def band_reduce(A: np.ndarray, b: int):
+    """Hermitian A -> (B, Q1) with A = Q1 B Q1^H and B banded: B_ij = 0 for |i - j| > b.
+    Column j's entries below row j + b are annihilated by a reflector on rows j + b.."""
+    A = np.array(A, dtype=np.result_type(A, np.float64), copy=True)
+    n = A.shape[0]
+    Q = np.eye(n, dtype=A.dtype)
+    for j in range(n - b - 1):
+        v, tau, _ = householder(A[j + b:, j])
+        A, Q = _apply_similarity(A, Q, v, tau, j + b)
+    return A, Q
+
+
+def bulge_chase(B: np.ndarray, b: int):
+    """Banded Hermitian B (bandwidth b) -> (T, Q2) with B = Q2 T Q2^H, T tridiagonal.
+    Sweep i annihilates column i below the subdiagonal with a reflector on rows i+1..i+b;
+    the fill it creates below the band is chased down: the reflector of the next window
+    (rows r0..r0+b-1, r0 one past the previous window) annihilates the first column of
+    the previous window below row r0, until the window leaves the matrix."""
+    T = np.array(B, dtype=np.result_type(B, np.float64), copy=True)
+    n = T.shape[0]
+    Q = np.eye(n, dtype=T.dtype)
+    for i in range(n - 2):
+        r0, r1 = i + 1, min(i + b, n - 1)
+        v, tau, _ = householder(T[r0:r1 + 1, i])
+        T, Q = _apply_similarity(T, Q, v, tau, r0)
+        c = r0
+        while True:
+            q0 = r1 + 1
+            if q0 >= n:
+                break
+            q1 = min(q0 + b - 1, n - 1)
+            v, tau, _ = householder(T[q0:q1 + 1, c])
+            T, Q = _apply_similarity(T, Q, v, tau, q0)
+            c, r1 = q0, q1
+    return T, Q
 
 
 def tridiagonal_eig(d: np.ndarray, e: np.ndarray):

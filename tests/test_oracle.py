@@ -507,3 +507,57 @@ def test_oracle_within_its_bound_of_the_truth(tiling):
     beta = O.eig_condition(H, S, eps, C)
     assert np.all(np.abs(eps - lam) <= np.maximum(1e-10, 8 * beta))
     assert np.abs(lam4 - lam).max() <= 1e-13 * max(1.0, np.abs(lam).max())
+
+
+# ------------------------------------------------------------------ two-stage stage references
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_householder_reflector(cplx):
+    rng = np.random.default_rng(21 + cplx)
+    for m in (1, 2, 7):
+        x = rng.standard_normal(m) + (1j * rng.standard_normal(m) if cplx else 0)
+        v, tau, beta = O.householder(x)
+        H = np.eye(m) - tau * np.outer(v, np.conj(v))
+        y = H.conj().T @ x
+        assert abs(y[0] - beta) <= 1e-14 * np.linalg.norm(x) and np.abs(y[1:]).max(initial=0.0) <= 1e-14 * np.linalg.norm(x)
+        assert np.abs(H.conj().T @ H - np.eye(m)).max() <= 1e-14
+    v, tau, beta = O.householder(np.array([2.0, 0.0, 0.0]))  # nothing to annihilate
+    assert tau == 0.0 and beta == 2.0
+
+
+def _chain_in_random_basis(n, cplx, seed):
+    """A = Q C Q^H with C the S = I chain (eigenvalues e0 + 2t cos(j pi/(n+1))) and Q a random
+    unitary: the closed-form spectrum hidden in a dense Hermitian matrix."""
+    rng = np.random.default_rng(seed)
+    e0, t = 0.3, -1.0
+    C = np.diag(np.full(n, e0)) + np.diag(np.full(n - 1, t), 1) + np.diag(np.full(n - 1, t), -1)
+    Z = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    Q, _ = np.linalg.qr(Z)
+    A = Q @ C @ Q.conj().T
+    A = 0.5 * (A + A.conj().T)
+    lam = np.sort(e0 + 2 * t * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))
+    return A, lam
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n,b", [(40, 4), (37, 6), (25, 1), (30, 8)])
+def test_band_reduce_and_bulge_chase(cplx, n, b):
+    """Dense -> band -> tridiagonal: exact zeros outside the band / tridiagonal (to rounding),
+    unitary transforms that reproduce their input, and the chain's closed-form spectrum at
+    the end (tridiagonal eigenvalues by the oracle's implicit QL after a diagonal phase)."""
+    A, lam = _chain_in_random_basis(n, cplx, 100 * n + b + cplx)
+    i, j = np.indices((n, n))
+    B, Q1 = O.band_reduce(A, b)
+    scale = np.abs(A).max()
+    if (np.abs(i - j) > b).any():
+        assert np.abs(B[np.abs(i - j) > b]).max() <= 1e-13 * scale
+    assert np.abs(Q1 @ B @ Q1.conj().T - A).max() <= 1e-13 * scale
+    assert np.abs(Q1.conj().T @ Q1 - np.eye(n)).max() <= 1e-13
+    T, Q2 = O.bulge_chase(B, b)
+    assert np.abs(T[np.abs(i - j) > 1]).max() <= 1e-13 * scale
+    assert np.abs(Q2 @ T @ Q2.conj().T - B).max() <= 1e-13 * scale
+    assert np.abs(Q2.conj().T @ Q2 - np.eye(n)).max() <= 1e-13
+    d = np.real(np.diag(T))
+    e = np.abs(np.diag(T, -1))
+    ev, _ = O.tridiagonal_eig(d, e)
+    assert np.abs(np.sort(ev) - lam).max() <= 1e-13 * n
