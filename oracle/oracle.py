@@ -160,12 +160,14 @@ def band_reduce(A: np.ndarray, b: int):
     return A, Q
 
 
-def bulge_chase(B: np.ndarray, b: int):
+def bulge_chase(B: np.ndarray, b: int, reflectors: list | None = None):
     """Banded Hermitian B (bandwidth b) -> (T, Q2) with B = Q2 T Q2^H, T tridiagonal.
     Sweep i annihilates column i below the subdiagonal with a reflector on rows i+1..i+b;
     the fill it creates below the band is chased down: the reflector of the next window
     (rows r0..r0+b-1, r0 one past the previous window) annihilates the first column of
-    the previous window below row r0, until the window leaves the matrix."""
+    the previous window below row r0, until the window leaves the matrix.  Window j of
+    sweep i starts at row i + 1 + j b.  With `reflectors` (a list), each reflector is
+    appended as (i, j, first row, v, tau) in generation order, Q2 = their product."""
     T = np.array(B, dtype=np.result_type(B, np.float64), copy=True)
     n = T.shape[0]
     Q = np.eye(n, dtype=T.dtype)
@@ -173,7 +175,9 @@ def bulge_chase(B: np.ndarray, b: int):
         r0, r1 = i + 1, min(i + b, n - 1)
         v, tau, _ = householder(T[r0:r1 + 1, i])
         T, Q = _apply_similarity(T, Q, v, tau, r0)
-        c = r0
+        if reflectors is not None:
+            reflectors.append((i, 0, r0, v, tau))
+        c, j = r0, 0
         while True:
             q0 = r1 + 1
             if q0 >= n:
@@ -181,8 +185,39 @@ def bulge_chase(B: np.ndarray, b: int):
             q1 = min(q0 + b - 1, n - 1)
             v, tau, _ = householder(T[q0:q1 + 1, c])
             T, Q = _apply_similarity(T, Q, v, tau, q0)
+            j += 1
+            if reflectors is not None:
+                reflectors.append((i, j, q0, v, tau))
             c, r1 = q0, q1
     return T, Q
+
+
+def apply_q2_grouped(reflectors: list, X: np.ndarray, nbs: int) -> np.ndarray:
+    """Q2 X with the bulge-chasing reflectors regrouped for block application: sweeps in
+    groups of nbs, and within a group one block per window index j,
+    B_{g,j} = H_{s0,j} H_{s0+1,j} ... (compact WY, I - V T V^H).  Since a reflector of sweep
+    s, window j meets none of later sweeps' higher windows, Q2 = prod_g prod_{j desc}
+    B_{g,j}; so X is multiplied by groups from the last, windows ascending."""
+    X = np.array(X, dtype=np.result_type(X, reflectors[0][3] if reflectors else X), copy=True)
+    groups = {}
+    for (i, j, r0, v, tau) in reflectors:
+        groups.setdefault(i // nbs, {}).setdefault(j, []).append((r0, v, tau))
+    for g in sorted(groups, reverse=True):
+        for j in sorted(groups[g]):
+            blk = groups[g][j]  # sweeps ascending
+            top = min(r0 for r0, _, _ in blk)
+            bot = max(r0 + v.size for r0, v, _ in blk)
+            k = len(blk)
+            V = np.zeros((bot - top, k), dtype=X.dtype)
+            for c, (r0, v, _) in enumerate(blk):
+                V[r0 - top:r0 - top + v.size, c] = v
+            taus = [t for _, _, t in blk]
+            Tm = np.zeros((k, k), dtype=X.dtype)
+            for c in range(k):  # forward accumulation: T[:c, c] = -tau_c T[:c,:c] V[:, :c]^H v_c
+                Tm[:c, c] = -taus[c] * (Tm[:c, :c] @ (V[:, :c].conj().T @ V[:, c]))
+                Tm[c, c] = taus[c]
+            X[top:bot] -= V @ (Tm @ (V.conj().T @ X[top:bot]))
+    return X
 
 
 def tridiagonal_eig(d: np.ndarray, e: np.ndarray):

@@ -561,3 +561,17 @@ def test_band_reduce_and_bulge_chase(cplx, n, b):
     e = np.abs(np.diag(T, -1))
     ev, _ = O.tridiagonal_eig(d, e)
     assert np.abs(np.sort(ev) - lam).max() <= 1e-13 * n
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n,b,nbs", [(40, 4, 4), (37, 6, 5), (30, 3, 8), (25, 1, 3)])
+def test_bulge_chase_reflectors_regroup_into_blocks(cplx, n, b, nbs):
+    """The bulge-chasing reflectors, regrouped into sweep-group x window blocks and applied
+    groups-descending / windows-ascending as compact WY blocks, reproduce Q2 X."""
+    rng = np.random.default_rng(7 * n + b + cplx)
+    Xr = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    B, _ = O.band_reduce(Xr + Xr.conj().T, b)
+    refl = []
+    _, Q2 = O.bulge_chase(B, b, refl)
+    Y = rng.standard_normal((n, 7)) + (1j * rng.standard_normal((n, 7)) if cplx else 0)
+    assert np.abs(O.apply_q2_grouped(refl, Y, nbs) - Q2 @ Y).max() <= 1e-13 * np.abs(Y).max()
