@@ -160,6 +160,42 @@ def band_reduce(A: np.ndarray, b: int):
     return A, Q
 
 
+def band_reduce_blocked(A: np.ndarray, b: int):
+    """The same dense -> band reduction in panel form: for the panel of columns [k, k+b),
+    QR of the block below the band by Householder reflectors (V unit lower trapezoidal,
+    T from the forward accumulation), then the two-sided update of the trailing block
+        X = A22 V T,  W = X - (1/2) V (T^H V^H X),  A22 <- A22 - V W^H - W V^H.
+    Returns (B, Q1) like band_reduce (same reflectors, so the same B up to rounding)."""
+    A = np.array(A, dtype=np.result_type(A, np.float64), copy=True)
+    n = A.shape[0]
+    Q = np.eye(n, dtype=A.dtype)
+    for k in range(0, max(n - b - 1, 0), b):
+        r0 = k + b               # first row below the band for this panel
+        kb = min(b, n - b - 1 - k)  # columns of the panel that still have entries to annihilate
+        m = n - r0
+        P = A[r0:, k:k + b].copy()  # all b columns of the panel receive Q^H; kb reflectors
+        V = np.zeros((m, kb), dtype=A.dtype)
+        taus = np.zeros(kb, dtype=A.dtype)
+        for c in range(kb):      # unblocked QR of the panel
+            v, tau, _ = householder(P[c:, c])
+            V[c:, c] = v
+            taus[c] = tau
+            P[c:, c:] -= np.outer(v, (np.conj(tau) * (np.conj(v) @ P[c:, c:])))
+        Tm = np.zeros((kb, kb), dtype=A.dtype)
+        for c in range(kb):
+            Tm[:c, c] = -taus[c] * (Tm[:c, :c] @ (V[:, :c].conj().T @ V[:, c]))
+            Tm[c, c] = taus[c]
+        # panel and its mirror: Q^H applied from the left to the panel columns
+        A[r0:, k:k + b] = P
+        A[k:k + b, r0:] = P.conj().T
+        A22 = A[r0:, r0:]
+        X = A22 @ V @ Tm
+        W = X - 0.5 * V @ (Tm.conj().T @ (V.conj().T @ X))
+        A[r0:, r0:] = A22 - V @ W.conj().T - W @ V.conj().T
+        Q[:, r0:] = Q[:, r0:] - (Q[:, r0:] @ V) @ Tm @ V.conj().T
+    return A, Q
+
+
 def bulge_chase(B: np.ndarray, b: int, reflectors: list | None = None):
     """Banded Hermitian B (bandwidth b) -> (T, Q2) with B = Q2 T Q2^H, T tridiagonal.
     Sweep i annihilates column i below the subdiagonal with a reflector on rows i+1..i+b;

@@ -575,3 +575,20 @@ def test_bulge_chase_reflectors_regroup_into_blocks(cplx, n, b, nbs):
     _, Q2 = O.bulge_chase(B, b, refl)
     Y = rng.standard_normal((n, 7)) + (1j * rng.standard_normal((n, 7)) if cplx else 0)
     assert np.abs(O.apply_q2_grouped(refl, Y, nbs) - Q2 @ Y).max() <= 1e-13 * np.abs(Y).max()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n,b", [(40, 4), (37, 6), (25, 1), (30, 8), (20, 3), (12, 11)])
+def test_band_reduce_panel_form_matches_columnwise(cplx, n, b):
+    """The panel form (QR of the block below the band, X = A V T, W = X - V T^H V^H X / 2,
+    A22 -= V W^H + W V^H) gives the band of the column-by-column reduction, partial last
+    panels included, with a unitary Q1 that reproduces A."""
+    rng = np.random.default_rng(3 * n + b + cplx)
+    Xr = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    A = Xr + Xr.conj().T
+    B1, _ = O.band_reduce(A, b)
+    B2, Q = O.band_reduce_blocked(A, b)
+    scale = np.abs(A).max()
+    assert np.abs(B1 - B2).max() <= 1e-13 * scale
+    assert np.abs(Q @ B2 @ Q.conj().T - A).max() <= 1e-13 * scale
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() <= 1e-13
