@@ -363,30 +363,43 @@ def solve(H, S, kT, n_elec, spin="collinear", kweights=None) -> Solution:
 
 
 class GKSSolve(torch.autograd.Function):
-    """eps, rho, E_band = GKSSolve.apply(H, S, kT, n_elec, spin, kweights).
+    """eps, rho, E_band, mu = GKSSolve.apply(H, S, kT, n_elec, spin, kweights, recompute).
 
     Forward runs gks_solve; backward runs gks_adjoint (n_elec fixed).  H and S must be
     Hermitian (the solver reads their lower triangles); the gradients returned are the
-    Hermitian ones, i.e. those of a loss evaluated on Hermitian H and S."""
+    Hermitian ones, i.e. those of a loss evaluated on Hermitian H and S.  With
+    recompute=True the eigenvectors are not kept between forward and backward (nk M^2
+    elements): backward solves the saved H, S again (the solve is deterministic, so it
+    reproduces the forward's C, eps and mu) and then runs the adjoint."""
 
     @staticmethod
-    def forward(ctx, H, S, kT, n_elec, spin="collinear", kweights=None):
+    def forward(ctx, H, S, kT, n_elec, spin="collinear", kweights=None, recompute=False):
         c = context(H.device.index)
-        Hb = H if H.dim() == 3 else H[None]
-        Sb = S if S.dim() == 3 else S[None]
-        sol = c.solve(Hb.contiguous(), Sb.contiguous(), kT, n_elec, spin, kweights)
-        ctx.save_for_backward(sol.C, sol.eps, sol.mu, Sb)
-        ctx.kT, ctx.spin, ctx.kweights, ctx.hshape, ctx.sshape = kT, spin, kweights, H.shape, S.shape
+        Hb = (H if H.dim() == 3 else H[None]).contiguous()
+        Sb = (S if S.dim() == 3 else S[None]).contiguous()
+        sol = c.solve(Hb, Sb, kT, n_elec, spin, kweights)
+        if recompute:
+            ctx.save_for_backward(Hb, Sb)
+        else:
+            ctx.save_for_backward(sol.C, sol.eps, sol.mu, Sb)
+        ctx.recompute = bool(recompute)
+        ctx.kT, ctx.n_elec, ctx.spin, ctx.kweights = kT, n_elec, spin, kweights
+        ctx.hshape, ctx.sshape = H.shape, S.shape
         ctx.mark_non_differentiable(sol.mu)
         return sol.eps, sol.rho, sol.e_band, sol.mu
 
     @staticmethod
     def backward(ctx, g_eps, g_rho, g_eband, g_mu):
-        C, eps, mu, Sb = ctx.saved_tensors
-        c = context(C.device.index)
-        sol = Solution(eps, C, mu, None, None)
+        if ctx.recompute:
+            Hb, Sb = ctx.saved_tensors
+            c = context(Hb.device.index)
+            sol = c.solve(Hb, Sb, ctx.kT, ctx.n_elec, ctx.spin, ctx.kweights)
+        else:
+            C, eps, mu, Sb = ctx.saved_tensors
+            c = context(C.device.index)
+            sol = Solution(eps, C, mu, None, None)
         eb = 0.0 if g_eband is None else float(g_eband.reshape(-1)[0].item())
         Hbar, Sbar = c.adjoint(sol, Sb, ctx.kT, ctx.spin, ctx.kweights,
-                           rho_bar=None if g_rho is None else g_rho.contiguous(),
-                           eps_bar=None if g_eps is None else g_eps.contiguous(), e_band_bar=eb)
-        return Hbar.reshape(ctx.hshape), Sbar.reshape(ctx.sshape), None, None, None, None
+                               rho_bar=None if g_rho is None else g_rho.contiguous(),
+                               eps_bar=None if g_eps is None else g_eps.contiguous(), e_band_bar=eb)
+        return Hbar.reshape(ctx.hshape), Sbar.reshape(ctx.sshape), None, None, None, None, None

@@ -196,3 +196,18 @@ def test_autograd_function(ctx):
                          eps_bar=torch.ones_like(sol.eps), e_band_bar=1.0)
     assert torch.allclose(Ht.grad, Hb, rtol=1e-9, atol=1e-9 * Hb.abs().max().item())
     assert torch.allclose(St.grad, Sb, rtol=1e-9, atol=1e-9 * Sb.abs().max().item())
+
+
+def test_autograd_recompute_matches_saved(ctx):
+    """recompute=True (no eigenvectors kept; backward solves again) gives the same gradients
+    bit for bit: the solve is deterministic."""
+    from paper_2606_09058_gb300.gks import GKSSolve
+    H, S = I.random_pencil(70, 5, True, 10.0)
+    grads = []
+    for rec in (False, True):
+        Ht = _cuda(H[None]).requires_grad_(True)
+        St = _cuda(S[None]).requires_grad_(True)
+        eps, rho, e_band, mu = GKSSolve.apply(Ht, St, 0.1, 40.0, "collinear", None, rec)
+        (e_band.sum() + (rho.abs() ** 2).sum() + eps.sum()).backward()
+        grads.append((Ht.grad.clone(), St.grad.clone()))
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
