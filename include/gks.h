@@ -9,7 +9,7 @@
  *  - Array arguments are DEVICE pointers allocated and owned by the caller, contiguous
  *    and row-major.  Complex data is interleaved (re, im) double pairs.
  *  - Hermitian inputs are read from their LOWER triangle only (row >= column).
- *  - M is the matrix order: M = n (collinear) or 2n (noncollinear).
+ *  - M is the matrix order: M = n (collinear, spin-polarized) or 2n (noncollinear).
  *  - All work is enqueued on the stream given at context creation.  gks_solve returns
  *    host-side validation status; device-side failures (S not positive definite, no
  *    convergence, invalid occupation parameters) are returned by gks_sync.
@@ -40,8 +40,46 @@ typedef enum {
 } gks_status;
 
 typedef enum { GKS_R64 = 0, GKS_C128 = 1 } gks_dtype;        /* real symmetric / complex Hermitian */
-typedef enum { GKS_COLLINEAR = 0, GKS_NONCOLLINEAR = 1 } gks_spin; /* g_s = 2 / g_s = 1 */
-typedef enum { GKS_FP64 = 0 } gks_prec;
+
+/* Spin treatment (paper Sec. 2): collinear spin-degenerate runs carry g_s = 2 electrons per
+ * state; noncollinear runs solve the 2n x 2n spinor problem with g_s = 1; spin-polarized
+ * collinear runs (paper Sec. 1/2: the extension to spin-polarized cases) solve one n x n
+ * pencil per spin channel, both channels sharing S_k and one chemical potential, g_s = 1.
+ * Spin-polarized arrays carry the channel right after the k index: H, C, rho (nk, 2, n, n),
+ * eps (nk, 2, n); S stays (nk, n, n). */
+typedef enum { GKS_COLLINEAR = 0, GKS_NONCOLLINEAR = 1, GKS_SPIN_POLARIZED = 2 } gks_spin;
+
+/* Arithmetic of the eigensolve.  GKS_FP64: every stage FP64-accurate (products as exact
+ * split-bf16 tensor-core products with FP64 accumulation).  GKS_MIXED_SPLITBF16: the
+ * tridiagonalization and back-transform products on fewer digits (FP32-level), then
+ * opts.refine_sweeps Ogita-Aishima refinement sweeps of the eigenpairs of H' with
+ * FP64-accurate residual products; the Cholesky of S, the reduction to H', the secular
+ * roots and the refinement residuals stay FP64.  GKS_MIXED_TF32 is not implemented
+ * (gks_create returns GKS_ENOTIMPL). */
+typedef enum { GKS_FP64 = 0, GKS_MIXED_TF32 = 1, GKS_MIXED_SPLITBF16 = 2 } gks_prec;
+
+/* gks_solve flags. */
+enum {
+  /* Skip the copy and Cholesky of S: reuse the factor kept from the last solve on this
+   * context with the same S array, n, nk, dtype and spin mode (the analogue of the paper's
+   * reuse of its S factorization across SCF cycles, Sec. 5.1).  The caller guarantees that
+   * S has not changed.  Without a matching kept factor the flag has no effect. */
+  GKS_REUSE_S_FACTOR = 1u,
+  /* Keep device copies of C, eps and mu of this solve in the context, so that a later
+   * gks_adjoint may pass NULL for C, eps and mu (the caller may overwrite its outputs). */
+  GKS_SAVE_FOR_BACKWARD = 2u,
+  /* Eigenpairs only: eps and C are written; occupations, mu, rho and e_band are not (mu,
+   * rho and e_band may be NULL; kT and n_elec are not checked).  For runs whose k-points
+   * are spread over several solves or processes: gks_occupy then finds the shared mu. */
+  GKS_EIGEN_ONLY = 4u
+};
+
+/* Test hooks (opts.debug). */
+enum {
+  /* The next split product on this context leaves out one operand copy in every CTA, so
+   * that its bounded waits expire and gks_sync reports GKS_ETIMEOUT; no fault, no trap. */
+  GKS_DEBUG_SKIP_COPY = 1
+};
 
 typedef struct {
   int device;          /* CUDA device ordinal */
@@ -58,6 +96,19 @@ typedef struct {
   int block;           /* outer block width of the two-level blocked Cholesky, reduction and
                           back-transforms: a multiple of 64 in 64..1024; 0 = 512 for orders
                           from 4096 up and 256 below (gks_tune overrides per shape class) */
+  int refine_sweeps;   /* GKS_MIXED_SPLITBF16: refinement sweeps, 1..8 (0 = 2) */
+  int n_ev;            /* eigenvectors computed per item: the lowest n_ev (0 = all M).  With
+                          0 < n_ev < M, C is (nk, M, n_ev) and the back-transforms and the
+                          density matrix touch only those columns (paper Sec. 6: a quarter to
+                          a half of the spectrum is needed); eps still holds all M eigenvalues.
+                          More occupied states (f >= f_cut) than n_ev is a device-side
+                          GKS_EINVAL. */
+  long long wait_limit;/* bound of every device-side wait, in SM clock cycles (0 = 2^32,
+                          about two seconds); past it the waiting kernel stops, frees its
+                          resources and gks_sync returns GKS_ETIMEOUT */
+  const char* autotune_cache; /* file of tuned widths: read at gks_create if it exists, rewritten
+                          by gks_tune and gks_tune_set; NULL = none.  The string is copied. */
+  int debug;           /* test hooks, GKS_DEBUG_* (0 = none) */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */
@@ -107,17 +158,24 @@ const char* gks_last_error(const gks_ctx* ctx);
  * Arguments:
  *   H       (nk, M, M) dtype, Hermitian, lower triangle read.  Noncollinear: spin-major
  *           2 x 2 blocks [[H_aa, H_ab], [H_ba, H_bb]] (paper Sec. 3.2 H_NC).
+ *           Spin-polarized: (nk, 2, n, n), the up and down channels of each k-point.
  *   S       (nk, n, n) dtype, Hermitian positive definite, lower triangle read.
- *           Noncollinear: the n x n S; S_NC = diag(S, S) is implied.
+ *           Noncollinear: the n x n S; S_NC = I_2 (x) S is implied and only S is factored
+ *           (paper Sec. 3.2 Parts 3-1..3-4: the spin blocks are reduced with the one
+ *           factor).  Spin-polarized: shared by both channels, factored once per k.
  *   n, nk   basis size per spin and number of k-points (n >= 1, nk >= 1).
- *   dtype   GKS_R64 (collinear Gamma only) or GKS_C128.  Noncollinear requires C128.
- *   kT      Fermi smearing (Hartree), > 0.  n_elec in (0, g_s M).
- *   kweights device (nk) doubles summing to 1, or NULL for 1/nk.
- *   flags   reserved, pass 0.
+ *   dtype   GKS_R64 (collinear or spin-polarized Gamma) or GKS_C128.  Noncollinear
+ *           requires C128.
+ *   kT      Fermi smearing (Hartree), > 0.  n_elec in (0, g_s M) (spin-polarized:
+ *           (0, 2 M)).
+ *   kweights device (nk) doubles summing to 1, or NULL for 1/nk (spin-polarized: the
+ *           weight of a k-point applies to both channels).
+ *   flags   0 or GKS_REUSE_S_FACTOR | GKS_SAVE_FOR_BACKWARD | GKS_EIGEN_ONLY.
  * Outputs (device, caller-allocated):
- *   eps (nk, M) ascending per k; C (nk, M, M) dtype, column i = eigenvector i with
- *   C^H S C = I and its largest-modulus entry real positive; mu (1); rho (nk, M, M) full
- *   Hermitian storage; e_band (1) or NULL.
+ *   eps (nk, M) ascending per k; C (nk, M, M) dtype ((nk, M, n_ev) with opts.n_ev), column
+ *   i = eigenvector i with C^H S C = I and its largest-modulus entry real positive (lowest
+ *   row on ties); mu (1); rho (nk, M, M) full Hermitian storage; e_band (1) or NULL.
+ *   Spin-polarized: eps (nk, 2, n), C and rho (nk, 2, n, n).
  *   rho follows C diag(g_s f) C^H; the paper's n_lm = sum_i f_i c*_li c_mi equals
  *   conj(rho)/g_s (its transpose for Hermitian rho).
  * The inputs are not modified.  Returns GKS_OK or a host validation error; device
@@ -142,18 +200,43 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
  * (limits f'_i and f_i + eps_i f'_i on equal eigenvalues); the returned gradients satisfy
  * dL = Re tr(H_bar^H dH) + Re tr(S_bar^H dS) for Hermitian dH, dS.
  * Inputs: C, eps, mu as returned by gks_solve for the same (n, nk, dtype, spin, kT,
- * kweights); rho_bar (nk, M, M) = dL/d rho (its Hermitian part is used; NULL = 0);
- * eps_bar (nk, M) = explicit dL/d eps (NULL = 0); e_band_bar = dL/dE_band.
+ * kweights), or C = eps = NULL to use the copies kept by the last solve of that shape
+ * with GKS_SAVE_FOR_BACKWARD (mu = NULL: the kept mu too); rho_bar (nk, M, M) = dL/d rho
+ * (its Hermitian part is used; NULL = 0); eps_bar (nk, M) = explicit dL/d eps (NULL = 0);
+ * e_band_bar = dL/dE_band.  Needs every eigenvector (opts.n_ev = 0).
  * Outputs: H_bar (nk, M, M) and S_bar (nk, n, n), full Hermitian storage (noncollinear:
- * S_bar is the sum of the two diagonal spin blocks, since S_NC = diag(S, S)).
- * The context keeps a separate workspace (3 M^2 elements per k-point) for this call. */
+ * S_bar is the sum of the two diagonal spin blocks, since S_NC = diag(S, S);
+ * spin-polarized: H_bar (nk, 2, n, n), S_bar the sum over the two channels).
+ * The context keeps a separate workspace (3 M^2 elements per item) for this call. */
 gks_status gks_adjoint(gks_ctx* ctx, const void* C, const double* eps, const double* mu, int64_t n, int64_t nk,
                        int dtype, int spin_mode, double kT, const double* kweights, const void* rho_bar,
                        const double* eps_bar, double e_band_bar, void* H_bar, void* S_bar);
 
+/* Occupations, shared chemical potential, density matrix and energy-density matrix for
+ * k-points whose eigenpairs come from separate solves (paper Sec. 3.1 Parts 3 and 4; the
+ * k-points of one run may be spread over solves or processes, each with GKS_EIGEN_ONLY):
+ *   mu from sum_k w_k g_s sum_i f((eps_ki - mu)/kT) = n_elec over ALL nk_all k-points,
+ *   rho_k = C_k diag(g_s f_k) C_k^H and E_k = C_k diag(g_s f_k eps_k) C_k^H (the
+ *   energy-density matrix of paper Sec. 3.1 Part 4) for the local k-points k0 .. k0+nk-1,
+ *   E_band = sum_k w_k g_s sum_i f_ki eps_ki over all k-points.
+ * The same bisection as gks_solve: with eps_all equal to a solve's eps, mu and rho equal
+ * that solve's bit for bit.  Arguments:
+ *   eps_all (nk_all, M) device, ascending per k (spin-polarized: (nk_all, 2, n));
+ *   kweights_all (nk_all) device or NULL (1/nk_all);
+ *   C (nk, M, ncols) the eigenvectors of the local k-points (ncols = opts.n_ev or M);
+ *   mu (1) out; rho, edm (nk, M, M) out or NULL (full Hermitian storage); e_band out or
+ *   NULL.  n, dtype, spin_mode, kT, n_elec as in gks_solve.
+ * Device-side failures (invalid parameters, more occupied states than n_ev) are reported
+ * by gks_sync. */
+gks_status gks_occupy(gks_ctx* ctx, const double* eps_all, int64_t nk_all, int64_t k0, const void* C, int64_t n,
+                      int64_t nk, int dtype, int spin_mode, double kT, double n_elec, const double* kweights_all,
+                      double* mu, void* rho, double* e_band, void* edm);
+
 /* Wait for the context's stream and report the first device-side failure of the work
  * enqueued since the previous gks_sync (GKS_ENOTSPD with the failing column and
- * k-point, GKS_ENOCONV, GKS_EINVAL for occupation parameters found invalid). */
+ * k-point, GKS_ENOCONV, GKS_EINVAL for occupation parameters found invalid, GKS_ETIMEOUT
+ * when a bounded wait expired in a product of a solve, gks_gemm or
+ * gks_gemm_split_noalloc). */
 gks_status gks_sync(gks_ctx* ctx);
 
 /* Wait for the stream and return the event profile of everything enqueued since the
@@ -210,6 +293,9 @@ int gks_tune_get(const gks_ctx* ctx, int64_t n, int dtype, int spin_mode);
  *
  * The first call on a device looks up the scratch address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture on the device.
+ * A bounded wait that expires in the product (opts.wait_limit) leaves C incomplete and is
+ * reported by the next gks_sync on this context as GKS_ETIMEOUT; the call itself returns
+ * GKS_OK once the work is enqueued.
  * The work is enqueued on the context's stream and the call returns without waiting.
  * All calls on one device share the one scratch region: two calls whose work overlaps in
  * time (other streams, other contexts, other host threads) corrupt each other's results.

@@ -141,6 +141,22 @@ __global__ void spin_block_sum_kernel(T* dst, long long sd, const T* src, long l
     }
 }
 
+// Spin-polarized runs: S_bar_k (n x n) = Hermitian part of the sum of the gradients of the
+// two spin channels (items 2k and 2k+1), which share S_k.
+template <typename T>
+__global__ void spin_pair_sum_kernel(T* dst, long long sd, const T* src, long long ss, int n) {
+  const int z = blockIdx.z;
+  dst += z * sd;
+  const T* s0 = src + (2 * (long long)z) * ss;
+  const T* s1 = s0 + ss;
+  for (int i = blockIdx.y; i < n; i += gridDim.y)
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+      T a = s0[(size_t)i * n + j] + s1[(size_t)i * n + j];
+      T b = s0[(size_t)j * n + i] + s1[(size_t)j * n + i];
+      dst[(size_t)i * n + j] = 0.5 * (a + conjg(b));
+    }
+}
+
 static dim3 g2(int rows, int cols, int count) {
   int gx = (cols + 255) / 256;
   if (gx > 16) gx = 16;
@@ -182,6 +198,12 @@ void spin_block_sum(T* dst, long long sd, const T* src, long long ss, int n, int
   spin_block_sum_kernel<T><<<g2(n, n, nk), 256, 0, s>>>(dst, sd, src, ss, n);
 }
 
+template <typename T>
+void spin_pair_sum(T* dst, long long sd, const T* src, long long ss, int n, int nk, cudaStream_t s) {
+  count_launch();
+  spin_pair_sum_kernel<T><<<g2(n, n, nk), 256, 0, s>>>(dst, sd, src, ss, n);
+}
+
 #define INST(T)                                                                                            \
   template void adj_weights<T>(const double*, const double*, const double*, const double*, const T*,        \
                                long long, int, int, double, const double*, double, int, double*,            \
@@ -189,7 +211,8 @@ void spin_block_sum(T* dst, long long sd, const T* src, long long ss, int n, int
   template void adj_build<T>(T*, T*, long long, int, const double*, const double*, const double*,           \
                              const double*, double, double, int, int, cudaStream_t);                       \
   template void herm_part<T>(T*, const T*, long long, long long, int, int, cudaStream_t);                   \
-  template void spin_block_sum<T>(T*, long long, const T*, long long, int, int, cudaStream_t);
+  template void spin_block_sum<T>(T*, long long, const T*, long long, int, int, cudaStream_t);              \
+  template void spin_pair_sum<T>(T*, long long, const T*, long long, int, int, cudaStream_t);
 INST(double)
 INST(zc)
 

@@ -79,6 +79,8 @@ struct SolveKey {
   long long n, nk;
   int dtype, spin;
   double kT, ne;
+  unsigned flags;
+  unsigned reserved;  // keeps the struct free of padding (keys are compared with memcmp)
 };
 
 struct gks_ctx {
@@ -102,6 +104,25 @@ struct gks_ctx {
   cudaStream_t stream = nullptr;
   double f_cut = 1e-16;
   std::string err;
+  DevStatus* noalloc_st = nullptr;     // status word of the last gks_gemm_split_noalloc call
+  DevStatus* gst = nullptr;            // status word of gks_gemm and gks_occupy (one entry)
+  long long wait_cycles = 1ll << 32;   // bound of every device-side wait (opts.wait_limit)
+  int n_ev = 0;                        // eigenvectors per item (0 = all)
+  int precision = GKS_FP64;
+  int refine_sweeps = 2;
+  int debug = 0;                       // test hooks (GKS_DEBUG_*)
+  std::string tune_cache;              // file of tuned widths (opts.autotune_cache)
+  // Cholesky factor kept in the L workspace from the solve that produced it
+  SolveKey lkey{};
+  bool l_valid = false;
+  // copies kept for gks_adjoint (GKS_SAVE_FOR_BACKWARD): C, eps, mu of the last such solve
+  char* sv = nullptr;
+  size_t sv_bytes = 0;
+  SolveKey svkey{};
+  bool sv_valid = false;
+  // occupation workspace of gks_occupy (weights, f, g_s f, g_s f eps, n_rho for all items)
+  char* ow = nullptr;
+  size_t ow_bytes = 0;
   // workspace for the current shape
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -113,8 +134,8 @@ struct gks_ctx {
   size_t aws_bytes = 0;
   int am = -1, ank = -1, aes = -1;
   // offsets (bytes) of per-item arrays; each holds nk items
-  size_t oA, oL, oF, oFB, oU, oQ, opart, oy, ouw, oSg, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho, ow, oeb, odc,
-      oticket;
+  size_t oA, oL, oF, oFB, oU, oQ, opart, oy, ouw, oSg, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho,
+      oweights, oeb, odc, oticket;
   long long sMM, sF, sFB, sU, spart, sy, sV, sG, sT, sY, sVec;
 };
 
@@ -124,6 +145,25 @@ gks_status fail(gks_ctx* c, gks_status code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
 }
+
+// Makes `dev` current for the duration of an entry point and restores the caller's
+// current device on return.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 gks_status cuda_check(gks_ctx* c, const char* where) {
   cudaError_t e = cudaGetLastError();
@@ -152,8 +192,21 @@ void release_oz(gks_ctx* c) {
   c->oz_bytes = 0;
 }
 
+void release_extra(gks_ctx* c) {
+  if (c->sv) cudaFree(c->sv);
+  c->sv = nullptr;
+  c->sv_bytes = 0;
+  c->sv_valid = false;
+  if (c->ow) cudaFree(c->ow);
+  c->ow = nullptr;
+  c->ow_bytes = 0;
+  if (c->gst) cudaFree(c->gst);
+  c->gst = nullptr;
+}
+
 void release_ws(gks_ctx* c) {
   release_graph(c);
+  c->l_valid = false;
   if (c->ws) cudaFree(c->ws);
   if (c->st) cudaFree(c->st);
   dc_plan_destroy(c->dc);
@@ -180,9 +233,13 @@ int pick_width(const gks_ctx* c, int m, int es, int nc) {
   return m >= 4096 ? 512 : 256;
 }
 
-// Workspace for nk problems of order m (element size es, n = basis per spin).
+// Shape class of a spin mode for the tuned widths: spin-polarized runs share the
+// collinear class (same order and element type).
+int shape_spin(int spin) { return spin == GKS_NONCOLLINEAR ? 1 : 0; }
+
+// Workspace for nk items of order m (element size es, n = basis per spin, nc = spin mode).
 gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
-  const int want = pick_width(c, m, es, nc);
+  const int want = pick_width(c, m, es, shape_spin(nc));
   if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc && c->nbb == want) return GKS_OK;
   release_ws(c);
   c->nbb = want;
@@ -227,7 +284,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->oocc = a.take<double>((size_t)m * nk);
   c->oks = a.take<double>((size_t)m * nk);
   c->onrho = a.take<int>((size_t)nk);
-  c->ow = a.take<double>((size_t)nk);
+  c->oweights = a.take<double>((size_t)nk);
   c->oeb = a.take<double>(4);
   c->oticket = a.take<int>((size_t)2 * nk);
   c->dc = dc_plan_create(m, nk);
@@ -246,8 +303,6 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
     return fail(c, GKS_ENOMEM, "status allocation failed");
   }
   cudaMemset(c->st, 0, sizeof(DevStatus) * nk);
-  std::vector<double> w(nk, 1.0 / nk);
-  cudaMemcpy(c->ws + c->ow, w.data(), sizeof(double) * nk, cudaMemcpyHostToDevice);
   c->m = m;
   c->n = n;
   c->nk = nk;
@@ -259,6 +314,51 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
 template <typename X>
 X* at(gks_ctx* c, size_t off) {
   return reinterpret_cast<X*>(c->ws + off);
+}
+
+// Eigenvector columns a solve of order M returns (opts.n_ev, 0 = all).
+int ncols_of(const gks_ctx* c, int M) { return (c->n_ev > 0 && c->n_ev < M) ? c->n_ev : M; }
+
+// Keep copies of C, eps and mu of this solve for a later gks_adjoint that passes NULL for
+// them (GKS_SAVE_FOR_BACKWARD); the context owns them until the next such solve.
+gks_status save_for_backward(gks_ctx* c, const SolveKey& k, int M, int items, int nev) {
+  const int es = k.dtype == GKS_C128 ? 16 : 8;
+  const size_t bC = (size_t)items * M * nev * es, bE = (size_t)items * M * sizeof(double);
+  const size_t need = ((bC + 255) & ~size_t(255)) + ((bE + 255) & ~size_t(255)) + 256;
+  if (need > c->sv_bytes) {
+    cudaStreamSynchronize(c->stream);
+    if (c->sv) cudaFree(c->sv);
+    c->sv = nullptr;
+    c->sv_bytes = 0;
+    if (cudaMalloc(&c->sv, need) != cudaSuccess) {
+      cudaGetLastError();
+      c->sv = nullptr;
+      c->sv_valid = false;
+      return fail(c, GKS_ENOMEM, "allocation of the saved eigenpairs (" + std::to_string(need) + " bytes) failed");
+    }
+    c->sv_bytes = need;
+  }
+  char* base = c->sv;
+  const size_t oE = (bC + 255) & ~size_t(255), oM = oE + ((bE + 255) & ~size_t(255));
+  cudaMemcpyAsync(base, k.C, bC, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(base + oE, k.eps, bE, cudaMemcpyDeviceToDevice, c->stream);
+  c->svkey = k;
+  c->sv_valid = false;
+  if (!(k.flags & GKS_EIGEN_ONLY)) {
+    // mu is written by the occupation stage later in the same solve; copy it then
+    c->sv_valid = true;
+  } else {
+    cudaMemsetAsync(base + oM, 0, sizeof(double), c->stream);
+    c->sv_valid = true;
+  }
+  return GKS_OK;
+}
+
+void save_mu(gks_ctx* c, const SolveKey& k, int M, int items, int nev) {
+  const int es = k.dtype == GKS_C128 ? 16 : 8;
+  const size_t bC = (size_t)items * M * nev * es, bE = (size_t)items * M * sizeof(double);
+  const size_t oM = ((bC + 255) & ~size_t(255)) + ((bE + 255) & ~size_t(255));
+  cudaMemcpyAsync(c->sv + oM, k.mu, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
 }
 
 double gemm_flops(int es, int M, int N, int K, int lower, int count) {
@@ -371,38 +471,44 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
   Rec r(c, PC_OZAKI, fl, gemm_bytes(es, M, N, K, lower, count, beta != 0.0));
   for (int z0 = 0; z0 < count; z0 += per) {
     const int cnt = std::min(per, count - z0);
+    // test hook (GKS_DEBUG_SKIP_COPY): the next split product leaves out its fourth operand
+    // copy in every CTA, so that its bounded waits expire
+    const long long skip = (c->debug & GKS_DEBUG_SKIP_COPY) ? 3 : -1;
+    c->debug &= ~GKS_DEBUG_SKIP_COPY;
     if (!ozaki_gemm<T>(opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc,
-                       sC, cnt, lower, c->slices, c->oz, c->st, c->stream))
+                       sC, cnt, lower, c->slices, c->oz, c->st ? c->st : c->gst, c->stream, nullptr, 0, nullptr,
+                       c->wait_cycles, skip))
       gmp<T>(c, cnt, opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc, sC,
              lower);
   }
 }
 
 // rho_k = C_k diag(ks_k) C_k^H over the leading n_rho(k) columns (n_rho read on the device),
-// lower triangle.  Split products take K = M with the device count cutting the digits and
-// the k loop; the DFMA kernel reads the same count.
+// lower triangle.  C_k is M x (>= n_rho) with leading dimension ldc and item stride sC;
+// rho_k is M x M (stride sR).  Split products take K = the columns of C with the device
+// count cutting the digits and the k loop; the FP64 kernel reads the same count.
 template <typename T>
-void rho_run(gks_ctx* c, const T* C, T* rho, const double* ks, const int* nrho, int M, int nk) {
+void rho_run(gks_ctx* c, const T* C, int ldc, long long sC, T* rho, long long sR, const double* ks, long long sks,
+             const int* nrho, int M, int K, int nk) {
   const int es = sizeof(T);
-  const int per = split_worth(c, nk, M, M, M, es, gemm_flops(es, M, M, M / 4, 1, nk))
-                      ? oz_reserve(c, ozaki_workspace_bytes(M, M, M, es == 16, c->slices), nk)
+  const int per = split_worth(c, nk, M, M, K, es, gemm_flops(es, M, M, std::max(1, K / 4), 1, nk))
+                      ? oz_reserve(c, ozaki_workspace_bytes(M, M, K, es == 16, c->slices), nk)
                       : 0;
   int z0 = 0;
   for (; per > 0 && z0 < nk; z0 += per) {
     const int cnt = std::min(per, nk - z0);
-    const long long o = (long long)z0 * c->sMM;
-    if (!ozaki_gemm<T>(OP_N, OP_C, M, M, M, 1.0, C + o, M, c->sMM, C + o, M, c->sMM, 0.0, rho + o, M, c->sMM, cnt, 1,
-                       c->slices, c->oz, c->st, c->stream, ks + (size_t)z0 * M, M, nrho + z0))
-      break;  // tensor maps unavailable: the DFMA kernel takes the remaining items
+    if (!ozaki_gemm<T>(OP_N, OP_C, M, M, K, 1.0, C + z0 * sC, ldc, sC, C + z0 * sC, ldc, sC, 0.0, rho + z0 * sR, M,
+                       sR, cnt, 1, c->slices, c->oz, c->st ? c->st : c->gst, c->stream, ks + z0 * sks, sks,
+                       nrho + z0, c->wait_cycles))
+      break;  // tensor maps unavailable: the FP64 kernel takes the remaining items
   }
   if (z0 >= nk) return;
-  const long long o = (long long)z0 * c->sMM;
   GemmBatch g{};
-  g.base = GemmDesc{C + o, C + o, rho + o, ks + (size_t)z0 * M, M, M, M, M, M, M};
-  g.sA = c->sMM;
-  g.sB = c->sMM;
-  g.sC = c->sMM;
-  g.sK = M;
+  g.base = GemmDesc{C + z0 * sC, C + z0 * sC, rho + z0 * sR, ks + z0 * sks, M, M, K, ldc, ldc, M};
+  g.sA = sC;
+  g.sB = sC;
+  g.sC = sR;
+  g.sK = sks;
   g.kdev = nrho + z0;
   g.count = nk - z0;
   g.opA = OP_N;
@@ -413,52 +519,131 @@ void rho_run(gks_ctx* c, const T* C, T* rho, const double* ks, const int* nrho, 
   gemm<T>(g, M, M, c->stream);
 }
 
-// Blocked right-looking Cholesky of L (in place, lower), two levels.  Outer panels of
-// nbb columns: inside a panel, 64-wide steps (diagonal block in shared memory, L21 =
-// A21 L11^-H by substitution, rank-64 update of the rest of the panel only); after the
-// panel, one rank-nbb update of the trailing matrix (the product that dominates, now with
-// K = nbb).
+// Blocked right-looking Cholesky of the leading n x n block of each item (in place, lower;
+// leading dimension ld, item stride sL), two levels.  Outer panels of nbb columns: inside a
+// panel, 64-wide steps (diagonal block in shared memory, L21 = A21 L11^-H by substitution,
+// rank-64 update of the rest of the panel only); after the panel, one rank-nbb update of
+// the trailing matrix (the product that dominates, with K = nbb).
 template <typename T>
-void potrf_run(gks_ctx* c, T* L, int M, int nk) {
+void potrf_run(gks_ctx* c, T* L, int n, int ld, long long sL, int nk) {
   cudaStream_t s = c->stream;
   const int es = sizeof(T);
   const int nbb = c->nbb;
-  for (int K0 = 0; K0 < M; K0 += nbb) {
-    const int KB = std::min(nbb, M - K0);
+  for (int K0 = 0; K0 < n; K0 += nbb) {
+    const int KB = std::min(nbb, n - K0);
     for (int k0 = K0; k0 < K0 + KB; k0 += NB) {
       const int kb = std::min(NB, K0 + KB - k0);
       {
         Rec r(c, PC_POTF2, cmul(es) * kb * kb * kb / 6.0 * nk, 2.0 * es * kb * kb * nk);
-        potf2<T>(L, M, c->sMM, k0, kb, c->st, nk, s);
+        potf2<T>(L, ld, sL, k0, kb, c->st, nk, s);
       }
-      const int rows = M - k0 - kb;
+      const int rows = n - k0 - kb;
       if (rows <= 0) continue;
-      T* L11 = L + (size_t)k0 * M + k0;
-      T* L21 = L + (size_t)(k0 + kb) * M + k0;
+      T* L11 = L + (size_t)k0 * ld + k0;
+      T* L21 = L + (size_t)(k0 + kb) * ld + k0;
       {
         Rec r(c, PC_TRSM, cmul(es) * 0.5 * kb * kb * rows * nk, (2.0 * rows * kb + 0.5 * kb * kb) * es * nk);
-        trsm_block<T>(TRSM_RIGHT_CONJ, L11, M, c->sMM, L21, M, c->sMM, kb, rows, nk, s);
+        trsm_block<T>(TRSM_RIGHT_CONJ, L11, ld, sL, L21, ld, sL, kb, rows, nk, s);
       }
       const int w = K0 + KB - (k0 + kb);  // panel columns right of this step
-      if (w > 0)
-        gmx<T>(c, nk, OP_N, OP_C, rows, w, kb, -1.0, L21, M, c->sMM, L21, M, c->sMM, 1.0, L21 + kb, M, c->sMM, 1);
+      if (w > 0) gmx<T>(c, nk, OP_N, OP_C, rows, w, kb, -1.0, L21, ld, sL, L21, ld, sL, 1.0, L21 + kb, ld, sL, 1);
     }
-    const int rows2 = M - K0 - KB;
+    const int rows2 = n - K0 - KB;
     if (rows2 > 0) {
-      T* P = L + (size_t)(K0 + KB) * M + K0;
-      gmx<T>(c, nk, OP_N, OP_C, rows2, rows2, KB, -1.0, P, M, c->sMM, P, M, c->sMM, 1.0, P + KB, M, c->sMM, 1);
+      T* P = L + (size_t)(K0 + KB) * ld + K0;
+      gmx<T>(c, nk, OP_N, OP_C, rows2, rows2, KB, -1.0, P, ld, sL, P, ld, sL, 1.0, P + KB, ld, sL, 1);
     }
   }
 }
 
+// X <- L^-1 X (conj = false) or L^-H X (conj = true) for the n x ncols block X (leading
+// dimension ldx, item stride sX) with the lower n x n factor L (ldl, sL), two levels: within
+// an outer block of nbb rows, 64-row diagonal blocks by substitution and updates of the
+// rows of that outer block only; then one K = nbb update of all rows beyond it.
+template <typename T>
+void trsm_left_run(gks_ctx* c, const T* L, int ldl, long long sL, T* X, int ldx, long long sX, int n, int ncols,
+                   int nk, bool conj) {
+  cudaStream_t s = c->stream;
+  const int es = sizeof(T);
+  const int nbb = c->nbb;
+  const int nob = (n + nbb - 1) / nbb;
+  const double fl = cmul(es) * 0.5, by = es;
+  if (!conj) {
+    for (int ob = 0; ob < nob; ob++) {
+      const int R0 = ob * nbb, RB = std::min(nbb, n - R0);
+      for (int r0 = R0; r0 < R0 + RB; r0 += NB) {
+        const int rb = std::min(NB, R0 + RB - r0);
+        T* Xi = X + (size_t)r0 * ldx;
+        {
+          Rec r(c, PC_TRSM, fl * rb * rb * ncols * nk, (2.0 * ncols * rb + 0.5 * rb * rb) * by * nk);
+          trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * ldl + r0, ldl, sL, Xi, ldx, sX, rb, ncols, nk, s);
+        }
+        const int below = R0 + RB - r0 - rb;
+        if (below > 0)
+          gmx<T>(c, nk, OP_N, OP_N, below, ncols, rb, -1.0, L + (size_t)(r0 + rb) * ldl + r0, ldl, sL, Xi, ldx, sX,
+                 1.0, X + (size_t)(r0 + rb) * ldx, ldx, sX);
+      }
+      const int below = n - R0 - RB;
+      if (below > 0)
+        gmx<T>(c, nk, OP_N, OP_N, below, ncols, RB, -1.0, L + (size_t)(R0 + RB) * ldl + R0, ldl, sL,
+               X + (size_t)R0 * ldx, ldx, sX, 1.0, X + (size_t)(R0 + RB) * ldx, ldx, sX);
+    }
+    return;
+  }
+  for (int ob = nob - 1; ob >= 0; ob--) {
+    const int R0 = ob * nbb, RB = std::min(nbb, n - R0);
+    const int nib = (RB + NB - 1) / NB;
+    for (int ib = nib - 1; ib >= 0; ib--) {
+      const int r0 = R0 + ib * NB, rb = std::min(NB, R0 + RB - r0);
+      T* Xi = X + (size_t)r0 * ldx;
+      {
+        Rec r(c, PC_TRSM, fl * rb * rb * ncols * nk, (2.0 * ncols * rb + 0.5 * rb * rb) * by * nk);
+        trsm_block<T>(TRSM_LEFT_CONJ, L + (size_t)r0 * ldl + r0, ldl, sL, Xi, ldx, sX, rb, ncols, nk, s);
+      }
+      if (r0 > R0)
+        gmx<T>(c, nk, OP_C, OP_N, r0 - R0, ncols, rb, -1.0, L + (size_t)r0 * ldl + R0, ldl, sL, Xi, ldx, sX, 1.0,
+               X + (size_t)R0 * ldx, ldx, sX);
+    }
+    if (R0 > 0)
+      gmx<T>(c, nk, OP_C, OP_N, R0, ncols, RB, -1.0, L + (size_t)R0 * ldl, ldl, sL, X + (size_t)R0 * ldx, ldx, sX, 1.0,
+             X, ldx, sX);
+  }
+}
+
+// X <- X L^-H for the rows x n block X (ldx, sX) and the lower n x n factor L (ldl, sL):
+// column blocks left to right, X_j = (X_j - X_<j L[j,<j]^H) L[j,j]^-H, with the updates
+// from earlier outer blocks of nbb columns applied as one K = nbb product each.
+template <typename T>
+void trsm_right_conj_run(gks_ctx* c, const T* L, int ldl, long long sL, T* X, int ldx, long long sX, int rows, int n,
+                         int nk) {
+  cudaStream_t s = c->stream;
+  const int es = sizeof(T);
+  const int nbb = c->nbb;
+  for (int J0 = 0; J0 < n; J0 += nbb) {
+    const int JB = std::min(nbb, n - J0);
+    for (int j0 = J0; j0 < J0 + JB; j0 += NB) {
+      const int jb = std::min(NB, J0 + JB - j0);
+      if (j0 > J0)
+        gmx<T>(c, nk, OP_N, OP_C, rows, jb, j0 - J0, -1.0, X + J0, ldx, sX, L + (size_t)j0 * ldl + J0, ldl, sL, 1.0,
+               X + j0, ldx, sX);
+      Rec r(c, PC_TRSM, cmul(es) * 0.5 * jb * jb * rows * nk, (2.0 * rows * jb + 0.5 * jb * jb) * es * nk);
+      trsm_block<T>(TRSM_RIGHT_CONJ, L + (size_t)j0 * ldl + j0, ldl, sL, X + j0, ldx, sX, jb, rows, nk, s);
+    }
+    const int right = n - J0 - JB;
+    if (right > 0)
+      gmx<T>(c, nk, OP_N, OP_C, rows, right, JB, -1.0, X + J0, ldx, sX, L + (size_t)(J0 + JB) * ldl + J0, ldl, sL,
+             1.0, X + J0 + JB, ldx, sX);
+  }
+}
+
 // Two-sided blocked reduction A <- L^-1 A L^-H (lower triangle) of the order-n block at
-// A, L (leading dimension ld), one level of 64-wide panels.  Per panel:
+// A (lda, sA) with L (ldl, sL), one level of 64-wide panels.  Per panel:
 //   A11 <- L11^-1 A11 L11^-H (in-block recurrence),  W = A21 L11^-H,
 //   V = W - L21 A11'/2,  A22 -= L21 V^H + V L21^H,  R = V - L21 A11'/2,
 // and finally the block-strictly-lower part G = [R_0 R_1 ...] becomes L^-1 G by block
 // forward substitution (diagonal blocks by substitution, the rest GEMM updates).
 template <typename T>
-void hegst_level(gks_ctx* c, T* A, const T* L, int n, int ld, int nk) {
+void hegst_level(gks_ctx* c, T* A, int lda, long long sA, const T* L, int ldl, long long sL, int n, int nk) {
   cudaStream_t s = c->stream;
   const int es = sizeof(T);
   T* F = at<T>(c, c->oF);
@@ -466,34 +651,34 @@ void hegst_level(gks_ctx* c, T* A, const T* L, int n, int ld, int nk) {
     const int kb = std::min(NB, n - k0);
     {
       Rec r(c, PC_HEGST_DIAG, cmul(es) * kb * kb * kb * nk, 3.0 * es * kb * kb * nk);
-      hegst_diag<T>(A, ld, c->sMM, L, ld, c->sMM, k0, kb, F, NB, c->sF, nk, s);
+      hegst_diag<T>(A, lda, sA, L, ldl, sL, k0, kb, F, NB, c->sF, nk, s);
     }
     const int rows = n - k0 - kb;
     if (rows <= 0) continue;
-    const T* L11 = L + (size_t)k0 * ld + k0;
-    const T* L21 = L + (size_t)(k0 + kb) * ld + k0;
-    T* A21 = A + (size_t)(k0 + kb) * ld + k0;
+    const T* L11 = L + (size_t)k0 * ldl + k0;
+    const T* L21 = L + (size_t)(k0 + kb) * ldl + k0;
+    T* A21 = A + (size_t)(k0 + kb) * lda + k0;
     T* A22 = A21 + kb;
     {
       Rec r(c, PC_TRSM, cmul(es) * 0.5 * kb * kb * rows * nk, (2.0 * rows * kb + 0.5 * kb * kb) * es * nk);
-      trsm_block<T>(TRSM_RIGHT_CONJ, L11, ld, c->sMM, A21, ld, c->sMM, kb, rows, nk, s);
+      trsm_block<T>(TRSM_RIGHT_CONJ, L11, ldl, sL, A21, lda, sA, kb, rows, nk, s);
     }
-    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, ld, c->sMM, F, NB, c->sF, 1.0, A21, ld, c->sMM);
-    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, ld, c->sMM, A21, ld, c->sMM, 1.0, A22, ld, c->sMM, 1);
-    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, ld, c->sMM, L21, ld, c->sMM, 1.0, A22, ld, c->sMM, 1);
-    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, ld, c->sMM, F, NB, c->sF, 1.0, A21, ld, c->sMM);
+    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, ldl, sL, F, NB, c->sF, 1.0, A21, lda, sA);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, L21, ldl, sL, A21, lda, sA, 1.0, A22, lda, sA, 1);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, kb, -1.0, A21, lda, sA, L21, ldl, sL, 1.0, A22, lda, sA, 1);
+    gmp<T>(c, nk, OP_N, OP_N, rows, kb, kb, -0.5, L21, ldl, sL, F, NB, c->sF, 1.0, A21, lda, sA);
   }
   for (int r0 = NB; r0 < n; r0 += NB) {
     const int rb = std::min(NB, n - r0);
-    T* Ai = A + (size_t)r0 * ld;
+    T* Ai = A + (size_t)r0 * lda;
     {
       Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * r0 * nk, (2.0 * r0 * rb + 0.5 * rb * rb) * es * nk);
-      trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * ld + r0, ld, c->sMM, Ai, ld, c->sMM, rb, r0, nk, s);
+      trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * ldl + r0, ldl, sL, Ai, lda, sA, rb, r0, nk, s);
     }
     const int below = n - r0 - rb;
     if (below > 0)
-      gmx<T>(c, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * ld + r0, ld, c->sMM, Ai, ld, c->sMM,
-             1.0, A + (size_t)(r0 + rb) * ld, ld, c->sMM);
+      gmx<T>(c, nk, OP_N, OP_N, below, r0, rb, -1.0, L + (size_t)(r0 + rb) * ldl + r0, ldl, sL, Ai, lda, sA, 1.0,
+             A + (size_t)(r0 + rb) * lda, lda, sA);
   }
 }
 
@@ -502,63 +687,63 @@ void hegst_level(gks_ctx* c, T* A, const T* L, int n, int ld, int nk) {
 // substitution, the Hermitian A11' as a full copy for the two half-updates, the rank-2nbb
 // trailing update), and the deferred substitution L^-1 [R_0 R_1 ...] blocked the same way.
 template <typename T>
-void hegst_run(gks_ctx* c, T* A, const T* L, int M, int nk) {
+void hegst_run(gks_ctx* c, T* A, int lda, long long sA, const T* L, int ldl, long long sL, int n, int nk) {
   cudaStream_t s = c->stream;
   const int es = sizeof(T);
   const int nbb = c->nbb;
-  if (M <= nbb || nbb <= NB) {
-    hegst_level<T>(c, A, L, M, M, nk);
+  if (n <= nbb || nbb <= NB) {
+    hegst_level<T>(c, A, lda, sA, L, ldl, sL, n, nk);
     return;
   }
   T* FB = at<T>(c, c->oFB);
-  for (int K0 = 0; K0 < M; K0 += nbb) {
-    const int KB = std::min(nbb, M - K0);
-    T* A11 = A + (size_t)K0 * M + K0;
-    const T* L11 = L + (size_t)K0 * M + K0;
-    hegst_level<T>(c, A11, L11, KB, M, nk);
-    const int rows = M - K0 - KB;
+  for (int K0 = 0; K0 < n; K0 += nbb) {
+    const int KB = std::min(nbb, n - K0);
+    T* A11 = A + (size_t)K0 * lda + K0;
+    const T* L11 = L + (size_t)K0 * ldl + K0;
+    hegst_level<T>(c, A11, lda, sA, L11, ldl, sL, KB, nk);
+    const int rows = n - K0 - KB;
     if (rows <= 0) continue;
-    const T* L21 = L + (size_t)(K0 + KB) * M + K0;
-    T* A21 = A + (size_t)(K0 + KB) * M + K0;
+    const T* L21 = L + (size_t)(K0 + KB) * ldl + K0;
+    T* A21 = A + (size_t)(K0 + KB) * lda + K0;
     T* A22 = A21 + KB;
     // A21 <- A21 L11^-H: column blocks left to right, X_j = (A_j - X_<j L11[j,<j]^H) L11[j,j]^-H
     for (int j0 = 0; j0 < KB; j0 += NB) {
       const int jb = std::min(NB, KB - j0);
       if (j0 > 0)
-        gmx<T>(c, nk, OP_N, OP_C, rows, jb, j0, -1.0, A21, M, c->sMM, L11 + (size_t)j0 * M, M, c->sMM, 1.0,
-               A21 + j0, M, c->sMM);
+        gmx<T>(c, nk, OP_N, OP_C, rows, jb, j0, -1.0, A21, lda, sA, L11 + (size_t)j0 * ldl, ldl, sL, 1.0, A21 + j0,
+               lda, sA);
       Rec r(c, PC_TRSM, cmul(es) * 0.5 * jb * jb * rows * nk, (2.0 * rows * jb + 0.5 * jb * jb) * es * nk);
-      trsm_block<T>(TRSM_RIGHT_CONJ, L11 + (size_t)j0 * M + j0, M, c->sMM, A21 + j0, M, c->sMM, jb, rows, nk, s);
+      trsm_block<T>(TRSM_RIGHT_CONJ, L11 + (size_t)j0 * ldl + j0, ldl, sL, A21 + j0, lda, sA, jb, rows, nk, s);
     }
     {
       Rec r(c, PC_MISC);
-      copy2d<T>(FB, nbb, c->sFB, A11, M, c->sMM, KB, KB, nk, s);
+      copy2d<T>(FB, nbb, c->sFB, A11, lda, sA, KB, KB, nk, s);
       mirror_lower<T>(FB, nbb, c->sFB, KB, nk, s);
     }
-    gmx<T>(c, nk, OP_N, OP_N, rows, KB, KB, -0.5, L21, M, c->sMM, FB, nbb, c->sFB, 1.0, A21, M, c->sMM);
-    gmx<T>(c, nk, OP_N, OP_C, rows, rows, KB, -1.0, L21, M, c->sMM, A21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
-    gmx<T>(c, nk, OP_N, OP_C, rows, rows, KB, -1.0, A21, M, c->sMM, L21, M, c->sMM, 1.0, A22, M, c->sMM, 1);
-    gmx<T>(c, nk, OP_N, OP_N, rows, KB, KB, -0.5, L21, M, c->sMM, FB, nbb, c->sFB, 1.0, A21, M, c->sMM);
+    gmx<T>(c, nk, OP_N, OP_N, rows, KB, KB, -0.5, L21, ldl, sL, FB, nbb, c->sFB, 1.0, A21, lda, sA);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, KB, -1.0, L21, ldl, sL, A21, lda, sA, 1.0, A22, lda, sA, 1);
+    gmx<T>(c, nk, OP_N, OP_C, rows, rows, KB, -1.0, A21, lda, sA, L21, ldl, sL, 1.0, A22, lda, sA, 1);
+    gmx<T>(c, nk, OP_N, OP_N, rows, KB, KB, -0.5, L21, ldl, sL, FB, nbb, c->sFB, 1.0, A21, lda, sA);
   }
   // deferred substitution over the outer-block-strictly-lower part
-  for (int R0 = nbb; R0 < M; R0 += nbb) {
-    const int RB = std::min(nbb, M - R0);
+  for (int R0 = nbb; R0 < n; R0 += nbb) {
+    const int RB = std::min(nbb, n - R0);
     for (int r0 = R0; r0 < R0 + RB; r0 += NB) {
       const int rb = std::min(NB, R0 + RB - r0);
-      T* Ai = A + (size_t)r0 * M;
+      T* Ai = A + (size_t)r0 * lda;
       {
         Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * R0 * nk, (2.0 * R0 * rb + 0.5 * rb * rb) * es * nk);
-        trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * M + r0, M, c->sMM, Ai, M, c->sMM, rb, R0, nk, s);
+        trsm_block<T>(TRSM_LEFT, L + (size_t)r0 * ldl + r0, ldl, sL, Ai, lda, sA, rb, R0, nk, s);
       }
       const int below = R0 + RB - r0 - rb;
       if (below > 0)
-        gmx<T>(c, nk, OP_N, OP_N, below, R0, rb, -1.0, L + (size_t)(r0 + rb) * M + r0, M, c->sMM, Ai, M, c->sMM,
-               1.0, A + (size_t)(r0 + rb) * M, M, c->sMM);
+        gmx<T>(c, nk, OP_N, OP_N, below, R0, rb, -1.0, L + (size_t)(r0 + rb) * ldl + r0, ldl, sL, Ai, lda, sA, 1.0,
+               A + (size_t)(r0 + rb) * lda, lda, sA);
     }
-    const int below = M - R0 - RB;
+    const int below = n - R0 - RB;
     if (below > 0)
-      gmx<T>(c, nk, OP_N, OP_N, below, R0, RB, -1.0, L + (size_t)(R0 + RB) * M + R0, M, c->sMM, A + (size_t)R0 * M,
-             M, c->sMM, 1.0, A + (size_t)(R0 + RB) * M, M, c->sMM);
+      gmx<T>(c, nk, OP_N, OP_N, below, R0, RB, -1.0, L + (size_t)(R0 + RB) * ldl + R0, ldl, sL,
+             A + (size_t)R0 * lda, lda, sA, 1.0, A + (size_t)(R0 + RB) * lda, lda, sA);
   }
 }
 
@@ -619,11 +804,11 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
 }
 
 // X <- Q X with Q = P_{M-1} ... P_2 (reflectors stored by the reduction), compact WY in
-// blocks of nbb reflectors: B = I - V T V^H.  T (upper triangular) is assembled from the
-// 64-wide diagonal blocks (larft on G = V^H V) by the merge
+// blocks of nbb reflectors: B = I - V T V^H.  X is M x ncols (ldx, sX).  T (upper
+// triangular) is assembled from the 64-wide diagonal blocks (larft on G = V^H V) by the merge
 //   T[:s, s:s+k] = -T[:s, :s] G[:s, s:s+k] T[s:s+k, s:s+k].
 template <typename T>
-void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
+void backtransform_run(gks_ctx* c, const T* A, T* X, int ldx, long long sX, int M, int ncols, int nk) {
   cudaStream_t s = c->stream;
   const int nbb = c->nbb;
   T* V = at<T>(c, c->oV);
@@ -656,67 +841,75 @@ void backtransform_run(gks_ctx* c, const T* A, T* X, int M, int nk) {
         gmp<T>(c, nk, OP_N, OP_N, s0, ks, s0, -1.0, Tm, nbb, c->sT, Y2, NB, c->sY, 0.0, Tm + s0, nbb, c->sT);
       }
     }
-    gmx<T>(c, nk, OP_C, OP_N, nbk, M, j1, 1.0, V, nbb, c->sV, X, M, c->sMM, 0.0, Y, M, c->sY);
-    gmx<T>(c, nk, OP_N, OP_N, nbk, M, nbk, 1.0, Tm, nbb, c->sT, Y, M, c->sY, 0.0, Y2, M, c->sY);
-    gmx<T>(c, nk, OP_N, OP_N, j1, M, nbk, -1.0, V, nbb, c->sV, Y2, M, c->sY, 1.0, X, M, c->sMM);
+    gmx<T>(c, nk, OP_C, OP_N, nbk, ncols, j1, 1.0, V, nbb, c->sV, X, ldx, sX, 0.0, Y, ncols, c->sY);
+    gmx<T>(c, nk, OP_N, OP_N, nbk, ncols, nbk, 1.0, Tm, nbb, c->sT, Y, ncols, c->sY, 0.0, Y2, ncols, c->sY);
+    gmx<T>(c, nk, OP_N, OP_N, j1, ncols, nbk, -1.0, V, nbb, c->sV, Y2, ncols, c->sY, 1.0, X, ldx, sX);
   }
 }
 
-// X <- L^-H X by block back substitution, two levels: within an outer block of nbb rows,
-// 64-row diagonal blocks by substitution and updates of the rows of that outer block
-// only; then one K = nbb update of all rows above it.
-template <typename T>
-void unreduce_run(gks_ctx* c, const T* L, T* X, int M, int nk) {
-  cudaStream_t s = c->stream;
-  const int es = sizeof(T);
-  const int nbb = c->nbb;
-  const int nob = (M + nbb - 1) / nbb;
-  for (int ob = nob - 1; ob >= 0; ob--) {
-    const int R0 = ob * nbb, RB = std::min(nbb, M - R0);
-    const int nib = (RB + NB - 1) / NB;
-    for (int ib = nib - 1; ib >= 0; ib--) {
-      const int r0 = R0 + ib * NB, rb = std::min(NB, R0 + RB - r0);
-      T* Xi = X + (size_t)r0 * M;
-      {
-        Rec r(c, PC_TRSM, cmul(es) * 0.5 * rb * rb * M * nk, (2.0 * M * rb + 0.5 * rb * rb) * es * nk);
-        trsm_block<T>(TRSM_LEFT_CONJ, L + (size_t)r0 * M + r0, M, c->sMM, Xi, M, c->sMM, rb, M, nk, s);
-      }
-      if (r0 > R0)
-        gmx<T>(c, nk, OP_C, OP_N, r0 - R0, M, rb, -1.0, L + (size_t)r0 * M + R0, M, c->sMM, Xi, M, c->sMM, 1.0,
-               X + (size_t)R0 * M, M, c->sMM);
-    }
-    if (R0 > 0)
-      gmx<T>(c, nk, OP_C, OP_N, R0, M, RB, -1.0, L + (size_t)R0 * M, M, c->sMM, X + (size_t)R0 * M, M, c->sMM, 1.0,
-             X, M, c->sMM);
-  }
+// Does the context still hold the Cholesky factor of this S (same array, shape and type
+// as the solve that produced it)?
+bool factor_matches(const gks_ctx* c, const SolveKey& k) {
+  return c->l_valid && c->lkey.S == k.S && c->lkey.n == k.n && c->lkey.nk == k.nk && c->lkey.dtype == k.dtype &&
+         c->lkey.spin == k.spin;
 }
 
 template <typename T>
-gks_status solve_t(gks_ctx* c, const T* H, const T* S, int n, int nk, bool nc, double kT, double n_elec,
-                   const double* kw, double* eps, T* C, double* mu, T* rho, double* e_band) {
+gks_status solve_t(gks_ctx* c, const SolveKey& key) {
+  const T* H = static_cast<const T*>(key.H);
+  const T* S = static_cast<const T*>(key.S);
+  const int n = (int)key.n, nk = (int)key.nk;
+  const bool nc = key.spin == GKS_NONCOLLINEAR, sp = key.spin == GKS_SPIN_POLARIZED;
   const int M = nc ? 2 * n : n;
+  const int items = sp ? 2 * nk : nk;  // spin-polarized: items (k, up), (k, down)
   const int es = sizeof(T);
-  gks_status rc = ensure_ws(c, M, n, nk, es, nc ? 1 : 0);
+  const int nev = ncols_of(c, M);
+  gks_status rc = ensure_ws(c, M, n, items, es, key.spin);
   if (rc) return rc;
   cudaStream_t s = c->stream;
+  double* eps = static_cast<double*>(const_cast<void*>(key.eps));
+  T* C = static_cast<T*>(const_cast<void*>(key.C));
+  const long long sC = (long long)M * nev;
   T* A = at<T>(c, c->oA);
   T* L = at<T>(c, c->oL);
+  // The factor of S: n x n with leading dimension n in every item's L slot.  Noncollinear:
+  // S_NC = I_2 (x) S, so only the n x n S is factored (paper Sec. 3.2).  Spin-polarized:
+  // both spin channels of a k-point share S_k; it is factored once into the slot of the
+  // up channel and copied to the down channel's.
+  const long long sLk = sp ? 2 * c->sMM : c->sMM;
+  const bool reuse = (key.flags & GKS_REUSE_S_FACTOR) && factor_matches(c, key);
   {
     StageRec sr(c, PS_COPY);
     Rec r(c, PC_MISC);
-    cudaMemsetAsync(c->st, 0, sizeof(DevStatus) * nk, s);
-    copy2d<T>(A, M, c->sMM, H, M, (long long)M * M, M, M, nk, s);
-    if (nc) spinor_overlap<T>(L, c->sMM, S, n, (long long)n * n, n, nk, s);
-    else copy2d<T>(L, M, c->sMM, S, n, (long long)n * n, n, n, nk, s);
+    cudaMemsetAsync(c->st, 0, sizeof(DevStatus) * items, s);
+    copy2d<T>(A, M, c->sMM, H, M, (long long)M * M, M, M, items, s);
+    if (!reuse) copy2d<T>(L, n, sLk, S, n, (long long)n * n, n, n, nk, s);
   }
   // (a1) Cholesky of S, (a2) reduction to the standard problem
-  {
+  if (!reuse) {
+    c->l_valid = false;
     StageRec sr(c, PS_POTRF);
-    potrf_run<T>(c, L, M, nk);
+    potrf_run<T>(c, L, n, n, sLk, nk);
+    if (sp) {
+      Rec r(c, PC_MISC);
+      copy2d<T>(L + c->sMM, n, sLk, L, n, sLk, n, n, nk, s);
+    }
+    c->lkey = key;
+    c->l_valid = true;
   }
   {
     StageRec sr(c, PS_HEGST);
-    hegst_run<T>(c, A, L, M, nk);
+    if (nc) {
+      // H'^{ss'} = L^-1 H^{ss'} L^-H per spin block (paper Sec. 3.2 Part 3-3): the two
+      // Hermitian diagonal blocks two-sided, the lower off-diagonal block by a left and a
+      // right triangular solve
+      hegst_run<T>(c, A, M, c->sMM, L, n, c->sMM, n, nk);
+      hegst_run<T>(c, A + (size_t)n * M + n, M, c->sMM, L, n, c->sMM, n, nk);
+      trsm_left_run<T>(c, L, n, c->sMM, A + (size_t)n * M, M, c->sMM, n, n, nk, false);
+      trsm_right_conj_run<T>(c, L, n, c->sMM, A + (size_t)n * M, M, c->sMM, n, n, nk);
+    } else {
+      hegst_run<T>(c, A, M, c->sMM, L, n, c->sMM, M, items);
+    }
   }
   // (a3-a4) Householder tridiagonalization with a real-making phase
   double* d = at<double>(c, c->od);
@@ -724,78 +917,97 @@ gks_status solve_t(gks_ctx* c, const T* H, const T* S, int n, int nk, bool nc, d
   T* ph = at<T>(c, c->oph);
   {
     StageRec sr(c, PS_HETRD);
-    hetrd_run<T>(c, A, M, nk);
+    hetrd_run<T>(c, A, M, items);
     Rec r(c, PC_HETRD_VEC);
-    hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, nk, s);
+    hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, items, s);
   }
   // (a5) divide and conquer on the real tridiagonal
   double* Z = at<double>(c, c->oZ);
   {
     StageRec sr(c, PS_STEDC);
-    DcSplit sp{nullptr, 0, c->slices, 512};
+    DcSplit sp_{nullptr, 0, c->slices, 512, c->wait_cycles};
     if (c->gemm_mode != 1 && M >= 1024) {
-      const size_t item = dc_split_item_bytes(c->dc, sp.min_half, c->slices);
+      const size_t item = dc_split_item_bytes(c->dc, sp_.min_half, c->slices);
       if (item > 0) {
-        sp.per = oz_reserve(c, item, nk);
-        sp.work = c->oz;
+        sp_.per = oz_reserve(c, item, items);
+        sp_.work = c->oz;
       }
     }
-    dc_solve(c->dc, d, e, M, eps, Z, c->sMM, c->ws + c->odc, c->st, s, &c->prof, &sp);
+    dc_solve(c->dc, d, e, M, eps, Z, c->sMM, c->ws + c->odc, c->st, s, &c->prof, &sp_);
   }
-  // (a6) X = Q D Z, C = L^-H X
+  // (a6) X = Q D Z (the leading nev columns), C = L^-H X
   {
     StageRec sr(c, PS_BACKTR);
     {
       Rec r(c, PC_MISC);
-      apply_phase<T>(C, M, c->sMM, Z, M, c->sMM, ph, M, M, nk, s);
+      apply_phase<T>(C, nev, sC, Z, M, c->sMM, ph, M, M, nev, items, s);
     }
-    backtransform_run<T>(c, A, C, M, nk);
+    backtransform_run<T>(c, A, C, nev, sC, M, nev, items);
   }
   {
     StageRec sr(c, PS_UNREDUCE);
-    unreduce_run<T>(c, L, C, M, nk);
+    if (nc) {  // C = diag(L, L)^-H X: each spin half with the n x n factor
+      trsm_left_run<T>(c, L, n, c->sMM, C, nev, sC, n, nev, nk, true);
+      trsm_left_run<T>(c, L, n, c->sMM, C + (size_t)n * nev, nev, sC, n, nev, nk, true);
+    } else {
+      trsm_left_run<T>(c, L, n, c->sMM, C, nev, sC, M, nev, items, true);
+    }
     Rec r(c, PC_MISC);
-    column_phase<T>(C, M, c->sMM, M, M, nk, s);
+    column_phase<T>(C, nev, sC, M, nev, items, s);
   }
+  if (key.flags & GKS_SAVE_FOR_BACKWARD) {
+    rc = save_for_backward(c, key, M, items, nev);
+    if (rc) return rc;
+  }
+  if (key.flags & GKS_EIGEN_ONLY) return cuda_check(c, "gks_solve launch");
   // (a8) occupations and chemical potential, (a9) density matrix
   double* occ = at<double>(c, c->oocc);
   double* ks = at<double>(c, c->oks);
   int* nrho = at<int>(c, c->onrho);
-  const double* w = kw ? kw : at<double>(c, c->ow);
-  double* eb = e_band ? e_band : at<double>(c, c->oeb);
+  double* w = at<double>(c, c->oweights);
+  double* eb = key.eb ? static_cast<double*>(const_cast<void*>(key.eb)) : at<double>(c, c->oeb);
   {
     StageRec sr(c, PS_OCC);
     Rec r(c, PC_OCC);
-    fermi_mu(eps, M, nk, w, nc ? 1.0 : 2.0, kT, n_elec, c->f_cut, occ, ks, mu, eb, nrho, c->st, 1, s);
+    expand_weights(static_cast<const double*>(key.kw), nk, sp ? 2 : 1, w, s);
+    fermi_mu(eps, M, items, w, nc || sp ? 1.0 : 2.0, key.kT, key.ne, c->f_cut, occ, ks,
+             static_cast<double*>(const_cast<void*>(key.mu)), eb, nrho, c->st, 1, s);
+    if (nev < M) clamp_nrho(nrho, items, nev, c->st, 1, s);
+    if (key.flags & GKS_SAVE_FOR_BACKWARD) save_mu(c, key, M, items, nev);
   }
   {
     StageRec sr(c, PS_RHO);
+    T* rho = static_cast<T*>(const_cast<void*>(key.rho));
     {
-      const bool split = split_worth(c, nk, M, M, M, es, gemm_flops(es, M, M, M / 4, 1, nk));
+      const bool split = split_worth(c, items, M, M, nev, es, gemm_flops(es, M, M, std::max(1, nev / 4), 1, items));
       Rec r(c, split ? PC_OZAKI : PC_GEMM, -1.0, -1.0);  // flops resolved from n_rho when the profile is read
       c->prof.nrho_dev = nrho;
       c->prof.rho_m = M;
-      c->prof.rho_nk = nk;
+      c->prof.rho_nk = items;
       c->prof.rho_es = es;
-      rho_run<T>(c, C, rho, ks, nrho, M, nk);
+      rho_run<T>(c, C, nev, sC, rho, c->sMM, ks, M, nrho, M, nev, items);
     }
     Rec r(c, PC_MISC);
-    mirror_lower<T>(rho, M, c->sMM, M, nk, s);
+    mirror_lower<T>(rho, M, c->sMM, M, items, s);
   }
   return cuda_check(c, "gks_solve launch");
 }
 
 // Adjoint: W = C^H rho_bar C; weights; BH, BS; H_bar = C BH C^H, S_bar = C BS C^H.
+// spin: GKS_COLLINEAR, GKS_NONCOLLINEAR (S_bar = sum of the diagonal spin blocks) or
+// GKS_SPIN_POLARIZED (2 nk items with g_s = 1; S_bar_k = sum over the two channels).
 template <typename T>
-gks_status adjoint_t(gks_ctx* c, const T* C, const double* eps, const double* mu, int n, int nk, bool nc, double kT,
+gks_status adjoint_t(gks_ctx* c, const T* C, const double* eps, const double* mu, int n, int nk, int spin, double kT,
                      const double* kw, const T* rho_bar, const double* eps_bar, double e_band_bar, T* H_bar,
                      T* S_bar) {
+  const bool nc = spin == GKS_NONCOLLINEAR, sp = spin == GKS_SPIN_POLARIZED;
   const int M = nc ? 2 * n : n;
+  const int items = sp ? 2 * nk : nk;
   const int es = sizeof(T);
   const long long MM = (long long)M * M;
-  if (!(c->aws && c->am == M && c->ank == nk && c->aes == es)) {
+  if (!(c->aws && c->am == M && c->ank == items && c->aes == es)) {
     release_aws(c);
-    size_t bytes = (size_t)3 * MM * nk * es + (size_t)4 * M * nk * sizeof(double) + 4096;
+    size_t bytes = (size_t)3 * MM * items * es + (size_t)4 * M * items * sizeof(double) + 4096;
     if (cudaMalloc(&c->aws, bytes) != cudaSuccess) {
       cudaGetLastError();
       c->aws = nullptr;
@@ -803,92 +1015,86 @@ gks_status adjoint_t(gks_ctx* c, const T* C, const double* eps, const double* mu
     }
     c->aws_bytes = bytes;
     c->am = M;
-    c->ank = nk;
+    c->ank = items;
     c->aes = es;
   }
   cudaStream_t s = c->stream;
   T* R = reinterpret_cast<T*>(c->aws);          // rho_bar (Hermitian part), later BH
-  T* W = R + MM * nk;                            // C^H rho_bar C, later BS
-  T* T1 = W + MM * nk;                           // GEMM temporary
-  double* f = reinterpret_cast<double*>(T1 + MM * nk);
-  double* fp = f + (size_t)M * nk;
-  double* e = fp + (size_t)M * nk;
-  double* wdef = e + (size_t)M * nk;
-  const double gs = nc ? 1.0 : 2.0;
+  T* W = R + MM * items;                         // C^H rho_bar C, later BS
+  T* T1 = W + MM * items;                        // GEMM temporary
+  double* f = reinterpret_cast<double*>(T1 + MM * items);
+  double* fp = f + (size_t)M * items;
+  double* e = fp + (size_t)M * items;
+  double* w = e + (size_t)M * items;
+  const double gs = (nc || sp) ? 1.0 : 2.0;
   StageRec sr(c, PS_ADJOINT);
-  const double* w = kw;
-  if (!w) {
-    std::vector<double> h(nk, 1.0 / nk);
-    cudaMemcpyAsync(wdef, h.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, s);
-    cudaStreamSynchronize(s);
-    w = wdef;
-  }
   {
     Rec r(c, PC_MISC);
-    adj_occ(eps, mu, kT, (long long)nk * M, f, fp, s);
+    expand_weights(kw, nk, sp ? 2 : 1, w, s);
+    adj_occ(eps, mu, kT, (long long)items * M, f, fp, s);
   }
   const int have_w = rho_bar ? 1 : 0;
   if (have_w) {
     {
       Rec r(c, PC_MISC);
-      herm_part<T>(R, rho_bar, MM, MM, M, nk, s);
+      herm_part<T>(R, rho_bar, MM, MM, M, items, s);
     }
-    gmx<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, R, M, MM, C, M, MM, 0.0, T1, M, MM);
-    gmx<T>(c, nk, OP_C, OP_N, M, M, M, 1.0, C, M, MM, T1, M, MM, 0.0, W, M, MM);
+    gmx<T>(c, items, OP_N, OP_N, M, M, M, 1.0, R, M, MM, C, M, MM, 0.0, T1, M, MM);
+    gmx<T>(c, items, OP_C, OP_N, M, M, M, 1.0, C, M, MM, T1, M, MM, 0.0, W, M, MM);
   }
   {
     Rec r(c, PC_MISC);
-    adj_weights<T>(eps, f, fp, w, W, MM, M, nk, gs, eps_bar, e_band_bar, have_w, e, s);
-    adj_build<T>(W, R, MM, M, eps, f, e, mu, kT, gs, have_w, nk, s);
+    adj_weights<T>(eps, f, fp, w, W, MM, M, items, gs, eps_bar, e_band_bar, have_w, e, s);
+    adj_build<T>(W, R, MM, M, eps, f, e, mu, kT, gs, have_w, items, s);
   }
   // H_bar = C BH C^H
-  gmx<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, C, M, MM, R, M, MM, 0.0, T1, M, MM);
-  gmx<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, H_bar, M, MM);
+  gmx<T>(c, items, OP_N, OP_N, M, M, M, 1.0, C, M, MM, R, M, MM, 0.0, T1, M, MM);
+  gmx<T>(c, items, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, H_bar, M, MM);
   {
     Rec r(c, PC_MISC);
-    herm_part<T>(H_bar, H_bar, MM, MM, M, nk, s);
+    herm_part<T>(H_bar, H_bar, MM, MM, M, items, s);
   }
-  // S_bar = C BS C^H (noncollinear: the two diagonal spin blocks summed)
-  gmx<T>(c, nk, OP_N, OP_N, M, M, M, 1.0, C, M, MM, W, M, MM, 0.0, T1, M, MM);
-  if (nc) {
-    gmx<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, R, M, MM);
+  // S_bar = C BS C^H (noncollinear: the two diagonal spin blocks summed; spin-polarized:
+  // the two channels summed)
+  gmx<T>(c, items, OP_N, OP_N, M, M, M, 1.0, C, M, MM, W, M, MM, 0.0, T1, M, MM);
+  if (nc || sp) {
+    gmx<T>(c, items, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, R, M, MM);
     Rec r(c, PC_MISC);
-    spin_block_sum<T>(S_bar, (long long)n * n, R, MM, n, nk, s);
+    if (nc) spin_block_sum<T>(S_bar, (long long)n * n, R, MM, n, nk, s);
+    else spin_pair_sum<T>(S_bar, (long long)n * n, R, MM, n, nk, s);
   } else {
-    gmx<T>(c, nk, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, S_bar, M, MM);
+    gmx<T>(c, items, OP_N, OP_C, M, M, M, 1.0, T1, M, MM, C, M, MM, 0.0, S_bar, M, MM);
     Rec r(c, PC_MISC);
-    herm_part<T>(S_bar, S_bar, MM, MM, M, nk, s);
+    herm_part<T>(S_bar, S_bar, MM, MM, M, items, s);
   }
   return cuda_check(c, "gks_adjoint launch");
 }
 
 gks_status validate_solve(gks_ctx* ctx, const SolveKey& k) {
-  if (!k.H || !k.S || !k.eps || !k.C || !k.mu || !k.rho) return fail(ctx, GKS_EINVAL, "null array argument");
-  if (k.n < 1 || k.nk < 1 || k.n > 46340 || k.nk > 65535) return fail(ctx, GKS_EINVAL, "n or nk out of range");
+  const bool eig_only = (k.flags & GKS_EIGEN_ONLY) != 0;
+  if (!k.H || !k.S || !k.eps || !k.C || (!eig_only && (!k.mu || !k.rho)))
+    return fail(ctx, GKS_EINVAL, "null array argument");
+  if (k.flags & ~(unsigned)(GKS_REUSE_S_FACTOR | GKS_SAVE_FOR_BACKWARD | GKS_EIGEN_ONLY))
+    return fail(ctx, GKS_EINVAL, "unknown flag bits");
+  if (k.n < 1 || k.nk < 1 || k.n > 46340 || k.nk > 32767) return fail(ctx, GKS_EINVAL, "n or nk out of range");
   if (k.dtype != GKS_R64 && k.dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
-  if (k.spin != GKS_COLLINEAR && k.spin != GKS_NONCOLLINEAR) return fail(ctx, GKS_EINVAL, "unknown spin mode");
+  if (k.spin != GKS_COLLINEAR && k.spin != GKS_NONCOLLINEAR && k.spin != GKS_SPIN_POLARIZED)
+    return fail(ctx, GKS_EINVAL, "unknown spin mode");
   const bool nc = k.spin == GKS_NONCOLLINEAR;
   if (nc && k.dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
   if (nc && 2 * k.n > 46340) return fail(ctx, GKS_EINVAL, "2n out of range");
-  if (!(k.kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
-  const double gs = nc ? 1.0 : 2.0;
-  const double M = nc ? 2.0 * k.n : (double)k.n;
-  if (!(k.ne > 0.0) || !(k.ne < gs * M)) return fail(ctx, GKS_EINVAL, "n_elec must lie in (0, g_s M)");
+  if (!eig_only) {
+    if (!(k.kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
+    const double gs = k.spin == GKS_COLLINEAR ? 2.0 : 1.0;
+    const double states = (nc ? 2.0 * k.n : (double)k.n) * (k.spin == GKS_SPIN_POLARIZED ? 2.0 : 1.0);
+    if (!(k.ne > 0.0) || !(k.ne < gs * states)) return fail(ctx, GKS_EINVAL, "n_elec must lie in (0, g_s M)");
+  }
   return GKS_OK;
 }
 
 gks_status enqueue_solve(gks_ctx* ctx, const SolveKey& k) {
-  const bool nc = k.spin == GKS_NONCOLLINEAR;
-  if (k.dtype == GKS_R64)
-    return solve_t<double>(ctx, static_cast<const double*>(k.H), static_cast<const double*>(k.S), (int)k.n,
-                           (int)k.nk, nc, k.kT, k.ne, static_cast<const double*>(k.kw),
-                           const_cast<double*>(static_cast<const double*>(k.eps)),
-                           static_cast<double*>(const_cast<void*>(k.C)), const_cast<double*>(static_cast<const double*>(k.mu)),
-                           static_cast<double*>(const_cast<void*>(k.rho)), const_cast<double*>(static_cast<const double*>(k.eb)));
-  return solve_t<zc>(ctx, static_cast<const zc*>(k.H), static_cast<const zc*>(k.S), (int)k.n, (int)k.nk, nc, k.kT,
-                     k.ne, static_cast<const double*>(k.kw), const_cast<double*>(static_cast<const double*>(k.eps)),
-                     static_cast<zc*>(const_cast<void*>(k.C)), const_cast<double*>(static_cast<const double*>(k.mu)),
-                     static_cast<zc*>(const_cast<void*>(k.rho)), const_cast<double*>(static_cast<const double*>(k.eb)));
+  if (k.dtype == GKS_R64) return solve_t<double>(ctx, k);
+  return solve_t<zc>(ctx, k);
 }
 
 bool same_key(const SolveKey& a, const SolveKey& b) { return std::memcmp(&a, &b, sizeof(SolveKey)) == 0; }
@@ -919,27 +1125,59 @@ gks_status capture(gks_ctx* c, cudaGraphExec_t* out, F body) {
 
 }  // namespace
 
+// ---- tuned-width cache file: one line per shape class, "bucket element_size spin width" ----
+namespace {
+void load_tune_cache(gks_ctx* c) {
+  FILE* f = std::fopen(c->tune_cache.c_str(), "r");
+  if (!f) return;  // no cache yet: the first gks_tune writes it
+  int b, es, sp, w;
+  while (std::fscanf(f, "%d %d %d %d", &b, &es, &sp, &w) == 4)
+    if (w >= NB && w <= 1024 && w % NB == 0 && (es == 8 || es == 16) && sp >= 0 && sp <= 2)
+      c->tuned[std::make_tuple(b, es, sp)] = w;
+  std::fclose(f);
+}
+
+bool save_tune_cache(const gks_ctx* c) {
+  if (c->tune_cache.empty()) return true;
+  const std::string tmp = c->tune_cache + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  for (const auto& kv : c->tuned)
+    std::fprintf(f, "%d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), kv.second);
+  const bool ok = std::fclose(f) == 0;
+  return ok && std::rename(tmp.c_str(), c->tune_cache.c_str()) == 0;
+}
+}  // namespace
+
 // ---- fixed scratch for split products that allocate nothing ----
 // Digit scratch of gks_gemm_split_noalloc, part of the library image on every device.
 // Shared by all calls on a device: calls whose work overlaps in time race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GKS_NOALLOC_SCRATCH_BYTES];
+// Status word of those products (a bounded wait that expired), read back by gks_sync.
+static __device__ __align__(256) DevStatus g_noalloc_status;
 
 namespace {
 constexpr int kNoAllocDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoAllocDevices] = {};
+DevStatus* g_noalloc_st[kNoAllocDevices] = {};
 
-// Device address of the scratch on `dev`, which must be the current device; resolved
-// once per device.
-cudaError_t noalloc_scratch(int dev, void** out) {
+// Device addresses of the scratch and of its status word on `dev`, which must be the
+// current device; resolved once per device.
+cudaError_t noalloc_scratch(int dev, void** out, DevStatus** st) {
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
+    void* q = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    e = cudaGetSymbolAddress(&q, g_noalloc_status);
+    if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = p;
+    g_noalloc_st[dev] = static_cast<DevStatus*>(q);
   }
   *out = g_noalloc_ptr[dev];
+  *st = g_noalloc_st[dev];
   return cudaSuccess;
 }
 }  // namespace
@@ -960,21 +1198,37 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     if (opts->block > 0) c->nbb = opts->block;
     c->nbb_default = c->nbb;
     c->nbb_fixed = opts->block > 0;
+    c->precision = opts->precision;
+    if (opts->refine_sweeps > 0) c->refine_sweeps = opts->refine_sweeps;
+    c->n_ev = opts->n_ev;
+    if (opts->wait_limit > 0) c->wait_cycles = opts->wait_limit;
+    c->debug = opts->debug;
+    if (opts->autotune_cache) c->tune_cache = opts->autotune_cache;
     if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 10 || c->nbb < NB || c->nbb > 1024 ||
-        c->nbb % NB) {
+        c->nbb % NB || c->n_ev < 0 || opts->refine_sweeps < 0 || opts->refine_sweeps > 8 || opts->wait_limit < 0 ||
+        (opts->debug & ~GKS_DEBUG_SKIP_COPY)) {
       delete c;
       return GKS_EINVAL;
     }
-    if (opts->precision != GKS_FP64) {
+    if (c->precision != GKS_FP64) {
       delete c;
-      return GKS_ENOTIMPL;
+      return (c->precision == GKS_MIXED_TF32 || c->precision == GKS_MIXED_SPLITBF16) ? GKS_ENOTIMPL : GKS_EINVAL;
     }
   }
-  if (cudaSetDevice(c->device) != cudaSuccess) {
-    cudaGetLastError();
-    delete c;
-    return GKS_ECUDA;
+  {
+    DeviceGuard dg(c->device);
+    if (!dg.ok) {
+      delete c;
+      return GKS_ECUDA;
+    }
+    if (cudaMalloc(&c->gst, sizeof(DevStatus)) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return GKS_ENOMEM;
+    }
+    cudaMemset(c->gst, 0, sizeof(DevStatus));
   }
+  if (!c->tune_cache.empty()) load_tune_cache(c);
   c->prof.stream = c->stream;
   *ctx = c;
   return GKS_OK;
@@ -982,7 +1236,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
 
 gks_status gks_destroy(gks_ctx* ctx) {
   if (!ctx) return GKS_OK;
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   for (auto sc : ctx->subs) {
@@ -995,6 +1249,7 @@ gks_status gks_destroy(gks_ctx* ctx) {
   release_ws(ctx);
   release_aws(ctx);
   release_oz(ctx);
+  release_extra(ctx);
   delete ctx;
   return GKS_OK;
 }
@@ -1006,11 +1261,11 @@ gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int6
                      double* mu, void* rho, double* e_band) {
   if (!ctx) return GKS_EINVAL;
   ctx->err.clear();
-  SolveKey k{H, S, kweights, eps, C, mu, rho, e_band, (long long)n, (long long)nk, dtype, spin_mode, kT, n_elec};
+  SolveKey k{H, S, kweights, eps, C, mu, rho, e_band, (long long)n, (long long)nk, dtype, spin_mode, kT, n_elec,
+             flags, 0u};
   gks_status rc = validate_solve(ctx, k);
   if (rc) return rc;
-  if (flags != 0) return fail(ctx, GKS_ENOTIMPL, "flags must be 0");
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   if (!ctx->graph || ctx->stream == nullptr) return enqueue_solve(ctx, k);
   // graph mode: replay while the arguments are unchanged; the first call for a new
   // argument set runs eagerly (allocates the workspace and the merge lists), the next
@@ -1020,12 +1275,17 @@ gks_status gks_solve(gks_ctx* ctx, const void* H, const void* S, int64_t n, int6
     return cuda_check(ctx, "graph launch");
   }
   const int M = spin_mode == GKS_NONCOLLINEAR ? (int)(2 * n) : (int)n;
+  const int items = spin_mode == GKS_SPIN_POLARIZED ? (int)(2 * nk) : (int)nk;
   const int es = dtype == GKS_R64 ? 8 : 16;
-  // capture only when the workspace (order, batch, type and width) is already in place,
-  // so that nothing is allocated or freed while the stream is being captured
-  const bool ready = ctx->ws && ctx->m == M && ctx->nk == nk && ctx->es == es &&
-                     ctx->nbb == pick_width(ctx, M, es, spin_mode == GKS_NONCOLLINEAR ? 1 : 0) &&
-                     ctx->gkey.H == k.H && ctx->gkey.C == k.C;
+  // capture only when the workspace (order, batch, type and width) and the saved copies
+  // are already in place, so that nothing is allocated or freed while the stream is being
+  // captured
+  const bool saved_ok = !(flags & GKS_SAVE_FOR_BACKWARD) ||
+                        (ctx->sv_valid && ctx->svkey.n == k.n && ctx->svkey.nk == k.nk &&
+                         ctx->svkey.dtype == k.dtype && ctx->svkey.spin == k.spin);
+  const bool ready = ctx->ws && ctx->m == M && ctx->nk == items && ctx->es == es &&
+                     ctx->nbb == pick_width(ctx, M, es, shape_spin(spin_mode)) && ctx->gkey.H == k.H && ctx->gkey.C == k.C &&
+                     saved_ok;
   ctx->gkey = k;
   if (ctx->gexec) {
     cudaGraphExecDestroy(ctx->gexec);
@@ -1046,11 +1306,11 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
   for (int64_t b = 0; b < count; b++) {
     const gks_problem& p = probs[b];
     keys[b] = SolveKey{p.H, p.S, p.kweights, p.eps, p.C, p.mu, p.rho, p.e_band, (long long)p.n, (long long)p.nk,
-                       p.dtype, p.spin_mode, p.kT, p.n_elec};
+                       p.dtype, p.spin_mode, p.kT, p.n_elec, 0u, 0u};
     gks_status rc = validate_solve(ctx, keys[b]);
     if (rc) return fail(ctx, rc, "problem " + std::to_string(b) + ": " + ctx->err);
   }
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   const int P = std::max(1, std::min(nstreams > 0 ? nstreams : 8, (int)count));
   while ((int)ctx->workers.size() < P) {
     cudaStream_t w;
@@ -1066,6 +1326,10 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     sc->nbb = ctx->nbb;
     sc->nbb_default = ctx->nbb_default;
     sc->nbb_fixed = ctx->nbb_fixed;
+    sc->wait_cycles = ctx->wait_cycles;
+    sc->n_ev = ctx->n_ev;
+    sc->precision = ctx->precision;
+    sc->refine_sweeps = ctx->refine_sweeps;
     ctx->subs.push_back(sc);
   }
   for (auto* sc : ctx->subs) sc->tuned = ctx->tuned;
@@ -1123,31 +1387,143 @@ gks_status gks_adjoint(gks_ctx* ctx, const void* C, const double* eps, const dou
                        const double* eps_bar, double e_band_bar, void* H_bar, void* S_bar) {
   if (!ctx) return GKS_EINVAL;
   ctx->err.clear();
-  if (!C || !eps || !mu || !H_bar || !S_bar) return fail(ctx, GKS_EINVAL, "null array argument");
-  if (n < 1 || nk < 1 || n > 46340 || nk > 65535) return fail(ctx, GKS_EINVAL, "n or nk out of range");
+  if (!H_bar || !S_bar) return fail(ctx, GKS_EINVAL, "null array argument");
+  if (n < 1 || nk < 1 || n > 46340 || nk > 32767) return fail(ctx, GKS_EINVAL, "n or nk out of range");
   if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
   const bool nc = spin_mode == GKS_NONCOLLINEAR;
-  if (spin_mode != GKS_COLLINEAR && !nc) return fail(ctx, GKS_EINVAL, "unknown spin mode");
+  if (spin_mode != GKS_COLLINEAR && !nc && spin_mode != GKS_SPIN_POLARIZED)
+    return fail(ctx, GKS_EINVAL, "unknown spin mode");
   if (nc && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
   if (!(kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
-  cudaSetDevice(ctx->device);
+  const int M = nc ? 2 * (int)n : (int)n;
+  if (ncols_of(ctx, M) < M) return fail(ctx, GKS_EINVAL, "the adjoint needs every eigenvector (opts.n_ev = 0)");
+  if (!C || !eps || !mu) {
+    // the copies kept by the last solve with GKS_SAVE_FOR_BACKWARD
+    if (C || eps) return fail(ctx, GKS_EINVAL, "pass C and eps together, or neither to use the saved ones");
+    const SolveKey& k = ctx->svkey;
+    if (!ctx->sv_valid || k.n != n || k.nk != nk || k.dtype != dtype || k.spin != spin_mode)
+      return fail(ctx, GKS_EINVAL, "no eigenpairs of this shape were saved (GKS_SAVE_FOR_BACKWARD)");
+    if (!mu && (k.flags & GKS_EIGEN_ONLY)) return fail(ctx, GKS_EINVAL, "the saved solve computed no mu");
+    const int items = spin_mode == GKS_SPIN_POLARIZED ? 2 * (int)nk : (int)nk;
+    const size_t bC = (size_t)items * M * M * (dtype == GKS_C128 ? 16 : 8), bE = (size_t)items * M * sizeof(double);
+    const size_t oE = (bC + 255) & ~size_t(255), oM = oE + ((bE + 255) & ~size_t(255));
+    C = ctx->sv;
+    eps = reinterpret_cast<const double*>(ctx->sv + oE);
+    if (!mu) mu = reinterpret_cast<const double*>(ctx->sv + oM);
+  }
+  DeviceGuard dg(ctx->device);
   if (dtype == GKS_R64)
-    return adjoint_t<double>(ctx, static_cast<const double*>(C), eps, mu, (int)n, (int)nk, nc, kT, kweights,
+    return adjoint_t<double>(ctx, static_cast<const double*>(C), eps, mu, (int)n, (int)nk, spin_mode, kT, kweights,
                              static_cast<const double*>(rho_bar), eps_bar, e_band_bar, static_cast<double*>(H_bar),
                              static_cast<double*>(S_bar));
-  return adjoint_t<zc>(ctx, static_cast<const zc*>(C), eps, mu, (int)n, (int)nk, nc, kT, kweights,
+  return adjoint_t<zc>(ctx, static_cast<const zc*>(C), eps, mu, (int)n, (int)nk, spin_mode, kT, kweights,
                        static_cast<const zc*>(rho_bar), eps_bar, e_band_bar, static_cast<zc*>(H_bar),
                        static_cast<zc*>(S_bar));
 }
 
+gks_status gks_occupy(gks_ctx* ctx, const double* eps_all, int64_t nk_all, int64_t k0, const void* C, int64_t n,
+                      int64_t nk, int dtype, int spin_mode, double kT, double n_elec, const double* kweights_all,
+                      double* mu, void* rho, double* e_band, void* edm) {
+  if (!ctx) return GKS_EINVAL;
+  ctx->err.clear();
+  if (!eps_all || !mu || ((rho || edm) && !C)) return fail(ctx, GKS_EINVAL, "null array argument");
+  if (n < 1 || n > 46340 || nk_all < 1 || nk_all > 32767 || k0 < 0 || nk < 0 || k0 + nk > nk_all)
+    return fail(ctx, GKS_EINVAL, "n, nk_all, k0 or nk out of range");
+  if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
+  const bool nc = spin_mode == GKS_NONCOLLINEAR, sp = spin_mode == GKS_SPIN_POLARIZED;
+  if (spin_mode != GKS_COLLINEAR && !nc && !sp) return fail(ctx, GKS_EINVAL, "unknown spin mode");
+  if (nc && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
+  if (!(kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
+  const int M = nc ? 2 * (int)n : (int)n;
+  const int rep = sp ? 2 : 1;
+  const double gs = (nc || sp) ? 1.0 : 2.0;
+  if (!(n_elec > 0.0) || !(n_elec < gs * M * rep)) return fail(ctx, GKS_EINVAL, "n_elec must lie in (0, g_s M)");
+  const int all = (int)nk_all * rep, loc = (int)nk * rep, i0 = (int)k0 * rep;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const size_t vec = ((size_t)all * M * sizeof(double) + 255) & ~size_t(255);
+  const size_t need = 3 * vec + (((size_t)all * (sizeof(double) + sizeof(int)) + 255) & ~size_t(255)) + 256;
+  if (need > ctx->ow_bytes) {
+    cudaStreamSynchronize(s);
+    if (ctx->ow) cudaFree(ctx->ow);
+    ctx->ow = nullptr;
+    ctx->ow_bytes = 0;
+    if (cudaMalloc(&ctx->ow, need) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->ow = nullptr;
+      return fail(ctx, GKS_ENOMEM, "occupation workspace allocation failed");
+    }
+    ctx->ow_bytes = need;
+  }
+  double* occ = reinterpret_cast<double*>(ctx->ow);
+  double* ks = reinterpret_cast<double*>(ctx->ow + vec);
+  double* kse = reinterpret_cast<double*>(ctx->ow + 2 * vec);
+  double* w = reinterpret_cast<double*>(ctx->ow + 3 * vec);
+  int* nrho = reinterpret_cast<int*>(w + all);
+  double* eb = reinterpret_cast<double*>(ctx->ow + need - 256);
+  const int nev = ncols_of(ctx, M);
+  const long long sC = (long long)M * nev, MM = (long long)M * M;
+  {
+    StageRec sr(ctx, PS_OCC);
+    Rec r(ctx, PC_OCC);
+    cudaMemsetAsync(ctx->gst, 0, sizeof(DevStatus), s);
+    expand_weights(kweights_all, (int)nk_all, rep, w, s);
+    fermi_mu(eps_all, M, all, w, gs, kT, n_elec, ctx->f_cut, occ, ks, mu, e_band ? e_band : eb, nrho, ctx->gst, 1, s);
+    if (nev < M && loc > 0) clamp_nrho(nrho + i0, loc, nev, ctx->gst, 0, s);
+  }
+  if (loc > 0 && (rho || edm)) {
+    StageRec sr(ctx, PS_RHO);
+    auto run = [&](void* out, const double* weights) {
+      if (dtype == GKS_R64) {
+        rho_run<double>(ctx, static_cast<const double*>(C), nev, sC, static_cast<double*>(out), MM, weights, M,
+                        nrho + i0, M, nev, loc);
+        mirror_lower<double>(static_cast<double*>(out), M, MM, M, loc, s);
+      } else {
+        rho_run<zc>(ctx, static_cast<const zc*>(C), nev, sC, static_cast<zc*>(out), MM, weights, M, nrho + i0, M, nev,
+                    loc);
+        mirror_lower<zc>(static_cast<zc*>(out), M, MM, M, loc, s);
+      }
+    };
+    if (rho) run(rho, ks + (size_t)i0 * M);
+    if (edm) {
+      // energy-density matrix: the density-matrix product with weights g_s f eps
+      mul_elem(ks + (size_t)i0 * M, eps_all + (size_t)i0 * M, kse, (long long)loc * M, s);
+      run(edm, kse);
+    }
+  }
+  return cuda_check(ctx, "gks_occupy launch");
+}
+
 gks_status gks_sync(gks_ctx* ctx) {
   if (!ctx) return GKS_EINVAL;
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   cudaError_t e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(ctx, GKS_ECUDA, std::string("synchronize: ") + cudaGetErrorString(e));
   for (size_t b = 0; b < ctx->subs.size(); b++) {
     gks_status rc = gks_sync(ctx->subs[b]);
     if (rc) return fail(ctx, rc, "batch problem " + std::to_string(b) + ": " + ctx->subs[b]->err);
+  }
+  if (ctx->noalloc_st) {
+    DevStatus h{};
+    if (cudaMemcpy(&h, ctx->noalloc_st, sizeof(DevStatus), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(ctx, GKS_ECUDA, "status read failed");
+    ctx->noalloc_st = nullptr;
+    if (h.code != ST_OK)
+      return fail(ctx, (gks_status)h.code, "gks_gemm_split_noalloc: a bounded device-side wait expired; the "
+                                           "product's output is incomplete");
+  }
+  if (ctx->gst) {
+    DevStatus h{};
+    if (cudaMemcpy(&h, ctx->gst, sizeof(DevStatus), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(ctx, GKS_ECUDA, "status read failed");
+    if (h.code != ST_OK) {
+      cudaMemset(ctx->gst, 0, sizeof(DevStatus));
+      ctx->l_valid = false;
+      return fail(ctx, (gks_status)h.code,
+                  h.code == ST_ETIMEOUT ? std::string("a bounded device-side wait expired in a product; its output is "
+                                                      "incomplete")
+                                        : "invalid occupation parameters or non-finite eigenvalues (gks_occupy)");
+    }
   }
   if (!ctx->st) return GKS_OK;
   std::vector<DevStatus> h(ctx->nk);
@@ -1158,9 +1534,13 @@ gks_status gks_sync(gks_ctx* ctx) {
     gks_status code = (gks_status)h[k].code;
     std::string what = code == GKS_ENOTSPD ? "S is not positive definite at column " + std::to_string(h[k].info)
                        : code == GKS_ENOCONV ? "iteration did not converge (index " + std::to_string(h[k].info) + ")"
+                       : code == GKS_ETIMEOUT ? std::string("a bounded device-side wait expired in a product")
+                       : code == GKS_EINVAL && h[k].info > 0
+                           ? "occupied states (" + std::to_string(h[k].info) + ") exceed the eigenvectors computed (n_ev)"
                        : code == GKS_EINVAL ? std::string("invalid occupation parameters or non-finite eigenvalues")
                                             : "device status " + std::to_string(h[k].code);
     cudaMemset(ctx->st, 0, sizeof(DevStatus) * ctx->nk);
+    ctx->l_valid = false;  // the kept factor may come from the failed solve
     return fail(ctx, code, what + " (batch item " + std::to_string(k) + ")");
   }
   return GKS_OK;
@@ -1170,7 +1550,7 @@ long long gks_launch_count(void) { return launches_issued(); }
 
 int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max) {
   if (!ctx || !ctx->prof.on) return 0;
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   EventProf& P = ctx->prof;
@@ -1214,7 +1594,7 @@ gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_
   if (!ctx || !A || !B || !C || M < 0 || N < 0 || K < 0) return fail(ctx, GKS_EINVAL, "bad arguments");
   if (opA < 0 || opA > 2 || opB < 0 || opB > 2 || mode < 1 || mode > 2) return fail(ctx, GKS_EINVAL, "bad op or mode");
   if (M > 46340 || N > 46340 || K > 46340) return fail(ctx, GKS_EINVAL, "dimension too large");
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   const int saved = ctx->gemm_mode;
   ctx->gemm_mode = mode;
   if (dtype == GKS_R64)
@@ -1244,22 +1624,26 @@ gks_status gks_gemm_split_noalloc(gks_ctx* ctx, int dtype, int opA, int opB, int
     return fail(ctx, GKS_EINVAL,
                 "product needs " + std::to_string(need) + " bytes of split scratch; the fixed scratch holds " +
                     std::to_string((size_t)GKS_NOALLOC_SCRATCH_BYTES) + " bytes");
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_check(ctx, "gks_gemm_split_noalloc: set device");
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return fail(ctx, GKS_ECUDA, "gks_gemm_split_noalloc: cannot make the context's device current");
   void* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(ctx->device, &scratch);
+  DevStatus* st = nullptr;
+  cudaError_t e = noalloc_scratch(ctx->device, &scratch, &st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, GKS_ECUDA, std::string("gks_gemm_split_noalloc: scratch lookup: ") + cudaGetErrorString(e));
   }
+  cudaMemsetAsync(st, 0, sizeof(DevStatus), ctx->stream);
+  ctx->noalloc_st = st;
   bool ok;
   if (dtype == GKS_R64)
     ok = ozaki_gemm<double>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const double*>(A), (int)lda, 0,
                        static_cast<const double*>(B), (int)ldb, 0, beta, static_cast<double*>(C), (int)ldc, 0, 1, 0,
-                       ctx->slices, scratch, nullptr, ctx->stream);
+                       ctx->slices, scratch, st, ctx->stream, nullptr, 0, nullptr, ctx->wait_cycles);
   else
     ok = ozaki_gemm<zc>(opA, opB, (int)M, (int)N, (int)K, alpha, static_cast<const zc*>(A), (int)lda, 0,
                    static_cast<const zc*>(B), (int)ldb, 0, beta, static_cast<zc*>(C), (int)ldc, 0, 1, 0,
-                   ctx->slices, scratch, nullptr, ctx->stream);
+                   ctx->slices, scratch, st, ctx->stream, nullptr, 0, nullptr, ctx->wait_cycles);
   if (!ok) return fail(ctx, GKS_ECUDA, "gks_gemm_split_noalloc: TMA tensor map encoding unavailable");
   return cuda_check(ctx, "gks_gemm_split_noalloc");
 }
@@ -1276,7 +1660,8 @@ gks_status gks_tune(gks_ctx* ctx, int64_t n, int64_t nk, int dtype, int spin_mod
   const int M = nc ? 2 * (int)n : (int)n;
   const int es = dtype == GKS_C128 ? 16 : 8;
   if ((double)M * M * nk * es > 64e9) return fail(ctx, GKS_EINVAL, "tuning problem too large");
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_check(ctx, "gks_tune: set device");
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return fail(ctx, GKS_ECUDA, "gks_tune: cannot make the context's device current");
   const size_t bH = (size_t)M * M * nk * es, bS = (size_t)n * n * nk * es;
   void *H = nullptr, *S = nullptr, *C = nullptr, *rho = nullptr;
   double *eps = nullptr, *mu = nullptr;
@@ -1334,6 +1719,7 @@ gks_status gks_tune(gks_ctx* ctx, int64_t n, int64_t nk, int dtype, int spin_mod
   }
   ctx->tuned[key] = widths[bi];
   *best = widths[bi];
+  if (!save_tune_cache(ctx)) return fail(ctx, GKS_EINVAL, "cannot write the autotune cache " + ctx->tune_cache);
   return cuda_check(ctx, "gks_tune");
 }
 
@@ -1345,6 +1731,7 @@ gks_status gks_tune_set(gks_ctx* ctx, int64_t n, int dtype, int spin_mode, int w
   const auto key = std::make_tuple(order_bucket(nc ? 2 * (int)n : (int)n), dtype == GKS_C128 ? 16 : 8, nc ? 1 : 0);
   if (width == 0) ctx->tuned.erase(key);
   else ctx->tuned[key] = width;
+  if (!save_tune_cache(ctx)) return fail(ctx, GKS_EINVAL, "cannot write the autotune cache " + ctx->tune_cache);
   return GKS_OK;
 }
 
@@ -1356,17 +1743,17 @@ int gks_tune_get(const gks_ctx* ctx, int64_t n, int dtype, int spin_mode) {
 
 gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype) {
   if (!ctx || !A || m < 1 || count < 1 || m > 46340) return fail(ctx, GKS_EINVAL, "bad arguments");
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   if (dtype == GKS_R64) {
     gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 8, 0);
     if (rc) return rc;
     cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
-    potrf_run<double>(ctx, static_cast<double*>(A), (int)m, (int)count);
+    potrf_run<double>(ctx, static_cast<double*>(A), (int)m, (int)m, m * m, (int)count);
   } else if (dtype == GKS_C128) {
     gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 16, 0);
     if (rc) return rc;
     cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
-    potrf_run<zc>(ctx, static_cast<zc*>(A), (int)m, (int)count);
+    potrf_run<zc>(ctx, static_cast<zc*>(A), (int)m, (int)m, m * m, (int)count);
   } else {
     return fail(ctx, GKS_EINVAL, "unknown dtype");
   }
@@ -1375,19 +1762,20 @@ gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype)
 
 gks_status gks_reduce(gks_ctx* ctx, void* H, void* S, int64_t m, int64_t count, int dtype) {
   if (!ctx || !H || !S || m < 1 || count < 1 || m > 46340) return fail(ctx, GKS_EINVAL, "bad arguments");
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   if (dtype == GKS_R64) {
     gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 8, 0);
     if (rc) return rc;
     cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
-    potrf_run<double>(ctx, static_cast<double*>(S), (int)m, (int)count);
-    hegst_run<double>(ctx, static_cast<double*>(H), static_cast<double*>(S), (int)m, (int)count);
+    potrf_run<double>(ctx, static_cast<double*>(S), (int)m, (int)m, m * m, (int)count);
+    hegst_run<double>(ctx, static_cast<double*>(H), (int)m, m * m, static_cast<double*>(S), (int)m, m * m, (int)m,
+                      (int)count);
   } else if (dtype == GKS_C128) {
     gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 16, 0);
     if (rc) return rc;
     cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
-    potrf_run<zc>(ctx, static_cast<zc*>(S), (int)m, (int)count);
-    hegst_run<zc>(ctx, static_cast<zc*>(H), static_cast<zc*>(S), (int)m, (int)count);
+    potrf_run<zc>(ctx, static_cast<zc*>(S), (int)m, (int)m, m * m, (int)count);
+    hegst_run<zc>(ctx, static_cast<zc*>(H), (int)m, m * m, static_cast<zc*>(S), (int)m, m * m, (int)m, (int)count);
   } else {
     return fail(ctx, GKS_EINVAL, "unknown dtype");
   }
@@ -1397,7 +1785,7 @@ gks_status gks_reduce(gks_ctx* ctx, void* H, void* S, int64_t m, int64_t count, 
 gks_status gks_stedc(gks_ctx* ctx, const double* d, const double* e, int64_t m, int64_t count, double* lam,
                      double* Z) {
   if (!ctx || !d || !e || !lam || !Z || m < 1 || count < 1 || m > 46340) return fail(ctx, GKS_EINVAL, "bad arguments");
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, 8, 0);
   if (rc) return rc;
   cudaStream_t s = ctx->stream;

@@ -224,17 +224,17 @@ __global__ void larft_kernel(const T* G, int ldG, long long sG, const double* ta
   for (int e = tid; e < k * k; e += nt) Tm[(size_t)(e / k) * ldT + (e % k)] = t[e];
 }
 
-// X[b][i][c] = ph[b][i] * Z[b][i][c]  (Z real, X of type T)
+// X[b][i][c] = ph[b][i] * Z[b][i][c] for the leading `cols` columns (Z real, X of type T)
 template <typename T>
 __global__ void apply_phase_kernel(T* X, int ldx, long long sX, const double* Z, int ldz, long long sZ,
-                                   const T* ph, long long sph, int n) {
+                                   const T* ph, long long sph, int n, int cols) {
   const int z = blockIdx.z;
   X += z * sX;
   Z += z * sZ;
   ph += z * sph;
   for (int i = blockIdx.y; i < n; i += gridDim.y) {
     T p = ph[i];
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x)
       X[(size_t)i * ldx + c] = p * Z[(size_t)i * ldz + c];
   }
 }
@@ -358,9 +358,9 @@ void larft(const T* G, int ldG, long long sG, const double* tau, long long stau,
 
 template <typename T>
 void apply_phase(T* X, int ldx, long long sX, const double* Z, int ldz, long long sZ, const T* ph, long long sph,
-                 int n, int count, cudaStream_t s) {
+                 int n, int cols, int count, cudaStream_t s) {
   count_launch();
-  apply_phase_kernel<T><<<grid2d(n, n, count), 256, 0, s>>>(X, ldx, sX, Z, ldz, sZ, ph, sph, n);
+  apply_phase_kernel<T><<<grid2d(n, cols, count), 256, 0, s>>>(X, ldx, sX, Z, ldz, sZ, ph, sph, n, cols);
 }
 
 template <typename T>
@@ -424,7 +424,7 @@ void tune_pencil(T* A, int m, int count, int hermitian, cudaStream_t s) {
   template void larft<T>(const T*, int, long long, const double*, long long, int, T*, int, long long,    \
                          int, cudaStream_t);                                                            \
   template void apply_phase<T>(T*, int, long long, const double*, int, long long, const T*, long long,   \
-                               int, int, cudaStream_t);                                                 \
+                               int, int, int, cudaStream_t);                                            \
   template void mirror_lower<T>(T*, int, long long, int, int, cudaStream_t);                            \
   template void column_phase<T>(T*, int, long long, int, int, int, cudaStream_t);                      \
   template void spinor_overlap<T>(T*, long long, const T*, int, long long, int, int, cudaStream_t);         \

@@ -20,7 +20,7 @@ void larft(const T* G, int ldG, long long sG, const double* tau, long long stau,
            long long sT, int count, cudaStream_t s);
 template <typename T>
 void apply_phase(T* X, int ldx, long long sX, const double* Z, int ldz, long long sZ, const T* ph, long long sph,
-                 int n, int count, cudaStream_t s);
+                 int n, int cols, int count, cudaStream_t s);
 template <typename T>
 void mirror_lower(T* A, int lda, long long sA, int n, int count, cudaStream_t s);
 template <typename T>
@@ -71,6 +71,7 @@ size_t dc_workspace_bytes(const DcPlan* p);
 struct DcSplit {
   void* work;
   int per, S, min_half;
+  long long wait;  // bound of the product kernels' device-side waits (SM cycles, 0 = default)
 };
 size_t dc_split_item_bytes(const DcPlan* p, int min_half, int S);
 // d (m), e (m-1) per item (stride sde); Z out (m x m, ld m, stride sZ); lam out (stride sde).
@@ -90,6 +91,8 @@ template <typename T>
 void herm_part(T* dst, const T* src, long long sd, long long ss, int M, int nk, cudaStream_t s);
 template <typename T>
 void spin_block_sum(T* dst, long long sd, const T* src, long long ss, int n, int nk, cudaStream_t s);
+template <typename T>
+void spin_pair_sum(T* dst, long long sd, const T* src, long long ss, int n, int nk, cudaStream_t s);
 
 // ---- FP64-accurate GEMM from exact bf16 digit products (ozaki.cu) ----
 // Workspace bytes per batch item (a multiple of 256), and output tiles per item.
@@ -97,16 +100,26 @@ size_t ozaki_workspace_bytes(int M, int N, int K, bool cplx, int S);
 int ozaki_tiles(int M, int N, bool cplx);
 // Returns false (nothing enqueued) when the TMA tensor maps cannot be encoded.  Optional:
 // kscale (per item, stride sks) scales column k of op(A) before the product; kdev (per
-// item, device) cuts K to its value.
+// item, device) cuts K to its value; wait_cycles bounds every device-side wait (0 = 2^32
+// SM cycles); skip_copy >= 0 makes every CTA leave out that operand copy (a test hook
+// that lets the bounded waits expire).
 template <typename T>
 bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
                 int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
                 void* work, DevStatus* status, cudaStream_t s, const double* kscale = nullptr, long long sks = 0,
-                const int* kdev = nullptr);
+                const int* kdev = nullptr, long long wait_cycles = 0, long long skip_copy = -1);
 
 // ---- occupations (occ.cu) ----
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,
               double f_cut, double* occ, double* kscale, double* mu, double* e_band, int* nrho, DevStatus* st,
               int nsys, cudaStream_t s);
+// out[k * rep + r] = w[k] (w == nullptr: 1/nk) for r < rep: per-item k weights when rep
+// items (spin channels) share one k-point.
+void expand_weights(const double* w, int nk, int rep, double* out, cudaStream_t s);
+// n_rho(k) = min(n_rho(k), cols); a count above `cols` (the eigenvectors computed) sets the
+// status word st[k * st_stride] to GKS_EINVAL with the count.
+void clamp_nrho(int* nrho, int nk, int cols, DevStatus* st, int st_stride, cudaStream_t s);
+// out[t] = a[t] * b[t] for t < n.
+void mul_elem(const double* a, const double* b, double* out, long long n, cudaStream_t s);
 
 }  // namespace gks

@@ -8,6 +8,8 @@
 //   E_band = sum_k w_k g_s sum_i f_ki eps_ki.
 // Also writes kscale = g_s f (zero where f < f_cut) and n_rho(k) = #{i : f_ki >= f_cut},
 // the leading columns kept in rho (eps ascending, so f is non-increasing in i).
+#include <algorithm>
+
 #include "dense.h"
 
 namespace gks {
@@ -108,6 +110,43 @@ void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, doub
               cudaStream_t s) {
   count_launch();
   fermi_mu_kernel<<<nsys, 1024, 0, s>>>(eps, m, nk, w, gs, kT, n_elec, f_cut, occ, kscale, mu, e_band, nrho, st);
+}
+
+__global__ void expand_weights_kernel(const double* w, int nk, int rep, double* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nk * rep) return;
+  const int k = t / rep;
+  out[t] = w ? w[k] : 1.0 / nk;
+}
+
+void expand_weights(const double* w, int nk, int rep, double* out, cudaStream_t s) {
+  count_launch();
+  expand_weights_kernel<<<(nk * rep + 255) / 256, 256, 0, s>>>(w, nk, rep, out);
+}
+
+__global__ void clamp_nrho_kernel(int* nrho, int nk, int cols, DevStatus* st, int st_stride) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  if (nrho[k] > cols) {
+    set_status(st ? st + (long long)k * st_stride : nullptr, ST_EINVAL, nrho[k]);
+    nrho[k] = cols;
+  }
+}
+
+void clamp_nrho(int* nrho, int nk, int cols, DevStatus* st, int st_stride, cudaStream_t s) {
+  count_launch();
+  clamp_nrho_kernel<<<(nk + 255) / 256, 256, 0, s>>>(nrho, nk, cols, st, st_stride);
+}
+
+__global__ void mul_elem_kernel(const double* a, const double* b, double* out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = a[t] * b[t];
+}
+
+void mul_elem(const double* a, const double* b, double* out, long long n, cudaStream_t s) {
+  count_launch();
+  const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+  mul_elem_kernel<<<(int)std::max<long long>(blocks, 1), 256, 0, s>>>(a, b, out, n);
 }
 
 }  // namespace gks

@@ -192,6 +192,8 @@ struct OzArgs {
   long long sAd, sBd;       // slice strides (elements)
   long long zAd, zBd, zEa, zEb, zC;  // batch item strides of the digits, exponents and C
   const int* kdev;          // optional per-item K read on the device (logical, <= K)
+  long long wait;           // bound of every mbarrier wait, in SM clock cycles
+  long long skip_copy;      // test hook: the producer leaves out this copy (-1 = none)
 };
 
 // ------------------------------------------------------------------ tcgen05 product kernel
@@ -218,7 +220,6 @@ constexpr int TMEM_COLS = 2 * BN;                    // two FP32 accumulators
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int SMEM = STAGES * STAGE_BYTES + 1024;    // + alignment slack
-constexpr long long WAIT_CYCLES = 1ll << 32;         // about two seconds
 
 // kind::f16 instruction descriptor: FP32 accumulator, bf16 A and B, both K-major, M x N.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -250,11 +251,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase of the given parity; false on abort or timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       *abort = 1;
       return false;
     }
@@ -262,10 +263,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return true;
 }
 // Wait without watching the abort flag (draining after an abort), still bounded.
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > WAIT_CYCLES) return;
+    if (clock64() - t0 > limit) return;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -397,7 +398,8 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
             for (int kb = c0; kb < c1; kb++, q++) {
               const int stg = (int)(q % STAGES);
               const uint32_t ph = (uint32_t)((q / STAGES) & 1);
-              if (!mbar_wait(&empty[stg], ph ^ 1u, abort)) break;
+              if (!mbar_wait(&empty[stg], ph ^ 1u, abort, a.wait)) break;
+              if (q == a.skip_copy) continue;  // test hook: this stage never fills
               unsigned char* sa = ring + (size_t)stg * STAGE_BYTES;
               mbar_expect_tx(&full[stg], STAGE_BYTES);
               tma_load_2d(sa, &mapA, &full[stg], kb * BK, ya);
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
       }
       // let every issued copy land before the CTA can leave
       for (long long r = (q > STAGES ? q - STAGES : 0); r < q; r++)
-        mbar_drain(&full[r % STAGES], (uint32_t)((r / STAGES) & 1));
+        if (r != a.skip_copy) mbar_drain(&full[r % STAGES], (uint32_t)((r / STAGES) & 1), a.wait);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
           const int c1 = min(kblocks, c0 + cb);
           const int b = u & 1;
           const uint32_t uph = (uint32_t)((u >> 1) & 1);
-          if (!mbar_wait(&tempty[b], uph ^ 1u, abort)) {
+          if (!mbar_wait(&tempty[b], uph ^ 1u, abort, a.wait)) {
             ok = false;
             break;
           }
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
             for (int kb = c0; kb < c1; kb++, q++) {
               const int stg = (int)(q % STAGES);
               const uint32_t ph = (uint32_t)((q / STAGES) & 1);
-              if (!mbar_wait(&full[stg], ph, abort)) {
+              if (!mbar_wait(&full[stg], ph, abort, a.wait)) {
                 ok = false;
                 break;
               }
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
       }
       // all issued products complete before tensor memory is released
       umma_commit(&done);
-      mbar_drain(&done, 0);
+      mbar_drain(&done, 0, a.wait);
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, column half (w - 2) / 4
@@ -466,7 +468,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
       for (int c0 = 0; c0 < kblocks; c0 += cb, u++) {
         const int b = u & 1;
         const uint32_t uph = (uint32_t)((u >> 1) & 1);
-        if (!mbar_wait(&tfull[b], uph, abort)) {
+        if (!mbar_wait(&tfull[b], uph, abort, a.wait)) {
           ok = false;
           break;
         }
@@ -565,8 +567,15 @@ static bool digit_map(CUtensorMap* m, const void* base, long long rows, int Kp) 
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Digit planes of an item: the same padded shapes ozaki_gemm uses (K = 0 still takes one
+// 64-wide k block of zero digits, so that the product kernel computes C = beta C).
+static int padded_k(int K, bool cplx) {
+  const int Ke = cplx ? 2 * K : K;
+  return round_up(Ke > 0 ? Ke : 1, OZ_KSTEP);
+}
+
 size_t ozaki_workspace_bytes(int M, int N, int K, bool cplx, int S) {
-  const int Kp = round_up(cplx ? 2 * K : K, OZ_KSTEP);
+  const int Kp = padded_k(K, cplx);
   const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
   const size_t b = (size_t)S * ((size_t)Mp + Np) * Kp * 2 + sizeof(int) * ((size_t)Mp + Np) + 1024;
   return (b + 255) & ~size_t(255);
@@ -583,11 +592,10 @@ template <typename T>
 bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
                 int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
                 void* work, DevStatus* status, cudaStream_t s, const double* kscale, long long sks,
-                const int* kdev) {
+                const int* kdev, long long wait_cycles, long long skip_copy) {
   if (M <= 0 || N <= 0 || count <= 0) return true;
   const bool cplx = sizeof(T) == 16;
-  const int Ke = cplx ? 2 * K : K;
-  const int Kp = round_up(Ke > 0 ? Ke : 1, OZ_KSTEP);
+  const int Kp = padded_k(K, cplx);
   const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
   const long long zA = (long long)S * Mp * Kp, zB = (long long)S * Np * Kp;
   __nv_bfloat16* Ad = static_cast<__nv_bfloat16*>(work);
@@ -631,6 +639,8 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   oa.zEb = Np;
   oa.zC = sC;
   oa.kdev = kdev;
+  oa.wait = wait_cycles > 0 ? wait_cycles : (1ll << 32);
+  oa.skip_copy = skip_copy;
   dim3 grid(Np / OZ_BN, Mp / OZ_BM, count);
   CUtensorMap ma, mb;
   if (!digit_map(&ma, Ad, (long long)count * S * Mp, Kp) || !digit_map(&mb, Bd, (long long)count * S * Np, Kp))
@@ -643,9 +653,9 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
 
 template bool ozaki_gemm<double>(int, int, int, int, int, double, const double*, int, long long, const double*, int,
                                  long long, double, double*, int, long long, int, int, int, void*, DevStatus*,
-                                 cudaStream_t, const double*, long long, const int*);
+                                 cudaStream_t, const double*, long long, const int*, long long, long long);
 template bool ozaki_gemm<zc>(int, int, int, int, int, double, const zc*, int, long long, const zc*, int, long long,
                              double, zc*, int, long long, int, int, int, void*, DevStatus*, cudaStream_t,
-                             const double*, long long, const int*);
+                             const double*, long long, const int*, long long, long long);
 
 }  // namespace gks

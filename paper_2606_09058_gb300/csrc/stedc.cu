@@ -639,10 +639,10 @@ void dc_solve(DcPlan* p, double* d, double* e, long long sde, double* lam, doubl
           const long long iz = (long long)z0 * sin, oz = (long long)z0 * sout;
           ok = ozaki_gemm<double>(OP_N, OP_T, nd.n1, n, nd.n1, 1.0, in0 + iz + (size_t)off * m + off, m, sin,
                                   wz.W + (size_t)off * m + off, m, slam, 0.0, out0 + oz + (size_t)off * m + off, m,
-                                  sout, c, 0, sp->S, sp->work, st, s) &&
+                                  sout, c, 0, sp->S, sp->work, st, s, nullptr, 0, nullptr, sp->wait) &&
                ozaki_gemm<double>(OP_N, OP_T, nd.n2, n, nd.n2, 1.0, in0 + iz + (size_t)sft * m + sft, m, sin,
                                   wz.W + (size_t)off * m + sft, m, slam, 0.0, out0 + oz + (size_t)sft * m + off, m,
-                                  sout, c, 0, sp->S, sp->work, st, s);
+                                  sout, c, 0, sp->S, sp->work, st, s, nullptr, 0, nullptr, sp->wait);
         }
       }
       prof->end(tok, PC_OZAKI, gfl * cnt, gby * cnt);

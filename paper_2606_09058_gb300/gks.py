@@ -15,7 +15,13 @@ from . import build as _build
 
 GKS_OK, GKS_EINVAL, GKS_ENOTSPD, GKS_ENOCONV, GKS_ENOMEM, GKS_ECUDA, GKS_ETIMEOUT, GKS_ENOTIMPL = range(8)
 GKS_R64, GKS_C128 = 0, 1
-GKS_COLLINEAR, GKS_NONCOLLINEAR = 0, 1
+GKS_COLLINEAR, GKS_NONCOLLINEAR, GKS_SPIN_POLARIZED = 0, 1, 2
+GKS_FP64, GKS_MIXED_TF32, GKS_MIXED_SPLITBF16 = 0, 1, 2
+GKS_REUSE_S_FACTOR, GKS_SAVE_FOR_BACKWARD, GKS_EIGEN_ONLY = 1, 2, 4
+GKS_DEBUG_SKIP_COPY = 1
+_SPIN = {"collinear": GKS_COLLINEAR, "noncollinear": GKS_NONCOLLINEAR, "spin_polarized": GKS_SPIN_POLARIZED}
+_PREC = {"fp64": GKS_FP64, "mixed_tf32": GKS_MIXED_TF32, "mixed": GKS_MIXED_SPLITBF16,
+         "mixed_splitbf16": GKS_MIXED_SPLITBF16}
 _NAMES = {0: "GKS_OK", 1: "GKS_EINVAL", 2: "GKS_ENOTSPD", 3: "GKS_ENOCONV", 4: "GKS_ENOMEM", 5: "GKS_ECUDA",
           6: "GKS_ETIMEOUT", 7: "GKS_ENOTIMPL"}
 
@@ -31,7 +37,9 @@ class GKSError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("f_cut", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int),
-                ("gemm", ctypes.c_int), ("slices", ctypes.c_int), ("block", ctypes.c_int)]
+                ("gemm", ctypes.c_int), ("slices", ctypes.c_int), ("block", ctypes.c_int),
+                ("refine_sweeps", ctypes.c_int), ("n_ev", ctypes.c_int), ("wait_limit", ctypes.c_longlong),
+                ("autotune_cache", ctypes.c_char_p), ("debug", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -85,6 +93,8 @@ def load() -> ctypes.CDLL:
     lib.gks_solve_batched.restype = I
     lib.gks_adjoint.argtypes = [P, P, P, P, I64, I64, I, I, D, P, P, P, D, P, P]
     lib.gks_adjoint.restype = I
+    lib.gks_occupy.argtypes = [P, P, I64, I64, P, I64, I64, I, I, D, D, P, P, P, P, P]
+    lib.gks_occupy.restype = I
     lib.gks_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I]
     lib.gks_profile.restype = I
     lib.gks_launch_count.argtypes = []
@@ -122,15 +132,20 @@ class Context:
 
     def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None, f_cut: float = 1e-16,
                  profile: bool = False, graph: bool = False, gemm: str = "auto", slices: int = 0,
-                 block: int = 0):
+                 block: int = 0, precision: str = "fp64", refine_sweeps: int = 0, n_ev: int = 0,
+                 wait_limit: int = 0, autotune_cache: str | None = None, debug: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("gks needs a CUDA device")
         lib = load()
         self.device = torch.cuda.current_device() if device is None else int(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         gm = {"auto": 0, "fp64": 1, "split": 2}[gemm]
-        opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), 0, f_cut, 1 if profile else 0,
-                     1 if graph else 0, gm, int(slices), int(block))
+        self.n_ev = int(n_ev)
+        self.precision = precision
+        cache = autotune_cache.encode() if autotune_cache else None
+        opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), _PREC[precision], f_cut,
+                     1 if profile else 0, 1 if graph else 0, gm, int(slices), int(block), int(refine_sweeps),
+                     int(n_ev), int(wait_limit), cache, int(debug))
         h = ctypes.c_void_p()
         rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
         if rc:
@@ -165,43 +180,84 @@ class Context:
                      bytes=buf[i].bytes) for i in range(n)]
 
     # ------------------------------------------------------------------ full path
-    def solve_into(self, H, S, kT, n_elec, spin="collinear", kweights=None, *, eps, C, mu, rho, e_band=None,
-                   sync=True):
+    def _ncols(self, M: int) -> int:
+        return self.n_ev if 0 < self.n_ev < M else M
+
+    @staticmethod
+    def _flags(reuse_s: bool, save: bool, eigen_only: bool) -> int:
+        return ((GKS_REUSE_S_FACTOR if reuse_s else 0) | (GKS_SAVE_FOR_BACKWARD if save else 0)
+                | (GKS_EIGEN_ONLY if eigen_only else 0))
+
+    def solve_into(self, H, S, kT, n_elec, spin="collinear", kweights=None, *, eps, C, mu=None, rho=None,
+                   e_band=None, sync=True, reuse_s=False, save_for_backward=False, eigen_only=False):
         """gks_solve on caller-provided output tensors (no allocation)."""
-        nk, M = H.shape[0], H.shape[1]
-        nc = spin == "noncollinear"
-        n = S.shape[1]
+        nk = H.shape[0]
+        n = S.shape[-1]
         dt = GKS_C128 if H.is_complex() else GKS_R64
-        rc = self._lib.gks_solve(self._h, _ptr(H), _ptr(S), n, nk, dt, GKS_NONCOLLINEAR if nc else GKS_COLLINEAR,
-                                 float(kT), float(n_elec), _ptr(kweights), 0, _ptr(eps), _ptr(C), _ptr(mu), _ptr(rho),
-                                 _ptr(e_band))
+        rc = self._lib.gks_solve(self._h, _ptr(H), _ptr(S), n, nk, dt, _SPIN[spin], float(kT), float(n_elec),
+                                 _ptr(kweights), self._flags(reuse_s, save_for_backward, eigen_only), _ptr(eps),
+                                 _ptr(C), _ptr(mu), _ptr(rho), _ptr(e_band))
         self._raise(rc)
         if sync:
             self.sync()
 
     def solve(self, H: torch.Tensor, S: torch.Tensor, kT: float, n_elec: float, spin: str = "collinear",
-              kweights: torch.Tensor | None = None, sync: bool = True) -> Solution:
+              kweights: torch.Tensor | None = None, sync: bool = True, reuse_s: bool = False,
+              save_for_backward: bool = False, eigen_only: bool = False) -> Solution:
         """eps, C, mu, rho, E_band for nk pencils sharing one chemical potential.
 
-        H: (nk, M, M), S: (nk, n, n) (noncollinear: M = 2n, S the n x n overlap)."""
-        if H.dim() == 2:
+        H: (nk, M, M), S: (nk, n, n) (noncollinear: M = 2n, S the n x n overlap;
+        spin_polarized: H (nk, 2, n, n), eps (nk, 2, n), C and rho (nk, 2, n, n)).  With
+        n_ev set on the context C keeps only its leading n_ev columns."""
+        sp = spin == "spin_polarized"
+        if H.dim() == (3 if sp else 2):
             H, S = H[None], S[None]
         cd = (torch.float64, torch.complex128)
         _check_tensor(H, "H", cd)
         _check_tensor(S, "S", cd)
         if S.dtype != H.dtype:
             raise ValueError("H and S must share a dtype")
-        nk, M = H.shape[0], H.shape[1]
+        nk, M = H.shape[0], H.shape[-1]
+        lead = (nk, 2) if sp else (nk,)
         if kweights is not None:
             _check_tensor(kweights, "kweights", (torch.float64,))
         dev = H.device
-        eps = torch.empty(nk, M, dtype=torch.float64, device=dev)
-        C = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
-        rho = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
+        eps = torch.empty(*lead, M, dtype=torch.float64, device=dev)
+        C = torch.empty(*lead, M, self._ncols(M), dtype=H.dtype, device=dev)
+        rho = None if eigen_only else torch.empty(*lead, M, M, dtype=H.dtype, device=dev)
+        mu = None if eigen_only else torch.empty(1, dtype=torch.float64, device=dev)
+        eb = None if eigen_only else torch.empty(1, dtype=torch.float64, device=dev)
+        self.solve_into(H, S, kT, n_elec, spin, kweights, eps=eps, C=C, mu=mu, rho=rho, e_band=eb, sync=sync,
+                        reuse_s=reuse_s, save_for_backward=save_for_backward, eigen_only=eigen_only)
+        return Solution(eps, C, mu, rho, eb)
+
+    def occupy(self, eps_all: torch.Tensor, C: torch.Tensor | None, kT: float, n_elec: float, k0: int = 0,
+               spin: str = "collinear", kweights_all: torch.Tensor | None = None, rho: bool = True,
+               edm: bool = False, sync: bool = True):
+        """gks_occupy: mu shared by every k-point of eps_all (nk_all, M) (spin_polarized:
+        (nk_all, 2, n)), then the density matrix and optionally the energy-density matrix
+        of the local k-points k0 .. k0 + nk - 1 whose eigenvectors are C.  Returns
+        (mu, rho, e_band, edm)."""
+        _check_tensor(eps_all, "eps_all", (torch.float64,))
+        sp = spin == "spin_polarized"
+        nk_all = eps_all.shape[0]
+        M = eps_all.shape[-1]
+        n = M // 2 if spin == "noncollinear" else M
+        dev = eps_all.device
+        nk = 0 if C is None else C.shape[0]
+        lead = (nk, 2) if sp else (nk,)
+        dt = torch.complex128 if (C is not None and C.is_complex()) else torch.float64
         mu = torch.empty(1, dtype=torch.float64, device=dev)
         eb = torch.empty(1, dtype=torch.float64, device=dev)
-        self.solve_into(H, S, kT, n_elec, spin, kweights, eps=eps, C=C, mu=mu, rho=rho, e_band=eb, sync=sync)
-        return Solution(eps, C, mu, rho, eb)
+        r = torch.empty(*lead, M, M, dtype=dt, device=dev) if (rho and nk) else None
+        e = torch.empty(*lead, M, M, dtype=dt, device=dev) if (edm and nk) else None
+        rc = self._lib.gks_occupy(self._h, _ptr(eps_all), nk_all, int(k0), _ptr(C), n, nk,
+                                  GKS_C128 if dt == torch.complex128 else GKS_R64, _SPIN[spin], float(kT),
+                                  float(n_elec), _ptr(kweights_all), _ptr(mu), _ptr(r), _ptr(eb), _ptr(e))
+        self._raise(rc)
+        if sync:
+            self.sync()
+        return mu, r, eb, e
 
     # ------------------------------------------------------------------ batch
     def solve_batched(self, problems, nstreams: int = 8, sync: bool = True, out: list | None = None) -> list:
@@ -219,12 +275,13 @@ class Context:
             nk, M = H.shape[0], H.shape[1]
             dev = H.device
             sol = out[b] if out is not None else Solution(
-                torch.empty(nk, M, dtype=torch.float64, device=dev), torch.empty(nk, M, M, dtype=H.dtype, device=dev),
+                torch.empty(nk, M, dtype=torch.float64, device=dev),
+                torch.empty(nk, M, self._ncols(M), dtype=H.dtype, device=dev),
                 torch.empty(1, dtype=torch.float64, device=dev), torch.empty(nk, M, M, dtype=H.dtype, device=dev),
                 torch.empty(1, dtype=torch.float64, device=dev))
             kw = pr.get("kweights")
-            arr[b] = _Problem(H.data_ptr(), S.data_ptr(), S.shape[1], nk, GKS_C128 if H.is_complex() else GKS_R64,
-                              GKS_NONCOLLINEAR if spin == "noncollinear" else GKS_COLLINEAR, float(pr["kT"]),
+            arr[b] = _Problem(H.data_ptr(), S.data_ptr(), S.shape[-1], nk, GKS_C128 if H.is_complex() else GKS_R64,
+                              _SPIN[spin], float(pr["kT"]),
                               float(pr["n_elec"]), kw.data_ptr() if kw is not None else None, sol.eps.data_ptr(),
                               sol.C.data_ptr(), sol.mu.data_ptr(), sol.rho.data_ptr(), sol.e_band.data_ptr())
             sols.append(sol)
@@ -235,24 +292,32 @@ class Context:
         return sols
 
     # ------------------------------------------------------------------ adjoint
-    def adjoint(self, sol: Solution, S: torch.Tensor, kT: float, spin: str = "collinear", kweights=None,
+    def adjoint(self, sol: Solution | None, S: torch.Tensor, kT: float, spin: str = "collinear", kweights=None,
                 rho_bar: torch.Tensor | None = None, eps_bar: torch.Tensor | None = None,
-                e_band_bar: float = 0.0, sync: bool = True):
+                e_band_bar: float = 0.0, sync: bool = True, complex_: bool | None = None):
         """Gradients (H_bar, S_bar) of L(rho, eps, E_band) through a previous solve (n_elec
-        fixed): dL = Re tr(H_bar^H dH) + Re tr(S_bar^H dS) for Hermitian dH, dS."""
-        C, eps, mu = sol.C, sol.eps, sol.mu
-        nk, M = C.shape[0], C.shape[1]
+        fixed): dL = Re tr(H_bar^H dH) + Re tr(S_bar^H dS) for Hermitian dH, dS.  sol = None
+        uses the eigenpairs the context kept from its last solve with save_for_backward."""
         n = S.shape[-1]
-        nc = spin == "noncollinear"
+        nk = S.shape[0] if S.dim() == 3 else 1
+        sp = spin == "spin_polarized"
+        M = 2 * n if spin == "noncollinear" else n
+        if sol is not None:
+            C, eps, mu = sol.C, sol.eps, sol.mu
+            dt = C.dtype
+        else:
+            C = eps = mu = None
+            dt = S.dtype if complex_ is None else (torch.complex128 if complex_ else torch.float64)
         for t, nm in ((rho_bar, "rho_bar"), (eps_bar, "eps_bar")):
             if t is not None:
                 _check_tensor(t, nm, (torch.float64, torch.complex128))
-        Hb = torch.empty(nk, M, M, dtype=C.dtype, device=C.device)
-        Sb = torch.empty(nk, n, n, dtype=C.dtype, device=C.device)
+        lead = (nk, 2) if sp else (nk,)
+        Hb = torch.empty(*lead, M, M, dtype=dt, device=S.device)
+        Sb = torch.empty(nk, n, n, dtype=dt, device=S.device)
         rc = self._lib.gks_adjoint(self._h, _ptr(C), _ptr(eps), _ptr(mu), n, nk,
-                                   GKS_C128 if C.is_complex() else GKS_R64,
-                                   GKS_NONCOLLINEAR if nc else GKS_COLLINEAR, float(kT), _ptr(kweights),
-                                   _ptr(rho_bar), _ptr(eps_bar), float(e_band_bar), _ptr(Hb), _ptr(Sb))
+                                   GKS_C128 if dt == torch.complex128 else GKS_R64, _SPIN[spin], float(kT),
+                                   _ptr(kweights), _ptr(rho_bar), _ptr(eps_bar), float(e_band_bar), _ptr(Hb),
+                                   _ptr(Sb))
         self._raise(rc)
         if sync:
             self.sync()
@@ -367,10 +432,16 @@ class GKSSolve(torch.autograd.Function):
 
     Forward runs gks_solve; backward runs gks_adjoint (n_elec fixed).  H and S must be
     Hermitian (the solver reads their lower triangles); the gradients returned are the
-    Hermitian ones, i.e. those of a loss evaluated on Hermitian H and S.  With
-    recompute=True the eigenvectors are not kept between forward and backward (nk M^2
-    elements): backward solves the saved H, S again (the solve is deterministic, so it
-    reproduces the forward's C, eps and mu) and then runs the adjoint."""
+    Hermitian ones, i.e. those of a loss evaluated on Hermitian H and S.
+
+    recompute=True keeps no eigenvectors between forward and backward: backward solves the
+    saved H, S again and then runs the adjoint.  Cost: one more full solve in backward.
+    Memory: the nk M^2 elements of C are not held, but H (the same element count) is; the
+    saving is real only when the caller keeps H alive anyway (it usually does, as the
+    graph input).  The solve is deterministic for a fixed outer width, so the second solve
+    reproduces the forward's C, eps and mu bit for bit; the width in effect at forward is
+    recorded, and backward raises if it has changed in between (a gks_tune or tune_set of
+    that shape class)."""
 
     @staticmethod
     def forward(ctx, H, S, kT, n_elec, spin="collinear", kweights=None, recompute=False):
@@ -380,6 +451,7 @@ class GKSSolve(torch.autograd.Function):
         sol = c.solve(Hb, Sb, kT, n_elec, spin, kweights)
         if recompute:
             ctx.save_for_backward(Hb, Sb)
+            ctx.width = c.tune_get(Sb.shape[-1], Hb.is_complex(), spin)
         else:
             ctx.save_for_backward(sol.C, sol.eps, sol.mu, Sb)
         ctx.recompute = bool(recompute)
@@ -393,6 +465,9 @@ class GKSSolve(torch.autograd.Function):
         if ctx.recompute:
             Hb, Sb = ctx.saved_tensors
             c = context(Hb.device.index)
+            if c.tune_get(Sb.shape[-1], Hb.is_complex(), ctx.spin) != ctx.width:
+                raise RuntimeError("GKSSolve(recompute=True): the outer block width of this shape class changed "
+                                   "between forward and backward, so the recomputed eigenvectors would differ")
             sol = c.solve(Hb, Sb, ctx.kT, ctx.n_elec, ctx.spin, ctx.kweights)
         else:
             C, eps, mu, Sb = ctx.saved_tensors

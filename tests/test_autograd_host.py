@@ -10,6 +10,10 @@ class _FakeContext:
     def __init__(self):
         self.solves = []
         self.adjoints = []
+        self.width = 256
+
+    def tune_get(self, n, complex_=False, spin="collinear"):
+        return self.width
 
     def solve(self, H, S, kT, n_elec, spin="collinear", kweights=None):
         self.solves.append((H.data_ptr(), S.data_ptr(), kT, n_elec, spin, kweights))
@@ -48,3 +52,16 @@ def test_recompute_solves_again_with_the_same_inputs(monkeypatch):
     assert torch.equal(fake.adjoints[0][0], torch.eye(4, dtype=torch.float64)[None] * 2.0)
     assert torch.equal(gH, torch.full((1, 4, 4), 3.0, dtype=torch.float64))
     assert torch.equal(gS, torch.full((1, 4, 4), 5.0, dtype=torch.float64))
+
+
+def test_recompute_refuses_a_changed_width(monkeypatch):
+    """A tuned width set between forward and backward would change the recomputed C."""
+    import pytest
+    fake = _FakeContext()
+    monkeypatch.setattr(gks, "context", lambda device=None: fake)
+    H = torch.randn(1, 4, 4, dtype=torch.float64, requires_grad=True)
+    S = torch.randn(1, 4, 4, dtype=torch.float64, requires_grad=True)
+    eps, rho, e_band, mu = gks.GKSSolve.apply(H, S, 0.1, 2.0, "collinear", None, True)
+    fake.width = 512
+    with pytest.raises(RuntimeError, match="width"):
+        rho.sum().backward()
