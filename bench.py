@@ -41,13 +41,18 @@ WORKLOADS = {
     "uneven48": dict(desc="48 independent Si clusters of 16-160 atoms (N=208-2080), the first 12 noncollinear "
                           "(2N up to 4160, complex128), the rest real; one batched launch sequence", tiling=None),
 }
-# FP64 pipe: nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock, i.e. 3.97 flops per
-# clock per SM over 152 SMs; the peak of a run scales with the SM clock sampled during it.
-FP64_FLOPS_PER_CLK_SM = 1.25e12 / (152 * 2070e6)
 
 
-def fp64_peak_tflops(sm_mhz):
-    return FP64_FLOPS_PER_CLK_SM * 152 * (sm_mhz or 2070.0) * 1e6 / 1e12
+def measured_fp64_peak(ctx, device):
+    """The FP64 FMA pipe's throughput measured by the library's probe (gks_measure_peak),
+    with the SM clock sampled while it ran; the FP64 roofline of a kernel timed at another
+    clock scales it by the ratio of the clocks."""
+    clk = ClockSampler(device)
+    clk.start()
+    dfma = ctx.measure_peak("dfma")
+    dmma = ctx.measure_peak("dmma")
+    c = clk.stop()
+    return {"dfma_tflops": dfma, "dmma_tflops": dmma, "sm_mhz": c["sm_mhz"]}
 
 
 def nominal_flops(M: int, complex_: bool, nrho) -> float:
@@ -126,71 +131,108 @@ class ClockSampler:
 # ------------------------------------------------------------------ CPU oracle leg
 
 SAMPLE_OF = {
-    # the same construction at 64 atoms, timed on one pencil
-    "kbatch512": ("periodic (2,2,2) cells, k-point 0", "periodic", (2, 2, 2)),
-    "kbatch64": ("periodic (2,2,2) cells, k-point 0", "periodic", (2, 2, 2)),
+    # one pencil of the same construction, sized for 10-30 s of the oracle on the host cores
+    "kbatch512": ("216-atom (3,3,3) supercell, k-point 0 of the 2x2x2 mesh", "periodic", (3, 3, 3)),
+    "kbatch64": ("64-atom (2,2,2) supercell, k-point 0", "periodic", (2, 2, 2)),
     "gamma64": ("the full 64-atom cluster", "cluster", (2, 2, 2)),
-    "adjoint216": ("64-atom (2,2,2) cluster", "cluster", (2, 2, 2)),
-    "nc384": ("16-atom (2,1,1) noncollinear cluster", "nc", (2, 1, 1)),
-    "uneven48": ("the full 64-atom (2,2,2) real cluster", "cluster", (2, 2, 2)),
+    "adjoint216": ("the full 216-atom (3,3,3) cluster", "cluster", (3, 3, 3)),
+    "nc384": ("64-atom (2,2,1) noncollinear cluster", "nc", (2, 2, 1)),
+    "uneven48": ("a 128-atom (4,2,2) real cluster of the batch's construction", "cluster", (4, 2, 2)),
 }
 
 
-def oracle_sample(workload: str, seconds_cap: float = 600.0) -> dict:
-    """Time the CPU oracle (one thread) on one pencil of the same construction at a size
-    it finishes in seconds; returns the nominal flops and seconds of that solve."""
-    desc, kind, tiling = SAMPLE_OF[workload]
-    code = f"""
-import sys, time, json
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OracleSampler:
+    """The CPU oracle on one pencil of the workload's construction, in a child process
+    (no CUDA) using every host core of the affinity mask; the pencil is built once."""
+
+    def __init__(self, workload: str, seconds_cap: float = 900.0):
+        self.workload = workload
+        self.cap = seconds_cap
+        self.cores = host_cores()
+        self.dir = tempfile.mkdtemp(prefix="gks_oracle_sample_")
+        desc, kind, tiling = SAMPLE_OF[workload]
+        self.desc = desc
+        code = f"""
+import sys
 sys.path.insert(0, {ROOT!r})
-import numpy as np, torch
-torch.set_num_threads(1)
-from oracle import oracle as O
+import numpy as np
 from paper_2606_09058_gb300 import inputs as I
 kind, tiling = {kind!r}, {tiling!r}
 if kind == "periodic":
-    p = I.periodic(tiling, 1, 0.01)
+    p = I.periodic(tiling, 1, 0.01, 4.0 * 8 * tiling[0] * tiling[1] * tiling[2], kidx=[0])
 elif kind == "nc":
     p = I.noncollinear(tiling, 2, 0.01)
 else:
     p = I.collinear_gamma(tiling, 0, 0.01)
-H = p.H[:1].numpy(); S = p.S[:1].numpy()
+np.save({self.dir!r} + "/H.npy", p.H[:1].numpy()); np.save({self.dir!r} + "/S.npy", p.S[:1].numpy())
+np.save({self.dir!r} + "/meta.npy", np.array([p.kT, p.n_elec, 1.0 if p.spin == "noncollinear" else 0.0]))
+"""
+        self._run(code)
+
+    def _env(self):
+        n = str(self.cores)
+        return dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n, CUDA_VISIBLE_DEVICES="")
+
+    def _run(self, code):
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=self._env(),
+                           timeout=self.cap)
+        if r.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+        return r.stdout
+
+    def run(self) -> dict:
+        code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import oracle as O
+d = {self.dir!r}
+H = np.load(d + "/H.npy"); S = np.load(d + "/S.npy"); kT, ne, nc = np.load(d + "/meta.npy")
 t = time.perf_counter()
-r = O.solve(H, S, p.kT, p.n_elec, p.spin)
+r = O.solve(H, S, kT, ne, "noncollinear" if nc else "collinear")
 dt = time.perf_counter() - t
 M = H.shape[1]; cplx = bool(np.iscomplexobj(H))
 fl = (36.0 if cplx else 9.0) * M ** 3 + (4.0 if cplx else 1.0) * M * M * float(r.n_rho[0])
 print(json.dumps(dict(seconds=dt, flops=fl, n=M, complex=cplx)))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=seconds_cap)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    res = json.loads(r.stdout.strip().splitlines()[-1])
-    res["desc"] = desc
-    return res
+        res = json.loads(self._run(code).strip().splitlines()[-1])
+        res["desc"] = self.desc
+        res["cores"] = self.cores
+        return res
+
+
+def oracle_sample(workload: str, seconds_cap: float = 900.0) -> dict:
+    return OracleSampler(workload, seconds_cap).run()
 
 
 def _sample_text(workload, smp):
     return (f"one {smp['n']}x{smp['n']} {'complex' if smp['complex'] else 'real'} pencil of the same construction "
-            f"({smp['desc']}) solved by the single-threaded unblocked FP64 oracle in {smp['seconds']:.1f} s, "
-            f"rate of the nominal FP64 count")
+            f"({smp['desc']}) solved by the plain FP64 oracle (OpenMP, {smp['cores']} host cores) in "
+            f"{smp['seconds']:.1f} s; rate of the nominal FP64 count")
 
 
 def reference_arm(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
+    sampler = OracleSampler(args.workload)
     samples = []
     for _ in range(args.warmup + args.steps):
-        samples.append(oracle_sample(args.workload))
+        samples.append(sampler.run())
     timed = samples[args.warmup:]
     secs = sum(s["seconds"] for s in timed)
     fl = sum(s["flops"] for s in timed)
     val = fl / secs / 1e12
     s0 = timed[0]
-    cpu = {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": _sample_text(args.workload, s0)}
+    cpu = {"value": val, "unit": "TFLOP/s", "cores": s0["cores"], "kind": "oracle",
+           "sample": _sample_text(args.workload, s0)}
     line = {"impl": "reference", "metric": "GKS eigensolve+rho throughput (nominal FP64 TFLOP/s)", "value": val,
             "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / len(timed), "higher_is_better": True, "scaling": "weak",
@@ -349,10 +391,11 @@ def run_uneven(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
             smp = oracle_sample(args.workload)
-            cpu = {"value": smp["flops"] / smp["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                   "sample": _sample_text(args.workload, smp)}
+            cpu = {"value": smp["flops"] / smp["seconds"] / 1e12, "unit": "TFLOP/s", "cores": smp["cores"],
+                   "kind": "oracle", "sample": _sample_text(args.workload, smp)}
         except Exception as ex:
-            cpu = {"value": None, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+            cpu = {"value": None, "unit": "TFLOP/s", "cores": host_cores(), "kind": "oracle",
+                   "sample": f"failed: {ex}"[:300]}
     if rank == 0:
         line = {"metric": "GKS eigensolve+rho throughput (nominal FP64 TFLOP/s)", "value": value, "unit": "TFLOP/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -372,6 +415,62 @@ def run_uneven(args):
     return 0
 
 
+def accuracy_report(workload, prob, H, S, eps, C, mu, nrho):
+    """Accuracy of the timed step's results: eigenvalues of every k-point against the oracle's
+    (tests/golden/kbatch512_oracle.npz holds k-points 0..3; k and -k share a spectrum), over
+    the occupied states (f >= 1e-16) and over all states, against the gate max(1e-10, 8 beta_i);
+    scaled S-orthonormality and backward error of every column of k-point 0 (FP64 products
+    in torch); Tr(rho S) is checked by the tests.  None for workloads without stored results."""
+    import numpy as np
+    import torch
+    out = {}
+    gpath = os.path.join(ROOT, "tests", "golden", f"{workload}_oracle.npz")
+    if workload == "kbatch512" and os.path.exists(gpath):
+        g = np.load(gpath)
+        e = eps.cpu().numpy()
+        worst_occ = worst_all = ratio = 0.0
+        nbig = 0
+        for k in range(e.shape[0]):
+            r = k if k < 4 else 7 - k
+            if f"eps{r}" not in g.files:
+                continue
+            d = np.abs(e[k] - g[f"eps{r}"])
+            gate = np.maximum(1e-10, 8 * g[f"beta{r}"])
+            worst_occ = max(worst_occ, float(d[:nrho[k]].max()))
+            worst_all = max(worst_all, float(d.max()))
+            ratio = max(ratio, float((d / gate).max()))
+            nbig += int(np.sum(g[f"beta{r}"][:nrho[k]] > 1e-11))
+        out.update({"max_abs_deps_occupied": worst_occ, "max_abs_deps_all": worst_all,
+                    "max_deps_over_gate": ratio,
+                    "gate": "max(1e-10, 8 beta_i), beta_i = u (|H| + |eps_i| |S|) |c_i|^2",
+                    "occupied_states_with_beta_above_1e-11": nbig,
+                    "reference": "oracle eigenvalues of the same pencils (tests/golden/kbatch512_oracle.npz)"})
+    if C.shape[1] != C.shape[2]:
+        return out or None
+    k = 0
+    Hk, Sk, Ck, ek = H[k], S[k], C[k], eps[k]
+    def norm2(A, iters=100):
+        v = torch.ones(A.shape[0], dtype=A.dtype, device=A.device) / A.shape[0] ** 0.5
+        lam = 0.0
+        for _ in range(iters):
+            w = A @ v
+            lam = float(torch.linalg.norm(w))
+            v = w / lam
+        return lam
+    nh, ns = norm2(Hk), norm2(Sk)
+    cn = torch.linalg.norm(Ck, dim=0)
+    SC = Sk @ Ck
+    G = Ck.conj().T @ SC
+    G.diagonal().sub_(1.0)
+    out["orthonormality_scaled_k0"] = float((G.abs() / torch.outer(cn, cn)).max()) / ns
+    del G
+    R = Hk @ Ck - SC * ek[None, :]
+    out["backward_error_scaled_k0"] = float((torch.linalg.norm(R, dim=0) / ((nh + ek.abs() * ns) * cn)).max())
+    out["orthonormality_gate"] = 1e-12 * Ck.shape[0] ** 0.5
+    del R, SC
+    return out
+
+
 def make_problem(workload: str, device: str):
     from paper_2606_09058_gb300 import inputs as I
     return I.workload(workload, device=device)
@@ -386,6 +485,7 @@ def main():
     ap.add_argument("--workload", default="kbatch512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--profile-json", default=None, help="write the per-class/per-stage event profile here")
     ap.add_argument("--no-tune", action="store_true", help="uneven48: skip the width tuner")
     ap.add_argument("--no-graph", action="store_true", help="uneven48: eager launches instead of graph replay")
@@ -444,6 +544,7 @@ def main():
     for _ in range(args.warmup):
         step(H, S, sync=True)
     ctx.profile()  # drop warm-up records
+    peak = measured_fp64_peak(ctx, local)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -485,14 +586,17 @@ def main():
     if dom:
         per = args.steps
         achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12 if dom["ms"] > 0 else 0.0
-        peak = fp64_peak_tflops(clk["sm_mhz"])
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
+        scale = (clk["sm_mhz"] / peak["sm_mhz"]) if (clk["sm_mhz"] and peak["sm_mhz"]) else 1.0
+        pk = peak["dfma_tflops"] * scale
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk,
                 "traffic": (TRAFFIC_RATIO[dom["name"]] * dom["bytes"] / dom["groups"]
                             if dom["name"] in TRAFFIC_RATIO and dom.get("groups") else None),
                 "kernel": dom["name"],
                 "kernel_ms_per_step": dom["ms"] / per, "kernel_share": dom["ms"] / (ms * per),
-                "peak_basis": "FP64 DFMA pipe, nominal 1.25 TFLOP/s at 2070 MHz scaled to the sampled SM clock"}
+                "peak_basis": (f"FP64 DFMA pipe measured by gks_measure_peak in this run: {peak['dfma_tflops']:.3f} "
+                               f"TFLOP/s at {peak['sm_mhz']} MHz, scaled to the timed region's median SM clock "
+                               f"(DMMA measured {peak['dmma_tflops']:.3f})")}
     stages = {p["name"][6:]: round(p["ms"] / args.steps, 3) for p in prof if p["name"].startswith("stage:")}
     classes = {p["name"]: {"ms": round(p["ms"] / args.steps, 3),
                            "tflops": round(p["flops"] / (p["ms"] / 1e3) / 1e12, 4) if p["ms"] > 0 and p["flops"] > 0
@@ -511,6 +615,8 @@ def main():
         eps_out = torch.empty(eps.shape, dtype=eps.dtype, pin_memory=True)
         mu_out = torch.empty(1, dtype=torch.float64, pin_memory=True)
         eb_out = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        C_out = torch.empty(C.shape, dtype=C.dtype, pin_memory=True)
+        rho_out = torch.empty(rho.shape, dtype=rho.dtype, pin_memory=True)
         Hd = torch.empty_like(H)
         Sd = torch.empty_like(S)
         torch.cuda.synchronize()
@@ -526,6 +632,8 @@ def main():
             eps_out.copy_(eps, non_blocking=True)
             mu_out.copy_(mu, non_blocking=True)
             eb_out.copy_(eb, non_blocking=True)
+            C_out.copy_(C, non_blocking=True)
+            rho_out.copy_(rho, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
         ctx.sync()
@@ -533,19 +641,25 @@ def main():
         ems = max_over_ranks(f0.elapsed_time(f1) / args.steps, dev)
         e2e = {"value": fl_step * world / (ems / 1e3) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(Hh.numel() * Hh.element_size() + Sh.numel() * Sh.element_size()),
-               "d2h_bytes_per_step": int(eps_out.numel() * 8 + 16), "ms_per_step": ems}
-        del Hh, Sh, Hd, Sd
+               "d2h_bytes_per_step": int(eps_out.numel() * 8 + 16 + C_out.numel() * C_out.element_size()
+                                         + rho_out.numel() * rho_out.element_size()),
+               "ms_per_step": ems, "outputs_copied": "eps, mu, E_band, C, rho to pinned host memory"}
+        del Hh, Sh, Hd, Sd, C_out, rho_out
 
+    accuracy = None
+    if rank == 0 and not args.no_accuracy:
+        accuracy = accuracy_report(args.workload, prob, H, S, eps, C, mu_h, nrho)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
             del C, rho
             torch.cuda.empty_cache()
             smp = oracle_sample(args.workload)
-            cpu = {"value": smp["flops"] / smp["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                   "sample": _sample_text(args.workload, smp)}
+            cpu = {"value": smp["flops"] / smp["seconds"] / 1e12, "unit": "TFLOP/s", "cores": smp["cores"],
+                   "kind": "oracle", "sample": _sample_text(args.workload, smp)}
         except Exception as ex:  # the CPU leg must not hide the GPU result
-            cpu = {"value": None, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+            cpu = {"value": None, "unit": "TFLOP/s", "cores": host_cores(), "kind": "oracle",
+                   "sample": f"failed: {ex}"[:300]}
 
     if rank == 0:
         line = {"metric": "GKS eigensolve+rho throughput (nominal FP64 TFLOP/s)", "value": value, "unit": "TFLOP/s",
@@ -560,6 +674,7 @@ def main():
                            "nominal_tflop_per_step": fl_step / 1e12, "n_rho": nrho},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+                "accuracy": accuracy, "fp64_peaks_measured": peak,
                 "stages_ms": stages, "kernels": classes}
         print(json.dumps(line), flush=True)
     if world > 1:

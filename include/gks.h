@@ -247,6 +247,14 @@ int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max);
 /* Number of kernel launches this library has issued in the calling process. */
 long long gks_launch_count(void);
 
+/* Measured throughput of an FP64 unit of the context's device, the denominator of the
+ * FP64 rooflines (the paper quotes the H100's FP64 peaks, Sec. 6; this GPU's are
+ * measured, not taken from a datasheet): which = 0 DFMA (fma.rn.f64, the FP64 pipe the
+ * matrix-vector steps and the FP64 product kernel use), 1 DMMA (mma.sync m8n8k4 f64).
+ * Runs about 0.3 s of probes on the context's stream (every SM, independent register
+ * chains) and writes the best rate in TFLOP/s to *tflops (host).  Synchronizes. */
+gks_status gks_measure_peak(gks_ctx* ctx, int which, double* tflops);
+
 /* C = alpha op(A) op(B) + beta C for one product (row-major, op 0 = N, 1 = T, 2 = conjugate
  * transpose; op(A) is M x K, op(B) K x N).  mode 1: the FP64 pipe; mode 2: exact split-
  * bf16 tensor-core products with FP64 accumulation (the path large products of gks_solve

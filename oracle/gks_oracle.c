@@ -10,6 +10,12 @@
  * makes the off-diagonal real; (4) implicit QL with Wilkinson shift on the real
  * tridiagonal with rotation accumulation; (5) ascending sort; (6) X = Q D Z and
  * C = L^-H X by explicit back substitution.
+ *
+ * OpenMP runs the independent loops of these steps in parallel (rows of a rank-1/rank-2
+ * update, rows of a matrix-vector product, columns of a substitution, rows receiving a
+ * sweep's rotations); every matrix element still receives the same operations, with the
+ * same operands, in the same order as in the sequential loops, so the results do not
+ * depend on the thread count.
  */
 #include <complex.h>
 #include <math.h>
@@ -25,7 +31,16 @@
  * block [p, q]; the shift is the eigenvalue of the leading 2 x 2 of the block that is
  * closer to d[p]; the bulge is chased from the bottom of the block to the top.
  * Returns 0, or 1 + p if the block starting at p needs more than 60 sweeps. */
+static int tridiag_ql_(int n, double *d, double *e, double *Z, double *rc_, double *rs_);
 static int tridiag_ql(int n, double *d, double *e, double *Z) {
+  double *rc_ = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double *rs_ = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  int r = tridiag_ql_(n, d, e, Z, rc_, rs_);
+  free(rc_);
+  free(rs_);
+  return r;
+}
+static int tridiag_ql_(int n, double *d, double *e, double *Z, double *rc_, double *rs_) {
   const double eps = 2.220446049250313e-16;
   for (int p = 0; p < n; p++) {
     int sweeps = 0;
@@ -42,7 +57,8 @@ static int tridiag_ql(int n, double *d, double *e, double *Z) {
       double delta = 0.5 * (d[p + 1] - d[p]);
       double r = hypot(delta, e[p]);
       double shift = d[p] - e[p] * e[p] / (delta + (delta >= 0.0 ? r : -r));
-      /* implicit QL sweep: rotations in planes (k-1, k), k = q .. p+1 */
+      /* implicit QL sweep: rotations in planes (k-1, k), k = q .. p+1; the rotations only
+       * depend on d and e, so they are recorded and applied to the rows of Z afterwards */
       double x = d[q] - shift;
       double z = e[q - 1];
       for (int k = q; k > p; k--) {
@@ -55,15 +71,22 @@ static int tridiag_ql(int n, double *d, double *e, double *Z) {
         d[k - 1] = a * c * c - 2.0 * b * c * s + cc * s * s;
         d[k] = a * s * s + 2.0 * b * c * s + cc * c * c;
         e[k - 1] = c * s * (a - cc) + b * (c * c - s * s);
-        for (int row = 0; row < n; row++) {     /* Z <- Z R on columns (k-1, k) */
-          double zl = Z[(size_t)row * n + (k - 1)], zr = Z[(size_t)row * n + k];
-          Z[(size_t)row * n + (k - 1)] = c * zl - s * zr;
-          Z[(size_t)row * n + k] = s * zl + c * zr;
-        }
+        rc_[k] = c;
+        rs_[k] = s;
         if (k - 1 > p) {                        /* new bulge at (k-2, k) */
           x = e[k - 1];
           z = s * e[k - 2];
           e[k - 2] = c * e[k - 2];
+        }
+      }
+      /* Z <- Z R_q R_{q-1} ... R_{p+1}: each row takes the sweep's rotations in order */
+#pragma omp parallel for schedule(static) if ((size_t)n * (q - p) > 20000)
+      for (int row = 0; row < n; row++) {
+        double *zr_ = Z + (size_t)row * n;
+        for (int k = q; k > p; k--) {
+          double zl = zr_[k - 1], zk = zr_[k];
+          zr_[k - 1] = rc_[k] * zl - rs_[k] * zk;
+          zr_[k] = rs_[k] * zl + rc_[k] * zk;
         }
       }
     }
@@ -82,15 +105,19 @@ static void sort_ascending(int n, double *d, double *Z, int *perm) {
     perm[j + 1] = pi;
   }
   double *dd = (double *)malloc(sizeof(double) * n);
-  double *row = (double *)malloc(sizeof(double) * n);
   for (int i = 0; i < n; i++) dd[i] = d[perm[i]];
   memcpy(d, dd, sizeof(double) * n);
-  for (int r = 0; r < n; r++) {
-    for (int c = 0; c < n; c++) row[c] = Z[(size_t)r * n + perm[c]];
-    memcpy(Z + (size_t)r * n, row, sizeof(double) * n);
+#pragma omp parallel
+  {
+    double *row = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+#pragma omp for schedule(static)
+    for (int r = 0; r < n; r++) {
+      for (int c = 0; c < n; c++) row[c] = Z[(size_t)r * n + perm[c]];
+      memcpy(Z + (size_t)r * n, row, sizeof(double) * n);
+    }
+    free(row);
   }
   free(dd);
-  free(row);
 }
 
 int oracle_tridiag_eig(int n, double *d, double *e, double *Z) {

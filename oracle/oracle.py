@@ -42,13 +42,13 @@ U_ROUND = 2.0 ** -53
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle (gcc, no architecture-specific flags)."""
+    """Compile the C oracle (gcc with OpenMP, no architecture-specific flags)."""
     src = os.path.join(_HERE, "gks_oracle.c")
     inc = os.path.join(_HERE, "oracle_core.inc")
     newest = max(os.path.getmtime(src), os.path.getmtime(inc))
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -359,6 +359,15 @@ def density_matrix(C: np.ndarray, occ: np.ndarray, gs: float, f_cut: float = F_C
     return (Ck * (gs * occ[keep])[None, :]) @ Ck.conj().T
 
 
+def energy_density_matrix(C: np.ndarray, occ: np.ndarray, eps: np.ndarray, gs: float, f_cut: float = F_CUT):
+    """E = C diag(g_s f eps) C^H over the columns with f >= f_cut: the energy-density matrix
+    that accompanies rho (paper Sec. 3.1 Part 4, needed for forces); tr(E S) = E_band per k
+    before the k weight."""
+    keep = occ >= f_cut
+    Ck = C[:, keep]
+    return (Ck * (gs * occ[keep] * eps[keep])[None, :]) @ Ck.conj().T
+
+
 @dataclass
 class Result:
     eps: np.ndarray        # (nk, M)
@@ -386,6 +395,8 @@ def solve(H, S, kT: float, n_elec: float, spin: str = "collinear", kweights=None
     H: (nk, M, M); S: (nk, N, N) with M = N (collinear) or 2N (noncollinear)."""
     H = np.asarray(H)
     S = np.asarray(S)
+    if spin == "spin_polarized":
+        return _solve_spin_polarized(H, S, kT, n_elec, kweights, f_cut)
     if H.ndim == 2:
         H = H[None]
         S = S[None]
@@ -406,13 +417,56 @@ def solve(H, S, kT: float, n_elec: float, spin: str = "collinear", kweights=None
     return Result(eps, C, mu, occ, rho, e_band, n_rho)
 
 
+def _solve_spin_polarized(H, S, kT, n_elec, kweights, f_cut):
+    """Spin-polarized collinear run (paper Sec. 2, one Kohn-Sham problem per spin channel):
+    H (nk, 2, N, N) holds the up and down channels of each k-point, S (nk, N, N) is shared by
+    both.  Each channel is solved on its own; one mu for all k-points and both channels,
+    g_s = 1, the weight w_k applying to both channels.  Arrays keep the channel axis after k."""
+    if H.ndim == 3:
+        H = H[None]
+        S = S[None]
+    nk, _, N, _ = H.shape
+    w = np.full(nk, 1.0 / nk) if kweights is None else np.asarray(kweights, float)
+    dt = np.complex128 if (np.iscomplexobj(H) or np.iscomplexobj(S)) else np.float64
+    eps = np.zeros((nk, 2, N))
+    C = np.zeros((nk, 2, N, N), dtype=dt)
+    for k in range(nk):
+        for s_ in range(2):
+            eps[k, s_], C[k, s_] = eigh_generalized(H[k, s_].astype(dt), S[k].astype(dt))
+    flat = eps.reshape(2 * nk, N)
+    wi = np.repeat(w, 2)
+    mu = chemical_potential(flat, wi, 1.0, kT, n_elec)
+    occ = np.stack([fermi((flat[i] - mu) / kT) for i in range(2 * nk)]).reshape(nk, 2, N)
+    rho = np.stack([[density_matrix(C[k, s_], occ[k, s_], 1.0, f_cut) for s_ in range(2)] for k in range(nk)])
+    e_band = float(sum(w[k] * np.sum(occ[k] * eps[k]) for k in range(nk)))
+    n_rho = np.array([[int(np.sum(occ[k, s_] >= f_cut)) for s_ in range(2)] for k in range(nk)])
+    return Result(eps, C, mu, occ, rho, e_band, n_rho)
+
+
 # ----------------------------- error measures -----------------------------
 
-def eig_condition(H, S, eps, C):
+def hermitian_norm2(A, iters: int = 300, seed: int = 0) -> float:
+    """||A||_2 of a Hermitian A by power iteration (the largest |eigenvalue|): a lower bound
+    that reaches the norm to well under a percent after a few hundred steps; O(iters n^2),
+    for orders where a full SVD would dominate the oracle's own cost."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(A.shape[0]).astype(A.dtype)
+    v /= np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(iters):
+        w = A @ v
+        lam = float(np.linalg.norm(w))
+        if lam == 0.0:
+            return 0.0
+        v = w / lam
+    return lam
+
+
+def eig_condition(H, S, eps, C, norms=None):
     """beta_i = u (||H||_2 + |eps_i| ||S||_2) ||c_i||_2^2: first-order FP64 floor of eps_i
-    for a backward-stable method on an S-normalized eigenpair."""
-    nh = np.linalg.norm(H, 2)
-    ns = np.linalg.norm(S, 2)
+    for a backward-stable method on an S-normalized eigenpair.  norms = (||H||_2, ||S||_2)
+    if already known (e.g. from hermitian_norm2 at large orders)."""
+    nh, ns = norms if norms is not None else (np.linalg.norm(H, 2), np.linalg.norm(S, 2))
     cn = np.sum(np.abs(C) ** 2, axis=0)
     return U_ROUND * (nh + np.abs(eps) * ns) * cn
 

@@ -1548,6 +1548,44 @@ gks_status gks_sync(gks_ctx* ctx) {
 
 long long gks_launch_count(void) { return launches_issued(); }
 
+gks_status gks_measure_peak(gks_ctx* ctx, int which, double* tflops) {
+  if (!ctx || !tflops || which < 0 || which > 1) return fail(ctx, GKS_EINVAL, "bad arguments");
+  DeviceGuard dg(ctx->device);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms < 1)
+    return cuda_check(ctx, "gks_measure_peak: device attribute");
+  double* out = nullptr;
+  if (cudaMalloc(&out, sizeof(double) * (size_t)sms * 1024) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, GKS_ENOMEM, "gks_measure_peak: allocation failed");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // size the probe to about 100 ms from a short first run, then take the best of three
+  long long iters = 1 << 14;
+  double best = 0.0;
+  for (int rep = 0; rep < 4; rep++) {
+    cudaEventRecord(e0, ctx->stream);
+    const double fl = peak_probe(which, sms, iters, out, ctx->stream);
+    cudaEventRecord(e1, ctx->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep == 0) {
+      iters = (long long)((double)iters * 100.0 / std::max(1e-3, (double)ms));
+      iters = std::max(1ll << 12, std::min(iters, 1ll << 26));
+      continue;
+    }
+    best = std::max(best, fl / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *tflops = best;
+  return cuda_check(ctx, "gks_measure_peak");
+}
+
 int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max) {
   if (!ctx || !ctx->prof.on) return 0;
   DeviceGuard dg(ctx->device);
@@ -1591,7 +1629,7 @@ int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max) {
 gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha,
                     const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
                     int mode) {
-  if (!ctx || !A || !B || !C || M < 0 || N < 0 || K < 0) return fail(ctx, GKS_EINVAL, "bad arguments");
+  if (!ctx || ((!A || !B) && K > 0) || !C || M < 0 || N < 0 || K < 0) return fail(ctx, GKS_EINVAL, "bad arguments");
   if (opA < 0 || opA > 2 || opB < 0 || opB > 2 || mode < 1 || mode > 2) return fail(ctx, GKS_EINVAL, "bad op or mode");
   if (M > 46340 || N > 46340 || K > 46340) return fail(ctx, GKS_EINVAL, "dimension too large");
   DeviceGuard dg(ctx->device);
@@ -1614,7 +1652,7 @@ gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_
 gks_status gks_gemm_split_noalloc(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_t N, int64_t K,
                                   double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
                                   double beta, void* C, int64_t ldc) {
-  if (!ctx || !A || !B || !C || M < 0 || N < 0 || K < 0) return fail(ctx, GKS_EINVAL, "bad arguments");
+  if (!ctx || ((!A || !B) && K > 0) || !C || M < 0 || N < 0 || K < 0) return fail(ctx, GKS_EINVAL, "bad arguments");
   if (opA < 0 || opA > 2 || opB < 0 || opB > 2) return fail(ctx, GKS_EINVAL, "bad op");
   if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
   if (M > 46340 || N > 46340 || K > 46340) return fail(ctx, GKS_EINVAL, "dimension too large");

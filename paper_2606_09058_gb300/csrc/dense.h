@@ -109,6 +109,11 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
                 void* work, DevStatus* status, cudaStream_t s, const double* kscale = nullptr, long long sks = 0,
                 const int* kdev = nullptr, long long wait_cycles = 0, long long skip_copy = -1);
 
+// ---- FP64 unit throughput probes (peaks.cu) ----
+// which 0: DFMA, 1: DMMA (mma.sync f64).  Enqueues one probe on sms x 4 CTAs and returns
+// the flops it executes; `out` needs sms * 1024 doubles.
+double peak_probe(int which, int sms, long long iters, double* out, cudaStream_t s);
+
 // ---- occupations (occ.cu) ----
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,
               double f_cut, double* occ, double* kscale, double* mu, double* e_band, int* nrho, DevStatus* st,

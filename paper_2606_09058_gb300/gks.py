@@ -97,6 +97,8 @@ def load() -> ctypes.CDLL:
     lib.gks_occupy.restype = I
     lib.gks_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I]
     lib.gks_profile.restype = I
+    lib.gks_measure_peak.argtypes = [P, I, ctypes.POINTER(ctypes.c_double)]
+    lib.gks_measure_peak.restype = I
     lib.gks_launch_count.argtypes = []
     lib.gks_launch_count.restype = ctypes.c_longlong
     for f in ("gks_create", "gks_destroy", "gks_solve", "gks_sync", "gks_potrf", "gks_reduce", "gks_stedc"):
@@ -322,6 +324,13 @@ class Context:
         if sync:
             self.sync()
         return Hb, Sb
+
+    def measure_peak(self, unit: str = "dfma") -> float:
+        """gks_measure_peak: measured TFLOP/s of the FP64 FMA pipe ("dfma") or of the FP64
+        mma.sync instruction ("dmma") on this device."""
+        out = ctypes.c_double()
+        self._raise(self._lib.gks_measure_peak(self._h, {"dfma": 0, "dmma": 1}[unit], ctypes.byref(out)))
+        return out.value
 
     # ------------------------------------------------------------------ stages
     def gemm(self, A, B, C, opA="N", opB="N", alpha=1.0, beta=0.0, mode="split"):

@@ -115,7 +115,7 @@ class Problem:
     S: torch.Tensor
     n: int
     nk: int
-    spin: str                 # "collinear" | "noncollinear"
+    spin: str                 # "collinear" | "noncollinear" | "spin_polarized"
     kT: float
     n_elec: float
     kweights: np.ndarray
@@ -181,16 +181,18 @@ def lattice_images(L: np.ndarray, tol: float = 1e-18) -> list:
 
 
 def periodic(tiling, index: int, kT: float, n_elec: float | None = None, device="cpu",
-             mesh=(2, 2, 2)) -> Problem:
+             mesh=(2, 2, 2), kidx=None) -> Problem:
     """Bloch-summed H(k), S(k) (paper Sec. 2, Bloch-sum basis and S(k)) over the lattice
     images of `lattice_images` (27 for the 512-atom supercell), complex128 Hermitian per
-    k-point; the S-sandwiched random term uses S(k) at each k."""
+    k-point; the S-sandwiched random term uses S(k) at each k.  kidx: build only these
+    k-points of the mesh (the random draws do not depend on it; weights stay 1/nk_mesh)."""
     rng = np.random.default_rng(seed_for(index))
     pos = diamond_positions(tiling, rng)
     c, a = _basis(pos)
     n = c.shape[0]
     L = np.array(tiling, float) * A_BOHR
-    kf = mp_kpoints(mesh)
+    kmesh = mp_kpoints(mesh)
+    kf = kmesh if kidx is None else kmesh[list(kidx)]
     nk = kf.shape[0]
     images = lattice_images(L)
     Sk = torch.zeros(nk, n, n, dtype=torch.complex128, device=device)
@@ -215,7 +217,7 @@ def periodic(tiling, index: int, kT: float, n_elec: float | None = None, device=
         Hk[ik] = _hermitize(Hk[ik])
     natoms = pos.shape[0]
     ne = 4.0 * natoms if n_elec is None else n_elec
-    return Problem(Hk, Sk, n, nk, "collinear", kT, ne, np.full(nk, 1.0 / nk),
+    return Problem(Hk, Sk, n, nk, "collinear", kT, ne, np.full(nk, 1.0 / kmesh.shape[0]),
                    name=f"periodic{tuple(tiling)}k{nk}", meta={"atoms": natoms, "kpoints": kf})
 
 
@@ -271,6 +273,24 @@ def noncollinear(tiling, index: int, kT: float, n_elec: float | None = None, dev
                    np.ones(1), name=f"nc{tuple(tiling)}",
                    meta={"atoms": natoms, "delta": delta, "lam": lam, "H": H, "S": S,
                          "moments": m, "KA": KA})
+
+
+def spin_polarized(tiling, index: int, kT: float, n_elec: float | None = None, device="cpu",
+                   delta: float = 0.05) -> Problem:
+    """Collinear spin-polarized Gamma-point problem on a cluster: seeded per-atom moments
+    m_A ~ U(-1, 1) along one axis and the S-consistent on-site exchange term of the
+    noncollinear construction, H_up = H + D S_z, H_down = H - D S_z (S_z = S blockdiag(m_A
+    S_AA^-1) S).  H is (1, 2, N, N) (channel after k), S (1, N, N)."""
+    H, S, pos, rng = cluster(tiling, seed_for(index), device)
+    natoms = pos.shape[0]
+    m = np.zeros((natoms, 3))
+    m[:, 2] = rng.uniform(-1.0, 1.0, natoms)
+    HN = spinor_hamiltonian(H, S, m, np.zeros((natoms, N_PER_ATOM, N_PER_ATOM)), delta, 0.0).real
+    n = H.shape[0]
+    Hs = torch.stack([HN[:n, :n], HN[n:, n:]]).contiguous()
+    ne = 4.0 * natoms if n_elec is None else n_elec
+    return Problem(Hs[None], S[None], n, 1, "spin_polarized", kT, ne, np.ones(1), name=f"sp{tuple(tiling)}",
+                   meta={"atoms": natoms, "delta": delta, "moments": m, "H": H, "S": S})
 
 
 # ---------------------------------------------------------------------------------

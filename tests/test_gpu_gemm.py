@@ -120,3 +120,15 @@ def test_solve_with_split_products_matches_oracle(ctx):
             assert bwd <= 1e-12 * np.sqrt(H.shape[0])
             d = np.abs(S @ (sol.rho.cpu().numpy()[k] - ref.rho[k]) @ S).max()
             assert d <= 1e-9 * max(1.0, beta.max() / 1e-10)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("mode", ["split", "fp64"])
+def test_gemm_empty_inner_dimension(ctx, cplx, mode):
+    """K = 0 gives C = beta C on both product paths."""
+    dt = torch.complex128 if cplx else torch.float64
+    A = torch.zeros(300, 0, dtype=dt, device="cuda")
+    B = torch.zeros(0, 200, dtype=dt, device="cuda")
+    C0 = torch.randn(300, 200, dtype=dt, device="cuda")
+    out = ctx.gemm(A, B, C0.clone(), alpha=2.0, beta=0.25, mode=mode)
+    assert torch.equal(out, 0.25 * C0)

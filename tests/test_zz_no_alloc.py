@@ -83,3 +83,17 @@ def test_noalloc_rejects_products_beyond_the_scratch(ctx):
     B = torch.eye(64, dtype=torch.float64, device="cuda")
     out = ctx.gemm_split_noalloc(B, B, torch.zeros(64, 64, dtype=torch.float64, device="cuda"))
     assert torch.equal(out, B)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_noalloc_empty_inner_dimension(ctx, cplx):
+    """K = 0: no digits to multiply, C = beta C, on the fixed scratch as on the allocating
+    path (the scratch takes one zero block of digits)."""
+    dt = torch.complex128 if cplx else torch.float64
+    A = torch.zeros(64, 0, dtype=dt, device="cuda")
+    B = torch.zeros(0, 64, dtype=dt, device="cuda")
+    C0 = torch.randn(64, 64, dtype=dt, device="cuda")
+    got = ctx.gemm_split_noalloc(A, B, C0.clone(), alpha=0.7, beta=-0.5)
+    ref = ctx.gemm(A, B, C0.clone(), alpha=0.7, beta=-0.5, mode="split")
+    assert torch.equal(got, ref)
+    assert torch.equal(got, -0.5 * C0)
