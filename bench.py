@@ -486,6 +486,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the mixed-precision and one-problem-per-call forms of the step")
     ap.add_argument("--profile-json", default=None, help="write the per-class/per-stage event profile here")
     ap.add_argument("--no-tune", action="store_true", help="uneven48: skip the width tuner")
     ap.add_argument("--no-graph", action="store_true", help="uneven48: eager launches instead of graph replay")
@@ -605,6 +607,55 @@ def main():
         with open(args.profile_json, "w") as fh:
             json.dump({"ms_per_step": ms, "profile": prof, "steps": args.steps}, fh, indent=1)
 
+    # the other forms of the same step on the same GPU: mixed precision + refinement, and the
+    # plain FP64 path one problem (k-point) per call
+    compare = None
+    if not args.no_compare and not args.per_k and args.gemm == "auto" and rank == 0:
+        compare = {}
+
+        def timed(fn, steps):
+            fn()
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(steps):
+                fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            return a0.elapsed_time(a1) / steps
+        if M <= 18000:
+            cm = gks.Context(local, stream, precision="mixed", block=args.block)
+            eps_m = torch.empty_like(eps)
+            C_m = torch.empty_like(C)
+            rho_m = torch.empty_like(rho)
+            mu_m = torch.empty_like(mu)
+            eb_m = torch.empty_like(eb)
+            mms = timed(lambda: cm.solve_into(H, S, prob.kT, prob.n_elec, spin, kw, eps=eps_m, C=C_m, mu=mu_m,
+                                              rho=rho_m, e_band=eb_m, sync=False), args.steps)
+            cm.sync()
+            st = cm.refine_stats()
+            nrho_m = [int(sum(1 for v in eps_m.cpu().numpy()[k] if fermi((v - float(mu_m.item())) / prob.kT) >= 1e-16))
+                      for k in range(nk)]
+            compare["mixed"] = {
+                "ms_per_step": mms, "value": fl_step * world / (mms / 1e3) / 1e12, "unit": "TFLOP/s",
+                "speedup_vs_fp64": ms / mms, "refine_sweeps": int(st.shape[0] // max(1, nk)),
+                "refine_orthonormality_defect_per_sweep": [float(x) for x in st[:, 0].reshape(-1, nk).max(axis=1)],
+                "abs_dmu_vs_fp64": abs(float(mu_m.item()) - mu_h),
+                "accuracy": accuracy_report(args.workload, prob, H, S, eps_m, C_m, float(mu_m.item()), nrho_m)
+                if not args.no_accuracy else None}
+            del cm, eps_m, C_m, rho_m
+            torch.cuda.empty_cache()
+        if nk > 1:
+            saved = args.per_k
+            args.per_k = True
+            pms = timed(lambda: step(H, S), 1)
+            args.per_k = saved
+            ctx.sync()
+            compare["fp64_per_problem"] = {"ms_per_step": pms, "value": fl_step * world / (pms / 1e3) / 1e12,
+                                           "unit": "TFLOP/s", "batched_speedup": pms / ms,
+                                           "note": "one gks_solve per k-point (nk = 1 each, 1 timed step)"}
+        ctx.profile()
+
     # end to end through the C ABI with host buffers (pinned), H2D and D2H inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -674,7 +725,7 @@ def main():
                            "nominal_tflop_per_step": fl_step / 1e12, "n_rho": nrho},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-                "accuracy": accuracy, "fp64_peaks_measured": peak,
+                "accuracy": accuracy, "compare": compare, "fp64_peaks_measured": peak,
                 "stages_ms": stages, "kernels": classes}
         print(json.dumps(line), flush=True)
     if world > 1:

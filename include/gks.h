@@ -50,12 +50,14 @@ typedef enum { GKS_R64 = 0, GKS_C128 = 1 } gks_dtype;        /* real symmetric /
 typedef enum { GKS_COLLINEAR = 0, GKS_NONCOLLINEAR = 1, GKS_SPIN_POLARIZED = 2 } gks_spin;
 
 /* Arithmetic of the eigensolve.  GKS_FP64: every stage FP64-accurate (products as exact
- * split-bf16 tensor-core products with FP64 accumulation).  GKS_MIXED_SPLITBF16: the
- * tridiagonalization and back-transform products on fewer digits (FP32-level), then
- * opts.refine_sweeps Ogita-Aishima refinement sweeps of the eigenpairs of H' with
- * FP64-accurate residual products; the Cholesky of S, the reduction to H', the secular
- * roots and the refinement residuals stay FP64.  GKS_MIXED_TF32 is not implemented
- * (gks_create returns GKS_ENOTIMPL). */
+ * split-bf16 tensor-core products with FP64 accumulation).  GKS_MIXED_SPLITBF16: H' is
+ * rounded to single precision and tridiagonalized on the FP32 pipe, the divide and
+ * conquer stays FP64, the back-transform products take 5 digits (about FP32 accuracy),
+ * then opts.refine_sweeps Ogita-Aishima sweeps refine every eigenpair of H' with
+ * FP64-accurate products (Ogita & Aishima 2018); the Cholesky of S, the reduction to H',
+ * the secular roots, the refinement residuals and C = L^-H X stay FP64.  Mixed precision
+ * needs opts.n_ev = 0 and M <= 18000.  GKS_MIXED_TF32 is not implemented (gks_create
+ * returns GKS_ENOTIMPL). */
 typedef enum { GKS_FP64 = 0, GKS_MIXED_TF32 = 1, GKS_MIXED_SPLITBF16 = 2 } gks_prec;
 
 /* gks_solve flags. */
@@ -243,6 +245,13 @@ gks_status gks_sync(gks_ctx* ctx);
  * previous gks_profile call (requires opts->profile = 1): up to `max` entries are written
  * to `out`; the return value is the number of entries (0 when profiling is off). */
 int gks_profile(gks_ctx* ctx, gks_prof_entry* out, int max);
+
+/* Refinement statistics of the last GKS_MIXED_SPLITBF16 solve on this context (the
+ * contraction of the Ogita-Aishima sweeps): out[2 (s items + b) + 0] = the bound on
+ * ||I - X^H X||_2 and out[... + 1] = the bound on ||X^H H' X - diag(l)||_2 measured at the
+ * start of sweep s for item b (largest absolute row sums).  Waits for the stream; returns
+ * the number of values written (at most max), 0 without a mixed-precision solve. */
+int gks_refine_stats(gks_ctx* ctx, double* out, int max);
 
 /* Number of kernel launches this library has issued in the calling process. */
 long long gks_launch_count(void);

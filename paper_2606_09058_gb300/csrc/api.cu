@@ -4,8 +4,9 @@
 #include <cstring>
 #include <map>
 #include <mutex>
-#include <tuple>
 #include <string>
+#include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "dense.h"
@@ -15,6 +16,8 @@ using namespace gks;
 
 namespace {
 constexpr int NB = 64;  // panel / reflector block width
+constexpr int kMaxSweeps = 8;   // refinement sweeps of the mixed-precision path (opts bound)
+constexpr int kLowSlices = 5;   // digits per operand of the mixed path's back-transform products
 
 struct Arena {
   size_t off = 0;
@@ -33,7 +36,7 @@ const char* kClassNames[PC_NCLASS] = {"gemm", "potf2", "trsm_block", "hegst_diag
                                       "occupations", "misc", "split_gemm"};
 const char* kStageNames[PS_NSTAGE] = {"stage:copy", "stage:potrf", "stage:hegst", "stage:hetrd", "stage:stedc",
                                       "stage:backtransform", "stage:unreduce", "stage:occupations", "stage:rho",
-                                      "stage:adjoint"};
+                                      "stage:adjoint", "stage:refine"};
 
 struct EventProf : Prof {
   cudaStream_t stream = nullptr;
@@ -120,13 +123,14 @@ struct gks_ctx {
   size_t sv_bytes = 0;
   SolveKey svkey{};
   bool sv_valid = false;
+  int rstat_sweeps = 0, rstat_items = 0;  // shape of the refinement statistics of the last solve
   // occupation workspace of gks_occupy (weights, f, g_s f, g_s f eps, n_rho for all items)
   char* ow = nullptr;
   size_t ow_bytes = 0;
   // workspace for the current shape
   char* ws = nullptr;
   size_t ws_bytes = 0;
-  int m = -1, n = -1, nk = -1, es = -1, nc = -1;
+  int m = -1, n = -1, nk = -1, es = -1, nc = -1, wsmixed = 0;
   DcPlan* dc = nullptr;
   DevStatus* st = nullptr;
   // adjoint workspace (separate arena, sized for the last adjoint shape)
@@ -135,7 +139,7 @@ struct gks_ctx {
   int am = -1, ank = -1, aes = -1;
   // offsets (bytes) of per-item arrays; each holds nk items
   size_t oA, oL, oF, oFB, oU, oQ, opart, oy, ouw, oSg, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho,
-      oweights, oeb, odc, oticket;
+      oweights, oeb, odc, oticket, oAf, oRY, oRT, oRR, onrm, orstat, operm, oflag;
   long long sMM, sF, sFB, sU, spart, sy, sV, sG, sT, sY, sVec;
 };
 
@@ -240,7 +244,10 @@ int shape_spin(int spin) { return spin == GKS_NONCOLLINEAR ? 1 : 0; }
 // Workspace for nk items of order m (element size es, n = basis per spin, nc = spin mode).
 gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   const int want = pick_width(c, m, es, shape_spin(nc));
-  if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc && c->nbb == want) return GKS_OK;
+  const int mixed = c->precision != GKS_FP64 ? 1 : 0;
+  if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc && c->nbb == want &&
+      c->wsmixed == mixed)
+    return GKS_OK;
   release_ws(c);
   c->nbb = want;
   const size_t MM = (size_t)m * m;
@@ -289,6 +296,18 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->oticket = a.take<int>((size_t)2 * nk);
   c->dc = dc_plan_create(m, nk);
   c->odc = a.take<char>(dc_workspace_bytes(c->dc));
+  if (mixed) {
+    // single-precision copy of H' for the tridiagonalization, refinement products Y, T, R,
+    // the per-item norms, and the reordering buffers
+    c->oAf = a.take<char>(elems(c->sMM) / 2);
+    c->oRY = a.take<char>(elems(c->sMM));
+    c->oRT = a.take<char>(elems(c->sMM));
+    c->oRR = a.take<char>(elems(c->sMM));
+    c->onrm = a.take<double>((size_t)3 * nk);
+    c->orstat = a.take<double>((size_t)2 * kMaxSweeps * nk);
+    c->operm = a.take<int>((size_t)m * nk);
+    c->oflag = a.take<int>((size_t)nk);
+  }
   c->ws_bytes = a.off;
   if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -303,6 +322,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
     return fail(c, GKS_ENOMEM, "status allocation failed");
   }
   cudaMemset(c->st, 0, sizeof(DevStatus) * nk);
+  c->wsmixed = mixed;
   c->m = m;
   c->n = n;
   c->nk = nk;
@@ -459,6 +479,11 @@ template <typename T>
 void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA,
          const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC, int lower = 0) {
   if (M <= 0 || N <= 0) return;
+  if constexpr (!std::is_same<T, double>::value && !std::is_same<T, zc>::value) {
+    // single precision (the FP32 tridiagonalization): the FP32 pipe
+    gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
+    return;
+  } else {
   const int es = sizeof(T);
   const double fl = gemm_flops(es, M, N, K, lower, count);
   const int per = split_worth(c, count, M, N, K, es, fl)
@@ -480,6 +505,7 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
                        c->wait_cycles, skip))
       gmp<T>(c, cnt, opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc, sC,
              lower);
+  }
   }
 }
 
@@ -807,8 +833,8 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
 // blocks of nbb reflectors: B = I - V T V^H.  X is M x ncols (ldx, sX).  T (upper
 // triangular) is assembled from the 64-wide diagonal blocks (larft on G = V^H V) by the merge
 //   T[:s, s:s+k] = -T[:s, :s] G[:s, s:s+k] T[s:s+k, s:s+k].
-template <typename T>
-void backtransform_run(gks_ctx* c, const T* A, T* X, int ldx, long long sX, int M, int ncols, int nk) {
+template <typename T, typename TA = T>
+void backtransform_run(gks_ctx* c, const TA* A, T* X, int ldx, long long sX, int M, int ncols, int nk) {
   cudaStream_t s = c->stream;
   const int nbb = c->nbb;
   T* V = at<T>(c, c->oV);
@@ -824,7 +850,7 @@ void backtransform_run(gks_ctx* c, const T* A, T* X, int ldx, long long sX, int 
     const int j1 = std::min(j0 + nbb - 1, M - 1), nbk = j1 - j0 + 1;
     {
       Rec r(c, PC_BACKTR_AUX);
-      gather_reflectors<T>(A, M, c->sMM, tau, M, j0, j1, V, nbb, c->sV, tb, nbb, nk, s);
+      gather_reflectors<TA, T>(A, M, c->sMM, tau, M, j0, j1, V, nbb, c->sV, tb, nbb, nk, s);
     }
     gmx<T>(c, nk, OP_C, OP_N, nbk, nbk, j1, 1.0, V, nbb, c->sV, V, nbb, c->sV, 0.0, G, nbb, c->sG);
     for (int s0 = 0; s0 < nbk; s0 += NB) {
@@ -845,6 +871,54 @@ void backtransform_run(gks_ctx* c, const T* A, T* X, int ldx, long long sX, int 
     gmx<T>(c, nk, OP_N, OP_N, nbk, ncols, nbk, 1.0, Tm, nbb, c->sT, Y, ncols, c->sY, 0.0, Y2, ncols, c->sY);
     gmx<T>(c, nk, OP_N, OP_N, j1, ncols, nbk, -1.0, V, nbb, c->sV, Y2, ncols, c->sY, 1.0, X, ldx, sX);
   }
+}
+
+// Ogita-Aishima sweeps (refine.cu) on X (C, order M, all columns) for the standard problem
+// H' (lower triangle in A, made full here): each sweep Y = H' X, T = X^H Y, G = X^H X as
+// FP64-accurate products (the context's digit count), the correction E, X <- X + X E.  lam
+// receives the refined eigenvalues in ascending order; per sweep and item the bounds of
+// ||R|| and ||T - diag(l)|| go to the statistics buffer (gks_refine_stats).
+template <typename T>
+void refine_run(gks_ctx* c, T* A, T* X, int M, int items, double* lam) {
+  cudaStream_t s = c->stream;
+  const long long MM = c->sMM;
+  T* Y = at<T>(c, c->oRY);
+  T* Tm = at<T>(c, c->oRT);
+  T* G = at<T>(c, c->oRR);
+  double* nrm = at<double>(c, c->onrm);
+  double* rst = at<double>(c, c->orstat);
+  {
+    Rec r(c, PC_MISC);
+    mirror_lower<T>(A, M, MM, M, items, s);
+  }
+  T* Xc = X;
+  T* Xo = Y;
+  const int sweeps = std::min(kMaxSweeps, std::max(1, c->refine_sweeps));
+  for (int sw = 0; sw < sweeps; sw++) {
+    gmx<T>(c, items, OP_N, OP_N, M, M, M, 1.0, A, M, MM, Xc, M, MM, 0.0, Xo, M, MM);        // Y = H' X
+    gmx<T>(c, items, OP_C, OP_N, M, M, M, 1.0, Xc, M, MM, Xo, M, MM, 0.0, Tm, M, MM, 1);    // T = X^H Y
+    gmx<T>(c, items, OP_C, OP_N, M, M, M, 1.0, Xc, M, MM, Xc, M, MM, 0.0, G, M, MM, 1);     // G = X^H X
+    {
+      Rec r(c, PC_MISC);
+      mirror_lower<T>(Tm, M, MM, M, items, s);
+      mirror_lower<T>(G, M, MM, M, items, s);
+      oa_prepare<T>(Tm, G, MM, M, lam, nrm, items, s);
+      // statistics: (||R|| bound, ||T - diag(l)|| bound) per item for this sweep
+      cudaMemcpy2DAsync(rst + (size_t)sw * 2 * items, 2 * sizeof(double), nrm + 1, 3 * sizeof(double),
+                        sizeof(double), items, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpy2DAsync(rst + (size_t)sw * 2 * items + 1, 2 * sizeof(double), nrm, 3 * sizeof(double),
+                        sizeof(double), items, cudaMemcpyDeviceToDevice, s);
+      oa_correction<T>(Tm, G, MM, M, lam, nrm, items, s);
+      copy2d<T>(Xo, M, MM, Xc, M, MM, M, M, items, s);
+    }
+    gmx<T>(c, items, OP_N, OP_N, M, M, M, 1.0, Xc, M, MM, Tm, M, MM, 1.0, Xo, M, MM);       // X + X E
+    std::swap(Xc, Xo);
+  }
+  Rec r(c, PC_MISC);
+  if (Xc != X) copy2d<T>(X, M, MM, Xc, M, MM, M, M, items, s);
+  oa_order<T>(lam, X, Y, MM, M, at<int>(c, c->operm), at<int>(c, c->oflag), items, s);
+  c->rstat_sweeps = sweeps;
+  c->rstat_items = items;
 }
 
 // Does the context still hold the Cholesky factor of this S (same array, shape and type
@@ -915,11 +989,28 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
   double* d = at<double>(c, c->od);
   double* e = at<double>(c, c->oe);
   T* ph = at<T>(c, c->oph);
+  const bool mixed = c->precision == GKS_MIXED_SPLITBF16;
+  using TL = typename Low<T>::type;
+  TL* Af = mixed ? at<TL>(c, c->oAf) : nullptr;
   {
     StageRec sr(c, PS_HETRD);
-    hetrd_run<T>(c, A, M, items);
-    Rec r(c, PC_HETRD_VEC);
-    hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, items, s);
+    if (mixed) {
+      // mixed precision: H' rounded to single precision and tridiagonalized on the FP32
+      // pipe (FP64 H' stays in A for the refinement)
+      {
+        Rec r(c, PC_MISC);
+        narrow_lower<T, TL>(A, M, c->sMM, Af, M, c->sMM, M, items, s);
+      }
+      hetrd_run<TL>(c, Af, M, items);
+      Rec r(c, PC_HETRD_VEC);
+      TL* phl = at<TL>(c, c->ou);
+      hetrd_finish<TL>(Af, M, c->sMM, M, d, e, M, phl, M, items, s);
+      widen_copy<TL, T>(phl, ph, (long long)M * items, s);
+    } else {
+      hetrd_run<T>(c, A, M, items);
+      Rec r(c, PC_HETRD_VEC);
+      hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, items, s);
+    }
   }
   // (a5) divide and conquer on the real tridiagonal
   double* Z = at<double>(c, c->oZ);
@@ -942,7 +1033,20 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
       Rec r(c, PC_MISC);
       apply_phase<T>(C, nev, sC, Z, M, c->sMM, ph, M, M, nev, items, s);
     }
-    backtransform_run<T>(c, A, C, nev, sC, M, nev, items);
+    if (mixed) {
+      // single-precision reflectors, products on fewer digits (about FP32 accuracy)
+      const int sv = c->slices;
+      c->slices = std::min(sv, kLowSlices);
+      backtransform_run<T, TL>(c, Af, C, nev, sC, M, nev, items);
+      c->slices = sv;
+    } else {
+      backtransform_run<T>(c, A, C, nev, sC, M, nev, items);
+    }
+  }
+  // (a7) mixed precision: Ogita-Aishima refinement of (eps, X) on the FP64 H'
+  if (mixed) {
+    StageRec sr(c, PS_REFINE);
+    refine_run<T>(c, A, C, M, items, eps);
   }
   {
     StageRec sr(c, PS_UNREDUCE);
@@ -1083,6 +1187,12 @@ gks_status validate_solve(gks_ctx* ctx, const SolveKey& k) {
   const bool nc = k.spin == GKS_NONCOLLINEAR;
   if (nc && k.dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
   if (nc && 2 * k.n > 46340) return fail(ctx, GKS_EINVAL, "2n out of range");
+  if (ctx->precision == GKS_MIXED_SPLITBF16) {
+    const long long M = nc ? 2 * k.n : k.n;
+    if (ctx->n_ev > 0 && ctx->n_ev < M)
+      return fail(ctx, GKS_EINVAL, "mixed precision refines every eigenvector: opts.n_ev must be 0");
+    if (M > 18000) return fail(ctx, GKS_EINVAL, "mixed precision supports orders up to 18000");
+  }
   if (!eig_only) {
     if (!(k.kT > 0.0)) return fail(ctx, GKS_EINVAL, "kT must be positive");
     const double gs = k.spin == GKS_COLLINEAR ? 2.0 : 1.0;
@@ -1210,9 +1320,9 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
       delete c;
       return GKS_EINVAL;
     }
-    if (c->precision != GKS_FP64) {
+    if (c->precision != GKS_FP64 && c->precision != GKS_MIXED_SPLITBF16) {
       delete c;
-      return (c->precision == GKS_MIXED_TF32 || c->precision == GKS_MIXED_SPLITBF16) ? GKS_ENOTIMPL : GKS_EINVAL;
+      return c->precision == GKS_MIXED_TF32 ? GKS_ENOTIMPL : GKS_EINVAL;
     }
   }
   {
@@ -1547,6 +1657,19 @@ gks_status gks_sync(gks_ctx* ctx) {
 }
 
 long long gks_launch_count(void) { return launches_issued(); }
+
+int gks_refine_stats(gks_ctx* ctx, double* out, int max) {
+  if (!ctx || !out || max < 1 || !ctx->ws || !ctx->wsmixed || ctx->rstat_sweeps == 0) return 0;
+  DeviceGuard dg(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  const int n = std::min(max, 2 * ctx->rstat_sweeps * ctx->rstat_items);
+  if (cudaMemcpy(out, at<double>(ctx, ctx->orstat), sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
 
 gks_status gks_measure_peak(gks_ctx* ctx, int which, double* tflops) {
   if (!ctx || !tflops || which < 0 || which > 1) return fail(ctx, GKS_EINVAL, "bad arguments");

@@ -56,10 +56,17 @@ void hetrd_pupdate(T* A, int lda, long long sA, int j, T* u, const T* p, long lo
 template <typename T>
 void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e, long long sde, T* ph,
                   long long sph, int count, cudaStream_t s);
-// Gather reflectors j0..j1 (descending) into Vblk (rows x (j1-j0+1)) and their taus.
-template <typename T>
+// Gather reflectors j0..j1 (descending) into Vblk (rows x (j1-j0+1)) and their taus; TV may
+// be the FP64 partner of a single-precision T.
+template <typename T, typename TV>
 void gather_reflectors(const T* A, int lda, long long sA, const double* tau, long long stau, int j0, int j1,
-                       T* V, int ldv, long long sV, double* tb, long long stb, int count, cudaStream_t s);
+                       TV* V, int ldv, long long sV, double* tb, long long stb, int count, cudaStream_t s);
+// dst[t] = src[t] widened to FP64 (single-precision phases of the mixed-precision path).
+template <typename T, typename TV>
+void widen_copy(const T* src, TV* dst, long long n, cudaStream_t s);
+// Lower triangle of the order-n FP64 A rounded to single precision in B.
+template <typename T, typename TL>
+void narrow_lower(const T* A, int lda, long long sA, TL* B, int ldb, long long sB, int n, int count, cudaStream_t s);
 
 // ---- divide and conquer (stedc.cu) ----
 struct DcPlan;
@@ -113,6 +120,21 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
 // which 0: DFMA, 1: DMMA (mma.sync f64).  Enqueues one probe on sms x 4 CTAs and returns
 // the flops it executes; `out` needs sms * 1024 doubles.
 double peak_probe(int which, int sms, long long iters, double* out, cudaStream_t s);
+
+// ---- Ogita-Aishima refinement (refine.cu) ----
+// Per item (stride sMM, order M, full storage): G = X^H X becomes R = I - X^H X, lam = the
+// refined Rayleigh quotients t_ii/(1 - r_ii) of T = X^H H' X, nrm[3 z + 0..2] = row-sum bounds
+// of ||T - diag(lam)||_2 and ||R||_2 and max |lam|.
+template <typename T>
+void oa_prepare(const T* Tm, T* G, long long sMM, int M, double* lam, double* nrm, int count, cudaStream_t s);
+// T <- E, the sweep's correction (cluster threshold from nrm).
+template <typename T>
+void oa_correction(T* Tm, const T* R, long long sMM, int M, const double* lam, const double* nrm, int count,
+                   cudaStream_t s);
+// Restore ascending lam (and the columns of X with it, through Y) where refinement swapped
+// near-degenerate eigenvalues; M * 12 bytes of shared memory per item.
+template <typename T>
+void oa_order(double* lam, T* X, T* Y, long long sMM, int M, int* perm, int* flag, int count, cudaStream_t s);
 
 // ---- occupations (occ.cu) ----
 void fermi_mu(const double* eps, int m, int nk, const double* w, double gs, double kT, double n_elec,

@@ -23,6 +23,14 @@ template <> struct GemmTile<double> {
 template <> struct GemmTile<zc> {
   static constexpr int TM = 2, TN = 2, BK = 16;
 };
+// single precision (panel updates of the FP32 tridiagonalization): the FP32 pipe is ~60x
+// the FP64 one, so larger register tiles pay
+template <> struct GemmTile<float> {
+  static constexpr int TM = 4, TN = 4, BK = 16;
+};
+template <> struct GemmTile<cf> {
+  static constexpr int TM = 4, TN = 4, BK = 16;
+};
 
 template <typename T>
 __device__ __forceinline__ T ld_op(const T* p, int op) {
@@ -152,8 +160,12 @@ void copy2d(T* dst, int ldd, long long sd, const T* src, int lds, long long ss, 
 
 template void gemm<double>(const GemmBatch&, int, int, cudaStream_t);
 template void gemm<zc>(const GemmBatch&, int, int, cudaStream_t);
+template void gemm<float>(const GemmBatch&, int, int, cudaStream_t);
+template void gemm<cf>(const GemmBatch&, int, int, cudaStream_t);
 template void copy2d<double>(double*, int, long long, const double*, int, long long, int, int, int,
                              cudaStream_t);
 template void copy2d<zc>(zc*, int, long long, const zc*, int, long long, int, int, int, cudaStream_t);
+template void copy2d<float>(float*, int, long long, const float*, int, long long, int, int, int, cudaStream_t);
+template void copy2d<cf>(cf*, int, long long, const cf*, int, long long, int, int, int, cudaStream_t);
 
 }  // namespace gks

@@ -70,6 +70,57 @@ __device__ __forceinline__ void macc(zc& acc, zc a, zc b) {
   acc.y = fma(-a.y, b.x, acc.y);
 }
 
+// ---- single precision (the FP32 tridiagonalization of the mixed-precision path) ----
+// float for real problems, cf (complex float, interleaved) for complex ones; scalars that
+// come in double (tau, alpha, beta of a product) are applied in double and rounded once.
+struct cf {
+  float x, y;
+};
+__host__ __device__ __forceinline__ float conjg(float a) { return a; }
+__host__ __device__ __forceinline__ cf conjg(cf a) { return cf{a.x, -a.y}; }
+__host__ __device__ __forceinline__ float re(float a) { return a; }
+__host__ __device__ __forceinline__ float re(cf a) { return a.x; }
+__host__ __device__ __forceinline__ float im(float) { return 0.0f; }
+__host__ __device__ __forceinline__ float im(cf a) { return a.y; }
+__host__ __device__ __forceinline__ float abs2(float a) { return a * a; }
+__host__ __device__ __forceinline__ float abs2(cf a) { return a.x * a.x + a.y * a.y; }
+template <> __host__ __device__ __forceinline__ float from_real<float>(double a) { return (float)a; }
+template <> __host__ __device__ __forceinline__ cf from_real<cf>(double a) { return cf{(float)a, 0.0f}; }
+__host__ __device__ __forceinline__ cf operator+(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
+__host__ __device__ __forceinline__ cf operator-(cf a, cf b) { return cf{a.x - b.x, a.y - b.y}; }
+__host__ __device__ __forceinline__ cf operator-(cf a) { return cf{-a.x, -a.y}; }
+__host__ __device__ __forceinline__ cf operator*(cf a, cf b) {
+  return cf{fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)};
+}
+__host__ __device__ __forceinline__ cf operator*(double s, cf a) { return cf{(float)(s * a.x), (float)(s * a.y)}; }
+__host__ __device__ __forceinline__ cf operator*(cf a, double s) { return cf{(float)(s * a.x), (float)(s * a.y)}; }
+__host__ __device__ __forceinline__ cf& operator+=(cf& a, cf b) { a.x += b.x; a.y += b.y; return a; }
+__host__ __device__ __forceinline__ cf& operator-=(cf& a, cf b) { a.x -= b.x; a.y -= b.y; return a; }
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ cf ldcg(const cf* p) {
+  float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return cf{v.x, v.y};
+}
+__device__ __forceinline__ void mac(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+__device__ __forceinline__ void mac(cf& acc, cf a, cf b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void macc(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+__device__ __forceinline__ void macc(cf& acc, cf a, cf b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// The single-precision partner of each FP64 element type.
+template <typename T> struct Low;
+template <> struct Low<double> { using type = float; };
+template <> struct Low<zc> { using type = cf; };
+
 // ---- warp / block reductions ----
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -77,6 +128,16 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 __device__ __forceinline__ zc warp_sum(zc v) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ cf warp_sum(cf v) {
   v.x = warp_sum(v.x);
   v.y = warp_sum(v.y);
   return v;

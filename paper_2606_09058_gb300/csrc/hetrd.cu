@@ -251,6 +251,12 @@ __device__ __forceinline__ double group8_sum(double v) {
   return v;
 }
 __device__ __forceinline__ zc group8_sum(zc v) { return zc{group8_sum(v.x), group8_sum(v.y)}; }
+__device__ __forceinline__ float group8_sum(float v) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ cf group8_sum(cf v) { return cf{group8_sum(v.x), group8_sum(v.y)}; }
 
 // Step j, second half: q = tau (p_raw - U y1 - Q y2) - kq u for the rows of this CTA (64
 // per CTA), stored with u as column k of Q and U.  With rowupd, row j-1 of A (columns
@@ -374,10 +380,16 @@ __global__ void hetrd_finish_kernel(const T* A, int lda, long long sA, int m, do
   }
 }
 
-// V[:, c] = u'_{j1-c} (rows 0..j1-1), tb[c] = tau[j1-c].
-template <typename T>
+__device__ __forceinline__ double widen(double a) { return a; }
+__device__ __forceinline__ double widen(float a) { return (double)a; }
+__device__ __forceinline__ zc widen(zc a) { return a; }
+__device__ __forceinline__ zc widen(cf a) { return zc{(double)a.x, (double)a.y}; }
+
+// V[:, c] = u'_{j1-c} (rows 0..j1-1), tb[c] = tau[j1-c].  Reflectors stored in single
+// precision (the mixed-precision path) are widened exactly to FP64.
+template <typename T, typename TV>
 __global__ void gather_reflectors_kernel(const T* A, int lda, long long sA, const double* tau, long long stau,
-                                         int j0, int j1, T* V, int ldv, long long sV, double* tb, long long stb) {
+                                         int j0, int j1, TV* V, int ldv, long long sV, double* tb, long long stb) {
   const int z = blockIdx.z;
   A += z * sA;
   tau += z * stau;
@@ -387,9 +399,9 @@ __global__ void gather_reflectors_kernel(const T* A, int lda, long long sA, cons
   for (int i = blockIdx.y; i < j1; i += gridDim.y)
     for (int c = threadIdx.x; c < nbb; c += blockDim.x) {
       int jj = j1 - c;
-      T v = zero<T>();
-      if (i < jj - 1) v = A[(size_t)jj * lda + i];
-      else if (i == jj - 1) v = from_real<T>(1.0);
+      TV v = zero<TV>();
+      if (i < jj - 1) v = widen(A[(size_t)jj * lda + i]);
+      else if (i == jj - 1) v = from_real<TV>(1.0);
       V[(size_t)i * ldv + c] = v;
       if (i == 0) tb[c] = tau[jj];
     }
@@ -442,12 +454,51 @@ void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e
   hetrd_finish_kernel<T><<<count, 256, 0, s>>>(A, lda, sA, m, d, e, sde, ph, sph);
 }
 
-template <typename T>
+template <typename T, typename TV>
 void gather_reflectors(const T* A, int lda, long long sA, const double* tau, long long stau, int j0, int j1,
-                       T* V, int ldv, long long sV, double* tb, long long stb, int count, cudaStream_t s) {
+                       TV* V, int ldv, long long sV, double* tb, long long stb, int count, cudaStream_t s) {
   dim3 grid(1, j1 < 2048 ? j1 : 2048, count);
   count_launch();
-  gather_reflectors_kernel<T><<<grid, 64, 0, s>>>(A, lda, sA, tau, stau, j0, j1, V, ldv, sV, tb, stb);
+  gather_reflectors_kernel<T, TV><<<grid, 64, 0, s>>>(A, lda, sA, tau, stau, j0, j1, V, ldv, sV, tb, stb);
+}
+
+// ph (FP64 type) from the single-precision phases of the mixed-precision path.
+template <typename T, typename TV>
+__global__ void widen_kernel(const T* src, TV* dst, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    dst[t] = widen(src[t]);
+}
+
+template <typename T, typename TV>
+void widen_copy(const T* src, TV* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  count_launch();
+  const long long b = (n + 255) / 256;
+  widen_kernel<T, TV><<<(int)(b < 4096 ? b : 4096), 256, 0, s>>>(src, dst, n);
+}
+
+// Lower triangle of the FP64 A (lda, sA) rounded into the single-precision B (ldb, sB).
+template <typename T, typename TL>
+__global__ void narrow_lower_kernel(const T* A, int lda, long long sA, TL* B, int ldb, long long sB, int n) {
+  const int z = blockIdx.z;
+  A += z * sA;
+  B += z * sB;
+  for (int i = blockIdx.y; i < n; i += gridDim.y)
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i; j += gridDim.x * blockDim.x) {
+      const T a = A[(size_t)i * lda + j];
+      TL b;
+      if constexpr (sizeof(T) == 16) b = TL{(float)re(a), (float)im(a)};
+      else b = (TL)re(a);
+      B[(size_t)i * ldb + j] = b;
+    }
+}
+
+template <typename T, typename TL>
+void narrow_lower(const T* A, int lda, long long sA, TL* B, int ldb, long long sB, int n, int count, cudaStream_t s) {
+  if (n <= 0) return;
+  dim3 grid((n + 255) / 256 < 16 ? (n + 255) / 256 : 16, n < 2048 ? n : 2048, count);
+  count_launch();
+  narrow_lower_kernel<T, TL><<<grid, 256, 0, s>>>(A, lda, sA, B, ldb, sB, n);
 }
 
 #define INST(T)                                                                                            \
@@ -461,9 +512,32 @@ void gather_reflectors(const T* A, int lda, long long sA, const double* tau, lon
                                  double*);                                                                 \
   template void hetrd_finish<T>(const T*, int, long long, int, double*, double*, long long, T*, long long,   \
                                 int, cudaStream_t);                                                        \
-  template void gather_reflectors<T>(const T*, int, long long, const double*, long long, int, int, T*, int, \
-                                     long long, double*, long long, int, cudaStream_t);
+  template void gather_reflectors<T, T>(const T*, int, long long, const double*, long long, int, int, T*,    \
+                                        int, long long, double*, long long, int, cudaStream_t);
 INST(double)
 INST(zc)
+#undef INST
+#define INST(T)                                                                                            \
+  template void hetrd_reflector<T>(T*, int, long long, int, T*, long long, double*, long long, int,         \
+                                   cudaStream_t, double*);                                                 \
+  template void hetrd_phemv<T>(const T*, int, long long, int, const T*, T*, long long, const double*,        \
+                               long long, const T*, const T*, int, long long, int, T*, long long, T*, long long, \
+                               int*, int, cudaStream_t, const double*, const double*);                     \
+  template void hetrd_pupdate<T>(T*, int, long long, int, T*, const T*, long long, double*, long long, T*,  \
+                                 T*, int, long long, int, const T*, long long, int, int*, int, cudaStream_t, \
+                                 double*);                                                                 \
+  template void hetrd_finish<T>(const T*, int, long long, int, double*, double*, long long, T*, long long,   \
+                                int, cudaStream_t);
+INST(float)
+INST(cf)
+template void gather_reflectors<float, double>(const float*, int, long long, const double*, long long, int, int,
+                                               double*, int, long long, double*, long long, int, cudaStream_t);
+template void gather_reflectors<cf, zc>(const cf*, int, long long, const double*, long long, int, int, zc*, int,
+                                        long long, double*, long long, int, cudaStream_t);
+template void widen_copy<float, double>(const float*, double*, long long, cudaStream_t);
+template void widen_copy<cf, zc>(const cf*, zc*, long long, cudaStream_t);
+template void narrow_lower<double, float>(const double*, int, long long, float*, int, long long, int, int,
+                                          cudaStream_t);
+template void narrow_lower<zc, cf>(const zc*, int, long long, cf*, int, long long, int, int, cudaStream_t);
 
 }  // namespace gks

@@ -45,7 +45,8 @@ enum ProfClass : int {
   PC_DC_SECULAR, PC_DC_GEMM, PC_BACKTR_AUX, PC_OCC, PC_MISC, PC_OZAKI, PC_NCLASS
 };
 enum ProfStage : int {
-  PS_COPY = 0, PS_POTRF, PS_HEGST, PS_HETRD, PS_STEDC, PS_BACKTR, PS_UNREDUCE, PS_OCC, PS_RHO, PS_ADJOINT, PS_NSTAGE
+  PS_COPY = 0, PS_POTRF, PS_HEGST, PS_HETRD, PS_STEDC, PS_BACKTR, PS_UNREDUCE, PS_OCC, PS_RHO, PS_ADJOINT, PS_REFINE,
+  PS_NSTAGE
 };
 // Records CUDA events around launch groups (no-op when profiling is off).
 struct Prof {

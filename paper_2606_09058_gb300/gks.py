@@ -97,6 +97,8 @@ def load() -> ctypes.CDLL:
     lib.gks_occupy.restype = I
     lib.gks_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I]
     lib.gks_profile.restype = I
+    lib.gks_refine_stats.argtypes = [P, ctypes.POINTER(ctypes.c_double), I]
+    lib.gks_refine_stats.restype = I
     lib.gks_measure_peak.argtypes = [P, I, ctypes.POINTER(ctypes.c_double)]
     lib.gks_measure_peak.restype = I
     lib.gks_launch_count.argtypes = []
@@ -324,6 +326,16 @@ class Context:
         if sync:
             self.sync()
         return Hb, Sb
+
+    def refine_stats(self):
+        """Per sweep and item of the last mixed-precision solve: (bound on ||I - X^H X||,
+        bound on ||X^H H' X - diag(l)||) at the start of the sweep, as an array
+        (sweeps * items, 2) in sweep-major order."""
+        import numpy as np
+        buf = (ctypes.c_double * 4096)()
+        n = self._lib.gks_refine_stats(self._h, buf, 4096)
+        a = np.array(buf[:n])
+        return a.reshape(-1, 2)
 
     def measure_peak(self, unit: str = "dfma") -> float:
         """gks_measure_peak: measured TFLOP/s of the FP64 FMA pipe ("dfma") or of the FP64

@@ -1,12 +1,13 @@
-"""Inputs and oracle results for the parity tests at the workloads' own sizes.
+"""Inputs and oracle results for the parity test of the 48 uneven systems at their own sizes.
 
-The oracle is slow at these orders (minutes per pencil on the host cores), so the GPU test
-session starts it early: at the end of collection, when full-size tests are selected and
-a CUDA device is present, `start()` builds the inputs on the device (the same arrays the
-CUDA path will solve), writes the ones the oracle needs to a scratch directory, and
-launches `oracle_job.py` on them in a separate process (a fresh interpreter, so no CUDA
-state is shared).  The full-size tests, collected late, wait for its results with
-`oracle_result()`.  Nothing here computes an expected value: the job calls only oracle/.
+The oracle needs minutes for the whole batch on the host cores, so the GPU test session
+starts it early: at the end of collection, when the full-size tests are selected and a
+CUDA device is present, `start()` builds the 48 pencils on the device (the same arrays the
+CUDA path will solve), writes them to a scratch directory and launches `oracle_job.py` on
+them in a separate process (a fresh interpreter, so no CUDA state is shared).  The test,
+collected late, waits for its results with `oracle_result()`.  Nothing here computes an
+expected value: the job calls only oracle/.  (The 512-atom and 384-atom results, hours of
+oracle time, are stored under tests/golden/ by make_fullsize.py.)
 """
 from __future__ import annotations
 
@@ -43,17 +44,12 @@ def start() -> None:
     d = tempfile.mkdtemp(prefix="gks_fullsize_")
     _state["dir"] = d
     t0 = time.time()
-    kb = I.workload("kbatch512", device="cuda")
-    torch.cuda.synchronize()
-    _state["kbatch512"] = kb
-    np.save(os.path.join(d, "kb_H0.npy"), kb.H[0].cpu().numpy())
-    np.save(os.path.join(d, "kb_S0.npy"), kb.S[0].cpu().numpy())
     probs = I.uneven_batch(device="cuda")
     _state["uneven48"] = probs
     for b, p in enumerate(probs):
         np.save(os.path.join(d, f"u{b}_H.npy"), p.H[0].cpu().numpy())
         np.save(os.path.join(d, f"u{b}_S.npy"), p.S[0].cpu().numpy())
-    meta = {"kb": (kb.kT, kb.n_elec, kb.spin), "u": [(p.kT, p.n_elec, p.spin) for p in probs]}
+    meta = {"u": [(p.kT, p.n_elec, p.spin) for p in probs]}
     np.save(os.path.join(d, "meta.npy"), np.array(meta, dtype=object), allow_pickle=True)
     _state["gen_s"] = time.time() - t0
     n = str(cores())

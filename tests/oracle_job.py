@@ -1,10 +1,9 @@
-"""Oracle results for the full-size parity tests (run as a script by fullsize_support).
+"""Oracle results for the 48-system parity test (run as a script by fullsize_support).
 
 Reads the pencils written to DIR, solves them with the plain CPU oracle (OpenMP over its
-independent loops), and writes one .npz per case: eigenvalues, the S-sandwiched density
-matrix S rho S (what the tests compare, S-covariantly), mu, E_band and the condition
-numbers beta_i of the eigenvalues.  Cases in order: the 48 uneven systems (u.npz), then
-k-point 0 of the 512-atom k-batch solved as a pencil of its own (kbatch512_k0.npz)."""
+independent loops), and writes u.npz: per system the eigenvalues, the S-sandwiched density
+matrix S rho S (what the test compares, S-covariantly), mu, E_band and the condition
+numbers beta_i of the eigenvalues."""
 import os
 import sys
 import time
@@ -41,19 +40,6 @@ def main(d):
         out[f"eb{b}"] = np.array(r.e_band)
         print(f"system {b}: M={H.shape[0]} {time.time() - t0:.1f} s", flush=True)
     _save(d, "u", **out)
-    # k-point 0 of the 512-atom k-batch as a pencil of its own (its own mu for the same
-    # electron count per k-point: the shared mu needs all eight k-points)
-    kT, ne, spin = meta["kb"]
-    H = np.load(os.path.join(d, "kb_H0.npy"))
-    S = np.load(os.path.join(d, "kb_S0.npy"))
-    t1 = time.time()
-    r = O.solve(H[None], S[None], kT, ne, spin)
-    t2 = time.time()
-    beta = O.eig_condition(H, S, r.eps[0], r.C[0], (O.hermitian_norm2(H), O.hermitian_norm2(S)))
-    _save(d, "kbatch512_k0", eps=r.eps[0], srs=S @ r.rho[0] @ S, beta=beta, mu=np.array(r.mu),
-          eb=np.array(r.e_band), seconds=np.array(t2 - t1),
-          threads=np.array(int(os.environ.get("OMP_NUM_THREADS", "1"))))
-    print(f"kbatch512 k0: M={H.shape[0]} solve {t2 - t1:.1f} s", flush=True)
 
 
 if __name__ == "__main__":
