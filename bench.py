@@ -65,6 +65,32 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def kshard_range(nk: int, world: int, rank: int):
+    """Contiguous k-point range [k0, k1) of a rank: the k-points of one system spread as
+    evenly as possible (the first nk % world ranks take one more)."""
+    base, extra = divmod(nk, world)
+    k0 = rank * base + min(rank, extra)
+    return k0, k0 + base + (1 if rank < extra else 0)
+
+
+def gather_eps(eps_local, nk: int, world: int):
+    """All ranks' eigenvalues (nk, M) in k order from each rank's contiguous block (the one
+    exchange of the k-point sharding: nk M doubles); ranks with fewer k-points pad."""
+    import torch
+    import torch.distributed as dist
+    per = max(kshard_range(nk, world, r)[1] - kshard_range(nk, world, r)[0] for r in range(world))
+    M = eps_local.shape[-1]
+    buf = torch.zeros(per, M, dtype=eps_local.dtype, device=eps_local.device)
+    buf[:eps_local.shape[0]] = eps_local
+    out = torch.empty(world * per, M, dtype=eps_local.dtype, device=eps_local.device)
+    dist.all_gather_into_tensor(out, buf)
+    rows = []
+    for r in range(world):
+        k0, k1 = kshard_range(nk, world, r)
+        rows.append(out[r * per:r * per + (k1 - k0)])
+    return torch.cat(rows).contiguous()
+
+
 def max_over_ranks(value: float, device) -> float:
     """The slowest rank's value (whole-job time); the value itself on a single process."""
     import torch
@@ -520,13 +546,22 @@ def main():
         dist.barrier()
     from paper_2606_09058_gb300 import gks
 
-    # Each rank solves its own independent copy of the workload (weak scaling: the
-    # k-batch of one system is the unit; ranks share nothing on the data path).
+    # Under torchrun the k-points of the one system are sharded: rank r owns a contiguous
+    # k range, solves it (eigenpairs only), the eigenvalues of all k-points are allgathered
+    # (NCCL, nk M doubles) and every rank runs the same bisection for the shared mu
+    # (gks_occupy) before its own density matrices: strong scaling of one system.  A
+    # workload with fewer k-points than ranks runs replicas (weak scaling).
     prob = make_problem(args.workload, str(dev))
-    H, S = prob.H.contiguous(), prob.S.contiguous()
+    nk_all = prob.H.shape[0]
+    shard = world > 1 and nk_all >= world and prob.spin == "collinear" and not args.per_k
+    k0, k1 = kshard_range(nk_all, world, rank) if shard else (0, nk_all)
+    H, S = prob.H[k0:k1].contiguous(), prob.S[k0:k1].contiguous()
+    if shard:
+        del prob.H, prob.S
     nk, M = H.shape[0], H.shape[1]
     spin = prob.spin
-    kw = torch.as_tensor(np.asarray(prob.kweights, float), device=dev)
+    kw = torch.as_tensor(np.asarray(prob.kweights, float), device=dev)  # all k-points (1/nk_all)
+    kw_local = kw[k0:k1].contiguous()
     stream = torch.cuda.current_stream(dev)
     ctx = gks.Context(local, stream, profile=True, gemm=args.gemm, block=args.block)
     eps = torch.empty(nk, M, dtype=torch.float64, device=dev)
@@ -540,6 +575,15 @@ def main():
             for k in range(nk):
                 ctx.solve_into(Hd[k:k + 1], Sd[k:k + 1], prob.kT, prob.n_elec, spin, None,
                                eps=eps[k:k + 1], C=C[k:k + 1], mu=mu, rho=rho[k:k + 1], e_band=eb, sync=sync)
+            return
+        if shard:
+            ctx.solve_into(Hd, Sd, prob.kT, prob.n_elec, spin, kw_local, eps=eps, C=C, sync=False, eigen_only=True)
+            eps_all = gather_eps(eps, nk_all, world)
+            m_, r_, e_, _ = ctx.occupy(eps_all, C, prob.kT, prob.n_elec, k0=k0, spin=spin, kweights_all=kw,
+                                       sync=sync)
+            mu.copy_(m_)
+            rho.copy_(r_)
+            eb.copy_(e_)
             return
         ctx.solve_into(Hd, Sd, prob.kT, prob.n_elec, spin, kw, eps=eps, C=C, mu=mu, rho=rho, e_band=eb, sync=sync)
 
@@ -575,7 +619,13 @@ def main():
         return exp(-x) / (1 + exp(-x)) if x > 0 else 1 / (1 + exp(x))
     nrho = [int(sum(1 for v in eps_h[k] if fermi((v - mu_h) / prob.kT) >= 1e-16)) for k in range(nk)]
     fl_step = nominal_flops(M, H.is_complex(), nrho)
-    value = fl_step * world / (ms / 1e3) / 1e12
+    if shard:  # strong scaling: the k-points of one system over the ranks
+        ft = torch.tensor([fl_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(ft)
+        fl_job = float(ft.item())
+    else:      # replicas (weak scaling): every rank solves the whole workload
+        fl_job = fl_step * world
+    value = fl_job / (ms / 1e3) / 1e12
 
     # roofline: dominant kernel class over the timed region.  DRAM traffic per launch comes
     # from one ncu capture of the kernel on the 64-atom k-batch (profiles/), where it matched
@@ -610,7 +660,7 @@ def main():
     # the other forms of the same step on the same GPU: mixed precision + refinement, and the
     # plain FP64 path one problem (k-point) per call
     compare = None
-    if not args.no_compare and not args.per_k and args.gemm == "auto" and rank == 0:
+    if not args.no_compare and not args.per_k and args.gemm == "auto" and world == 1:
         compare = {}
 
         def timed(fn, steps):
@@ -690,7 +740,7 @@ def main():
         ctx.sync()
         ctx.profile()
         ems = max_over_ranks(f0.elapsed_time(f1) / args.steps, dev)
-        e2e = {"value": fl_step * world / (ems / 1e3) / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": fl_job / (ems / 1e3) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(Hh.numel() * Hh.element_size() + Sh.numel() * Sh.element_size()),
                "d2h_bytes_per_step": int(eps_out.numel() * 8 + 16 + C_out.numel() * C_out.element_size()
                                          + rho_out.numel() * rho_out.element_size()),
@@ -698,7 +748,7 @@ def main():
         del Hh, Sh, Hd, Sd, C_out, rho_out
 
     accuracy = None
-    if rank == 0 and not args.no_accuracy:
+    if world == 1 and not args.no_accuracy:
         accuracy = accuracy_report(args.workload, prob, H, S, eps, C, mu_h, nrho)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -715,9 +765,12 @@ def main():
     if rank == 0:
         line = {"metric": "GKS eigensolve+rho throughput (nominal FP64 TFLOP/s)", "value": value, "unit": "TFLOP/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
-                "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "M": M, "nk": nk,
+                "higher_is_better": True, "scaling": "strong" if shard else "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "M": M, "nk": nk_all,
+                           "parallelism": (f"k-point shard over {world} ranks (contiguous k ranges, allgather of "
+                                           f"eps, shared mu on every rank)") if shard else
+                           (f"{world} replicas" if world > 1 else "one GPU"),
                            "spin": spin, "precision": "fp64", "products": args.gemm,
                            "block": args.block or (512 if M >= 4096 else 256),
                            "batching": "one call per k-point" if args.per_k else "all k-points in one call",

@@ -60,6 +60,15 @@ typedef enum { GKS_COLLINEAR = 0, GKS_NONCOLLINEAR = 1, GKS_SPIN_POLARIZED = 2 }
  * returns GKS_ENOTIMPL). */
 typedef enum { GKS_FP64 = 0, GKS_MIXED_TF32 = 1, GKS_MIXED_SPLITBF16 = 2 } gks_prec;
 
+/* Reduction to the standard problem.  GKS_REDUCE_CHOLESKY: S = L L^H, H' = L^-1 H L^-H,
+ * C = L^-H X.  GKS_REDUCE_LOWDIN (the paper's own route, Sec. 3.1 Parts 2-1 .. 2-5):
+ * S = U diag(s) U^H by this library's standard eigensolve, V = U diag(s)^-1/2,
+ * H' = V^H H V, C = V X; V is what GKS_REUSE_S_FACTOR keeps.  On an ill-conditioned S the
+ * Loewdin factor carries s_min^-1/2 into every product, so its results are less accurate
+ * than Cholesky's (compare them with the tests); collinear and spin-polarized runs with
+ * n_ev = 0 only (noncollinear: GKS_ENOTIMPL). */
+typedef enum { GKS_REDUCE_CHOLESKY = 0, GKS_REDUCE_LOWDIN = 1 } gks_reduction;
+
 /* gks_solve flags. */
 enum {
   /* Skip the copy and Cholesky of S: reuse the factor kept from the last solve on this
@@ -98,7 +107,10 @@ typedef struct {
   int block;           /* outer block width of the two-level blocked Cholesky, reduction and
                           back-transforms: a multiple of 64 in 64..1024; 0 = 512 for orders
                           from 4096 up and 256 below (gks_tune overrides per shape class) */
-  int refine_sweeps;   /* GKS_MIXED_SPLITBF16: refinement sweeps, 1..8 (0 = 2) */
+  int refine_sweeps;   /* GKS_MIXED_SPLITBF16: refinement sweeps, 1..8 (0 = 4).  From the
+                          single-precision start the eigenvector error is about
+                          u32 ||H'|| / gap, up to 1e-2 on the Si Gaussian basis, so the first
+                          sweeps contract slowly; four reach the FP64 floor there */
   int n_ev;            /* eigenvectors computed per item: the lowest n_ev (0 = all M).  With
                           0 < n_ev < M, C is (nk, M, n_ev) and the back-transforms and the
                           density matrix touch only those columns (paper Sec. 6: a quarter to
@@ -111,6 +123,7 @@ typedef struct {
   const char* autotune_cache; /* file of tuned widths: read at gks_create if it exists, rewritten
                           by gks_tune and gks_tune_set; NULL = none.  The string is copied. */
   int debug;           /* test hooks, GKS_DEBUG_* (0 = none) */
+  int reduction;       /* gks_reduction: how H C = S C eps becomes a standard problem */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */

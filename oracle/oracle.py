@@ -304,6 +304,25 @@ def eigh_generalized(H: np.ndarray, S: np.ndarray):
     return eps, phase_fix(C)
 
 
+def eigh_lowdin(H: np.ndarray, S: np.ndarray):
+    """All eigenpairs of (H, S) by the Loewdin route of the paper (Sec. 3.1 Parts 2-1 to 2-5):
+    S = U diag(s) U^H (this oracle's eigensolver on the standard problem S), V = U s^-1/2,
+    H' = V^H H V, H' = C' diag(eps) C'^H, C = V C'.  Same eps and C (up to phases within
+    degenerate sets) as eigh_generalized in exact arithmetic."""
+    cplx = np.iscomplexobj(H) or np.iscomplexobj(S)
+    dt = np.complex128 if cplx else np.float64
+    S = np.asarray(S, dtype=dt)
+    I = np.eye(S.shape[0], dtype=dt)
+    s, U = eigh_generalized(S, I)
+    if np.any(s <= 0.0):
+        raise OracleError("S not positive definite (Loewdin)")
+    V = U / np.sqrt(s)[None, :]
+    Hp = V.conj().T @ np.asarray(H, dtype=dt) @ V
+    Hp = 0.5 * (Hp + Hp.conj().T)
+    eps, Cp = eigh_generalized(Hp, I)
+    return eps, phase_fix(V @ Cp)
+
+
 def phase_fix(C: np.ndarray) -> np.ndarray:
     """Column phase convention: the largest-modulus entry (lowest index on ties) is real
     and positive."""
@@ -389,7 +408,7 @@ def spinor_overlap(S: np.ndarray) -> np.ndarray:
 
 
 def solve(H, S, kT: float, n_elec: float, spin: str = "collinear", kweights=None,
-          f_cut: float = F_CUT) -> Result:
+          f_cut: float = F_CUT, reduction: str = "cholesky") -> Result:
     """Full path for nk pencils sharing one chemical potential.
 
     H: (nk, M, M); S: (nk, N, N) with M = N (collinear) or 2N (noncollinear)."""
@@ -406,9 +425,10 @@ def solve(H, S, kT: float, n_elec: float, spin: str = "collinear", kweights=None
     eps = np.zeros((nk, M))
     dt = np.complex128 if (np.iscomplexobj(H) or np.iscomplexobj(S) or spin != "collinear") else np.float64
     C = np.zeros((nk, M, M), dtype=dt)
+    eig = eigh_lowdin if reduction == "lowdin" else eigh_generalized
     for k in range(nk):
         Sk = spinor_overlap(S[k]) if spin == "noncollinear" else S[k]
-        eps[k], C[k] = eigh_generalized(H[k].astype(dt), Sk.astype(dt))
+        eps[k], C[k] = eig(H[k].astype(dt), Sk.astype(dt))
     mu = chemical_potential(eps, w, gs, kT, n_elec)
     occ = np.stack([fermi((eps[k] - mu) / kT) for k in range(nk)])
     rho = np.stack([density_matrix(C[k], occ[k], gs, f_cut) for k in range(nk)])

@@ -111,8 +111,9 @@ struct gks_ctx {
   DevStatus* gst = nullptr;            // status word of gks_gemm and gks_occupy (one entry)
   long long wait_cycles = 1ll << 32;   // bound of every device-side wait (opts.wait_limit)
   int n_ev = 0;                        // eigenvectors per item (0 = all)
+  int reduction = GKS_REDUCE_CHOLESKY; // Cholesky or Loewdin reduction to the standard problem
   int precision = GKS_FP64;
-  int refine_sweeps = 2;
+  int refine_sweeps = 4;
   int debug = 0;                       // test hooks (GKS_DEBUG_*)
   std::string tune_cache;              // file of tuned widths (opts.autotune_cache)
   // Cholesky factor kept in the L workspace from the solve that produced it
@@ -873,6 +874,37 @@ void backtransform_run(gks_ctx* c, const TA* A, T* X, int ldx, long long sX, int
   }
 }
 
+// All eigenpairs of the standard Hermitian problems in A (lower triangle, order M, items;
+// destroyed): w (M per item, ascending) and X (M x M, ldx M, stride sX) with the FP64 stages
+// of the main path (Householder, divide and conquer, back-transform).
+template <typename T>
+void standard_eig(gks_ctx* c, T* A, T* X, long long sX, double* w, int M, int items) {
+  cudaStream_t s = c->stream;
+  double* d = at<double>(c, c->od);
+  double* e = at<double>(c, c->oe);
+  T* ph = at<T>(c, c->oph);
+  hetrd_run<T>(c, A, M, items);
+  {
+    Rec r(c, PC_HETRD_VEC);
+    hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, items, s);
+  }
+  double* Z = at<double>(c, c->oZ);
+  DcSplit sp{nullptr, 0, c->slices, 512, c->wait_cycles};
+  if (c->gemm_mode != 1 && M >= 1024) {
+    const size_t item = dc_split_item_bytes(c->dc, sp.min_half, c->slices);
+    if (item > 0) {
+      sp.per = oz_reserve(c, item, items);
+      sp.work = c->oz;
+    }
+  }
+  dc_solve(c->dc, d, e, M, w, Z, c->sMM, c->ws + c->odc, c->st, s, &c->prof, &sp);
+  {
+    Rec r(c, PC_MISC);
+    apply_phase<T>(X, M, sX, Z, M, c->sMM, ph, M, M, M, items, s);
+  }
+  backtransform_run<T>(c, A, X, M, sX, M, M, items);
+}
+
 // Ogita-Aishima sweeps (refine.cu) on X (C, order M, all columns) for the standard problem
 // H' (lower triangle in A, made full here): each sweep Y = H' X, T = X^H Y, G = X^H X as
 // FP64-accurate products (the context's digit count), the correction E, X <- X + X E.  lam
@@ -959,8 +991,28 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
     copy2d<T>(A, M, c->sMM, H, M, (long long)M * M, M, M, items, s);
     if (!reuse) copy2d<T>(L, n, sLk, S, n, (long long)n * n, n, n, nk, s);
   }
+  const bool lowdin = c->reduction == GKS_REDUCE_LOWDIN;
   // (a1) Cholesky of S, (a2) reduction to the standard problem
-  if (!reuse) {
+  if (!reuse && lowdin) {
+    // Loewdin (paper Sec. 3.1 Parts 2-1, 2-2): S = U diag(s) U^H by the standard eigensolve
+    // of this library (S copied to the H' workspace, U in the output C), V = U diag(s)^-1/2
+    // kept in the factor slots
+    c->l_valid = false;
+    StageRec sr(c, PS_POTRF);
+    {
+      Rec r(c, PC_MISC);
+      copy2d<T>(A, M, sLk, S, n, (long long)n * n, n, n, nk, s);
+      if (sp) copy2d<T>(A + c->sMM, M, sLk, A, M, sLk, n, n, nk, s);
+    }
+    standard_eig<T>(c, A, C, sC, eps, M, items);
+    {
+      Rec r(c, PC_MISC);
+      lowdin_factor<T>(C, M, sC, eps, M, L, n, c->sMM, M, c->st, items, s);
+    }
+    c->lkey = key;
+    c->l_valid = true;
+    copy2d<T>(A, M, c->sMM, H, M, (long long)M * M, M, M, items, s);  // H again (A held S)
+  } else if (!reuse) {
     c->l_valid = false;
     StageRec sr(c, PS_POTRF);
     potrf_run<T>(c, L, n, n, sLk, nk);
@@ -973,7 +1025,16 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
   }
   {
     StageRec sr(c, PS_HEGST);
-    if (nc) {
+    if (lowdin) {
+      // H' = V^H H V (paper Sec. 3.1 Part 2-3): H made full, T1 = H V in the output C, the
+      // lower triangle of V^H T1 into A
+      {
+        Rec r(c, PC_MISC);
+        mirror_lower<T>(A, M, c->sMM, M, items, s);
+      }
+      gmx<T>(c, items, OP_N, OP_N, M, M, M, 1.0, A, M, c->sMM, L, n, c->sMM, 0.0, C, M, sC);
+      gmx<T>(c, items, OP_C, OP_N, M, M, M, 1.0, L, n, c->sMM, C, M, sC, 0.0, A, M, c->sMM, 1);
+    } else if (nc) {
       // H'^{ss'} = L^-1 H^{ss'} L^-H per spin block (paper Sec. 3.2 Part 3-3): the two
       // Hermitian diagonal blocks two-sided, the lower off-diagonal block by a left and a
       // right triangular solve
@@ -1050,7 +1111,11 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
   }
   {
     StageRec sr(c, PS_UNREDUCE);
-    if (nc) {  // C = diag(L, L)^-H X: each spin half with the n x n factor
+    if (lowdin) {  // C = V X (paper Sec. 3.1 Part 2-5), through A (free after the back-transform)
+      gmx<T>(c, items, OP_N, OP_N, M, M, M, 1.0, L, n, c->sMM, C, M, sC, 0.0, A, M, c->sMM);
+      Rec r(c, PC_MISC);
+      copy2d<T>(C, M, sC, A, M, c->sMM, M, M, items, s);
+    } else if (nc) {  // C = diag(L, L)^-H X: each spin half with the n x n factor
       trsm_left_run<T>(c, L, n, c->sMM, C, nev, sC, n, nev, nk, true);
       trsm_left_run<T>(c, L, n, c->sMM, C + (size_t)n * nev, nev, sC, n, nev, nk, true);
     } else {
@@ -1187,6 +1252,11 @@ gks_status validate_solve(gks_ctx* ctx, const SolveKey& k) {
   const bool nc = k.spin == GKS_NONCOLLINEAR;
   if (nc && k.dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "noncollinear problems are complex (GKS_C128)");
   if (nc && 2 * k.n > 46340) return fail(ctx, GKS_EINVAL, "2n out of range");
+  if (ctx->reduction == GKS_REDUCE_LOWDIN) {
+    if (nc) return fail(ctx, GKS_ENOTIMPL, "the Loewdin reduction is implemented for collinear runs");
+    if (ctx->n_ev > 0 && ctx->n_ev < k.n)
+      return fail(ctx, GKS_EINVAL, "the Loewdin reduction needs every eigenvector of S: opts.n_ev must be 0");
+  }
   if (ctx->precision == GKS_MIXED_SPLITBF16) {
     const long long M = nc ? 2 * k.n : k.n;
     if (ctx->n_ev > 0 && ctx->n_ev < M)
@@ -1311,11 +1381,13 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     c->precision = opts->precision;
     if (opts->refine_sweeps > 0) c->refine_sweeps = opts->refine_sweeps;
     c->n_ev = opts->n_ev;
+    c->reduction = opts->reduction;
     if (opts->wait_limit > 0) c->wait_cycles = opts->wait_limit;
     c->debug = opts->debug;
     if (opts->autotune_cache) c->tune_cache = opts->autotune_cache;
     if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 10 || c->nbb < NB || c->nbb > 1024 ||
         c->nbb % NB || c->n_ev < 0 || opts->refine_sweeps < 0 || opts->refine_sweeps > 8 || opts->wait_limit < 0 ||
+        (c->reduction != GKS_REDUCE_CHOLESKY && c->reduction != GKS_REDUCE_LOWDIN) ||
         (opts->debug & ~GKS_DEBUG_SKIP_COPY)) {
       delete c;
       return GKS_EINVAL;
@@ -1440,6 +1512,7 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     sc->n_ev = ctx->n_ev;
     sc->precision = ctx->precision;
     sc->refine_sweeps = ctx->refine_sweeps;
+    sc->reduction = ctx->reduction;
     ctx->subs.push_back(sc);
   }
   for (auto* sc : ctx->subs) sc->tuned = ctx->tuned;

@@ -297,6 +297,28 @@ __global__ void spinor_overlap_kernel(T* dst, long long sd, const T* S, int lds,
     }
 }
 
+// Loewdin factor V = U diag(s)^-1/2 (paper Sec. 3.1 Part 2-2) from the eigenvectors U
+// (ldu, sU) and eigenvalues s (ss per item) of S; a non-positive eigenvalue reports
+// GKS_ENOTSPD with its index and zeroes the column.
+template <typename T>
+__global__ void lowdin_factor_kernel(const T* U, int ldu, long long sU, const double* sv, long long ss, T* V, int ldv,
+                                     long long sV, int n, DevStatus* st) {
+  const int z = blockIdx.z;
+  U += z * sU;
+  V += z * sV;
+  sv += z * ss;
+  for (int i = blockIdx.y; i < n; i += gridDim.y)
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+      const double sj = sv[j];
+      if (!(sj > 0.0)) {
+        if (i == 0) set_status(st ? st + z : nullptr, ST_ENOTSPD, j);
+        V[(size_t)i * ldv + j] = zero<T>();
+      } else {
+        V[(size_t)i * ldv + j] = U[(size_t)i * ldu + j] * (1.0 / sqrt(sj));
+      }
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 
 static dim3 grid2d(int rows, int cols, int count) {
@@ -364,6 +386,13 @@ void apply_phase(T* X, int ldx, long long sX, const double* Z, int ldz, long lon
 }
 
 template <typename T>
+void lowdin_factor(const T* U, int ldu, long long sU, const double* sv, long long ss, T* V, int ldv, long long sV,
+                   int n, DevStatus* st, int count, cudaStream_t s) {
+  count_launch();
+  lowdin_factor_kernel<T><<<grid2d(n, n, count), 256, 0, s>>>(U, ldu, sU, sv, ss, V, ldv, sV, n, st);
+}
+
+template <typename T>
 void mirror_lower(T* A, int lda, long long sA, int n, int count, cudaStream_t s) {
   count_launch();
   mirror_lower_kernel<T><<<grid2d(n, n, count), 256, 0, s>>>(A, lda, sA, n);
@@ -426,6 +455,8 @@ void tune_pencil(T* A, int m, int count, int hermitian, cudaStream_t s) {
   template void apply_phase<T>(T*, int, long long, const double*, int, long long, const T*, long long,   \
                                int, int, int, cudaStream_t);                                            \
   template void mirror_lower<T>(T*, int, long long, int, int, cudaStream_t);                            \
+  template void lowdin_factor<T>(const T*, int, long long, const double*, long long, T*, int, long long, int, \
+                                 DevStatus*, int, cudaStream_t);                                           \
   template void column_phase<T>(T*, int, long long, int, int, int, cudaStream_t);                      \
   template void spinor_overlap<T>(T*, long long, const T*, int, long long, int, int, cudaStream_t);         \
   template void tune_pencil<T>(T*, int, int, int, cudaStream_t);

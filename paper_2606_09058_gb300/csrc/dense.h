@@ -23,6 +23,10 @@ void apply_phase(T* X, int ldx, long long sX, const double* Z, int ldz, long lon
                  int n, int cols, int count, cudaStream_t s);
 template <typename T>
 void mirror_lower(T* A, int lda, long long sA, int n, int count, cudaStream_t s);
+// V = U diag(s)^-1/2 (Loewdin factor); non-positive s_j: GKS_ENOTSPD with index j.
+template <typename T>
+void lowdin_factor(const T* U, int ldu, long long sU, const double* sv, long long ss, T* V, int ldv, long long sV,
+                   int n, DevStatus* st, int count, cudaStream_t s);
 template <typename T>
 void column_phase(T* C, int ldc, long long sC, int rows, int cols, int count, cudaStream_t s);
 template <typename T>

@@ -39,7 +39,7 @@ class _Opts(ctypes.Structure):
                 ("f_cut", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int),
                 ("gemm", ctypes.c_int), ("slices", ctypes.c_int), ("block", ctypes.c_int),
                 ("refine_sweeps", ctypes.c_int), ("n_ev", ctypes.c_int), ("wait_limit", ctypes.c_longlong),
-                ("autotune_cache", ctypes.c_char_p), ("debug", ctypes.c_int)]
+                ("autotune_cache", ctypes.c_char_p), ("debug", ctypes.c_int), ("reduction", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -137,7 +137,8 @@ class Context:
     def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None, f_cut: float = 1e-16,
                  profile: bool = False, graph: bool = False, gemm: str = "auto", slices: int = 0,
                  block: int = 0, precision: str = "fp64", refine_sweeps: int = 0, n_ev: int = 0,
-                 wait_limit: int = 0, autotune_cache: str | None = None, debug: int = 0):
+                 wait_limit: int = 0, autotune_cache: str | None = None, debug: int = 0,
+                 reduction: str = "cholesky"):
         if not torch.cuda.is_available():
             raise RuntimeError("gks needs a CUDA device")
         lib = load()
@@ -149,7 +150,7 @@ class Context:
         cache = autotune_cache.encode() if autotune_cache else None
         opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), _PREC[precision], f_cut,
                      1 if profile else 0, 1 if graph else 0, gm, int(slices), int(block), int(refine_sweeps),
-                     int(n_ev), int(wait_limit), cache, int(debug))
+                     int(n_ev), int(wait_limit), cache, int(debug), {"cholesky": 0, "lowdin": 1}[reduction])
         h = ctypes.c_void_p()
         rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
         if rc:

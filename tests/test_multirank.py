@@ -54,3 +54,56 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_kshard_ranges_partition_the_kpoints():
+    sys.path.insert(0, ROOT)
+    import bench
+    for nk in (1, 2, 7, 8, 9):
+        for world in range(1, nk + 1):
+            seen = []
+            for r in range(world):
+                k0, k1 = bench.kshard_range(nk, world, r)
+                assert 0 <= k0 <= k1 <= nk and k1 - k0 in (nk // world, nk // world + 1)
+                seen.extend(range(k0, k1))
+            assert seen == list(range(nk))
+
+
+def _kshard_worker(rank, world, port, out):
+    """Each rank solves its contiguous k range with the oracle, the eigenvalues are gathered
+    in k order over gloo (the one exchange of the k-point shard), and every rank runs the
+    same bisection: mu and E_band equal the single-process oracle's bit for bit."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from oracle import oracle as O
+    from paper_2606_09058_gb300 import inputs as I
+    p = I.periodic((1, 1, 1), 1, 0.01)
+    nk = p.nk
+    k0, k1 = bench.kshard_range(nk, world, rank)
+    eps_local = torch.as_tensor(np.stack([O.eigh_generalized(p.H[k].numpy(), p.S[k].numpy())[0]
+                                          for k in range(k0, k1)]))
+    eps_all = bench.gather_eps(eps_local, nk, world).numpy()
+    w = np.asarray(p.kweights, float)
+    mu = O.chemical_potential(eps_all, w, 2.0, p.kT, p.n_elec)
+    out[rank] = (mu, eps_all.tobytes())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_kshard_gather_and_shared_mu_gloo_two_ranks():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2606_09058_gb300 import inputs as I
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_kshard_worker, args=(2, port, out), nprocs=2, join=True)
+    p = I.periodic((1, 1, 1), 1, 0.01)
+    ref = O.solve(p.H.numpy(), p.S.numpy(), p.kT, p.n_elec, kweights=p.kweights)
+    for r in range(2):
+        mu, eb = out[r]
+        assert mu == ref.mu
+        assert eb == np.ascontiguousarray(ref.eps).tobytes()

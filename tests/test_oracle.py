@@ -592,3 +592,111 @@ def test_band_reduce_panel_form_matches_columnwise(cplx, n, b):
     assert np.abs(B1 - B2).max() <= 1e-13 * scale
     assert np.abs(Q @ B2 @ Q.conj().T - A).max() <= 1e-13 * scale
     assert np.abs(Q.conj().T @ Q - np.eye(n)).max() <= 1e-13
+
+
+# ------------------------------------------------------------------ conventions and variants
+
+def test_phase_fix_convention():
+    """The largest-modulus entry of every column becomes real positive, the lowest row on
+    ties; the column changes only by a unit-modulus factor."""
+    rng = np.random.default_rng(11)
+    C = (rng.standard_normal((9, 5)) + 1j * rng.standard_normal((9, 5))) * 0.1
+    C[3, 0] = 2.0 * np.exp(1j * 0.7)                    # unique maximum
+    C[2, 1] = 3.0 + 4.0j                                 # exact tie: rows 2 and 6 both modulus 5
+    C[6, 1] = -4.0 + 3.0j
+    C[:, 2] = 0.0                                        # zero column stays zero
+    C[8, 3] = -4.0                                       # negative real maximum
+    C[0, 4] = 1j * 3.0
+    C[4, 4] = -3.0                                       # tie between rows 0 and 4
+    F = O.phase_fix(C)
+    expect_row = {0: 3, 1: 2, 3: 8, 4: 0}
+    for j, r in expect_row.items():
+        assert abs(F[r, j].imag) <= 4 * O.U_ROUND * abs(F[r, j]) and F[r, j].real > 0
+        assert np.argmax(np.abs(F[:, j])) == r
+        assert abs(abs(F[r, j]) - abs(C[r, j])) <= 1e-15 * abs(C[r, j])
+        ph = F[r, j] / C[r, j]
+        assert abs(abs(ph) - 1.0) <= 1e-15
+        assert np.abs(F[:, j] - ph * C[:, j]).max() <= 1e-15 * np.abs(C[:, j]).max()
+    assert np.all(F[:, 2] == 0.0)
+    # real columns: the sign makes the largest entry positive
+    R = rng.standard_normal((6, 3))
+    R[5, 0] = -9.0
+    FR = O.phase_fix(R)
+    assert FR[5, 0] == 9.0 and np.array_equal(FR[:, 0], -R[:, 0])
+
+
+def test_hermitian_norm2_power_iteration():
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((80, 80)) + 1j * rng.standard_normal((80, 80)))
+    lam = np.concatenate([[-7.0, 5.0], rng.uniform(-3, 3, 78)])
+    A = (Q * lam) @ Q.conj().T
+    assert abs(O.hermitian_norm2(A) - 7.0) <= 1e-6 * 7.0
+    assert O.hermitian_norm2(A) <= 7.0 * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("n,s", [(5, 0.2), (40, -0.3), (90, 0.45)])
+def test_lowdin_generalized_chain_closed_form(n, s):
+    """The Loewdin route (eig S, V = U s^-1/2, V^H H V, C = V C') on the generalized chain."""
+    e0, t = -0.5, 0.7
+    H, S = I.chain(n, e0, t, s)
+    eps, C = O.eigh_lowdin(H, S)
+    th = np.arange(1, n + 1) * np.pi / (n + 1)
+    ref = np.sort((e0 + 2 * t * np.cos(th)) / (1 + 2 * s * np.cos(th)))
+    assert np.abs(eps - ref).max() <= 1e-12 * max(1, np.abs(ref).max())
+    assert np.abs(C.T @ S @ C - np.eye(n)).max() <= 1e-12
+    e2, C2 = O.eigh_generalized(H, S)
+    assert _match_columns(C, C2) <= 1e-10
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_lowdin_matches_cholesky_route(cplx):
+    H, S = I.random_pencil(70, 17, cplx, cond=1e3)
+    e1, C1 = O.eigh_lowdin(H, S)
+    e2, C2 = O.eigh_generalized(H, S)
+    assert np.abs(e1 - e2).max() <= 1e-11 * np.abs(e2).max()
+    assert _match_columns(C1, C2) <= 1e-8
+
+
+def test_spin_polarized_identical_channels_reduce_to_collinear():
+    """Equal up and down channels: each carries the collinear spectrum, mu is the collinear
+    one, rho_up + rho_down is the collinear rho (g_s = 2 split into two g_s = 1 channels)."""
+    p = I.collinear_gamma((1, 1, 1), 0, 0.01)
+    H, S = p.H.numpy(), p.S.numpy()
+    col = O.solve(H, S, p.kT, p.n_elec)
+    Hs = np.stack([H, H], axis=1)
+    sp = O.solve(Hs, S, p.kT, p.n_elec, spin="spin_polarized")
+    assert np.array_equal(sp.eps[0, 0], col.eps[0]) and np.array_equal(sp.eps[0, 1], col.eps[0])
+    assert abs(sp.mu - col.mu) <= 1e-12
+    assert np.abs(sp.rho[0, 0] + sp.rho[0, 1] - col.rho[0]).max() <= 1e-9 * np.abs(col.rho[0]).max()
+    assert abs(sp.e_band - col.e_band) <= 1e-10 * abs(col.e_band)
+
+
+def test_spin_polarized_uniform_exchange_shifts_spectra():
+    """H_up/down = H -/+ D S (a uniform S-consistent exchange shift): the channels' spectra
+    are the collinear one shifted by -D and +D exactly."""
+    H, S = I.random_pencil(40, 23, False, cond=1e2)
+    D = 0.05
+    Hs = np.stack([H - D * S, H + D * S])[None]
+    sp = O.solve(Hs, S[None], 0.05, 30.0, spin="spin_polarized")
+    e, _ = O.eigh_generalized(H, S)
+    assert np.abs(sp.eps[0, 0] - (e - D)).max() <= 1e-12 * np.abs(e).max()
+    assert np.abs(sp.eps[0, 1] - (e + D)).max() <= 1e-12 * np.abs(e).max()
+    # both channels share one mu: total electrons = n_elec, g_s = 1
+    tr = sum(np.trace(sp.rho[0, s_] @ S) for s_ in range(2))
+    assert abs(tr - 30.0) <= 1e-10 * 30.0
+
+
+def test_energy_density_matrix_chain_closed_form():
+    """S = I chain: E = C diag(g_s f eps) C^T with the sine eigenvectors and cosine
+    eigenvalues of the closed form; tr(E S) = sum g_s f eps."""
+    n, e0, t, kT = 30, 0.3, -1.0, 0.05
+    H, S = I.chain(n, e0, t)
+    res = O.solve(H[None], S[None], kT, 22.0)
+    j = np.arange(1, n + 1)
+    eps = e0 + 2 * t * np.cos(j * np.pi / (n + 1))
+    V = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(j, j) * np.pi / (n + 1))
+    f = O.fermi((eps - res.mu) / kT)
+    ref = (V * (2.0 * f * eps)[None, :]) @ V.T
+    E = O.energy_density_matrix(res.C[0], res.occ[0], res.eps[0], 2.0)
+    assert np.abs(E - ref).max() <= 1e-12
+    assert abs(np.trace(E @ S) - np.sum(2.0 * f * eps)) <= 1e-12 * n
