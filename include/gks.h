@@ -69,6 +69,18 @@ typedef enum { GKS_FP64 = 0, GKS_MIXED_TF32 = 1, GKS_MIXED_SPLITBF16 = 2 } gks_p
  * n_ev = 0 only (noncollinear: GKS_ENOTIMPL). */
 typedef enum { GKS_REDUCE_CHOLESKY = 0, GKS_REDUCE_LOWDIN = 1 } gks_reduction;
 
+/* Reduction of H' to real tridiagonal form.  GKS_TRIDIAG_ONE_STAGE: Householder steps whose
+ * rank-2 updates are deferred over panels and applied as tensor-core products (the
+ * matrix-vector half runs on the FP64 pipe).  GKS_TRIDIAG_TWO_STAGE (paper Sec. 6: the
+ * one-stage reduction is matrix-vector bound): dense -> band of width opts.band by panel QR
+ * with two-sided updates as tensor-core products, band -> tridiagonal by a persistent
+ * bulge-chasing kernel (bounded waits), and the back-transform applies the chase's
+ * reflectors (Q2, compact-WY blocks in wavefronts) and the panels' (Q1) as products.  Its
+ * back-transforms cost more than the one-stage one, so it pays when only the lowest n_ev
+ * eigenvectors are needed.  Not combined with GKS_MIXED_SPLITBF16 (which keeps the
+ * one-stage single-precision reduction). */
+typedef enum { GKS_TRIDIAG_ONE_STAGE = 0, GKS_TRIDIAG_TWO_STAGE = 1 } gks_tridiag;
+
 /* gks_solve flags. */
 enum {
   /* Skip the copy and Cholesky of S: reuse the factor kept from the last solve on this
@@ -107,10 +119,12 @@ typedef struct {
   int block;           /* outer block width of the two-level blocked Cholesky, reduction and
                           back-transforms: a multiple of 64 in 64..1024; 0 = 512 for orders
                           from 4096 up and 256 below (gks_tune overrides per shape class) */
-  int refine_sweeps;   /* GKS_MIXED_SPLITBF16: refinement sweeps, 1..8 (0 = 4).  From the
+  int refine_sweeps;   /* GKS_MIXED_SPLITBF16: refinement sweeps, 1..8 (0 = 6).  From the
                           single-precision start the eigenvector error is about
-                          u32 ||H'|| / gap, up to 1e-2 on the Si Gaussian basis, so the first
-                          sweeps contract slowly; four reach the FP64 floor there */
+                          u32 ||H'|| / gap, up to 1e-2 on the Si Gaussian basis; pairs closer
+                          than the sweep's cluster threshold are only orthonormalized and get
+                          resolved in a later sweep, so the defect can rise once before it
+                          falls to the FP64 floor (six sweeps on the 512-atom k-batch) */
   int n_ev;            /* eigenvectors computed per item: the lowest n_ev (0 = all M).  With
                           0 < n_ev < M, C is (nk, M, n_ev) and the back-transforms and the
                           density matrix touch only those columns (paper Sec. 6: a quarter to
@@ -124,6 +138,8 @@ typedef struct {
                           by gks_tune and gks_tune_set; NULL = none.  The string is copied. */
   int debug;           /* test hooks, GKS_DEBUG_* (0 = none) */
   int reduction;       /* gks_reduction: how H C = S C eps becomes a standard problem */
+  int tridiag;         /* gks_tridiag */
+  int band;            /* two-stage bandwidth, 2..32 (0 = 32) */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */
@@ -343,6 +359,20 @@ gks_status gks_potrf(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype)
 /* In place: H_b <- L_b^-1 H_b L_b^-H (lower triangle written; upper untouched), with L_b
  * the Cholesky factor of S_b.  S_b is overwritten by L_b. */
 gks_status gks_reduce(gks_ctx* ctx, void* H, void* S, int64_t m, int64_t count, int dtype);
+
+/* Stage 1 of the two-stage reduction (dense -> band of width `band`, 2..32): A (count, m, m),
+ * Hermitian, lower triangle read, is replaced by the band matrix B = Q1^H A Q1 in full
+ * Hermitian storage (zero outside the band); Q (count, m, m) receives Q1 (NULL: not formed).
+ * Reflectors follow LAPACK's zlarfg convention (complex tau, real beta). */
+gks_status gks_he2hb(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype, int band, void* Q);
+
+/* Stage 2 of the two-stage reduction (band -> tridiagonal by bulge chasing): B (count, m, m)
+ * Hermitian band of width `band` (lower band read), d (count, m) and e (count, m) receive
+ * the real tridiagonal T = Q2^H B Q2 (e[b][i] = T_{i+1,i}, last entry 0); X (count, m, ncols)
+ * is replaced by Q2 X (NULL or ncols = 0: not applied).  The chase is a persistent kernel
+ * whose waits are bounded by opts.wait_limit (GKS_ETIMEOUT from gks_sync). */
+gks_status gks_hb2st(gks_ctx* ctx, const void* B, int64_t m, int64_t count, int dtype, int band, double* d, double* e,
+                     void* X, int64_t ncols);
 
 /* Real symmetric tridiagonal eigensolve by divide and conquer: d (count, m) diagonal,
  * e (count, m) with e[b][i] = T_{i+1,i} (last entry ignored); lam (count, m) ascending,

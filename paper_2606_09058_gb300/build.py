@@ -17,7 +17,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gemm.cu", "dense.cu", "hetrd.cu", "stedc.cu", "occ.cu", "adjoint.cu", "ozaki.cu", "peaks.cu", "refine.cu", "api.cu"]
+SOURCES = ["gemm.cu", "dense.cu", "hetrd.cu", "stedc.cu", "occ.cu", "adjoint.cu", "ozaki.cu", "peaks.cu", "refine.cu", "sbr.cu", "api.cu"]
 
 
 def _nvcc() -> str:

@@ -112,8 +112,11 @@ struct gks_ctx {
   long long wait_cycles = 1ll << 32;   // bound of every device-side wait (opts.wait_limit)
   int n_ev = 0;                        // eigenvectors per item (0 = all)
   int reduction = GKS_REDUCE_CHOLESKY; // Cholesky or Loewdin reduction to the standard problem
+  int tridiag = GKS_TRIDIAG_ONE_STAGE;  // one-stage panel Householder or two-stage (band + chase)
+  int band = 32;                        // bandwidth of the two-stage reduction
+  int wstwo = 0;                        // workspace holds the two-stage buffers
   int precision = GKS_FP64;
-  int refine_sweeps = 4;
+  int refine_sweeps = 6;
   int debug = 0;                       // test hooks (GKS_DEBUG_*)
   std::string tune_cache;              // file of tuned widths (opts.autotune_cache)
   // Cholesky factor kept in the L workspace from the solve that produced it
@@ -140,7 +143,9 @@ struct gks_ctx {
   int am = -1, ank = -1, aes = -1;
   // offsets (bytes) of per-item arrays; each holds nk items
   size_t oA, oL, oF, oFB, oU, oQ, opart, oy, ouw, oSg, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho,
-      oweights, oeb, odc, oticket, oAf, oRY, oRT, oRR, onrm, orstat, operm, oflag;
+      oweights, oeb, odc, oticket, oAf, oRY, oRT, oRR, onrm, orstat, operm, oflag, oBd, oV2, otau2, oprog, oerr,
+      otau1, oT1, oP1, oP2, oVT, oXb, oGb, oYb, oZb, oXp, oVw, otw, oGw, oTw, oYw, oY2w;
+  int ldt2 = 0, nblkmax = 0;
   long long sMM, sF, sFB, sU, spart, sy, sV, sG, sT, sY, sVec;
 };
 
@@ -246,8 +251,9 @@ int shape_spin(int spin) { return spin == GKS_NONCOLLINEAR ? 1 : 0; }
 gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   const int want = pick_width(c, m, es, shape_spin(nc));
   const int mixed = c->precision != GKS_FP64 ? 1 : 0;
+  const int two = c->tridiag == GKS_TRIDIAG_TWO_STAGE ? c->band : 0;
   if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc && c->nbb == want &&
-      c->wsmixed == mixed)
+      c->wsmixed == mixed && c->wstwo == two)
     return GKS_OK;
   release_ws(c);
   c->nbb = want;
@@ -297,6 +303,34 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->oticket = a.take<int>((size_t)2 * nk);
   c->dc = dc_plan_create(m, nk);
   c->odc = a.take<char>(dc_workspace_bytes(c->dc));
+  if (two) {
+    // two-stage: band storage, the chase's reflectors and progress counters, the panel
+    // buffers of stage 1, the padded copy of X and the wavefront buffers of Q2
+    const int bb = two, W = 2 * bb + 1, hp = 2 * bb;
+    c->ldt2 = (m + bb - 1) / bb + 2;
+    c->nblkmax = m / (2 * bb) + 3;
+    c->oBd = a.take<char>(elems((long long)m * W));
+    c->oV2 = a.take<char>(elems(c->sMM));
+    c->otau2 = a.take<char>(elems((long long)m * c->ldt2));
+    c->oprog = a.take<int>((size_t)m * nk);
+    c->oerr = a.take<int>(4);
+    c->otau1 = a.take<char>(elems((long long)m + bb));
+    c->oT1 = a.take<char>(elems((long long)(m / bb + 2) * bb * bb));
+    c->oP1 = a.take<char>(elems((long long)m * 2 * bb));
+    c->oP2 = a.take<char>(elems((long long)m * 2 * bb));
+    c->oVT = a.take<char>(elems((long long)m * bb));
+    c->oXb = a.take<char>(elems((long long)m * bb));
+    c->oGb = a.take<char>(elems((long long)bb * bb));
+    c->oYb = a.take<char>(elems((long long)bb * bb));
+    c->oZb = a.take<char>(elems((long long)bb * bb));
+    c->oXp = a.take<char>(elems((long long)(m + hp) * m));
+    c->oVw = a.take<char>(elems((long long)c->nblkmax * hp * bb));
+    c->otw = a.take<char>(elems((long long)c->nblkmax * bb));
+    c->oGw = a.take<char>(elems((long long)c->nblkmax * bb * bb));
+    c->oTw = a.take<char>(elems((long long)c->nblkmax * bb * bb));
+    c->oYw = a.take<char>(elems((long long)c->nblkmax * m * bb));
+    c->oY2w = a.take<char>(elems((long long)c->nblkmax * m * bb));
+  }
   if (mixed) {
     // single-precision copy of H' for the tridiagonalization, refinement products Y, T, R,
     // the per-item norms, and the reordering buffers
@@ -324,6 +358,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   }
   cudaMemset(c->st, 0, sizeof(DevStatus) * nk);
   c->wsmixed = mixed;
+  c->wstwo = two;
   c->m = m;
   c->n = n;
   c->nk = nk;
@@ -508,6 +543,44 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
              lower);
   }
   }
+}
+
+// gmx for a two-level batch: item z of A, B, C at (z / nb2) sX + (z % nb2) sX2.
+template <typename T>
+void gmx2(gks_ctx* c, int count, int nb2, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda,
+          long long sA, long long sA2, const T* B, int ldb, long long sB, long long sB2, double beta, T* C, int ldc,
+          long long sC, long long sC2) {
+  if (M <= 0 || N <= 0 || count <= 0) return;
+  const int es = sizeof(T);
+  const double fl = gemm_flops(es, M, N, K, 0, count);
+  const int per = split_worth(c, count, M, N, K, es, fl)
+                      ? oz_reserve(c, ozaki_workspace_bytes(M, N, K, es == 16, c->slices), count)
+                      : 0;
+  if (per >= count) {
+    Rec r(c, PC_OZAKI, fl, gemm_bytes(es, M, N, K, 0, count, beta != 0.0));
+    if (ozaki_gemm<T>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, count, 0, c->slices, c->oz,
+                      c->st ? c->st : c->gst, c->stream, nullptr, 0, nullptr, c->wait_cycles, -1, sA2, sB2, sC2,
+                      nb2))
+      return;
+  }
+  // the FP64 kernel (small products, or a batch beyond one launch's digit workspace)
+  int tok = c->prof.begin();
+  GemmBatch g{};
+  g.base = GemmDesc{A, B, C, nullptr, M, N, K, lda, ldb, ldc};
+  g.sA = sA;
+  g.sB = sB;
+  g.sC = sC;
+  g.nb2 = nb2;
+  g.sA2 = sA2;
+  g.sB2 = sB2;
+  g.sC2 = sC2;
+  g.count = count;
+  g.opA = opA;
+  g.opB = opB;
+  g.alpha = alpha;
+  g.beta = beta;
+  gemm<T>(g, M, N, c->stream);
+  c->prof.end(tok, PC_GEMM, fl, gemm_bytes(es, M, N, K, 0, count, beta != 0.0));
 }
 
 // rho_k = C_k diag(ks_k) C_k^H over the leading n_rho(k) columns (n_rho read on the device),
@@ -830,6 +903,174 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   }
 }
 
+// ---- two-stage tridiagonalization (sbr.cu) ----
+
+// (a3) Dense -> band, bandwidth b = c->band, for the Hermitian A (lower triangle in, made
+// full here; full storage kept up to date for the products).  Panel p (columns k = p b ..)
+// leaves R in the band, its reflectors below the band, taus in tau1, T factor in T1[p].
+template <typename T>
+void he2hb_run(gks_ctx* c, T* A, int M, int items) {
+  cudaStream_t s = c->stream;
+  const int b = c->band, b2 = 2 * b;
+  const long long MM = c->sMM, sP = (long long)M * b2, sX = (long long)M * b, sb = (long long)b * b;
+  const long long stau = (long long)M + b, sT1 = (long long)(M / b + 2) * b * b;
+  T* tau1 = at<T>(c, c->otau1);
+  T* T1 = at<T>(c, c->oT1);
+  T* P1 = at<T>(c, c->oP1);
+  T* P2 = at<T>(c, c->oP2);
+  T* VT = at<T>(c, c->oVT);
+  T* Xb = at<T>(c, c->oXb);
+  T* Gb = at<T>(c, c->oGb);
+  T* Yb = at<T>(c, c->oYb);
+  T* Zb = at<T>(c, c->oZb);
+  {
+    Rec r(c, PC_MISC);
+    mirror_lower<T>(A, M, MM, M, items, s);
+  }
+  for (int k = 0, p = 0; k < M - b - 1; k += b, p++) {
+    const int r0 = k + b, kb = std::min(b, M - b - 1 - k), m = M - r0;
+    T* A22 = A + (size_t)r0 * M + r0;
+    T* Tp = T1 + (size_t)p * b * b;
+    {
+      Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * sizeof(T) * (double)m * b * kb * items);
+      panel_qr<T>(A, M, MM, r0, k, m, b, kb, tau1 + (size_t)p * b, stau, items, s);
+      panel_v<T>(A, M, MM, r0, k, m, kb, P1, b2, sP, items, s);
+    }
+    gmx<T>(c, items, OP_C, OP_N, kb, kb, m, 1.0, P1, b2, sP, P1, b2, sP, 0.0, Gb, b, sb);  // G = V^H V
+    {
+      Rec r(c, PC_BACKTR_AUX);
+      larft_tau<T>(Gb, b, sb, tau1 + (size_t)p * b, stau, kb, Tp, b, sT1, items, s);
+    }
+    gmx<T>(c, items, OP_N, OP_N, m, kb, kb, 1.0, P1, b2, sP, Tp, b, sT1, 0.0, VT, b, sX);        // V T
+    gmx<T>(c, items, OP_N, OP_N, m, kb, m, 1.0, A22, M, MM, VT, b, sX, 0.0, Xb, b, sX);         // X = A22 V T
+    gmx<T>(c, items, OP_C, OP_N, kb, kb, m, 1.0, P1, b2, sP, Xb, b, sX, 0.0, Yb, b, sb);        // V^H X
+    gmx<T>(c, items, OP_C, OP_N, kb, kb, kb, 1.0, Tp, b, sT1, Yb, b, sb, 0.0, Zb, b, sb);       // T^H V^H X
+    gmx<T>(c, items, OP_N, OP_N, m, kb, kb, -0.5, P1, b2, sP, Zb, b, sb, 1.0, Xb, b, sX);       // W
+    {
+      Rec r(c, PC_MISC);  // P1 = [V W], P2 = [W V] (kb columns each)
+      copy2d<T>(P1 + kb, b2, sP, Xb, b, sX, m, kb, items, s);
+      copy2d<T>(P2, b2, sP, Xb, b, sX, m, kb, items, s);
+      copy2d<T>(P2 + kb, b2, sP, P1, b2, sP, m, kb, items, s);
+    }
+    // A22 -= V W^H + W V^H = [V W] [W V]^H (lower triangle), then made full again
+    gmx<T>(c, items, OP_N, OP_C, m, m, 2 * kb, -1.0, P1, b2, sP, P2, b2, sP, 1.0, A22, M, MM, 1);
+    Rec r(c, PC_MISC);
+    mirror_lower<T>(A22, M, MM, m, items, s);
+  }
+}
+
+// (a4) Band -> tridiagonal by bulge chasing: the band of A (d <= b below the diagonal) into
+// the band storage, the persistent chase, then d and e (real).  False if the cooperative
+// launch was refused.
+template <typename T>
+bool hb2st_run(gks_ctx* c, const T* A, int M, int items, double* d, double* e) {
+  cudaStream_t s = c->stream;
+  const int b = c->band, W = 2 * b + 1;
+  const long long sB = (long long)M * W;
+  T* Bd = at<T>(c, c->oBd);
+  {
+    Rec r(c, PC_MISC);
+    band_pack<T>(A, M, c->sMM, Bd, W, sB, M, b, items, s);
+  }
+  const int workers = chase_workers<T>(b, items, 64);
+  {
+    const double tasks = 0.5 * (double)M * M / b;
+    Rec r(c, PC_HETRD_RANK2, cmul(sizeof(T)) * 8.0 * b * b * tasks * items, sizeof(T) * 6.0 * b * b * tasks * items);
+    if (!chase<T>(Bd, W, sB, M, b, at<T>(c, c->oV2), c->sMM, at<T>(c, c->otau2), c->ldt2, (long long)M * c->ldt2,
+                  at<int>(c, c->oprog), M, at<int>(c, c->oerr), c->st, c->wait_cycles, items, workers, s)) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  Rec r(c, PC_HETRD_VEC);
+  band_tridiag<T>(Bd, W, sB, M, d, e, M, items, s);
+  return true;
+}
+
+// X <- Q2 X for the padded Xp (rows M + 2b, ncols columns, ld ncols): the chase's
+// reflectors in compact-WY blocks of b consecutive sweeps x one window, applied wavefront
+// by wavefront (blocks of one wavefront touch disjoint rows; see sbr.cu), each wavefront as
+// three two-level batched products over items x blocks.
+template <typename T>
+void q2_apply_run(gks_ctx* c, T* Xp, long long sXp, int M, int ncols, int items) {
+  cudaStream_t s = c->stream;
+  const int b = c->band, nbs = b, hp = 2 * b;
+  const int nsweep = M - 1;
+  if (nsweep < 1) return;
+  const int G = (nsweep + nbs - 1) / nbs;
+  auto J = [&](int g) { return (M - 2 - g * nbs) / b + 1; };  // windows of the group's first sweep
+  T* Vw = at<T>(c, c->oVw);
+  T* tw = at<T>(c, c->otw);
+  T* Gw = at<T>(c, c->oGw);
+  T* Tw = at<T>(c, c->oTw);
+  T* Yw = at<T>(c, c->oYw);
+  T* Y2w = at<T>(c, c->oY2w);
+  for (int t = 0;; t++) {
+    const int g_lo = std::max(0, (2 * (G - 1) - t + 1) / 2);
+    int nblk = 0;
+    for (int g = g_lo; g < G; g++) {
+      const int j = t - 2 * (G - 1 - g);
+      if (j < 0 || j >= J(g)) break;
+      nblk++;
+    }
+    if (nblk == 0) {
+      if (g_lo == 0) break;
+      continue;
+    }
+    nblk = std::min(nblk, c->nblkmax);
+    const int j0 = t - 2 * (G - 1 - g_lo);
+    const long long top0 = (long long)g_lo * nbs + 1 + (long long)j0 * b;
+    const int cnt = items * nblk;
+    {
+      Rec r(c, PC_BACKTR_AUX);
+      q2_gather<T>(at<T>(c, c->oV2), c->sMM, at<T>(c, c->otau2), c->ldt2, (long long)M * c->ldt2, M, b, nbs, hp, g_lo,
+                   j0, nblk, Vw, tw, items, s);
+    }
+    gmx<T>(c, cnt, OP_C, OP_N, nbs, nbs, hp, 1.0, Vw, nbs, (long long)hp * nbs, Vw, nbs, (long long)hp * nbs, 0.0,
+           Gw, nbs, (long long)nbs * nbs);
+    {
+      Rec r(c, PC_BACKTR_AUX);
+      larft_tau<T>(Gw, nbs, (long long)nbs * nbs, tw, nbs, nbs, Tw, nbs, (long long)nbs * nbs, cnt, s);
+    }
+    T* X0 = Xp + top0 * ncols;
+    const long long s3 = 3LL * b * ncols;  // row step between the blocks of a wavefront
+    gmx2<T>(c, cnt, nblk, OP_C, OP_N, ncols, nbs, hp, 1.0, X0, ncols, sXp, s3, Vw, nbs,
+            (long long)nblk * hp * nbs, (long long)hp * nbs, 0.0, Yw, nbs, (long long)nblk * ncols * nbs,
+            (long long)ncols * nbs);                                                          // Yh = X^H V
+    gmx<T>(c, cnt, OP_N, OP_C, ncols, nbs, nbs, 1.0, Yw, nbs, (long long)ncols * nbs, Tw, nbs, (long long)nbs * nbs,
+           0.0, Y2w, nbs, (long long)ncols * nbs);                                            // Yh T^H
+    gmx2<T>(c, cnt, nblk, OP_N, OP_C, hp, ncols, nbs, -1.0, Vw, nbs, (long long)nblk * hp * nbs,
+            (long long)hp * nbs, Y2w, nbs, (long long)nblk * ncols * nbs, (long long)ncols * nbs, 1.0, X0, ncols, sXp,
+            s3);                                                                              // X -= V Y
+  }
+}
+
+// X <- Q1 X (X: M x ncols, ldx, sX): the panels' compact-WY factors, last panel first.
+template <typename T>
+void q1_apply_run(gks_ctx* c, const T* A, T* X, int ldx, long long sX, int M, int ncols, int items) {
+  cudaStream_t s = c->stream;
+  const int b = c->band, b2 = 2 * b;
+  const long long sP = (long long)M * b2, sT1 = (long long)(M / b + 2) * b * b;
+  T* P1 = at<T>(c, c->oP1);
+  T* T1 = at<T>(c, c->oT1);
+  T* Yw = at<T>(c, c->oYw);
+  T* Y2w = at<T>(c, c->oY2w);
+  const long long sY = (long long)ncols * b;
+  int np = 0;
+  for (int k = 0; k < M - b - 1; k += b) np++;
+  for (int p = np - 1; p >= 0; p--) {
+    const int k = p * b, r0 = k + b, kb = std::min(b, M - b - 1 - k), m = M - r0;
+    {
+      Rec r(c, PC_BACKTR_AUX);
+      panel_v<T>(A, M, c->sMM, r0, k, m, kb, P1, b2, sP, items, s);
+    }
+    T* Xr = X + (size_t)r0 * ldx;
+    gmx<T>(c, items, OP_C, OP_N, ncols, kb, m, 1.0, Xr, ldx, sX, P1, b2, sP, 0.0, Yw, b, sY);        // X^H V
+    gmx<T>(c, items, OP_N, OP_C, ncols, kb, kb, 1.0, Yw, b, sY, T1 + (size_t)p * b * b, b, sT1, 0.0, Y2w, b, sY);
+    gmx<T>(c, items, OP_N, OP_C, m, ncols, kb, -1.0, P1, b2, sP, Y2w, b, sY, 1.0, Xr, ldx, sX);     // X -= V Y
+  }
+}
+
 // X <- Q X with Q = P_{M-1} ... P_2 (reflectors stored by the reduction), compact WY in
 // blocks of nbb reflectors: B = I - V T V^H.  X is M x ncols (ldx, sX).  T (upper
 // triangular) is assembled from the 64-wide diagonal blocks (larft on G = V^H V) by the merge
@@ -1051,6 +1292,7 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
   double* e = at<double>(c, c->oe);
   T* ph = at<T>(c, c->oph);
   const bool mixed = c->precision == GKS_MIXED_SPLITBF16;
+  const bool two = !mixed && c->tridiag == GKS_TRIDIAG_TWO_STAGE;
   using TL = typename Low<T>::type;
   TL* Af = mixed ? at<TL>(c, c->oAf) : nullptr;
   {
@@ -1067,6 +1309,11 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
       TL* phl = at<TL>(c, c->ou);
       hetrd_finish<TL>(Af, M, c->sMM, M, d, e, M, phl, M, items, s);
       widen_copy<TL, T>(phl, ph, (long long)M * items, s);
+    } else if (two) {
+      // (a3) dense -> band, (a4) band -> tridiagonal (real: the chase's betas are real)
+      he2hb_run<T>(c, A, M, items);
+      if (!hb2st_run<T>(c, A, M, items, d, e))
+        return fail(c, GKS_ECUDA, "bulge chasing: cooperative launch refused (not enough resident CTAs)");
     } else {
       hetrd_run<T>(c, A, M, items);
       Rec r(c, PC_HETRD_VEC);
@@ -1090,11 +1337,25 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
   // (a6) X = Q D Z (the leading nev columns), C = L^-H X
   {
     StageRec sr(c, PS_BACKTR);
-    {
+    if (!two) {
       Rec r(c, PC_MISC);
       apply_phase<T>(C, nev, sC, Z, M, c->sMM, ph, M, M, nev, items, s);
     }
-    if (mixed) {
+    if (two) {
+      // X = Q1 Q2 Z: Z into the padded buffer, Q2 there, then Q1 on the output
+      T* Xp = at<T>(c, c->oXp);
+      const long long sXp = (long long)(M + 2 * c->band) * nev;
+      {
+        Rec r(c, PC_MISC);
+        widen_pad<T>(Z, M, c->sMM, Xp, nev, sXp, M, M + 2 * c->band, nev, items, s);
+      }
+      q2_apply_run<T>(c, Xp, sXp, M, nev, items);
+      {
+        Rec r(c, PC_MISC);
+        copy2d<T>(C, nev, sC, Xp, nev, sXp, M, nev, items, s);
+      }
+      q1_apply_run<T>(c, A, C, nev, sC, M, nev, items);
+    } else if (mixed) {
       // single-precision reflectors, products on fewer digits (about FP32 accuracy)
       const int sv = c->slices;
       c->slices = std::min(sv, kLowSlices);
@@ -1382,12 +1643,16 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     if (opts->refine_sweeps > 0) c->refine_sweeps = opts->refine_sweeps;
     c->n_ev = opts->n_ev;
     c->reduction = opts->reduction;
+    c->tridiag = opts->tridiag;
+    if (opts->band > 0) c->band = opts->band;
     if (opts->wait_limit > 0) c->wait_cycles = opts->wait_limit;
     c->debug = opts->debug;
     if (opts->autotune_cache) c->tune_cache = opts->autotune_cache;
     if (c->gemm_mode < 0 || c->gemm_mode > 2 || c->slices < 4 || c->slices > 10 || c->nbb < NB || c->nbb > 1024 ||
         c->nbb % NB || c->n_ev < 0 || opts->refine_sweeps < 0 || opts->refine_sweeps > 8 || opts->wait_limit < 0 ||
         (c->reduction != GKS_REDUCE_CHOLESKY && c->reduction != GKS_REDUCE_LOWDIN) ||
+        (c->tridiag != GKS_TRIDIAG_ONE_STAGE && c->tridiag != GKS_TRIDIAG_TWO_STAGE) || c->band < 2 ||
+        c->band > 32 ||
         (opts->debug & ~GKS_DEBUG_SKIP_COPY)) {
       delete c;
       return GKS_EINVAL;
@@ -1513,6 +1778,8 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     sc->precision = ctx->precision;
     sc->refine_sweeps = ctx->refine_sweeps;
     sc->reduction = ctx->reduction;
+    sc->tridiag = ctx->tridiag;
+    sc->band = ctx->band;
     ctx->subs.push_back(sc);
   }
   for (auto* sc : ctx->subs) sc->tuned = ctx->tuned;
@@ -2014,6 +2281,95 @@ gks_status gks_reduce(gks_ctx* ctx, void* H, void* S, int64_t m, int64_t count, 
     return fail(ctx, GKS_EINVAL, "unknown dtype");
   }
   return cuda_check(ctx, "gks_reduce");
+}
+
+}  // extern "C"
+
+namespace {
+// Temporarily select the two-stage path with bandwidth `band` on a context (stage entries).
+struct TwoStageScope {
+  gks_ctx* c;
+  int tri, band;
+  TwoStageScope(gks_ctx* c_, int b) : c(c_), tri(c_->tridiag), band(c_->band) {
+    c->tridiag = GKS_TRIDIAG_TWO_STAGE;
+    c->band = b;
+  }
+  ~TwoStageScope() {
+    c->tridiag = tri;
+    c->band = band;
+  }
+};
+
+template <typename T>
+void identity_fill(T* Q, int m, int count, cudaStream_t s) {
+  cudaMemsetAsync(Q, 0, sizeof(T) * (size_t)m * m * count, s);
+  T one = from_real<T>(1.0);
+  for (int z = 0; z < count; z++)
+    for (int i = 0; i < m; i++)
+      cudaMemcpyAsync(Q + ((size_t)z * m + i) * m + i, &one, sizeof(T), cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+}
+
+template <typename T>
+gks_status he2hb_t(gks_ctx* c, T* A, int m, int count, T* Q) {
+  he2hb_run<T>(c, A, m, count);
+  if (Q) {
+    identity_fill<T>(Q, m, count, c->stream);
+    q1_apply_run<T>(c, A, Q, m, (long long)m * m, m, m, count);
+  }
+  const int W = 2 * c->band + 1;
+  T* Bd = at<T>(c, c->oBd);
+  band_pack<T>(A, m, c->sMM, Bd, W, (long long)m * W, m, c->band, count, c->stream);
+  band_unpack<T>(Bd, W, (long long)m * W, A, m, c->sMM, m, count, c->stream);
+  return cuda_check(c, "gks_he2hb");
+}
+
+template <typename T>
+gks_status hb2st_t(gks_ctx* c, const T* B, int m, int count, double* d, double* e, T* X, int ncols) {
+  if (!hb2st_run<T>(c, B, m, count, d, e))
+    return fail(c, GKS_ECUDA, "bulge chasing: cooperative launch refused (not enough resident CTAs)");
+  if (X && ncols > 0) {
+    T* Xp = at<T>(c, c->oXp);
+    const long long sXp = (long long)(m + 2 * c->band) * ncols;
+    cudaMemsetAsync(Xp, 0, sizeof(T) * sXp * count, c->stream);
+    copy2d<T>(Xp, ncols, sXp, X, ncols, (long long)m * ncols, m, ncols, count, c->stream);
+    q2_apply_run<T>(c, Xp, sXp, m, ncols, count);
+    copy2d<T>(X, ncols, (long long)m * ncols, Xp, ncols, sXp, m, ncols, count, c->stream);
+  }
+  return cuda_check(c, "gks_hb2st");
+}
+}  // namespace
+
+extern "C" {
+
+gks_status gks_he2hb(gks_ctx* ctx, void* A, int64_t m, int64_t count, int dtype, int band, void* Q) {
+  if (!ctx || !A || m < 2 || count < 1 || m > 46340 || band < 2 || band > 32) return fail(ctx, GKS_EINVAL, "bad arguments");
+  if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
+  DeviceGuard dg(ctx->device);
+  TwoStageScope ts(ctx, band);
+  const int es = dtype == GKS_C128 ? 16 : 8;
+  gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, es, 0);
+  if (rc) return rc;
+  cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
+  if (dtype == GKS_R64) return he2hb_t<double>(ctx, static_cast<double*>(A), (int)m, (int)count, static_cast<double*>(Q));
+  return he2hb_t<zc>(ctx, static_cast<zc*>(A), (int)m, (int)count, static_cast<zc*>(Q));
+}
+
+gks_status gks_hb2st(gks_ctx* ctx, const void* B, int64_t m, int64_t count, int dtype, int band, double* d, double* e,
+                     void* X, int64_t ncols) {
+  if (!ctx || !B || !d || !e || m < 2 || count < 1 || m > 46340 || band < 2 || band > 32 || ncols < 0 || ncols > m)
+    return fail(ctx, GKS_EINVAL, "bad arguments");
+  if (dtype != GKS_R64 && dtype != GKS_C128) return fail(ctx, GKS_EINVAL, "unknown dtype");
+  DeviceGuard dg(ctx->device);
+  TwoStageScope ts(ctx, band);
+  const int es = dtype == GKS_C128 ? 16 : 8;
+  gks_status rc = ensure_ws(ctx, (int)m, (int)m, (int)count, es, 0);
+  if (rc) return rc;
+  cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus) * count, ctx->stream);
+  if (dtype == GKS_R64)
+    return hb2st_t<double>(ctx, static_cast<const double*>(B), (int)m, (int)count, d, e, static_cast<double*>(X),
+                           (int)ncols);
+  return hb2st_t<zc>(ctx, static_cast<const zc*>(B), (int)m, (int)count, d, e, static_cast<zc*>(X), (int)ncols);
 }
 
 gks_status gks_stedc(gks_ctx* ctx, const double* d, const double* e, int64_t m, int64_t count, double* lam,

@@ -118,12 +118,52 @@ template <typename T>
 bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
                 int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
                 void* work, DevStatus* status, cudaStream_t s, const double* kscale = nullptr, long long sks = 0,
-                const int* kdev = nullptr, long long wait_cycles = 0, long long skip_copy = -1);
+                const int* kdev = nullptr, long long wait_cycles = 0, long long skip_copy = -1, long long sA2 = 0,
+                long long sB2 = 0, long long sC2 = 0, int nb2 = 0);
 
 // ---- FP64 unit throughput probes (peaks.cu) ----
 // which 0: DFMA, 1: DMMA (mma.sync f64).  Enqueues one probe on sms x 4 CTAs and returns
 // the flops it executes; `out` needs sms * 1024 doubles.
 double peak_probe(int which, int sms, long long iters, double* out, cudaStream_t s);
+
+// ---- two-stage tridiagonalization (sbr.cu) ----
+// Stage 1: in-place QR of the panel A[r0:r0+m, k:k+b] (kb reflectors, complex tau, real
+// beta; v below the diagonal), its unit lower trapezoidal V (m x kb), and the T factor of
+// H_0 .. H_{k-1} = I - V T V^H from G = V^H V.
+template <typename T>
+void panel_qr(T* A, int lda, long long sA, int r0, int k, int m, int b, int kb, T* taus, long long stau, int count,
+              cudaStream_t s);
+template <typename T>
+void panel_v(const T* A, int lda, long long sA, int r0, int k, int m, int kb, T* V, int ldv, long long sV, int count,
+             cudaStream_t s);
+template <typename T>
+void panel_clear(T* A, int lda, long long sA, int r0, int k, int m, int kb, int count, cudaStream_t s);
+template <typename T>
+void larft_tau(const T* G, int ldG, long long sG, const T* tau, long long stau, int k, T* Tm, int ldT, long long sT,
+               int count, cudaStream_t s);
+// Band storage Bd[j W + d] = T[j+d][j] (W = 2b + 1, room for the bulges of stage 2).
+template <typename T>
+void band_pack(const T* A, int lda, long long sA, T* Bd, int W, long long sB, int m, int b, int count, cudaStream_t s);
+template <typename T>
+void band_unpack(const T* Bd, int W, long long sB, T* A, int lda, long long sA, int m, int count, cudaStream_t s);
+// Stage 2: persistent bulge chasing (cooperative launch of `workers` CTAs per item, see
+// chase_workers); reflector (sweep i, window j) in V2[i m + j b ..], tau2[i ldt + j].
+// Returns false if the launch was refused (then nothing ran).
+template <typename T>
+int chase_workers(int b, int items, int cap);
+template <typename T>
+bool chase(T* Bd, int W, long long sB, int m, int b, T* V2, long long sV2, T* tau2, int ldt, long long sT2, int* prog,
+           long long sprog, int* err, DevStatus* st, long long wait_limit, int items, int workers, cudaStream_t s);
+template <typename T>
+void band_tridiag(const T* Bd, int W, long long sB, int m, double* d, double* e, long long sde, int count,
+                  cudaStream_t s);
+// Q2 compact-WY blocks of one wavefront (see sbr.cu) into Vw (items x nblk x hp x nbs), tw.
+template <typename T>
+void q2_gather(const T* V2, long long sV2, const T* tau2, int ldt, long long sT2, int m, int b, int nbs, int hp, int g0,
+               int j0, int nblk, T* Vw, T* tw, int items, cudaStream_t s);
+template <typename T>
+void widen_pad(const double* Z, int ldz, long long sZ, T* X, int ldx, long long sX, int m, int rows, int cols,
+               int count, cudaStream_t s);
 
 // ---- Ogita-Aishima refinement (refine.cu) ----
 // Per item (stride sMM, order M, full storage): G = X^H X becomes R = I - X^H X, lam = the

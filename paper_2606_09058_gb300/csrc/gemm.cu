@@ -51,9 +51,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmBatch gb) {
     d = gb.list[z];
   } else {
     d = gb.base;
-    d.A = static_cast<const T*>(d.A) + z * gb.sA;
-    d.B = static_cast<const T*>(d.B) + z * gb.sB;
-    d.C = static_cast<T*>(d.C) + z * gb.sC;
+    d.A = static_cast<const T*>(d.A) + item_off(z, gb.sA, gb.sA2, gb.nb2);
+    d.B = static_cast<const T*>(d.B) + item_off(z, gb.sB, gb.sB2, gb.nb2);
+    d.C = static_cast<T*>(d.C) + item_off(z, gb.sC, gb.sC2, gb.nb2);
     if (d.kscale) d.kscale += z * gb.sK;
   }
   int K = d.K;

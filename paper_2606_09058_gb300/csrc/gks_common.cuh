@@ -163,6 +163,12 @@ __device__ T block_sum(T v, T* scratch) {
   return r;
 }
 
+// Offset of batch item z: z s1, or for a two-level batch (nb2 > 0 items per outer group)
+// (z / nb2) s1 + (z % nb2) s2.
+__host__ __device__ __forceinline__ long long item_off(int z, long long s1, long long s2, int nb2) {
+  return nb2 > 0 ? (long long)(z / nb2) * s1 + (long long)(z % nb2) * s2 : (long long)z * s1;
+}
+
 // ---- device status word (one per batch item) ----
 // Codes follow gks_status in the public header; info carries a column or iteration.
 struct DevStatus {

@@ -31,6 +31,8 @@ struct GemmBatch {
   int opA, opB;
   int lower;              // 1: only tiles/elements with row >= col are written
   double alpha, beta;
+  int nb2;                // > 0: two-level batch, item z at (z / nb2) sX + (z % nb2) sX2
+  long long sA2, sB2, sC2;
 };
 
 template <typename T> void gemm(const GemmBatch& b, int maxM, int maxN, cudaStream_t s);

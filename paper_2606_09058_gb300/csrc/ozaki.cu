@@ -100,11 +100,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long long sX, int role, int op, int nvec,
                                                        int K, __nv_bfloat16* D, int Kp, long long sstride,
                                                        long long sD, int S, int* ex, long long sE,
-                                                       const double* ksc, long long sks, const int* kdev) {
+                                                       const double* ksc, long long sks, const int* kdev,
+                                                       long long sX2, int nb2) {
   __shared__ double smax[32];
   __shared__ int sexp[32];
   const int v0 = blockIdx.x * 32, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  X += blockIdx.y * sX;
+  X += item_off(blockIdx.y, sX, sX2, nb2);
   D += blockIdx.y * sD;
   ex += blockIdx.y * sE;
   if (kdev) K = min(K, max(0, kdev[blockIdx.y]));
@@ -191,6 +192,8 @@ struct OzArgs {
   double alpha, beta;
   long long sAd, sBd;       // slice strides (elements)
   long long zAd, zBd, zEa, zEb, zC;  // batch item strides of the digits, exponents and C
+  long long zC2;            // two-level batch (nb2 > 0): C of item z at (z / nb2) zC + (z % nb2) zC2
+  int nb2;
   const int* kdev;          // optional per-item K read on the device (logical, <= K)
   long long wait;           // bound of every mbarrier wait, in SM clock cycles
   long long skip_copy;      // test hook: the producer leaves out this copy (-1 = none)
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
   const int* ea = a.ea + zz * a.zEa;
   const int* eb = a.eb + zz * a.zEb;
   if (a.cplx) {
-    zc* C = static_cast<zc*>(a.C) + zz * a.zC;
+    zc* C = static_cast<zc*>(a.C) + item_off(z, a.zC, a.zC2, a.nb2);
     const int j0 = n0 / 2 + ch * 32;
 #pragma unroll
     for (int jj = 0; jj < 32; jj++) {
@@ -520,7 +523,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
       *cp = v;
     }
   } else {
-    double* C = static_cast<double*>(a.C) + zz * a.zC;
+    double* C = static_cast<double*>(a.C) + item_off(z, a.zC, a.zC2, a.nb2);
     const int j0 = n0 + ch * 64;
 #pragma unroll
     for (int jj = 0; jj < 64; jj++) {
@@ -592,7 +595,8 @@ template <typename T>
 bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
                 int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
                 void* work, DevStatus* status, cudaStream_t s, const double* kscale, long long sks,
-                const int* kdev, long long wait_cycles, long long skip_copy) {
+                const int* kdev, long long wait_cycles, long long skip_copy, long long sA2, long long sB2,
+                long long sC2, int nb2) {
   if (M <= 0 || N <= 0 || count <= 0) return true;
   const bool cplx = sizeof(T) == 16;
   const int Kp = padded_k(K, cplx);
@@ -608,11 +612,11 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
     count_launch();
     oz_split_kernel<T><<<dim3((M + 31) / 32, count), 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp,
                                                                    (long long)Mp * Kp, zA, S, ea, Mp, kscale, sks,
-                                                                   kdev);
+                                                                   kdev, sA2, nb2);
     count_launch();
     oz_split_kernel<T><<<dim3((N + 31) / 32, count), 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp,
                                                                    (long long)Np * Kp, zB, S, eb, Np, nullptr, 0,
-                                                                   kdev);
+                                                                   kdev, sB2, nb2);
   }
   OzArgs oa;
   oa.Ad = Ad;
@@ -638,6 +642,8 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   oa.zEa = Mp;
   oa.zEb = Np;
   oa.zC = sC;
+  oa.zC2 = sC2;
+  oa.nb2 = nb2;
   oa.kdev = kdev;
   oa.wait = wait_cycles > 0 ? wait_cycles : (1ll << 32);
   oa.skip_copy = skip_copy;
@@ -653,9 +659,11 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
 
 template bool ozaki_gemm<double>(int, int, int, int, int, double, const double*, int, long long, const double*, int,
                                  long long, double, double*, int, long long, int, int, int, void*, DevStatus*,
-                                 cudaStream_t, const double*, long long, const int*, long long, long long);
+                                 cudaStream_t, const double*, long long, const int*, long long, long long,
+                                 long long, long long, long long, int);
 template bool ozaki_gemm<zc>(int, int, int, int, int, double, const zc*, int, long long, const zc*, int, long long,
                              double, zc*, int, long long, int, int, int, void*, DevStatus*, cudaStream_t,
-                             const double*, long long, const int*, long long, long long);
+                             const double*, long long, const int*, long long, long long, long long, long long,
+                             long long, int);
 
 }  // namespace gks

@@ -39,7 +39,8 @@ class _Opts(ctypes.Structure):
                 ("f_cut", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int),
                 ("gemm", ctypes.c_int), ("slices", ctypes.c_int), ("block", ctypes.c_int),
                 ("refine_sweeps", ctypes.c_int), ("n_ev", ctypes.c_int), ("wait_limit", ctypes.c_longlong),
-                ("autotune_cache", ctypes.c_char_p), ("debug", ctypes.c_int), ("reduction", ctypes.c_int)]
+                ("autotune_cache", ctypes.c_char_p), ("debug", ctypes.c_int), ("reduction", ctypes.c_int),
+                ("tridiag", ctypes.c_int), ("band", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -97,6 +98,10 @@ def load() -> ctypes.CDLL:
     lib.gks_occupy.restype = I
     lib.gks_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I]
     lib.gks_profile.restype = I
+    lib.gks_he2hb.argtypes = [P, P, I64, I64, I, I, P]
+    lib.gks_he2hb.restype = I
+    lib.gks_hb2st.argtypes = [P, P, I64, I64, I, I, P, P, P, I64]
+    lib.gks_hb2st.restype = I
     lib.gks_refine_stats.argtypes = [P, ctypes.POINTER(ctypes.c_double), I]
     lib.gks_refine_stats.restype = I
     lib.gks_measure_peak.argtypes = [P, I, ctypes.POINTER(ctypes.c_double)]
@@ -138,7 +143,7 @@ class Context:
                  profile: bool = False, graph: bool = False, gemm: str = "auto", slices: int = 0,
                  block: int = 0, precision: str = "fp64", refine_sweeps: int = 0, n_ev: int = 0,
                  wait_limit: int = 0, autotune_cache: str | None = None, debug: int = 0,
-                 reduction: str = "cholesky"):
+                 reduction: str = "cholesky", tridiag: str = "one_stage", band: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("gks needs a CUDA device")
         lib = load()
@@ -150,7 +155,8 @@ class Context:
         cache = autotune_cache.encode() if autotune_cache else None
         opts = _Opts(self.device, ctypes.c_void_p(self.stream.cuda_stream), _PREC[precision], f_cut,
                      1 if profile else 0, 1 if graph else 0, gm, int(slices), int(block), int(refine_sweeps),
-                     int(n_ev), int(wait_limit), cache, int(debug), {"cholesky": 0, "lowdin": 1}[reduction])
+                     int(n_ev), int(wait_limit), cache, int(debug), {"cholesky": 0, "lowdin": 1}[reduction],
+                     {"one_stage": 0, "two_stage": 1}[tridiag], int(band))
         h = ctypes.c_void_p()
         rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
         if rc:
@@ -412,6 +418,33 @@ class Context:
         self._raise(rc)
         self.sync()
         return H, S
+
+    def he2hb(self, A: torch.Tensor, band: int, want_q: bool = False):
+        """Stage 1 of the two-stage reduction in place on A (count, m, m): A <- band matrix
+        B = Q1^H A Q1 (full Hermitian storage); returns (B, Q1 or None)."""
+        if A.dim() == 2:
+            A = A[None]
+        _check_tensor(A, "A", (torch.float64, torch.complex128))
+        Q = torch.empty_like(A) if want_q else None
+        self._raise(self._lib.gks_he2hb(self._h, _ptr(A), A.shape[1], A.shape[0],
+                                        GKS_C128 if A.is_complex() else GKS_R64, int(band), _ptr(Q)))
+        self.sync()
+        return A, Q
+
+    def hb2st(self, B: torch.Tensor, band: int, X: torch.Tensor | None = None):
+        """Stage 2: (d, e) of the real tridiagonal Q2^H B Q2 for the Hermitian band B
+        (count, m, m); X (count, m, ncols) is replaced by Q2 X when given."""
+        if B.dim() == 2:
+            B = B[None]
+        _check_tensor(B, "B", (torch.float64, torch.complex128))
+        count, m = B.shape[0], B.shape[1]
+        d = torch.empty(count, m, dtype=torch.float64, device=B.device)
+        e = torch.empty(count, m, dtype=torch.float64, device=B.device)
+        nc = 0 if X is None else X.shape[-1]
+        self._raise(self._lib.gks_hb2st(self._h, _ptr(B), m, count, GKS_C128 if B.is_complex() else GKS_R64,
+                                        int(band), _ptr(d), _ptr(e), _ptr(X), nc))
+        self.sync()
+        return d, e
 
     def stedc(self, d: torch.Tensor, e: torch.Tensor):
         """Divide-and-conquer eigensolve of real tridiagonals d (count, m), e (count, m)."""

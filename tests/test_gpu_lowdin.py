@@ -44,7 +44,10 @@ def test_lowdin_random_pencil_raw_gates(ctx, cplx, m):
     orth, bwd = _scaled(H, S, eps, C)
     assert orth <= 1e-12 * math.sqrt(m) and bwd <= 1e-12 * math.sqrt(m), (orth, bwd)
     assert np.abs(S @ (rho - ref.rho[0]) @ S).max() <= 1e-9
-    assert abs(sol.mu.item() - ref.mu) <= 1e-9
+    # mu inside a wide gap is ill-determined (its bracket is flat): check the electron count
+    # it gives on the oracle's eigenvalues instead
+    count = 2.0 * O.fermi((ref.eps[0] - sol.mu.item()) / 0.1).sum()
+    assert abs(count - 0.6 * m) <= 1e-9 * m
 
 
 @pytest.mark.parametrize("tiling", [(1, 1, 1), (2, 1, 1)])
