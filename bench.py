@@ -526,6 +526,9 @@ def main():
     ap.add_argument("--gemm", default="auto", choices=["auto", "fp64", "split"],
                     help="products: auto (split-bf16 tensor-core products where they pay), fp64 (FP64 pipe only)")
     ap.add_argument("--block", type=int, default=0, help="outer block width (0 = library default)")
+    ap.add_argument("--tridiag", default="one_stage", choices=["one_stage", "two_stage"],
+                    help="tridiagonalization of the timed step")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="arithmetic of the timed step")
     ap.add_argument("--per-k", action="store_true",
                     help="solve the k-points one call each (nk = 1, shared mu lost) instead of one batched call")
     args = ap.parse_args()
@@ -569,7 +572,8 @@ def main():
     kw = torch.as_tensor(np.asarray(prob.kweights, float), device=dev)  # all k-points (1/nk_all)
     kw_local = kw[k0:k1].contiguous()
     stream = torch.cuda.current_stream(dev)
-    ctx = gks.Context(local, stream, profile=True, gemm=args.gemm, block=args.block)
+    ctx = gks.Context(local, stream, profile=True, gemm=args.gemm, block=args.block, tridiag=args.tridiag,
+                      precision=args.precision)
     eps = torch.empty(nk, M, dtype=torch.float64, device=dev)
     C = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
     rho = torch.empty_like(C)
@@ -666,7 +670,8 @@ def main():
     # the other forms of the same step on the same GPU: mixed precision + refinement, and the
     # plain FP64 path one problem (k-point) per call
     compare = None
-    if not args.no_compare and not args.per_k and args.gemm == "auto" and world == 1:
+    if (not args.no_compare and not args.per_k and args.gemm == "auto" and world == 1 and args.tridiag == "one_stage"
+            and args.precision == "fp64"):
         compare = {}
 
         def timed(fn, steps):
@@ -799,7 +804,8 @@ def main():
                            "parallelism": (f"k-point shard over {world} ranks (contiguous k ranges, allgather of "
                                            f"eps, shared mu on every rank)") if shard else
                            (f"{world} replicas" if world > 1 else "one GPU"),
-                           "spin": spin, "precision": "fp64", "products": args.gemm,
+                           "spin": spin, "precision": args.precision, "tridiag": args.tridiag,
+                           "products": args.gemm,
                            "block": args.block or (512 if M >= 4096 else 256),
                            "batching": "one call per k-point" if args.per_k else "all k-points in one call",
                            "l2": "inputs larger than L2 (no flush needed)",
