@@ -272,10 +272,26 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+RESIDUE_MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193]
+
+
+def split_products(form, Kp, bits=54):
+    """bf16 products per split product: 45 digit pairs for nine 6-bit digits, or the number
+    of moduli n of the residue form (the fewest with 2 Kp 2^{2p} <= prod m, p >= bits)."""
+    if form == "digits":
+        return 45
+    M = 1
+    for n, m in enumerate(RESIDUE_MODULI, 1):
+        M *= m
+        if min((M // (2 * Kp)).bit_length() - 1, 124) // 2 >= bits:
+            return n
+    return 45
+
+
 def run_product(args):
-    """One complex 4096^3 product through gks_gemm (split-bf16 digits, FP64 accumulation),
+    """One complex 4096^3 product through gks_gemm (split-bf16 products in the chosen form),
     with the tensor roofline of the executed bf16 work: per product 2 Mp N'p K'p bf16 flops
-    for each of the 45 digit pairs of S = 9 (N' = 2N, K' = 2K for the real embedding)."""
+    for each bf16 product of the form (N' = 2N, K' = 2K for the real embedding)."""
     import numpy as np
     import torch
     rank, world, local = env_rank()
@@ -290,7 +306,7 @@ def run_product(args):
     Bm = torch.randn(n, n, dtype=torch.complex128, device=dev, generator=g)
     C = torch.zeros(n, n, dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = gks.Context(local, stream)
+    ctx = gks.Context(local, stream, split=args.split)
     lib, h = ctx._lib, ctx._h
 
     def prod():
@@ -319,7 +335,8 @@ def run_product(args):
         ref = A[:64] @ Bm
         ref_err = float(((C[:64] - ref).abs().max() / ref.abs().max()).item())
     fl = 8.0 * n ** 3
-    bf16 = 2.0 * n * (2 * n) * (2 * n) * 45
+    nprod = split_products(args.split, 2 * n)
+    bf16 = 2.0 * n * (2 * n) * (2 * n) * nprod
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -331,12 +348,15 @@ def run_product(args):
         line = {"metric": "FP64-accurate complex product throughput (FP64-equivalent TFLOP/s)",
                 "value": fl / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16 digits, fp32 tensor accumulation, fp64 sums", "data": "synthetic",
+                "vs_baseline": None, "dtype": "bf16 split values, fp32 tensor accumulation", "data": "synthetic",
                 "config": {"workload": "product4096", "desc": WORKLOADS["product4096"]["desc"],
+                           "split_form": args.split, "bf16_products": nprod,
                            "max_rel_err_vs_fp64_rows0_63": ref_err,
                            "l2": "operands and digits (1.8 GB) larger than L2 (no flush needed)"},
                 "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
-                             "frac": ach / bf16_peak, "traffic": None, "kernel": "oz_tc_kernel + oz_split_kernel",
+                             "frac": ach / bf16_peak, "traffic": None,
+                             "kernel": ("crt_tc_kernel + oz_split_kernel + crt_recon_kernel" if args.split == "residues"
+                                        else "oz_tc_kernel + oz_split_kernel"),
                              "peak_basis": "bf16 dense, MEASURED_PEAKS.json burst"},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches),
                 "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
@@ -529,6 +549,8 @@ def main():
     ap.add_argument("--tridiag", default="one_stage", choices=["one_stage", "two_stage"],
                     help="tridiagonalization of the timed step")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="arithmetic of the timed step")
+    ap.add_argument("--split", default="residues", choices=["residues", "digits"],
+                    help="form of the FP64-accurate tensor-core products")
     ap.add_argument("--per-k", action="store_true",
                     help="solve the k-points one call each (nk = 1, shared mu lost) instead of one batched call")
     args = ap.parse_args()
@@ -573,7 +595,7 @@ def main():
     kw_local = kw[k0:k1].contiguous()
     stream = torch.cuda.current_stream(dev)
     ctx = gks.Context(local, stream, profile=True, gemm=args.gemm, block=args.block, tridiag=args.tridiag,
-                      precision=args.precision)
+                      precision=args.precision, split=args.split)
     eps = torch.empty(nk, M, dtype=torch.float64, device=dev)
     C = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
     rho = torch.empty_like(C)
@@ -685,7 +707,7 @@ def main():
             torch.cuda.synchronize()
             return a0.elapsed_time(a1) / steps
         if M <= 18000:
-            cm = gks.Context(local, stream, precision="mixed", block=args.block)
+            cm = gks.Context(local, stream, precision="mixed", block=args.block, split=args.split)
             eps_m = torch.empty_like(eps)
             C_m = torch.empty_like(C)
             rho_m = torch.empty_like(rho)
@@ -706,11 +728,14 @@ def main():
                 if not args.no_accuracy else None}
             del cm, eps_m, C_m, rho_m
             torch.cuda.empty_cache()
-        # two-stage tridiagonalization, all eigenvectors and the lowest n_ev (occupied + margin)
+        # the other split-product form; two-stage tridiagonalization, all eigenvectors and the
+        # lowest n_ev (occupied + margin)
         n_ev = min(M, max(nrho) + 64)
-        for name, kw_ in (("two_stage", dict(tridiag="two_stage")),
-                          ("one_stage_partial", dict(n_ev=n_ev)),
-                          ("two_stage_partial", dict(tridiag="two_stage", n_ev=n_ev))):
+        other = "digits" if args.split == "residues" else "residues"
+        for name, kw_ in ((f"split_{other}", dict(split=other)),
+                          ("two_stage", dict(tridiag="two_stage", split=args.split)),
+                          ("one_stage_partial", dict(n_ev=n_ev, split=args.split)),
+                          ("two_stage_partial", dict(tridiag="two_stage", n_ev=n_ev, split=args.split))):
             try:
                 cx = gks.Context(local, stream, block=args.block, **kw_)
                 ncol = kw_.get("n_ev", M)
@@ -805,7 +830,7 @@ def main():
                                            f"eps, shared mu on every rank)") if shard else
                            (f"{world} replicas" if world > 1 else "one GPU"),
                            "spin": spin, "precision": args.precision, "tridiag": args.tridiag,
-                           "products": args.gemm,
+                           "products": args.gemm, "split_form": args.split,
                            "block": args.block or (512 if M >= 4096 else 256),
                            "batching": "one call per k-point" if args.per_k else "all k-points in one call",
                            "l2": "inputs larger than L2 (no flush needed)",

@@ -81,6 +81,17 @@ typedef enum { GKS_REDUCE_CHOLESKY = 0, GKS_REDUCE_LOWDIN = 1 } gks_reduction;
  * one-stage single-precision reduction). */
 typedef enum { GKS_TRIDIAG_ONE_STAGE = 0, GKS_TRIDIAG_TWO_STAGE = 1 } gks_tridiag;
 
+/* Form of the FP64-accurate tensor-core products (opts.split).  Both scale each row of the
+ * left operand and each column of the right one by a power of two and multiply exact bf16
+ * integers with FP32 accumulation (the error-free splittings of Ozaki, Ogita, Oishi and
+ * Rump, and of Ozaki, Uchino and Imamura).  GKS_SPLIT_RESIDUES: operands truncated to
+ * integers of p >= 6 * opts.slices bits, the integer product recovered from its residues
+ * modulo n pairwise coprime moduli <= 256 by the Chinese remainder theorem (one product per
+ * modulus; 16 moduli give p = 55 for inner dimensions up to 16384).  GKS_SPLIT_DIGITS:
+ * opts.slices digits of 6 bits per operand, products of digit pairs up to slices + 1 levels
+ * (45 products for 9 digits). */
+typedef enum { GKS_SPLIT_RESIDUES = 0, GKS_SPLIT_DIGITS = 1 } gks_split;
+
 /* gks_solve flags. */
 enum {
   /* Skip the copy and Cholesky of S: reuse the factor kept from the last solve on this
@@ -115,7 +126,8 @@ typedef struct {
   int gemm;            /* FP64 products: 0 = large ones as exact split-bf16 tensor-core products
                           with FP64 accumulation, small ones on the FP64 pipe (default);
                           1 = FP64 pipe only; 2 = split products for every product */
-  int slices;          /* 6-bit digits per operand in split products (4..10, 0 = 9) */
+  int slices;          /* precision of split products in 6-bit units (4..10, 0 = 9): digits per
+                          operand (GKS_SPLIT_DIGITS) or at least 6 slices bits (residues) */
   int block;           /* outer block width of the two-level blocked Cholesky, reduction and
                           back-transforms: a multiple of 64 in 64..1024; 0 = 512 for orders
                           from 4096 up and 256 below (gks_tune overrides per shape class) */
@@ -140,6 +152,7 @@ typedef struct {
   int reduction;       /* gks_reduction: how H C = S C eps becomes a standard problem */
   int tridiag;         /* gks_tridiag */
   int band;            /* two-stage bandwidth, 2..32 (0 = 32) */
+  int split;           /* gks_split: form of the split products (0 = residues) */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */
@@ -294,9 +307,9 @@ long long gks_launch_count(void);
 gks_status gks_measure_peak(gks_ctx* ctx, int which, double* tflops);
 
 /* C = alpha op(A) op(B) + beta C for one product (row-major, op 0 = N, 1 = T, 2 = conjugate
- * transpose; op(A) is M x K, op(B) K x N).  mode 1: the FP64 pipe; mode 2: exact split-
- * bf16 tensor-core products with FP64 accumulation (the path large products of gks_solve
- * take).  Exposed to check the product kernels on their own. */
+ * transpose; op(A) is M x K, op(B) K x N).  mode 1: the FP64 pipe; mode 2: split-bf16
+ * tensor-core products in the context's opts.split form (the path large products of
+ * gks_solve take).  Exposed to check the product kernels on their own. */
 gks_status gks_gemm(gks_ctx* ctx, int dtype, int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha,
                     const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
                     int mode);
@@ -330,7 +343,8 @@ int gks_tune_get(const gks_ctx* ctx, int64_t n, int dtype, int spin_mode);
  * cannot afford the device-wide synchronization an allocation implies.  The paper has no
  * counterpart; this is a library service around the same product kernels.
  *
- * Arguments as in gks_gemm; the digit count is the context's opts->slices (S, default 9).
+ * Arguments as in gks_gemm; always the digit-pair form (GKS_SPLIT_DIGITS, whatever
+ * opts.split says) with the context's opts->slices digits (S, default 9).
  * The scratch needed is S * (Mp + Np) * Kp * 2 + 4 * (Mp + Np) + 1024 bytes with
  * Mp = M rounded up to 128, Np = N' rounded up to 128, Kp = K' rounded up to 64, where
  * N' = N, K' = K for GKS_R64 and N' = 2N, K' = 2K for GKS_C128 (e.g. real 512 x 512 x 512

@@ -9,6 +9,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dense.h"
 #include "gks.h"
 
@@ -91,7 +93,8 @@ struct gks_ctx {
   int device = 0;
   bool graph = false;                  // capture solves into CUDA graphs
   int gemm_mode = 0;                   // 0 auto, 1 DFMA only, 2 split products always
-  int slices = 9;                      // 6-bit digits per operand in split products
+  int slices = 9;                      // split products: 6-bit digits per operand, or 6 slices bits
+  int split = 0;                       // split-product form: 0 residues (CRT), 1 digit pairs
   int nbb = 256;                       // outer block of the two-level blocked stages (active)
   int nbb_default = 256;               // opts.block, used for shapes the tuner has not seen
   bool nbb_fixed = false;              // opts.block given: no size-dependent default
@@ -150,6 +153,10 @@ struct gks_ctx {
 };
 
 namespace {
+
+// The split-product form and precision handed to ozaki_gemm: residues carrying at least
+// 6 slices bits (negative) or slices 6-bit digits.
+int sform(const gks_ctx* c) { return c->split == 0 ? -c->slices : c->slices; }
 
 gks_status fail(gks_ctx* c, gks_status code, const std::string& msg) {
   if (c) c->err = msg;
@@ -469,12 +476,19 @@ struct Rec {
   }
   ~Rec() { c->prof.end(tok, cls, flops, bytes); }
 };
-// Stage bracket (recorded as class PC_NCLASS + stage).
+// Stage bracket (recorded as class PC_NCLASS + stage), also an NVTX range named after the
+// stage for timeline tools (no cost without an attached tool).
 struct StageRec {
   gks_ctx* c;
   int tok, st;
-  StageRec(gks_ctx* c_, int st_) : c(c_), st(st_) { tok = c->prof.begin(); }
-  ~StageRec() { c->prof.end(tok, PC_NCLASS + st, 0.0, 0.0); }
+  StageRec(gks_ctx* c_, int st_) : c(c_), st(st_) {
+    nvtxRangePushA(kStageNames[st]);
+    tok = c->prof.begin();
+  }
+  ~StageRec() {
+    c->prof.end(tok, PC_NCLASS + st, 0.0, 0.0);
+    nvtxRangePop();
+  }
 };
 
 double cmul(int es) { return es == 16 ? 8.0 : 2.0; }
@@ -523,7 +537,7 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
   const int es = sizeof(T);
   const double fl = gemm_flops(es, M, N, K, lower, count);
   const int per = split_worth(c, count, M, N, K, es, fl)
-                      ? oz_reserve(c, ozaki_workspace_bytes(M, N, K, es == 16, c->slices), count)
+                      ? oz_reserve(c, ozaki_workspace_bytes(M, N, K, es == 16, sform(c)), count)
                       : 0;
   if (per == 0) {
     gmp<T>(c, count, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, lower);
@@ -537,7 +551,7 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
     const long long skip = (c->debug & GKS_DEBUG_SKIP_COPY) ? 3 : -1;
     c->debug &= ~GKS_DEBUG_SKIP_COPY;
     if (!ozaki_gemm<T>(opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc,
-                       sC, cnt, lower, c->slices, c->oz, c->st ? c->st : c->gst, c->stream, nullptr, 0, nullptr,
+                       sC, cnt, lower, sform(c), c->oz, c->st ? c->st : c->gst, c->stream, nullptr, 0, nullptr,
                        c->wait_cycles, skip))
       gmp<T>(c, cnt, opA, opB, M, N, K, alpha, A + z0 * sA, lda, sA, B + z0 * sB, ldb, sB, beta, C + z0 * sC, ldc, sC,
              lower);
@@ -554,11 +568,11 @@ void gmx2(gks_ctx* c, int count, int nb2, int opA, int opB, int M, int N, int K,
   const int es = sizeof(T);
   const double fl = gemm_flops(es, M, N, K, 0, count);
   const int per = split_worth(c, count, M, N, K, es, fl)
-                      ? oz_reserve(c, ozaki_workspace_bytes(M, N, K, es == 16, c->slices), count)
+                      ? oz_reserve(c, ozaki_workspace_bytes(M, N, K, es == 16, sform(c)), count)
                       : 0;
   if (per >= count) {
     Rec r(c, PC_OZAKI, fl, gemm_bytes(es, M, N, K, 0, count, beta != 0.0));
-    if (ozaki_gemm<T>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, count, 0, c->slices, c->oz,
+    if (ozaki_gemm<T>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, count, 0, sform(c), c->oz,
                       c->st ? c->st : c->gst, c->stream, nullptr, 0, nullptr, c->wait_cycles, -1, sA2, sB2, sC2,
                       nb2))
       return;
@@ -592,13 +606,13 @@ void rho_run(gks_ctx* c, const T* C, int ldc, long long sC, T* rho, long long sR
              const int* nrho, int M, int K, int nk) {
   const int es = sizeof(T);
   const int per = split_worth(c, nk, M, M, K, es, gemm_flops(es, M, M, std::max(1, K / 4), 1, nk))
-                      ? oz_reserve(c, ozaki_workspace_bytes(M, M, K, es == 16, c->slices), nk)
+                      ? oz_reserve(c, ozaki_workspace_bytes(M, M, K, es == 16, sform(c)), nk)
                       : 0;
   int z0 = 0;
   for (; per > 0 && z0 < nk; z0 += per) {
     const int cnt = std::min(per, nk - z0);
     if (!ozaki_gemm<T>(OP_N, OP_C, M, M, K, 1.0, C + z0 * sC, ldc, sC, C + z0 * sC, ldc, sC, 0.0, rho + z0 * sR, M,
-                       sR, cnt, 1, c->slices, c->oz, c->st ? c->st : c->gst, c->stream, ks + z0 * sks, sks,
+                       sR, cnt, 1, sform(c), c->oz, c->st ? c->st : c->gst, c->stream, ks + z0 * sks, sks,
                        nrho + z0, c->wait_cycles))
       break;  // tensor maps unavailable: the FP64 kernel takes the remaining items
   }
@@ -1130,9 +1144,9 @@ void standard_eig(gks_ctx* c, T* A, T* X, long long sX, double* w, int M, int it
     hetrd_finish<T>(A, M, c->sMM, M, d, e, M, ph, M, items, s);
   }
   double* Z = at<double>(c, c->oZ);
-  DcSplit sp{nullptr, 0, c->slices, 512, c->wait_cycles};
+  DcSplit sp{nullptr, 0, sform(c), 512, c->wait_cycles};
   if (c->gemm_mode != 1 && M >= 1024) {
-    const size_t item = dc_split_item_bytes(c->dc, sp.min_half, c->slices);
+    const size_t item = dc_split_item_bytes(c->dc, sp.min_half, sform(c));
     if (item > 0) {
       sp.per = oz_reserve(c, item, items);
       sp.work = c->oz;
@@ -1324,9 +1338,9 @@ gks_status solve_t(gks_ctx* c, const SolveKey& key) {
   double* Z = at<double>(c, c->oZ);
   {
     StageRec sr(c, PS_STEDC);
-    DcSplit sp_{nullptr, 0, c->slices, 512, c->wait_cycles};
+    DcSplit sp_{nullptr, 0, sform(c), 512, c->wait_cycles};
     if (c->gemm_mode != 1 && M >= 1024) {
-      const size_t item = dc_split_item_bytes(c->dc, sp_.min_half, c->slices);
+      const size_t item = dc_split_item_bytes(c->dc, sp_.min_half, sform(c));
       if (item > 0) {
         sp_.per = oz_reserve(c, item, items);
         sp_.work = c->oz;
@@ -1636,6 +1650,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     c->graph = opts->graph != 0;
     c->gemm_mode = opts->gemm;
     if (opts->slices > 0) c->slices = opts->slices;
+    c->split = opts->split;
     if (opts->block > 0) c->nbb = opts->block;
     c->nbb_default = c->nbb;
     c->nbb_fixed = opts->block > 0;
@@ -1652,7 +1667,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
         c->nbb % NB || c->n_ev < 0 || opts->refine_sweeps < 0 || opts->refine_sweeps > 8 || opts->wait_limit < 0 ||
         (c->reduction != GKS_REDUCE_CHOLESKY && c->reduction != GKS_REDUCE_LOWDIN) ||
         (c->tridiag != GKS_TRIDIAG_ONE_STAGE && c->tridiag != GKS_TRIDIAG_TWO_STAGE) || c->band < 2 ||
-        c->band > 32 ||
+        c->band > 32 || (c->split != GKS_SPLIT_RESIDUES && c->split != GKS_SPLIT_DIGITS) ||
         (opts->debug & ~GKS_DEBUG_SKIP_COPY)) {
       delete c;
       return GKS_EINVAL;
@@ -1770,6 +1785,7 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     sc->f_cut = ctx->f_cut;
     sc->gemm_mode = ctx->gemm_mode;
     sc->slices = ctx->slices;
+    sc->split = ctx->split;
     sc->nbb = ctx->nbb;
     sc->nbb_default = ctx->nbb_default;
     sc->nbb_fixed = ctx->nbb_fixed;

@@ -23,9 +23,13 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "dense.h"
+#include "tcgen05.cuh"
 
 namespace gks {
 
@@ -35,16 +39,50 @@ static constexpr int OZ_CHUNK = 4096; // exact FP32 accumulation length (63*63*4
 
 // ------------------------------------------------------------------ splitting
 
-// Digits of one value already scaled below 1 in magnitude.  The first S base-64 digits
-// of |r| truncated toward zero are the base-64 digits of the integer trunc(|r| 2^{6S})
-// (6S <= 60 bits): one conversion, then integer shifts.
-__device__ __forceinline__ void put_digits(double r, __nv_bfloat16* dst, long long sstride, int S) {
-  const long long q = __double2ll_rz(ldexp(fabs(r), OZ_BITS * S));
-  const float sg = r < 0.0 ? -1.0f : 1.0f;
-  for (int s = 0; s < S; s++) {
-    const int d = (int)((q >> (OZ_BITS * (S - 1 - s))) & 63);
-    dst[s * sstride] = __float2bfloat16_rn(sg * (float)d);
+// ------------------------------------------------------------------ residue moduli
+// Pairwise coprime moduli up to 256 (2^8, 3*5*17, 11*23, 251, 13*19, 241, 239, 233, 229,
+// 227, 223, 7*31, 211, 199, 197, 193), largest first: a residue in symmetric form has
+// |r| <= 128, an integer exact in bf16, and a product of two is at most 2^14.
+static constexpr int CRT_MAXMOD = 16;
+__host__ __device__ constexpr uint32_t crt_mod(int l) {
+  return l == 0 ? 256u : l == 1 ? 255u : l == 2 ? 253u : l == 3 ? 251u : l == 4 ? 247u : l == 5 ? 241u
+       : l == 6 ? 239u : l == 7 ? 233u : l == 8 ? 229u : l == 9 ? 227u : l == 10 ? 223u : l == 11 ? 217u
+       : l == 12 ? 211u : l == 13 ? 199u : l == 14 ? 197u : 193u;
+}
+
+// The split values of one element x of a vector whose entries are below 2^e in magnitude,
+// into o[0..S); sh = 6S - e (digits) or p - e (residues).
+// Digits (RES false): the first S base-64 digits of |x| 2^-e truncated toward zero (the
+// base-64 digits of the integer trunc(|x| 2^sh), 6S <= 60 bits), with the sign of x.
+// Residues (RES true): q = trunc(x 2^sh), |q| < 2^p <= 2^62, modulo each of the first S
+// moduli in symmetric form (|q| mod m from its two 32-bit halves, then q's sign).
+template <bool RES>
+__device__ __forceinline__ void split_vals(double x, int sh, int S, float (&o)[16]) {
+  if constexpr (RES) {
+    const long long q = __double2ll_rz(ldexp(x, sh));
+    const unsigned long long u = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const float sg = q < 0 ? -1.0f : 1.0f;
+#pragma unroll
+    for (int l = 0; l < CRT_MAXMOD; l++) {
+      const uint32_t m = crt_mod(l), w = (uint32_t)((1ull << 32) % m);
+      const uint32_t r = l < S ? ((hi % m) * w + lo % m) % m : 0u;
+      o[l] = sg * (float)(2u * r > m ? (int)r - (int)m : (int)r);
+    }
+  } else {
+    const long long q = __double2ll_rz(ldexp(fabs(x), sh));
+    const float sg = x < 0.0 ? -1.0f : 1.0f;
+#pragma unroll
+    for (int s = 0; s < 16; s++)
+      o[s] = s < S ? sg * (float)((q >> (OZ_BITS * max(S - 1 - s, 0))) & 63) : 0.0f;
   }
+}
+
+__device__ __forceinline__ void store_vals(const float (&o)[16], float sg, __nv_bfloat16* dst, long long sstride,
+                                           int S) {
+#pragma unroll
+  for (int s = 0; s < 16; s++)
+    if (s < S) dst[s * sstride] = __float2bfloat16_rn(sg * o[s]);
 }
 
 __device__ __forceinline__ int scale_exp(double mx) {
@@ -65,41 +103,44 @@ __device__ __forceinline__ T split_elem(const T* X, int ld, int role, int op, in
 __device__ __forceinline__ double amax(double x) { return fabs(x); }
 __device__ __forceinline__ double amax(zc x) { return fmax(fabs(x.x), fabs(x.y)); }
 
-// Write the digits of element k of vector v (scaled by 2^-e) into the embedded layout.
-template <typename T>
-__device__ __forceinline__ void emit(T x, int e, int role, int v, int k, __nv_bfloat16* D, int Kp, long long sstride,
-                                     int S);
-template <>
-__device__ __forceinline__ void emit<double>(double x, int e, int, int v, int k, __nv_bfloat16* D, int Kp,
-                                             long long sstride, int S) {
-  put_digits(ldexp(x, -e), D + (size_t)v * Kp + k, sstride, S);
+// Write the split values of element k of vector v (scaled by 2^-e) into the embedded
+// layout (complex B: column 2v = (Re, -Im), column 2v + 1 = (Im, Re) along k).
+template <bool RES>
+__device__ __forceinline__ void emit(double x, int e, int, int v, int k, __nv_bfloat16* D, int Kp, long long sstride,
+                                     int S, int p) {
+  float o[16];
+  split_vals<RES>(x, (RES ? p : OZ_BITS * S) - e, S, o);
+  store_vals(o, 1.0f, D + (size_t)v * Kp + k, sstride, S);
 }
-template <>
-__device__ __forceinline__ void emit<zc>(zc x, int e, int role, int v, int k, __nv_bfloat16* D, int Kp,
-                                         long long sstride, int S) {
-  const double re = ldexp(x.x, -e), im = ldexp(x.y, -e);
+template <bool RES>
+__device__ __forceinline__ void emit(zc x, int e, int role, int v, int k, __nv_bfloat16* D, int Kp, long long sstride,
+                                     int S, int p) {
+  float o[16];
+  __nv_bfloat16* r0 = role == 0 ? D + (size_t)v * Kp + 2 * k : D + (size_t)(2 * v) * Kp + 2 * k;
+  __nv_bfloat16* r1 = D + (size_t)(2 * v + 1) * Kp + 2 * k;
+  const int sh = (RES ? p : OZ_BITS * S) - e;
+  split_vals<RES>(x.x, sh, S, o);
+  store_vals(o, 1.0f, r0, sstride, S);
+  if (role != 0) store_vals(o, 1.0f, r1 + 1, sstride, S);
+  split_vals<RES>(x.y, sh, S, o);
   if (role == 0) {
-    put_digits(re, D + (size_t)v * Kp + 2 * k, sstride, S);
-    put_digits(im, D + (size_t)v * Kp + 2 * k + 1, sstride, S);
+    store_vals(o, 1.0f, r0 + 1, sstride, S);
   } else {
-    __nv_bfloat16* r0 = D + (size_t)(2 * v) * Kp + 2 * k;
-    __nv_bfloat16* r1 = D + (size_t)(2 * v + 1) * Kp + 2 * k;
-    put_digits(re, r0, sstride, S);
-    put_digits(-im, r0 + 1, sstride, S);
-    put_digits(im, r1, sstride, S);
-    put_digits(re, r1 + 1, sstride, S);
+    store_vals(o, -1.0f, r0 + 1, sstride, S);
+    store_vals(o, 1.0f, r1, sstride, S);
   }
 }
 
 // One CTA (256 threads) per 32 vectors.  Pass 1: per-vector max (thread per vector when the
 // vector index is the contiguous direction, else a warp sweeps each vector along k).
-// Pass 2: digits.  Padding vectors and k beyond K are written as zero digits elsewhere.
-// blockIdx.y runs over the batch items (strides sX, sD, sE).  Optional per item: kdev
-// (device) cuts K to its value, ksc scales element k by ksc[k] before splitting.
-template <typename T>
+// Pass 2: the S digits or residues (RES; residues of trunc(x 2^{p - e})).  Padding vectors
+// and k beyond K are written as zeros elsewhere.  blockIdx.y runs over the batch items
+// (strides sX, sD, sE).  Optional per item: kdev (device) cuts K to its value, ksc scales
+// element k by ksc[k] before splitting.
+template <typename T, bool RES>
 __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long long sX, int role, int op, int nvec,
                                                        int K, __nv_bfloat16* D, int Kp, long long sstride,
-                                                       long long sD, int S, int* ex, long long sE,
+                                                       long long sD, int S, int p, int* ex, long long sE,
                                                        const double* ksc, long long sks, const int* kdev,
                                                        long long sX2, int nb2) {
   __shared__ double smax[32];
@@ -149,7 +190,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long 
     for (int vv = warp; vv < 32; vv += 8) {
       const int v = v0 + vv;
       if (v >= nvec) continue;
-      for (int k = lane; k < K; k += 32) emit<T>(elem(v, k), sexp[vv], role, v, k, D, Kp, sstride, S);
+      for (int k = lane; k < K; k += 32) emit<RES>(elem(v, k), sexp[vv], role, v, k, D, Kp, sstride, S, p);
     }
   } else {
     // k strided in memory: stage 32 (k) x 32 (vectors) tiles through shared memory so that
@@ -163,7 +204,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long 
       __syncthreads();
       for (int vv = warp; vv < 32; vv += 8) {
         const int v = v0 + vv, k = k0 + lane;
-        if (v < nvec && k < K) emit<T>(tile[lane][vv], sexp[vv], role, v, k, D, Kp, sstride, S);
+        if (v < nvec && k < K) emit<RES>(tile[lane][vv], sexp[vv], role, v, k, D, Kp, sstride, S, p);
       }
       __syncthreads();
     }
@@ -171,10 +212,6 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long 
 }
 
 // ------------------------------------------------------------------ product kernel
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 static constexpr int OZ_BM = 128, OZ_BN = 128;  // output tile of the product kernel
 
@@ -215,95 +252,11 @@ struct OzArgs {
 // the CTA raises an abort flag and a timeout status, lets its copies and products land,
 // frees its tensor memory and exits.
 namespace tcg {
-constexpr int BM = 128, BN = 128, BK = 64;           // BK bf16 = 128 bytes = one swizzle row
-constexpr int STAGES = 6;
-constexpr int TILE_BYTES = BM * BK * 2;              // 16 KB per operand tile
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr int TMEM_COLS = 2 * BN;                    // two FP32 accumulators
-constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr int SMEM = STAGES * STAGE_BYTES + 1024;    // + alignment slack
-
-// kind::f16 instruction descriptor: FP32 accumulator, bf16 A and B, both K-major, M x N.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-
 // k blocks per unit of level L: (L - 1) pairs, digit products up to 63^2.
 __device__ __forceinline__ int level_blocks(int L) {
   const int cb = (int)((1u << 24) / ((unsigned)(L - 1) * 3969u * (unsigned)BK));
   return min(cb, OZ_CHUNK / BK);
 }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase of the given parity; false on abort or timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, long long limit) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort) return false;
-    if (clock64() - t0 > limit) {
-      *abort = 1;
-      return false;
-    }
-  }
-  return true;
-}
-// Wait without watching the abort flag (draining after an abort), still bounded.
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, long long limit) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > limit) return;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand tile of 8-row groups 1024 bytes apart,
-// 128-byte swizzle, descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          dtmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
 // x 2^-s as a double, for x an integer-valued float (the exact unit sums): built from the
 // float's bits with integer operations (sign, exponent shifted by 896 - s, mantissa moved
@@ -313,18 +266,6 @@ __device__ __forceinline__ double exact_scaled(uint32_t b, uint32_t s) {
   const uint32_t hi = (b & 0x80000000u) | ((e + 896u - s) << 20) | ((b & 0x7fffffu) >> 3);
   const uint32_t lo = b << 29;
   return e ? __hiloint2double((int)hi, (int)lo) : 0.0;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 }  // namespace tcg
 
@@ -537,6 +478,361 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
   }
 }
 
+// ------------------------------------------------------------------ residue products
+//
+// The modular form of the split product (the integer-modular scheme of Ozaki, Uchino and
+// Imamura, here on the bf16 tensor cores).  Row i of op(A) is scaled by 2^{p - e_i} and
+// truncated to integers A'_ik (|A'_ik| < 2^p), column j of op(B) the same, and the integer
+// product X = A'B' is recovered from its residues modulo n pairwise coprime m_l by the
+// Chinese remainder theorem, since |X| < Kp 2^{2p} <= M / 2 with M = m_1 ... m_n.  For each
+// modulus the kernel multiplies the residue planes of A' and B' over K: symmetric residues
+// are bf16-exact integers of magnitude <= 128, so a k chunk of 1024 sums exactly in the
+// FP32 accumulator (<= 2^24).  Eight epilogue warps fold each chunk into a residue kept
+// in FP32 registers (x - m round(x / m), exact on integers) while the tensor cores fill the
+// other accumulator, and write X mod m_l of every element as one byte when the modulus
+// ends.  One product per modulus: 16 moduli keep p = 55 bits for K up to 16384, where nine
+// 6-bit digits keep 54 bits with 45 digit-pair products.  crt_recon_kernel rebuilds X
+// from its residues in 32-bit limbs and scales it back by 2^{e_i + f_j - 2p}.
+constexpr int CRT_CHUNK_BLOCKS = 16;  // k blocks per exact chunk: 16 * 64 * 128^2 = 2^24
+
+struct CrtArgs {
+  const __nv_bfloat16* Ad;  // [count][n][Mp][Kp] residue planes of A'
+  const __nv_bfloat16* Bd;  // [count][n][Np][Kp] residue planes of B' (embedded columns, K-major)
+  uint8_t* R;               // [count][n][Mp][Np] residues of X
+  int Mp, Np, Kp, n, cplx, lower;
+  long long zR;             // item stride of R (bytes)
+  const int* kdev;          // optional per-item K read on the device (logical, <= K)
+  long long wait;           // bound of every mbarrier wait, in SM clock cycles
+  long long skip_copy;      // test hook: the producer leaves out this copy (-1 = none)
+};
+
+// x - m round(x / m) for an integer-valued float |x| <= 2^24: the quotient is rounded with
+// the 1.5 * 2^23 shift (|x / m| < 2^22), and the fused multiply-add is exact because the
+// result is a small integer.
+__device__ __forceinline__ float crt_fold(float x, float m, float inv) {
+  const float q = __fsub_rn(__fmaf_rn(x, inv, 12582912.0f), 12582912.0f);
+  return __fmaf_rn(-q, m, x);
+}
+
+__global__ void __launch_bounds__(tcg::THREADS, 1)
+    crt_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, CrtArgs a,
+                  DevStatus* status) {
+  using namespace tcg;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int m0, n0;  // grouped tile order, as in oz_tc_kernel
+  {
+    constexpr int G = 8;
+    const int ntn = gridDim.x, ntm = gridDim.y;
+    const int bid = blockIdx.y * ntn + blockIdx.x, per = G * ntn;
+    const int fm = (bid / per) * G, gs = min(ntm - fm, G), r = bid % per;
+    m0 = (fm + r % gs) * BM;
+    n0 = (r / gs) * BN;
+  }
+  const int z = blockIdx.z;
+  const int ncol0 = a.cplx ? n0 / 2 : n0;
+  if (a.lower && m0 + BM - 1 < ncol0) return;  // whole tile above the diagonal (uniform)
+
+  const int n = a.n;
+  int kblocks = a.Kp / BK;
+  if (a.kdev) {
+    const int ke = min(a.Kp, max(0, a.kdev[z]) * (a.cplx ? 2 : 1));
+    kblocks = (ke + BK - 1) / BK;
+  }
+  const int nchunk = (kblocks + CRT_CHUNK_BLOCKS - 1) / CRT_CHUNK_BLOCKS;
+
+  if (tid == 0) {
+    for (int i = 0; i < STAGES; i++) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_WARPS);
+    }
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  volatile int* abort = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: residue tiles of A' and B' for modulus l, k block kb
+      long long q = 0;
+      for (int l = 0; l < n && !*abort; l++) {
+        const int ya = (z * n + l) * a.Mp + m0, yb = (z * n + l) * a.Np + n0;
+        for (int kb = 0; kb < kblocks; kb++, q++) {
+          const int stg = (int)(q % STAGES);
+          const uint32_t ph = (uint32_t)((q / STAGES) & 1);
+          if (!mbar_wait(&empty[stg], ph ^ 1u, abort, a.wait)) break;
+          if (q == a.skip_copy) continue;  // test hook: this stage never fills
+          unsigned char* sa = ring + (size_t)stg * STAGE_BYTES;
+          mbar_expect_tx(&full[stg], STAGE_BYTES);
+          tma_load_2d(sa, &mapA, &full[stg], kb * BK, ya);
+          tma_load_2d(sa + TILE_BYTES, &mapB, &full[stg], kb * BK, yb);
+        }
+      }
+      for (long long r = (q > STAGES ? q - STAGES : 0); r < q; r++)
+        if (r != a.skip_copy) mbar_drain(&full[r % STAGES], (uint32_t)((r / STAGES) & 1), a.wait);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: one accumulator per (modulus, k chunk)
+      long long q = 0;
+      int u = 0;
+      bool ok = true;
+      for (int l = 0; l < n && ok; l++) {
+        for (int c = 0; c < nchunk && ok; c++, u++) {
+          const int b = u & 1;
+          const uint32_t uph = (uint32_t)((u >> 1) & 1);
+          if (!mbar_wait(&tempty[b], uph ^ 1u, abort, a.wait)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          uint32_t accum = 0;
+          const int kb1 = min(kblocks, (c + 1) * CRT_CHUNK_BLOCKS);
+          for (int kb = c * CRT_CHUNK_BLOCKS; kb < kb1; kb++, q++) {
+            const int stg = (int)(q % STAGES);
+            const uint32_t ph = (uint32_t)((q / STAGES) & 1);
+            if (!mbar_wait(&full[stg], ph, abort, a.wait)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(ring + (size_t)stg * STAGE_BYTES);
+            const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TILE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; kk++) {
+              umma(tmem + (uint32_t)(b * BN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), accum);
+              accum = 1u;
+            }
+            umma_commit(&empty[stg]);
+          }
+          if (!ok) break;
+          umma_commit(&tfull[b]);
+        }
+      }
+      umma_commit(&done);
+      mbar_drain(&done, 0, a.wait);
+    }
+  } else {
+    // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31 (tile rows) and column half (w - 2) / 4
+    const int lq = warp & 3, ch = (warp - 2) >> 2;
+    const int i = m0 + lq * 32 + lane;
+    int u = 0;
+    bool ok = true;
+    for (int l = 0; l < n && ok; l++) {
+      const float mf = (float)crt_mod(l), inv = __frcp_rn(mf);
+      float acc[64];
+#pragma unroll
+      for (int t = 0; t < 64; t++) acc[t] = 0.0f;
+      for (int c = 0; c < nchunk; c++, u++) {
+        const int b = u & 1;
+        const uint32_t uph = (uint32_t)((u >> 1) & 1);
+        if (!mbar_wait(&tfull[b], uph, abort, a.wait)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * BN + ch * 64);
+        uint32_t v[32];
+        tmem_ld32(taddr, v);
+#pragma unroll
+        for (int t = 0; t < 32; t++) acc[t] += crt_fold(__uint_as_float(v[t]), mf, inv);
+        tmem_ld32(taddr + 32, v);
+#pragma unroll
+        for (int t = 0; t < 32; t++) acc[32 + t] += crt_fold(__uint_as_float(v[t]), mf, inv);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
+      if (!ok) break;
+      // X mod m_l in [0, m_l) for this thread's row and 64 embedded columns, one byte each
+      uint32_t w[16];
+#pragma unroll
+      for (int t = 0; t < 16; t++) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int s4 = 0; s4 < 4; s4++) {
+          float r = crt_fold(acc[4 * t + s4], mf, inv);
+          r = r < 0.0f ? r + mf : r;
+          r = r >= mf ? r - mf : r;
+          word |= (uint32_t)r << (8 * s4);
+        }
+        w[t] = word;
+      }
+      uint4* dst = reinterpret_cast<uint4*>(a.R + z * a.zR + ((size_t)l * a.Mp + i) * a.Np + n0 + ch * 64);
+#pragma unroll
+      for (int t = 0; t < 4; t++) dst[t] = make_uint4(w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+  if (*abort && tid == 0) set_status(status, ST_ETIMEOUT, -2);
+}
+
+// Constants of the reconstruction for n moduli: X = sum_l t_l (M / m_l) mod M with
+// t_l = r_l y_l mod m_l, y_l = (M / m_l)^-1 mod m_l.
+struct CrtRecon {
+  uint32_t y[CRT_MAXMOD];
+  uint32_t Nl[CRT_MAXMOD][4];  // M / m_l, 32-bit limbs, least significant first
+  uint32_t Mv[4], Mh[4];       // M and M / 2
+  float inv_mf;                // 2^{32 b} / M
+  int b;                       // limb at which the quotient estimate starts: max(0, top limb of M - 1)
+  int n;
+};
+
+// 128-bit magnitude (hi, lo) to the nearest double (ties to even), from its bits.
+__device__ __forceinline__ double u128_to_double(unsigned long long hi, unsigned long long lo) {
+  if (hi == 0ull && lo == 0ull) return 0.0;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  unsigned long long h, l;
+  if (lz == 0) {
+    h = hi;
+    l = lo;
+  } else if (lz < 64) {
+    h = (hi << lz) | (lo >> (64 - lz));
+    l = lo << lz;
+  } else {
+    h = lo << (lz - 64);
+    l = 0ull;
+  }
+  unsigned long long mant = h >> 11;  // 53 significant bits
+  const unsigned long long rest = h & 0x7ffull;
+  if (rest > 0x400ull || (rest == 0x400ull && (l != 0ull || (mant & 1ull)))) mant++;
+  int ex = 127 - lz;  // position of the leading bit
+  if (mant >> 53) {
+    mant >>= 1;
+    ex++;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(ex + 1023) << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+__device__ __forceinline__ bool ge4(const uint32_t (&x)[4], const uint32_t (&y)[4]) {
+  for (int t = 3; t >= 0; t--)
+    if (x[t] != y[t]) return x[t] > y[t];
+  return true;
+}
+
+// The signed integer X with X = r_l (mod m_l) for the residues r_l at R[l * plane], |X| < M / 2,
+// as a double times 2^e.
+__device__ __forceinline__ double crt_value(const uint8_t* R, long long plane, const CrtRecon& cr, int e) {
+  uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;  // S = sum_l t_l M / m_l < 16 M
+#pragma unroll
+  for (int l = 0; l < CRT_MAXMOD; l++) {
+    if (l < cr.n) {
+      const uint32_t t = ((uint32_t)R[l * plane] * cr.y[l]) % crt_mod(l);
+      unsigned long long c = (unsigned long long)t * cr.Nl[l][0] + s0;
+      s0 = (uint32_t)c;
+      c = (c >> 32) + (unsigned long long)t * cr.Nl[l][1] + s1;
+      s1 = (uint32_t)c;
+      c = (c >> 32) + (unsigned long long)t * cr.Nl[l][2] + s2;
+      s2 = (uint32_t)c;
+      c = (c >> 32) + (unsigned long long)t * cr.Nl[l][3] + s3;
+      s3 = (uint32_t)c;
+      s4 += (uint32_t)(c >> 32);
+    }
+  }
+  // q = floor(S / M) within one: S / M < 16 estimated from the three limbs of S from limb b
+  // up (M 2^{-32 b} >= 2^32 unless M < 2^32, so the limbs below b do not matter)
+  const uint32_t a2 = cr.b == 0 ? s2 : cr.b == 1 ? s3 : s4;
+  const uint32_t a1 = cr.b == 0 ? s1 : cr.b == 1 ? s2 : s3;
+  const uint32_t a0 = cr.b == 0 ? s0 : cr.b == 1 ? s1 : s2;
+  const float sf = __fmaf_rn((float)a2, 18446744073709551616.0f, __fmaf_rn((float)a1, 4294967296.0f, (float)a0));
+  const unsigned q = (unsigned)(sf * cr.inv_mf);
+  uint32_t x[4];
+  long long d = 0;
+  unsigned long long pm = 0;
+  const uint32_t sl[4] = {s0, s1, s2, s3};
+#pragma unroll
+  for (int t = 0; t < 4; t++) {
+    pm += (unsigned long long)q * cr.Mv[t];
+    d += (long long)sl[t] - (long long)(uint32_t)pm;
+    x[t] = (uint32_t)d;
+    d >>= 32;
+    pm >>= 32;
+  }
+  d += (long long)s4 - (long long)pm;  // the top limb: -1, 0 or 1 after one of the corrections below
+  if (d < 0) {  // q one too large: X += M
+    unsigned long long c = 0;
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      c += (unsigned long long)x[t] + cr.Mv[t];
+      x[t] = (uint32_t)c;
+      c >>= 32;
+    }
+  } else if (d > 0 || ge4(x, cr.Mv)) {  // q one too small: X -= M
+    long long b = 0;
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      b += (long long)x[t] - (long long)cr.Mv[t];
+      x[t] = (uint32_t)b;
+      b >>= 32;
+    }
+  }
+  // symmetric representative: X > M / 2 stands for X - M
+  bool neg = false;
+  if (!ge4(cr.Mh, x)) {
+    neg = true;
+    long long b = 0;
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      b += (long long)cr.Mv[t] - (long long)x[t];
+      x[t] = (uint32_t)b;
+      b >>= 32;
+    }
+  }
+  const double v = u128_to_double(((unsigned long long)x[3] << 32) | x[2], ((unsigned long long)x[1] << 32) | x[0]);
+  return ldexp(neg ? -v : v, e);
+}
+
+// C = alpha 2^{e_i + f_j - 2p} X + beta C for the logical outputs (lower: j <= i only).
+template <typename T>
+__global__ void __launch_bounds__(256) crt_recon_kernel(const uint8_t* R, long long zR, int Mp, int Np, int M, int N,
+                                                        const int* ea, const int* eb, long long zEa, long long zEb,
+                                                        int sc, const CrtRecon cr, T* C, int ldc, long long zC,
+                                                        long long zC2, int nb2, double alpha, double beta,
+                                                        int lower) {
+  const int z = blockIdx.z, j = blockIdx.x * 256 + threadIdx.x;
+  if (j >= N) return;
+  const long long plane = (long long)Mp * Np;
+  for (int i = blockIdx.y; i < M; i += gridDim.y) {
+    if (lower && j > i) continue;
+    const uint8_t* Rz = R + z * zR + (size_t)i * Np;
+    const int e = ea[z * zEa + i] + eb[z * zEb + j] + sc;
+    T* cp = C + item_off(z, zC, zC2, nb2) + (size_t)i * ldc + j;
+    if constexpr (sizeof(T) == 16) {
+      zc v{alpha * crt_value(Rz + 2 * j, plane, cr, e), alpha * crt_value(Rz + 2 * j + 1, plane, cr, e)};
+      if (beta != 0.0) v = v + beta * (*cp);
+      *cp = v;
+    } else {
+      double v = alpha * crt_value(Rz + j, plane, cr, e);
+      if (beta != 0.0) v += beta * (*cp);
+      *cp = v;
+    }
+  }
+}
+
 // ---- tensor maps (driver entry point looked up once through the runtime)
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static std::once_flag once;
@@ -577,10 +873,64 @@ static int padded_k(int K, bool cplx) {
   return round_up(Ke > 0 ? Ke : 1, OZ_KSTEP);
 }
 
+// Residue plan for padded length Kp and at least `bits` bits per operand: the fewest
+// moduli n whose product M satisfies 2 Kp 2^{2p} <= M with p >= bits (p as large as M
+// allows, at most 62), and the reconstruction constants.  False if 16 moduli fall short.
+struct CrtPlan {
+  int n, p;
+  CrtRecon cr;
+};
+static bool crt_plan(int Kp, int bits, CrtPlan* pl) {
+  typedef unsigned __int128 u128;
+  u128 M = 1;
+  for (int n = 1; n <= CRT_MAXMOD; n++) {
+    M *= crt_mod(n - 1);
+    const u128 room = M / ((u128)2 * (u128)Kp);  // 2^{2p} <= room
+    int lg = -1;
+    for (u128 t = room; t; t >>= 1) lg++;
+    const int p = lg < 0 ? -1 : std::min(lg / 2, 62);
+    if (p < bits) continue;
+    pl->n = n;
+    pl->p = p;
+    CrtRecon& c = pl->cr;
+    c = CrtRecon{};
+    c.n = n;
+    int top = 0;
+    for (int t = 0; t < 4; t++) {
+      c.Mv[t] = (uint32_t)(M >> (32 * t));
+      c.Mh[t] = (uint32_t)((M >> 1) >> (32 * t));
+      if (c.Mv[t]) top = t;
+    }
+    c.b = std::max(0, top - 1);
+    c.inv_mf = (float)(std::ldexp(1.0, 32 * c.b) / (double)M);
+    for (int l = 0; l < n; l++) {
+      const uint32_t m = crt_mod(l);
+      const u128 Nl = M / m;
+      for (int t = 0; t < 4; t++) c.Nl[l][t] = (uint32_t)(Nl >> (32 * t));
+      const uint32_t r = (uint32_t)(Nl % m);
+      uint32_t y = 1;
+      while ((r * y) % m != 1u) y++;  // r is coprime to m
+      c.y[l] = y;
+    }
+    return true;
+  }
+  return false;
+}
+
+// S > 0: S digits of 6 bits (digit-pair products); S < 0: residues carrying at least 6|S|
+// bits (digit pairs again when 16 moduli cannot).
+static bool residue_form(int S, int Kp, CrtPlan* pl) { return S < 0 && crt_plan(Kp, OZ_BITS * -S, pl); }
+
 size_t ozaki_workspace_bytes(int M, int N, int K, bool cplx, int S) {
   const int Kp = padded_k(K, cplx);
   const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
-  const size_t b = (size_t)S * ((size_t)Mp + Np) * Kp * 2 + sizeof(int) * ((size_t)Mp + Np) + 1024;
+  CrtPlan pl;
+  size_t b;
+  if (residue_form(S, Kp, &pl))
+    b = (size_t)pl.n * (((size_t)Mp + Np) * Kp * 2 + (size_t)Mp * Np);
+  else
+    b = (size_t)std::abs(S) * ((size_t)Mp + Np) * Kp * 2;
+  b += sizeof(int) * ((size_t)Mp + Np) + 1024;
   return (b + 255) & ~size_t(255);
 }
 
@@ -589,8 +939,9 @@ int ozaki_tiles(int M, int N, bool cplx) {
 }
 
 // count items, item z at A + z sA, B + z sB, C + z sC.  work holds, for all items, the A
-// digits [count][S][Mp][Kp], then the B digits [count][S][Np][Kp], then the exponents
-// [count][Mp] and [count][Np] (within count * ozaki_workspace_bytes).
+// planes [count][P][Mp][Kp], then the B planes [count][P][Np][Kp] (P = S digits or n
+// residues), then (residues) the residues of the product [count][n][Mp][Np] as bytes, then
+// the exponents [count][Mp] and [count][Np] (within count * ozaki_workspace_bytes).
 template <typename T>
 bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda, long long sA, const T* B,
                 int ldb, long long sB, double beta, T* C, int ldc, long long sC, int count, int lower, int S,
@@ -601,22 +952,61 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   const bool cplx = sizeof(T) == 16;
   const int Kp = padded_k(K, cplx);
   const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
-  const long long zA = (long long)S * Mp * Kp, zB = (long long)S * Np * Kp;
+  CrtPlan pl;
+  const bool res = residue_form(S, Kp, &pl);
+  const int P = res ? pl.n : std::abs(S);  // planes per operand
+  const long long zA = (long long)P * Mp * Kp, zB = (long long)P * Np * Kp;
+  const long long zR = res ? (long long)P * Mp * Np : 0;
   __nv_bfloat16* Ad = static_cast<__nv_bfloat16*>(work);
   __nv_bfloat16* Bd = Ad + zA * count;
-  int* ea = reinterpret_cast<int*>(Bd + zB * count);
+  uint8_t* R = reinterpret_cast<uint8_t*>(Bd + zB * count);
+  int* ea = reinterpret_cast<int*>(R + zR * count);
   int* eb = ea + (size_t)Mp * count;
-  // zero digits and exponents (padding rows/columns and k beyond K stay zero)
-  cudaMemsetAsync(work, 0, ((size_t)(zA + zB) * 2 + sizeof(int) * ((size_t)Mp + Np)) * count, s);
+  // zero planes and exponents (padding rows/columns and k beyond K stay zero)
+  cudaMemsetAsync(work, 0, (size_t)(zA + zB) * 2 * count, s);
+  cudaMemsetAsync(ea, 0, sizeof(int) * ((size_t)Mp + Np) * count, s);
   if (K > 0) {
-    count_launch();
-    oz_split_kernel<T><<<dim3((M + 31) / 32, count), 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp,
-                                                                   (long long)Mp * Kp, zA, S, ea, Mp, kscale, sks,
-                                                                   kdev, sA2, nb2);
-    count_launch();
-    oz_split_kernel<T><<<dim3((N + 31) / 32, count), 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp,
-                                                                   (long long)Np * Kp, zB, S, eb, Np, nullptr, 0,
-                                                                   kdev, sB2, nb2);
+    const dim3 ga((M + 31) / 32, count), gb((N + 31) / 32, count);
+    count_launch(2);
+    if (res) {
+      oz_split_kernel<T, true><<<ga, 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, zA, P, pl.p,
+                                                  ea, Mp, kscale, sks, kdev, sA2, nb2);
+      oz_split_kernel<T, true><<<gb, 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, zB, P, pl.p,
+                                                  eb, Np, nullptr, 0, kdev, sB2, nb2);
+    } else {
+      oz_split_kernel<T, false><<<ga, 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, zA, P, 0,
+                                                   ea, Mp, kscale, sks, kdev, sA2, nb2);
+      oz_split_kernel<T, false><<<gb, 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, zB, P, 0,
+                                                   eb, Np, nullptr, 0, kdev, sB2, nb2);
+    }
+  }
+  const long long wait = wait_cycles > 0 ? wait_cycles : (1ll << 32);
+  dim3 grid(Np / OZ_BN, Mp / OZ_BM, count);
+  CUtensorMap ma, mb;
+  if (!digit_map(&ma, Ad, (long long)count * P * Mp, Kp) || !digit_map(&mb, Bd, (long long)count * P * Np, Kp))
+    return false;
+  if (res) {
+    CrtArgs ca;
+    ca.Ad = Ad;
+    ca.Bd = Bd;
+    ca.R = R;
+    ca.Mp = Mp;
+    ca.Np = Np;
+    ca.Kp = Kp;
+    ca.n = P;
+    ca.cplx = cplx ? 1 : 0;
+    ca.lower = lower;
+    ca.zR = zR;
+    ca.kdev = kdev;
+    ca.wait = wait;
+    ca.skip_copy = skip_copy;
+    cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM);
+    count_launch(2);
+    crt_tc_kernel<<<grid, tcg::THREADS, tcg::SMEM, s>>>(ma, mb, ca, status);
+    crt_recon_kernel<T><<<dim3((N + 255) / 256, std::min(M, 65535), count), 256, 0, s>>>(R, zR, Mp, Np, M, N, ea, eb, Mp, Np,
+                                                                         -2 * pl.p, pl.cr, C, ldc, sC, sC2, nb2,
+                                                                         alpha, beta, lower);
+    return true;
   }
   OzArgs oa;
   oa.Ad = Ad;
@@ -630,7 +1020,7 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   oa.Mp = Mp;
   oa.Np = Np;
   oa.Kp = Kp;
-  oa.S = S;
+  oa.S = P;
   oa.cplx = cplx ? 1 : 0;
   oa.lower = lower;
   oa.alpha = alpha;
@@ -645,12 +1035,8 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   oa.zC2 = sC2;
   oa.nb2 = nb2;
   oa.kdev = kdev;
-  oa.wait = wait_cycles > 0 ? wait_cycles : (1ll << 32);
+  oa.wait = wait;
   oa.skip_copy = skip_copy;
-  dim3 grid(Np / OZ_BN, Mp / OZ_BM, count);
-  CUtensorMap ma, mb;
-  if (!digit_map(&ma, Ad, (long long)count * S * Mp, Kp) || !digit_map(&mb, Bd, (long long)count * S * Np, Kp))
-    return false;
   cudaFuncSetAttribute(oz_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM);
   count_launch();
   oz_tc_kernel<<<grid, tcg::THREADS, tcg::SMEM, s>>>(ma, mb, oa, status);

@@ -60,3 +60,20 @@ def test_binding_refuses_without_cuda():
     from paper_2606_09058_gb300 import gks
     with pytest.raises(RuntimeError):
         gks.Context(0)
+
+
+def test_python_options_match_the_header_layout(tmp_path):
+    """gks_opts as the C compiler lays it out (offset of every field, total size) equals the
+    ctypes mirror the binding passes to gks_create."""
+    from paper_2606_09058_gb300 import gks
+    fields = [f for f, _ in gks._Opts._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gks.h"\nint main(void) {\n' +
+                    "".join(f'  printf("{f} %zu\\n", offsetof(gks_opts, {f}));\n' for f in fields) +
+                    '  printf("sizeof %zu\\n", sizeof(gks_opts));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n") if l)
+    for f in fields:
+        assert int(got[f]) == getattr(gks._Opts, f).offset, f
+    assert int(got["sizeof"]) == ctypes.sizeof(gks._Opts)
