@@ -92,6 +92,17 @@ typedef enum { GKS_TRIDIAG_ONE_STAGE = 0, GKS_TRIDIAG_TWO_STAGE = 1 } gks_tridia
  * (45 products for 9 digits). */
 typedef enum { GKS_SPLIT_RESIDUES = 0, GKS_SPLIT_DIGITS = 1 } gks_split;
 
+/* The Hermitian matrix-vector step of the one-stage reduction (opts.hemv), about half of
+ * the reduction's work and bound by the arithmetic unit that runs it (paper Sec. 6).
+ * GKS_HEMV_DIGITS: the stale block of each panel as 8 signed 7-bit digits of Re and Im of
+ * every entry (scaled by a power of two of the block's largest entry, 56 bits below it),
+ * the vector the same, products of digit pairs up to the 56-bit level as exact 8-bit
+ * integer dot products with 32-bit sums, weighted and summed in FP64: the error is that of
+ * the 56-bit truncation, relative to the largest entries (normwise).  GKS_HEMV_FP64: FP64
+ * multiply-adds (three real products per complex product).  Mixed precision keeps its
+ * single-precision step. */
+typedef enum { GKS_HEMV_DIGITS = 0, GKS_HEMV_FP64 = 1 } gks_hemv;
+
 /* gks_solve flags. */
 enum {
   /* Skip the copy and Cholesky of S: reuse the factor kept from the last solve on this
@@ -153,6 +164,7 @@ typedef struct {
   int tridiag;         /* gks_tridiag */
   int band;            /* two-stage bandwidth, 2..32 (0 = 32) */
   int split;           /* gks_split: form of the split products (0 = residues) */
+  int hemv;            /* gks_hemv: form of the one-stage matrix-vector step (0 = digits) */
 } gks_opts;
 
 /* One problem of gks_solve_batched: the arguments of gks_solve. */

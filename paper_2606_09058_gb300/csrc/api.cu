@@ -95,6 +95,8 @@ struct gks_ctx {
   int gemm_mode = 0;                   // 0 auto, 1 DFMA only, 2 split products always
   int slices = 9;                      // split products: 6-bit digits per operand, or 6 slices bits
   int split = 0;                       // split-product form: 0 residues (CRT), 1 digit pairs
+  int hemv = 0;                        // one-stage matrix-vector step: 0 integer digits, 1 FP64 pipe
+  int wsdig = 0;                       // workspace holds the digit planes of the stale block
   int nbb = 256;                       // outer block of the two-level blocked stages (active)
   int nbb_default = 256;               // opts.block, used for shapes the tuner has not seen
   bool nbb_fixed = false;              // opts.block given: no size-dependent default
@@ -146,7 +148,7 @@ struct gks_ctx {
   int am = -1, ank = -1, aes = -1;
   // offsets (bytes) of per-item arrays; each holds nk items
   size_t oA, oL, oF, oFB, oU, oQ, opart, oy, ouw, oSg, oV, oG, oT, oY, oY2, ou, op, oph, otau, otb, od, oe, oZ, oocc, oks, onrho,
-      oweights, oeb, odc, oticket, oAf, oRY, oRT, oRR, onrm, orstat, operm, oflag, oBd, oV2, otau2, oprog, oerr,
+      oweights, oeb, odc, oticket, oAf, oRY, oRT, oRR, onrm, orstat, operm, oflag, oBd, oV2, otau2, oprog, oerr, oqr, oD, oud, ofu, ormax,
       otau1, oT1, oP1, oP2, oVT, oXb, oGb, oYb, oZb, oXp, oVw, otw, oGw, oTw, oYw, oY2w;
   int ldt2 = 0, nblkmax = 0;
   long long sMM, sF, sFB, sU, spart, sy, sV, sG, sT, sY, sVec;
@@ -259,8 +261,9 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   const int want = pick_width(c, m, es, shape_spin(nc));
   const int mixed = c->precision != GKS_FP64 ? 1 : 0;
   const int two = c->tridiag == GKS_TRIDIAG_TWO_STAGE ? c->band : 0;
+  const int dig = c->hemv == 0 && !mixed ? 1 : 0;
   if (c->ws && c->m == m && c->n == n && c->nk == nk && c->es == es && c->nc == nc && c->nbb == want &&
-      c->wsmixed == mixed && c->wstwo == two)
+      c->wsmixed == mixed && c->wstwo == two && c->wsdig == dig)
     return GKS_OK;
   release_ws(c);
   c->nbb = want;
@@ -288,7 +291,15 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->opart = a.take<char>(elems(c->spart));
   c->oy = a.take<char>(elems(c->sy));
   c->ouw = a.take<double>((size_t)3 * m * nk);
-  c->oSg = es == 16 ? a.take<double>(MM * nk) : 0;
+  c->oSg = es == 16 && !dig ? a.take<double>(MM * nk) : 0;
+  if (dig) {
+    // digit planes of the stale block and of u (16 planes complex, 8 real), scale exponents
+    const size_t ldd = ((size_t)m + 15) / 16 * 16, npl = es == 16 ? 16 : 8;
+    c->oD = a.take<char>(ldd * ldd * npl * nk);  // rows up to the 16-multiple the panels reach
+    c->oud = a.take<char>(ldd * npl * nk);
+    c->ofu = a.take<int>((size_t)nk);
+    c->ormax = a.take<unsigned long long>(ldd * nk);
+  }
   c->oV = a.take<char>(elems(c->sV));
   c->oG = a.take<char>(elems(c->sG));
   c->oT = a.take<char>(elems(c->sT));
@@ -321,6 +332,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
     c->otau2 = a.take<char>(elems((long long)m * c->ldt2));
     c->oprog = a.take<int>((size_t)m * nk);
     c->oerr = a.take<int>(4);
+    c->oqr = a.take<char>(qr_scratch_bytes(nk, es));
     c->otau1 = a.take<char>(elems((long long)m + bb));
     c->oT1 = a.take<char>(elems((long long)(m / bb + 2) * bb * bb));
     c->oP1 = a.take<char>(elems((long long)m * 2 * bb));
@@ -366,6 +378,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   cudaMemset(c->st, 0, sizeof(DevStatus) * nk);
   c->wsmixed = mixed;
   c->wstwo = two;
+  c->wsdig = dig;
   c->m = m;
   c->n = n;
   c->nk = nk;
@@ -559,7 +572,9 @@ void gmx(gks_ctx* c, int count, int opA, int opB, int M, int N, int K, double al
   }
 }
 
-// gmx for a two-level batch: item z of A, B, C at (z / nb2) sX + (z % nb2) sX2.
+// gmx for a two-level batch: item z of A, B, C at (z / nb2) sX + (z % nb2) sX2 (count a
+// multiple of nb2).  Split products run in launches of whole outer groups when one group's
+// workspace fits, else of runs within a group (single-level, stride sX2).
 template <typename T>
 void gmx2(gks_ctx* c, int count, int nb2, int opA, int opB, int M, int N, int K, double alpha, const T* A, int lda,
           long long sA, long long sA2, const T* B, int ldb, long long sB, long long sB2, double beta, T* C, int ldc,
@@ -567,34 +582,54 @@ void gmx2(gks_ctx* c, int count, int nb2, int opA, int opB, int M, int N, int K,
   if (M <= 0 || N <= 0 || count <= 0) return;
   const int es = sizeof(T);
   const double fl = gemm_flops(es, M, N, K, 0, count);
-  const int per = split_worth(c, count, M, N, K, es, fl)
+  auto fp64 = [&](const T* Ap, const T* Bp, T* Cp, int cnt, int nb, long long a1, long long a2, long long b1,
+                  long long b2, long long c1, long long c2) {
+    int tok = c->prof.begin();
+    GemmBatch g{};
+    g.base = GemmDesc{Ap, Bp, Cp, nullptr, M, N, K, lda, ldb, ldc};
+    g.sA = a1;
+    g.sB = b1;
+    g.sC = c1;
+    g.nb2 = nb;
+    g.sA2 = a2;
+    g.sB2 = b2;
+    g.sC2 = c2;
+    g.count = cnt;
+    g.opA = opA;
+    g.opB = opB;
+    g.alpha = alpha;
+    g.beta = beta;
+    gemm<T>(g, M, N, c->stream);
+    c->prof.end(tok, PC_GEMM, gemm_flops(es, M, N, K, 0, cnt), gemm_bytes(es, M, N, K, 0, cnt, beta != 0.0));
+  };
+  const int per = (count % nb2 == 0 && split_worth(c, count, M, N, K, es, fl))
                       ? oz_reserve(c, ozaki_workspace_bytes(M, N, K, es == 16, sform(c)), count)
                       : 0;
-  if (per >= count) {
-    Rec r(c, PC_OZAKI, fl, gemm_bytes(es, M, N, K, 0, count, beta != 0.0));
-    if (ozaki_gemm<T>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, count, 0, sform(c), c->oz,
-                      c->st ? c->st : c->gst, c->stream, nullptr, 0, nullptr, c->wait_cycles, -1, sA2, sB2, sC2,
-                      nb2))
-      return;
+  if (per == 0) {
+    fp64(A, B, C, count, nb2, sA, sA2, sB, sB2, sC, sC2);
+    return;
   }
-  // the FP64 kernel (small products, or a batch beyond one launch's digit workspace)
-  int tok = c->prof.begin();
-  GemmBatch g{};
-  g.base = GemmDesc{A, B, C, nullptr, M, N, K, lda, ldb, ldc};
-  g.sA = sA;
-  g.sB = sB;
-  g.sC = sC;
-  g.nb2 = nb2;
-  g.sA2 = sA2;
-  g.sB2 = sB2;
-  g.sC2 = sC2;
-  g.count = count;
-  g.opA = opA;
-  g.opB = opB;
-  g.alpha = alpha;
-  g.beta = beta;
-  gemm<T>(g, M, N, c->stream);
-  c->prof.end(tok, PC_GEMM, fl, gemm_bytes(es, M, N, K, 0, count, beta != 0.0));
+  auto split = [&](const T* Ap, const T* Bp, T* Cp, int cnt, int nb, long long a1, long long a2, long long b1,
+                   long long b2, long long c1, long long c2) {
+    Rec r(c, PC_OZAKI, gemm_flops(es, M, N, K, 0, cnt), gemm_bytes(es, M, N, K, 0, cnt, beta != 0.0));
+    if (!ozaki_gemm<T>(opA, opB, M, N, K, alpha, Ap, lda, a1, Bp, ldb, b1, beta, Cp, ldc, c1, cnt, 0, sform(c), c->oz,
+                       c->st ? c->st : c->gst, c->stream, nullptr, 0, nullptr, c->wait_cycles, -1, a2, b2, c2, nb))
+      fp64(Ap, Bp, Cp, cnt, nb, a1, a2, b1, b2, c1, c2);
+  };
+  const int ng = count / nb2;
+  if (per >= nb2) {
+    const int gper = per / nb2;
+    for (int g0 = 0; g0 < ng; g0 += gper) {
+      const int gc = std::min(gper, ng - g0);
+      split(A + g0 * sA, B + g0 * sB, C + g0 * sC, gc * nb2, nb2, sA, sA2, sB, sB2, sC, sC2);
+    }
+    return;
+  }
+  for (int g = 0; g < ng; g++)
+    for (int j0 = 0; j0 < nb2; j0 += per) {
+      const int jc = std::min(per, nb2 - j0);
+      split(A + g * sA + j0 * sA2, B + g * sB + j0 * sB2, C + g * sC + j0 * sC2, jc, 0, sA2, 0, sB2, 0, sC2, 0);
+    }
 }
 
 // rho_k = C_k diag(ks_k) C_k^H over the leading n_rho(k) columns (n_rho read on the device),
@@ -884,30 +919,50 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   // panels of at most 128 steps: the per-step corrections grow with the panel length, the
   // deferred update runs fine at K = 128; small orders are latency-bound per step (64)
   const int pw = M < 2048 ? std::min(NB, ldu) : std::min(2 * NB, ldu);
-  // complex: three-multiplication products need Re + Im of the stale block (per panel)
-  double* uw = es == 16 ? at<double>(c, c->ouw) : nullptr;
-  double* Sg = es == 16 ? at<double>(c, c->oSg) : nullptr;
+  // digit form of the matrix-vector step (FP64 types): digits of the stale block per panel;
+  // else, complex: three-multiplication products need Re + Im of the stale block (per panel)
+  HemvDigits hdv{};
+  const HemvDigits* hd = nullptr;
+  if constexpr (std::is_same<T, double>::value || std::is_same<T, zc>::value) {
+    if (c->wsdig) {
+      const int ldd = (M + 15) / 16 * 16, npl = es == 16 ? 16 : 8;
+      hdv.D = at<signed char>(c, c->oD);
+      hdv.sD = (long long)ldd * ldd * npl;
+      hdv.ldd = ldd;
+      hdv.ud = at<signed char>(c, c->oud);
+      hdv.sud = (long long)ldd * npl;
+      hdv.fu = at<int>(c, c->ofu);
+      hdv.rmax = at<unsigned long long>(c, c->ormax);
+      hd = &hdv;
+    }
+  }
+  double* uw = es == 16 && !hd ? at<double>(c, c->ouw) : nullptr;
+  double* Sg = es == 16 && !hd ? at<double>(c, c->oSg) : nullptr;
+  const double npl = es == 16 ? 16.0 : 8.0;
   for (int jh = M - 1; jh >= 2; jh -= pw) {
     const int jl = std::max(2, jh - pw + 1);  // steps jh .. jl in this panel
     {
-      Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * es * jh * nk);
-      if (Sg) hetrd_sums(reinterpret_cast<const zc*>(A), M, c->sMM, jh, Sg, nk, s);
-      hetrd_reflector<T>(A, M, c->sMM, jh, u, c->sVec, tau, M, nk, s, uw);
+      Rec r(c, PC_HETRD_VEC, 0.0, (hd ? 0.5 * es + npl : 2.0 * es) * jh * (hd ? jh : 1) * nk);
+      if (hd) hetrd_digits<T>(A, M, c->sMM, jh, hdv, nk, s);
+      else if (Sg) hetrd_sums(reinterpret_cast<const zc*>(A), M, c->sMM, jh, Sg, nk, s);
+      hetrd_reflector<T>(A, M, c->sMM, jh, u, c->sVec, tau, M, nk, s, uw, hd);
     }
     for (int j = jh; j >= jl; j--) {
       const int k = jh - j;  // panel steps already taken
       const double jj = (double)j * j;
       {
+        // algorithmic bytes: the digit planes of the j x j block (full matrix), or the
+        // lower triangle (and Re + Im sums) in FP64
         Rec r(c, PC_HETRD_HEMV, cmul(es) * (jj + 2.0 * j * k) * nk,
-              (0.5 * jj * (es == 16 ? 1.5 : 1.0) + 2.0 * j * k + 4.0 * j) * es * nk);
+              ((hd ? jj * npl : 0.5 * jj * (es == 16 ? 1.5 : 1.0) * es) + (2.0 * j * k + 4.0 * j) * es) * nk);
         hetrd_phemv<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, U, Q, ldu, c->sU, k, part, c->spart, y, c->sy, tk,
-                       nk, s, Sg, uw);
+                       nk, s, Sg, uw, hd);
       }
       const int rowupd = (j > jl) ? 1 : 0;
       {
         Rec r(c, PC_HETRD_RANK2, cmul(es) * 2.0 * j * (k + 1) * (1 + rowupd) * nk, (2.0 * j * (k + 1) + 4.0 * j) * es * nk);
         hetrd_pupdate<T>(A, M, c->sMM, j, u, p, c->sVec, tau, M, U, Q, ldu, c->sU, k, y, c->sy, rowupd, tk + nk, nk,
-                         s, uw);
+                         s, uw, hd);
       }
     }
     // deferred rank-2k update of the trailing block [0:jl, 0:jl]
@@ -947,7 +1002,8 @@ void he2hb_run(gks_ctx* c, T* A, int M, int items) {
     T* Tp = T1 + (size_t)p * b * b;
     {
       Rec r(c, PC_HETRD_VEC, 0.0, 2.0 * sizeof(T) * (double)m * b * kb * items);
-      panel_qr<T>(A, M, MM, r0, k, m, b, kb, tau1 + (size_t)p * b, stau, items, s);
+      panel_qr<T>(A, M, MM, r0, k, m, b, kb, tau1 + (size_t)p * b, stau, items, at<char>(c, c->oqr), c->st,
+                  c->wait_cycles, s);
       panel_v<T>(A, M, MM, r0, k, m, kb, P1, b2, sP, items, s);
     }
     gmx<T>(c, items, OP_C, OP_N, kb, kb, m, 1.0, P1, b2, sP, P1, b2, sP, 0.0, Gb, b, sb);  // G = V^H V
@@ -1651,6 +1707,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
     c->gemm_mode = opts->gemm;
     if (opts->slices > 0) c->slices = opts->slices;
     c->split = opts->split;
+    c->hemv = opts->hemv;
     if (opts->block > 0) c->nbb = opts->block;
     c->nbb_default = c->nbb;
     c->nbb_fixed = opts->block > 0;
@@ -1668,6 +1725,7 @@ gks_status gks_create(gks_ctx** ctx, const gks_opts* opts) {
         (c->reduction != GKS_REDUCE_CHOLESKY && c->reduction != GKS_REDUCE_LOWDIN) ||
         (c->tridiag != GKS_TRIDIAG_ONE_STAGE && c->tridiag != GKS_TRIDIAG_TWO_STAGE) || c->band < 2 ||
         c->band > 32 || (c->split != GKS_SPLIT_RESIDUES && c->split != GKS_SPLIT_DIGITS) ||
+        (c->hemv != GKS_HEMV_DIGITS && c->hemv != GKS_HEMV_FP64) ||
         (opts->debug & ~GKS_DEBUG_SKIP_COPY)) {
       delete c;
       return GKS_EINVAL;
@@ -1786,6 +1844,7 @@ gks_status gks_solve_batched(gks_ctx* ctx, int64_t count, const gks_problem* pro
     sc->gemm_mode = ctx->gemm_mode;
     sc->slices = ctx->slices;
     sc->split = ctx->split;
+    sc->hemv = ctx->hemv;
     sc->nbb = ctx->nbb;
     sc->nbb_default = ctx->nbb_default;
     sc->nbb_fixed = ctx->nbb_fixed;

@@ -40,9 +40,32 @@ void tune_pencil(T* A, int m, int count, int hermitian, cudaStream_t s);
 // panel form U, Q (m x ldu), per-CTA shares (ceil(m/16) x (2 ldu + 2)) and y (2 ldu + 2).
 // hetrd_reflector starts a panel at step j; step j is hetrd_phemv then hetrd_pupdate (which
 // with rowupd also forms the reflector of step j-1).
+// Digit form of the panel matrix-vector step.  The stale block A = [0:n, 0:n] is
+// equilibrated symmetrically by powers of two, A = D Ã D with D = diag(2^{d_i}),
+// d_i = ceil(g_i / 2) for row maxima below 2^{g_i} (largest |Re|, |Im| over the full
+// row), so every |Re ã|, |Im ã| < 1; the full Hermitian Ã (upper triangle mirrored,
+// conjugated) is stored as 8 signed 7-bit digits of Re ã (planes 0..7, most significant
+// first) and Im ã (planes 8..15, complex only): ã = sum_s d_s 2^{-7 - 7s} up to 2^{-56}.
+// ũ = D u gets the same digits below its own scale 2^{fu}.  Then
+// (A u)_i = 2^{d_i} sum over digit pairs s + t <= 8 of exact integer dot products (dp4a,
+// int32 sums) weighted by 2^{fu - 14 - 7(s + t)}.
+// Layout: per row, blocks of 16 columns, each block the planes' 16 bytes one after the
+// other (a row's 16 columns of all planes are 128 or 256 contiguous bytes); ũ the same.
+struct HemvDigits {
+  signed char* D;            // [item][ldd][ldd / 16][planes][16]
+  long long sD;              // item stride (bytes)
+  int ldd;                   // columns per row, multiple of 16
+  signed char* ud;           // [item][ldd / 16][planes][16] digits of ũ (zero beyond the step's length)
+  long long sud;             // item stride (bytes)
+  int* fu;                   // [item] scale exponent of ũ
+  unsigned long long* rmax;  // [item][ldd] row maxima of the stale block (bits of doubles)
+};
 template <typename T>
 void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau, long long stau, int count,
-                     cudaStream_t s, double* uw = nullptr);
+                     cudaStream_t s, double* uw = nullptr, const HemvDigits* hd = nullptr);
+// Digits of the stale block [0:n, 0:n] (FP64 forms only).
+template <typename T>
+void hetrd_digits(const T* A, int lda, long long sA, int n, const HemvDigits& hd, int count, cudaStream_t s);
 // Complex panel form only: Sg = Re + Im of the stale block (lower, leading n x n, stride sA
 // per item, same indexing as A) and uw = (Re u, Im u - Re u, Re u + Im u) per element (3 sv
 // doubles per item); with both, the matrix-vector step uses three real products per
@@ -52,11 +75,11 @@ template <typename T>
 void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
                  long long stau, const T* U, const T* Q, int ldu, long long sU, int k, T* part, long long spart,
                  T* y, long long sy, int* ticket, int count, cudaStream_t s, const double* Sg = nullptr,
-                 const double* uw = nullptr);
+                 const double* uw = nullptr, const HemvDigits* hd = nullptr);
 template <typename T>
 void hetrd_pupdate(T* A, int lda, long long sA, int j, T* u, const T* p, long long sv, double* tau, long long stau,
                    T* U, T* Q, int ldu, long long sU, int k, const T* y, long long sy, int rowupd, int* ticket,
-                   int count, cudaStream_t s, double* uw = nullptr);
+                   int count, cudaStream_t s, double* uw = nullptr, const HemvDigits* hd = nullptr);
 template <typename T>
 void hetrd_finish(const T* A, int lda, long long sA, int m, double* d, double* e, long long sde, T* ph,
                   long long sph, int count, cudaStream_t s);
@@ -130,9 +153,14 @@ double peak_probe(int which, int sms, long long iters, double* out, cudaStream_t
 // Stage 1: in-place QR of the panel A[r0:r0+m, k:k+b] (kb reflectors, complex tau, real
 // beta; v below the diagonal), its unit lower trapezoidal V (m x kb), and the T factor of
 // H_0 .. H_{k-1} = I - V T V^H from G = V^H V.
+// The multi-CTA panel QR splits the rows over up to kQrMaxG CTAs per item (all resident,
+// bounded grid barriers: a wait past wait_limit cycles sets GKS_ETIMEOUT in st[item]);
+// scratch holds qr_scratch_bytes(count, sizeof(T)) bytes.
+constexpr int kQrMaxG = 64;
+size_t qr_scratch_bytes(int count, int es);
 template <typename T>
 void panel_qr(T* A, int lda, long long sA, int r0, int k, int m, int b, int kb, T* taus, long long stau, int count,
-              cudaStream_t s);
+              void* scratch, DevStatus* st, long long wait_limit, cudaStream_t s);
 template <typename T>
 void panel_v(const T* A, int lda, long long sA, int r0, int k, int m, int kb, T* V, int ldv, long long sV, int count,
              cudaStream_t s);

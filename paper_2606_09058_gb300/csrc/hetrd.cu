@@ -15,6 +15,8 @@
 // (16 flops per 16 bytes), above the DFMA pipe's balance point of ~0.15 flop/byte.  The
 // rank-2 updates are therefore deferred over panels of steps and applied as GEMMs (the
 // panel form below), which the product dispatcher can send to the tensor cores.
+#include <type_traits>
+
 #include "dense.h"
 
 namespace gks {
@@ -31,8 +33,106 @@ __device__ __forceinline__ void put_uw(double* uw, int i, double ur, double ui) 
   }
 }
 
+// Scale exponent of a block whose largest magnitude is mx (entries below 2^e).
+__device__ __forceinline__ int dscale(double mx) { return mx > 0.0 ? ilogb(mx) + 1 : 0; }
+// Equilibration exponent d_i = ceil(g_i / 2) of a row whose maximum (bits) lies below 2^{g_i}.
+__device__ __forceinline__ int deq(unsigned long long bits) {
+  return (dscale(__longlong_as_double((long long)bits)) + 1) >> 1;
+}
+
+// The 8 signed 7-bit digits of x (|x| < 2^e): trunc(|x| 2^{56 - e}) in base 128, most
+// significant first, with the sign of x, into d[0..7].
+__device__ __forceinline__ void digits7v(double x, int e, int (&d)[8]) {
+  const long long q = __double2ll_rz(ldexp(fabs(x), 56 - e));
+  const int sg = x < 0.0 ? -1 : 1;
+#pragma unroll
+  for (int s = 0; s < 8; s++) d[s] = sg * (int)((q >> (7 * (7 - s))) & 127);
+}
+
+// Digits of 16 consecutive entries (vals, nv of them valid) packed as the layout's block:
+// NPL planes of 16 bytes (Re planes, then Im planes for complex), stored with 16-byte writes.
+template <typename T, int NPL>
+__device__ __forceinline__ void store_digit_block(const T (&vals)[16], int e, signed char* dst) {
+  uint4 o[NPL];
+#pragma unroll
+  for (int q = 0; q < NPL; q++) o[q] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+  for (int el = 0; el < 16; el++) {
+    int d[8];
+    digits7v((double)re(vals[el]), e, d);
+#pragma unroll
+    for (int sp = 0; sp < 8; sp++) {
+      const uint32_t b = (uint32_t)(d[sp] & 0xff) << (8 * (el & 3));
+      if ((el >> 2) == 0) o[sp].x |= b;
+      else if ((el >> 2) == 1) o[sp].y |= b;
+      else if ((el >> 2) == 2) o[sp].z |= b;
+      else o[sp].w |= b;
+    }
+    if constexpr (NPL == 16) {
+      digits7v((double)im(vals[el]), e, d);
+#pragma unroll
+      for (int sp = 0; sp < 8; sp++) {
+        const uint32_t b = (uint32_t)(d[sp] & 0xff) << (8 * (el & 3));
+        if ((el >> 2) == 0) o[8 + sp].x |= b;
+        else if ((el >> 2) == 1) o[8 + sp].y |= b;
+        else if ((el >> 2) == 2) o[8 + sp].z |= b;
+        else o[8 + sp].w |= b;
+      }
+    }
+  }
+  uint4* out = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int q = 0; q < NPL; q++) out[q] = o[q];
+}
+
+// Digits of u (length j) into ud (blocks of 16 entries, each the planes' 16 bytes: Re
+// 0..7, Im 8..15; zeros from j up to the next multiple of 16) and its scale exponent fu;
+// every thread of the block takes part.
 template <typename T>
-__device__ void reflector_body(T* A, int lda, int j, T* u, double* tau, double* uw) {
+__device__ void u_digits(const T* u, int j, signed char* ud, int* fu, const unsigned long long* rmax) {
+  constexpr bool CPX = !std::is_same<T, double>::value && !std::is_same<T, float>::value;
+  constexpr int NPL = CPX ? 16 : 8;
+  __shared__ double mred[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __syncthreads();
+  double m = 0.0;
+  for (int i = tid; i < j; i += nt) {
+    const int d = deq(rmax[i]);
+    m = fmax(m, ldexp(fmax(fabs((double)re(u[i])), fabs((double)im(u[i]))), d));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) mred[tid >> 5] = m;
+  __syncthreads();
+  if (tid < 32) {
+    double v = tid < (nt >> 5) ? mred[tid] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (tid == 0) mred[0] = v;
+  }
+  __syncthreads();
+  const int e = dscale(mred[0]);
+  if (tid == 0) *fu = e;
+  const int nblk = (j + 15) >> 4;
+  for (int b = tid; b < nblk; b += nt) {
+    T vals[16];
+#pragma unroll
+    for (int el = 0; el < 16; el++) {
+      const int i = 16 * b + el;
+      T v = zero<T>();
+      if (i < j) {
+        const int d = deq(rmax[i]);
+        v = u[i];
+        if constexpr (CPX) v = T{ldexp(re(v), d), ldexp(im(v), d)};
+        else v = ldexp(v, d);
+      }
+      vals[el] = v;
+    }
+    store_digit_block<T, NPL>(vals, e, ud + (size_t)b * (NPL * 16));
+  }
+}
+
+template <typename T>
+__device__ void reflector_body(T* A, int lda, int j, T* u, double* tau, double* uw, signed char* ud = nullptr,
+                               int* fu = nullptr, const unsigned long long* rmax = nullptr) {
   __shared__ double redd[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   T* row = A + (size_t)j * lda;
@@ -47,6 +147,7 @@ __device__ void reflector_body(T* A, int lda, int j, T* u, double* tau, double* 
       put_uw(uw, i, i == j - 1 ? 1.0 : 0.0, 0.0);
     }
     if (tid == 0) tau[j] = 0.0;
+    if (ud) u_digits<T>(u, j, ud, fu, rmax);
     return;
   }
   const double xn = sqrt(xnorm2);
@@ -68,13 +169,16 @@ __device__ void reflector_body(T* A, int lda, int j, T* u, double* tau, double* 
     tau[j] = beta * abs2(upiv);
     row[j - 1] = conjg(ph) * (-xn);                     // lower-storage sub-diagonal
   }
+  if (ud) u_digits<T>(u, j, ud, fu, rmax);
 }
 
 template <typename T>
 __global__ void hetrd_reflector_kernel(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau,
-                                       long long stau, double* uw) {
+                                       long long stau, double* uw, signed char* ud, long long sud, int* fu,
+                                       const unsigned long long* rmax, int ldr) {
   const int z = blockIdx.x;
-  reflector_body<T>(A + z * sA, lda, j, u + z * sv, tau + z * stau, uw ? uw + z * 3 * sv : nullptr);
+  reflector_body<T>(A + z * sA, lda, j, u + z * sv, tau + z * stau, uw ? uw + z * 3 * sv : nullptr,
+                    ud ? ud + z * sud : nullptr, fu ? fu + z : nullptr, rmax ? rmax + (size_t)z * ldr : nullptr);
 }
 
 // Sg[r][c] = Re A[r][c] + Im A[r][c] over the lower triangle of the leading n x n block
@@ -88,6 +192,68 @@ __global__ void hetrd_sums_kernel(const zc* A, int lda, long long sA, int n, dou
       const zc a = A[(size_t)r * lda + c];
       Sg[(size_t)r * lda + c] = a.x + a.y;
     }
+}
+
+// The step's second part once this CTA's p_raw rows [c0, cend) are in prow (shared, one
+// per row): p, the CTA's shares of Q^H u, U^H u and u^H p_raw, and in the last CTA (atomic
+// ticket after a fence) their sums y1, y2, u^H p and kq.  Pointers are the item's.
+template <typename T>
+__device__ void phemv_tail(const T* prow, int c0, int cend, const T* u, T* p, double t, const T* U, const T* Q,
+                           int ldu, int k, T* part, T* y, int* ticket) {
+  __shared__ T red[32];
+  __shared__ int last;
+  const int tid = threadIdx.x;
+  const int pst = 2 * ldu + 2;
+  T d0 = zero<T>();
+  if (tid < cend - c0) {
+    const T pr = prow[tid];
+    p[c0 + tid] = pr;
+    macc(d0, u[c0 + tid], pr);
+  }
+  d0 = block_sum(d0, red);
+  T* mine = part + (size_t)blockIdx.x * pst;
+  if (tid == 0) mine[2 * ldu] = d0;
+  for (int s = tid; s < k; s += blockDim.x) {
+    T a1 = zero<T>(), a2 = zero<T>();
+    for (int r = c0; r < cend; r++) {
+      const T ur = u[r];
+      macc(a1, Q[(size_t)r * ldu + s], ur);
+      macc(a2, U[(size_t)r * ldu + s], ur);
+    }
+    mine[s] = a1;
+    mine[ldu + s] = a2;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(ticket, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  if (tid == 0) *ticket = 0;
+  const int nb = gridDim.x;
+  for (int e = tid; e < k; e += blockDim.x) {
+    T a1 = zero<T>(), a2 = zero<T>();
+    for (int b = 0; b < nb; b++) {
+      a1 += ldcg(part + (size_t)b * pst + e);
+      a2 += ldcg(part + (size_t)b * pst + ldu + e);
+    }
+    y[e] = a1;
+    y[ldu + e] = a2;
+  }
+  T tot = zero<T>();
+  if (tid == 0)
+    for (int b = 0; b < nb; b++) tot += ldcg(part + (size_t)b * pst + 2 * ldu);
+  __syncthreads();
+  T w = zero<T>();
+  for (int e = tid; e < k; e += blockDim.x) {
+    macc(w, y[ldu + e], y[e]);
+    macc(w, y[e], y[ldu + e]);
+  }
+  w = block_sum(w, red);
+  if (tid == 0) {
+    const T uhp = t * (tot - w);
+    y[2 * ldu] = tot;
+    y[2 * ldu + 1] = (0.5 * t) * uhp;
+  }
 }
 
 // Panel (blocked) form.  A panel of steps keeps the trailing block A[0:j,0:j] as it was
@@ -115,8 +281,6 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
   constexpr int NG = 256 / RB;
   __shared__ T colpart[NG][RB];
   __shared__ T rowacc[RB];
-  __shared__ T red[32];
-  __shared__ int last;
   const int z = blockIdx.y, tid = threadIdx.x;
   A += z * sA;
   u += z * sv;
@@ -128,7 +292,6 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
   const double t = tau[z * stau + j];
   const int c0 = blockIdx.x * RB;
   const int cend = min(c0 + RB, j);
-  const int pst = 2 * ldu + 2;
   const int warp = tid >> 5, lane = tid & 31;
   bool done = false;
   if constexpr (sizeof(T) == 16) {
@@ -190,58 +353,185 @@ __global__ void __launch_bounds__(256) hetrd_phemv_kernel(const T* A, int lda, l
     colpart[g][cc] = s;
   }
   __syncthreads();
-  T d0 = zero<T>();
   if (tid < RB && c0 + tid < cend) {
     T pr = rowacc[tid];
 #pragma unroll
     for (int g = 0; g < NG; g++) pr += colpart[g][tid];
-    p[c0 + tid] = pr;
-    macc(d0, u[c0 + tid], pr);
+    rowacc[tid] = pr;
   }
-  d0 = block_sum(d0, red);
-  T* mine = part + (size_t)blockIdx.x * pst;
-  if (tid == 0) mine[2 * ldu] = d0;
-  for (int s = tid; s < k; s += blockDim.x) {
-    T a1 = zero<T>(), a2 = zero<T>();
-    for (int r = c0; r < cend; r++) {
-      const T ur = u[r];
-      macc(a1, Q[(size_t)r * ldu + s], ur);
-      macc(a2, U[(size_t)r * ldu + s], ur);
+  phemv_tail<T>(rowacc, c0, cend, u, p, t, U, Q, ldu, k, part, y, ticket + z);
+}
+
+// ------------------------------------------------------------------ digit form of the step
+//
+// hetrd_dmax_kernel: row maxima of |Re|, |Im| over the full Hermitian rows of the stale
+// block from its lower triangle, where element (r, c) counts for rows r and c.  One CTA per
+// chunk of 64 rows: a warp per row for the rows' own maxima (c <= r), then a thread per
+// column for the column maxima below the diagonal (c < r), one global atomic max per row,
+// and per column and chunk (on the bits of non-negative doubles, which order like the
+// values).
+template <typename T>
+__global__ void __launch_bounds__(256) hetrd_dmax_kernel(const T* A, int lda, long long sA, int n,
+                                                         unsigned long long* rmax, int ldr) {
+  const int z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r0 = blockIdx.x * 64, r1 = min(n, r0 + 64);
+  A += z * sA;
+  rmax += (size_t)z * ldr;
+  for (int r = r0 + warp; r < r1; r += 8) {
+    double m = 0.0;
+    for (int c = lane; c <= r; c += 32) {
+      const T a = A[(size_t)r * lda + c];
+      m = fmax(m, fmax(fabs(re(a)), fabs(im(a))));
     }
-    mine[s] = a1;
-    mine[ldu + s] = a2;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m > 0.0) atomicMax(rmax + r, (unsigned long long)__double_as_longlong(m));
   }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) last = (atomicAdd(ticket + z, 1) == (int)gridDim.x - 1);
-  __syncthreads();
-  if (!last) return;
-  if (tid == 0) ticket[z] = 0;
-  const int nb = gridDim.x;
-  for (int e = tid; e < k; e += blockDim.x) {
-    T a1 = zero<T>(), a2 = zero<T>();
-    for (int b = 0; b < nb; b++) {
-      a1 += ldcg(part + (size_t)b * pst + e);
-      a2 += ldcg(part + (size_t)b * pst + ldu + e);
+  for (int c = tid; c < r1 - 1; c += blockDim.x) {
+    double mc = 0.0;
+    for (int r = max(r0, c + 1); r < r1; r++) {
+      const T a = A[(size_t)r * lda + c];
+      mc = fmax(mc, fmax(fabs(re(a)), fabs(im(a))));
     }
-    y[e] = a1;
-    y[ldu + e] = a2;
+    if (mc > 0.0) atomicMax(rmax + c, (unsigned long long)__double_as_longlong(mc));
   }
-  T tot = zero<T>();
-  if (tid == 0)
-    for (int b = 0; b < nb; b++) tot += ldcg(part + (size_t)b * pst + 2 * ldu);
+}
+
+// hetrd_digits_kernel: 32 x 32 tiles of the full Hermitian [0:n16, 0:n16] (zero outside
+// [0:n, 0:n]); tiles above the diagonal come from the transposed lower tile through shared
+// memory, conjugated.  64 threads: thread t packs row t / 2, columns 16 (t % 2) .. + 15.
+template <typename T>
+__global__ void __launch_bounds__(64) hetrd_digits_kernel(const T* A, int lda, long long sA, int n, HemvDigits hd) {
+  constexpr int NPL = sizeof(T) == 16 ? 16 : 8;
+  __shared__ T tile[32][33];
+  const int z = blockIdx.z, tid = threadIdx.x;
+  const int R0 = blockIdx.y * 32, C0 = blockIdx.x * 32;
+  const int n16 = (n + 15) & ~15;
+  if (R0 >= n16 || C0 >= n16) return;
+  A += z * sA;
+  const bool upper = C0 > R0;
+  // source tile: (R0, C0) itself, or (C0, R0) for tiles above the diagonal
+  const int sr0 = upper ? C0 : R0, sc0 = upper ? R0 : C0;
+  for (int e = tid; e < 32 * 32; e += 64) {
+    const int yy = e >> 5, xx = e & 31;
+    const int r = sr0 + yy, c = sc0 + xx;
+    tile[yy][xx] = (r < n && c < n && c <= r) ? A[(size_t)r * lda + c] : zero<T>();
+  }
   __syncthreads();
-  T w = zero<T>();
-  for (int e = tid; e < k; e += blockDim.x) {
-    macc(w, y[ldu + e], y[e]);
-    macc(w, y[e], y[ldu + e]);
+  const unsigned long long* rm = hd.rmax + (size_t)z * hd.ldd;
+  const int rr = tid >> 1, cbk = tid & 1;
+  const int r = R0 + rr;
+  if (r < n16 && C0 + 16 * cbk < n16) {
+    const int dr = r < n ? deq(rm[r]) : 0;
+    T vals[16];
+#pragma unroll
+    for (int el = 0; el < 16; el++) {
+      const int cc = 16 * cbk + el, c = C0 + cc;
+      T v;
+      if (upper) v = conjg(tile[cc][rr]);
+      else if (c <= r) v = tile[rr][cc];
+      else v = (r < n && c < n) ? conjg(tile[cc][rr]) : zero<T>();  // diagonal tile, upper part
+      const int sh = -(dr + (c < n ? deq(rm[c]) : 0));                  // ã = a 2^{-d_r - d_c}
+      if constexpr (sizeof(T) == 16) vals[el] = T{ldexp(re(v), sh), ldexp(im(v), sh)};
+      else vals[el] = ldexp(v, sh);
+    }
+    store_digit_block<T, NPL>(vals, 0, hd.D + z * hd.sD + (size_t)r * hd.ldd * NPL + (size_t)(C0 / 16 + cbk) * (NPL * 16));
   }
-  w = block_sum(w, red);
-  if (tid == 0) {
-    const T uhp = t * (tot - w);
-    y[2 * ldu] = tot;
-    y[2 * ldu + 1] = (0.5 * t) * uhp;
+}
+
+__device__ __forceinline__ int dp4(unsigned a, unsigned b, int c) { return __dp4a((int)a, (int)b, c); }
+__device__ __forceinline__ int dp4x4(uint4 a, uint4 b, int c) {
+  return dp4(a.w, b.w, dp4(a.z, b.z, dp4(a.y, b.y, dp4(a.x, b.x, c))));
+}
+
+// p_raw = A_stale[0:j, 0:j] u from the digits, 32 rows per CTA (lane = row), the columns in
+// eight ranges (warp w), exact int32 level sums per (row, product, level), summed over the
+// warps in shared memory, then weighted in FP64; then the common tail.  Digit pairs up to
+// level s + t = 8: the dropped rest lies below 2^-63 of the scales (the pairs of level 8
+// alone would otherwise add a one-signed error near the FP64 unit per term).  Complex: the four
+// real products Re a Re u, Im a Im u, Re a Im u, Im a Re u (Re p = first - second,
+// Im p = third + fourth); real: the first only.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) hetrd_phemv_dig_kernel(int j, const T* u, T* p, long long sv,
+                                                                 const double* tau, long long stau, const T* U,
+                                                                 const T* Q, int ldu, long long sU, int k, T* part,
+                                                                 long long spart, T* y, long long sy, int* ticket,
+                                                                 HemvDigits hd) {
+  constexpr bool CPX = sizeof(T) == 16;
+  constexpr int NP = CPX ? 4 : 1;  // real products
+  constexpr int NPL = CPX ? 16 : 8;
+  __shared__ int accs[NP * 9][33][8];
+  __shared__ uint4 ush[8][NPL];  // per warp: u's digits of the current 16 columns
+  __shared__ T prow[32];
+  const int z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c0 = blockIdx.x * 32, cend = min(c0 + 32, j);
+  const int r = min(c0 + lane, j - 1);  // lanes past the last row repeat it (results unused)
+  const int j16 = (j + 15) & ~15;
+  const int chunk = (((j16 + 7) / 8) + 15) & ~15;
+  const int cb = min(j16, warp * chunk), ce = min(j16, cb + chunk);
+  const signed char* D = hd.D + z * hd.sD + (size_t)r * hd.ldd * NPL;
+  const signed char* ud = hd.ud + z * hd.sud;
+  int acc[NP][9];
+#pragma unroll
+  for (int q = 0; q < NP; q++)
+#pragma unroll
+    for (int L = 0; L < 9; L++) acc[q][L] = 0;
+  for (int c = cb; c < ce; c += 16) {
+    // 16 columns: all digit planes of this lane's row (NPL x 16 contiguous bytes) in
+    // flight at once; u's digits (the same for every lane) through shared memory
+    const uint4* ab = reinterpret_cast<const uint4*>(D + (size_t)(c >> 4) * (NPL * 16));
+    uint4 av[NPL];
+#pragma unroll
+    for (int q = 0; q < NPL; q++) av[q] = __ldcs(ab + q);
+    __syncwarp();
+    if (lane < NPL) ush[warp][lane] = __ldg(reinterpret_cast<const uint4*>(ud + (size_t)(c >> 4) * (NPL * 16)) + lane);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+      const uint4 ur = ush[warp][t];
+      uint4 ui;
+      if constexpr (CPX) ui = ush[warp][8 + t];
+#pragma unroll
+      for (int s = 0; s < 8 && s + t <= 8; s++) {
+        acc[0][s + t] = dp4x4(av[s], ur, acc[0][s + t]);
+        if constexpr (CPX) {
+          acc[1][s + t] = dp4x4(av[8 + s], ui, acc[1][s + t]);
+          acc[2][s + t] = dp4x4(av[s], ui, acc[2][s + t]);
+          acc[3][s + t] = dp4x4(av[8 + s], ur, acc[3][s + t]);
+        }
+      }
+    }
   }
+#pragma unroll
+  for (int q = 0; q < NP; q++)
+#pragma unroll
+    for (int L = 0; L < 9; L++) accs[q * 9 + L][lane][warp] = acc[q][L];
+  __syncthreads();
+  if (tid < 32 && c0 + tid < cend) {
+    // exact sums over the warps, then 2^{d_i + fu - 14 - 7L} per level
+    const int E = deq(hd.rmax[(size_t)z * hd.ldd + c0 + tid]) + hd.fu[z] - 14;
+    double pre = 0.0, pim = 0.0;
+#pragma unroll
+    for (int L = 8; L >= 0; L--) {
+      long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+      for (int w = 0; w < 8; w++) {
+        s0 += accs[L][tid][w];
+        if constexpr (CPX) {
+          s1 += accs[9 + L][tid][w];
+          s2 += accs[18 + L][tid][w];
+          s3 += accs[27 + L][tid][w];
+        }
+      }
+      pre += ldexp((double)(s0 - s1), E - 7 * L);
+      if constexpr (CPX) pim += ldexp((double)(s2 + s3), E - 7 * L);
+    }
+    if constexpr (CPX) prow[tid] = T{pre, pim};
+    else prow[tid] = pre;
+  }
+  __syncthreads();
+  const double t = tau[z * stau + j];
+  phemv_tail<T>(prow, c0, cend, u + z * sv, p + z * sv, t, U + z * sU, Q + z * sU, ldu, k, part + z * spart,
+                y + z * sy, ticket + z);
 }
 
 // Sum over aligned groups of 8 lanes (every lane of the warp takes part).
@@ -268,7 +558,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) hetrd_pupdate_kernel(T* A, int lda, long long sA, int j, T* u,
                                                             const T* p, long long sv, double* tau, long long stau,
                                                             T* U, T* Q, int ldu, long long sU, int k, const T* y,
-                                                            long long sy, int rowupd, int* ticket, double* uw) {
+                                                            long long sy, int rowupd, int* ticket, double* uw,
+                                                            signed char* ud, long long sud, int* fu,
+                                                            const unsigned long long* rmax, int ldr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y1s = reinterpret_cast<T*>(smem_raw);
   T* y2s = y1s + (ldu + 1);
@@ -352,7 +644,8 @@ __global__ void __launch_bounds__(256) hetrd_pupdate_kernel(T* A, int lda, long 
   if (!last) return;
   if (tid == 0) ticket[z] = 0;
   __syncthreads();
-  reflector_body<T>(A, lda, j - 1, u, tau, uw);
+  reflector_body<T>(A, lda, j - 1, u, tau, uw, ud ? ud + z * sud : nullptr, fu ? fu + z : nullptr,
+                    rmax ? rmax + (size_t)z * ldr : nullptr);
 }
 
 // d_i = Re A_ii, e_i = |A_{i+1,i}|, ph_0 = 1, ph_{i+1} = ph_i A_{i+1,i}/|A_{i+1,i}|.
@@ -409,9 +702,21 @@ __global__ void gather_reflectors_kernel(const T* A, int lda, long long sA, cons
 
 template <typename T>
 void hetrd_reflector(T* A, int lda, long long sA, int j, T* u, long long sv, double* tau, long long stau, int count,
-                     cudaStream_t s, double* uw) {
+                     cudaStream_t s, double* uw, const HemvDigits* hd) {
   count_launch();
-  hetrd_reflector_kernel<T><<<count, 256, 0, s>>>(A, lda, sA, j, u, sv, tau, stau, uw);
+  hetrd_reflector_kernel<T><<<count, 256, 0, s>>>(A, lda, sA, j, u, sv, tau, stau, uw, hd ? hd->ud : nullptr,
+                                                  hd ? hd->sud : 0, hd ? hd->fu : nullptr, hd ? hd->rmax : nullptr,
+                                                  hd ? hd->ldd : 0);
+}
+
+template <typename T>
+void hetrd_digits(const T* A, int lda, long long sA, int n, const HemvDigits& hd, int count, cudaStream_t s) {
+  if (n <= 0) return;
+  cudaMemsetAsync(hd.rmax, 0, sizeof(unsigned long long) * hd.ldd * count, s);
+  count_launch(2);
+  hetrd_dmax_kernel<T><<<dim3((n + 63) / 64, count), 256, 0, s>>>(A, lda, sA, n, hd.rmax, hd.ldd);
+  const int nt = ((n + 15) / 16 * 16 + 31) / 32;
+  hetrd_digits_kernel<T><<<dim3(nt, nt, count), 64, 0, s>>>(A, lda, sA, n, hd);
 }
 
 void hetrd_sums(const zc* A, int lda, long long sA, int n, double* Sg, int count, cudaStream_t s) {
@@ -424,8 +729,16 @@ void hetrd_sums(const zc* A, int lda, long long sA, int n, double* Sg, int count
 template <typename T>
 void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, long long sv, const double* tau,
                  long long stau, const T* U, const T* Q, int ldu, long long sU, int k, T* part, long long spart,
-                 T* y, long long sy, int* ticket, int count, cudaStream_t s, const double* Sg, const double* uw) {
+                 T* y, long long sy, int* ticket, int count, cudaStream_t s, const double* Sg, const double* uw,
+                 const HemvDigits* hd) {
   count_launch();
+  if constexpr (std::is_same<T, double>::value || std::is_same<T, zc>::value) {
+    if (hd) {
+      hetrd_phemv_dig_kernel<T><<<dim3((j + 31) / 32, count), 256, 0, s>>>(j, u, p, sv, tau, stau, U, Q, ldu, sU,
+                                                                           k, part, spart, y, sy, ticket, *hd);
+      return;
+    }
+  }
   if ((long long)((j + 63) / 64) * count >= 4 * 152)
     hetrd_phemv_kernel<T, 64><<<dim3((j + 63) / 64, count), 256, 0, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q,
                                                                          ldu, sU, k, part, spart, y, sy, ticket, Sg,
@@ -439,12 +752,15 @@ void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, lon
 template <typename T>
 void hetrd_pupdate(T* A, int lda, long long sA, int j, T* u, const T* p, long long sv, double* tau, long long stau,
                    T* U, T* Q, int ldu, long long sU, int k, const T* y, long long sy, int rowupd, int* ticket,
-                   int count, cudaStream_t s, double* uw) {
+                   int count, cudaStream_t s, double* uw, const HemvDigits* hd) {
   const int sm = (int)(4 * sizeof(T) * (ldu + 1));
   if (sm > 48 * 1024) cudaFuncSetAttribute(hetrd_pupdate_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   count_launch();
   hetrd_pupdate_kernel<T><<<dim3((j + 63) / 64, count), 256, sm, s>>>(A, lda, sA, j, u, p, sv, tau, stau, U, Q, ldu,
-                                                                      sU, k, y, sy, rowupd, ticket, uw);
+                                                                      sU, k, y, sy, rowupd, ticket, uw,
+                                                                      hd ? hd->ud : nullptr, hd ? hd->sud : 0,
+                                                                      hd ? hd->fu : nullptr, hd ? hd->rmax : nullptr,
+                                                                      hd ? hd->ldd : 0);
 }
 
 template <typename T>
@@ -503,29 +819,30 @@ void narrow_lower(const T* A, int lda, long long sA, TL* B, int ldb, long long s
 
 #define INST(T)                                                                                            \
   template void hetrd_reflector<T>(T*, int, long long, int, T*, long long, double*, long long, int,         \
-                                   cudaStream_t, double*);                                                 \
+                                   cudaStream_t, double*, const HemvDigits*);                              \
   template void hetrd_phemv<T>(const T*, int, long long, int, const T*, T*, long long, const double*,        \
                                long long, const T*, const T*, int, long long, int, T*, long long, T*, long long, \
-                               int*, int, cudaStream_t, const double*, const double*);                     \
+                               int*, int, cudaStream_t, const double*, const double*, const HemvDigits*);  \
   template void hetrd_pupdate<T>(T*, int, long long, int, T*, const T*, long long, double*, long long, T*,  \
                                  T*, int, long long, int, const T*, long long, int, int*, int, cudaStream_t, \
-                                 double*);                                                                 \
+                                 double*, const HemvDigits*);                                              \
   template void hetrd_finish<T>(const T*, int, long long, int, double*, double*, long long, T*, long long,   \
                                 int, cudaStream_t);                                                        \
   template void gather_reflectors<T, T>(const T*, int, long long, const double*, long long, int, int, T*,    \
-                                        int, long long, double*, long long, int, cudaStream_t);
+                                        int, long long, double*, long long, int, cudaStream_t);               \
+  template void hetrd_digits<T>(const T*, int, long long, int, const HemvDigits&, int, cudaStream_t);
 INST(double)
 INST(zc)
 #undef INST
 #define INST(T)                                                                                            \
   template void hetrd_reflector<T>(T*, int, long long, int, T*, long long, double*, long long, int,         \
-                                   cudaStream_t, double*);                                                 \
+                                   cudaStream_t, double*, const HemvDigits*);                              \
   template void hetrd_phemv<T>(const T*, int, long long, int, const T*, T*, long long, const double*,        \
                                long long, const T*, const T*, int, long long, int, T*, long long, T*, long long, \
-                               int*, int, cudaStream_t, const double*, const double*);                     \
+                               int*, int, cudaStream_t, const double*, const double*, const HemvDigits*);  \
   template void hetrd_pupdate<T>(T*, int, long long, int, T*, const T*, long long, double*, long long, T*,  \
                                  T*, int, long long, int, const T*, long long, int, int*, int, cudaStream_t, \
-                                 double*);                                                                 \
+                                 double*, const HemvDigits*);                                              \
   template void hetrd_finish<T>(const T*, int, long long, int, double*, double*, long long, T*, long long,   \
                                 int, cudaStream_t);
 INST(float)

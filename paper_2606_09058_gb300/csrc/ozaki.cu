@@ -489,7 +489,8 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
 // are bf16-exact integers of magnitude <= 128, so a k chunk of 1024 sums exactly in the
 // FP32 accumulator (<= 2^24).  Eight epilogue warps fold each chunk into a residue kept
 // in FP32 registers (x - m round(x / m), exact on integers) while the tensor cores fill the
-// other accumulator, and write X mod m_l of every element as one byte when the modulus
+// other accumulator, and write t_l = (X mod m_l) y_l mod m_l of every element (the
+// weight of the reconstruction, y_l = (M / m_l)^-1 mod m_l) as one byte when the modulus
 // ends.  One product per modulus: 16 moduli keep p = 55 bits for K up to 16384, where nine
 // 6-bit digits keep 54 bits with 45 digit-pair products.  crt_recon_kernel rebuilds X
 // from its residues in 32-bit limbs and scales it back by 2^{e_i + f_j - 2p}.
@@ -501,6 +502,7 @@ struct CrtArgs {
   uint8_t* R;               // [count][n][Mp][Np] residues of X
   int Mp, Np, Kp, n, cplx, lower;
   long long zR;             // item stride of R (bytes)
+  float y[CRT_MAXMOD];      // (M / m_l)^-1 mod m_l: R holds t_l = (X mod m_l) y_l mod m_l
   const int* kdev;          // optional per-item K read on the device (logical, <= K)
   long long wait;           // bound of every mbarrier wait, in SM clock cycles
   long long skip_copy;      // test hook: the producer leaves out this copy (-1 = none)
@@ -662,7 +664,9 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
         if (lane == 0) mbar_arrive(&tempty[b]);
       }
       if (!ok) break;
-      // X mod m_l in [0, m_l) for this thread's row and 64 embedded columns, one byte each
+      // t_l = (X mod m_l) y_l mod m_l in [0, m_l) for this thread's row and 64 embedded
+      // columns, one byte each (both folds exact: |acc| < 2^24, r y_l < 2^16)
+      const float yl = a.y[l];
       uint32_t w[16];
 #pragma unroll
       for (int t = 0; t < 16; t++) {
@@ -670,6 +674,8 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
 #pragma unroll
         for (int s4 = 0; s4 < 4; s4++) {
           float r = crt_fold(acc[4 * t + s4], mf, inv);
+          r = r < 0.0f ? r + mf : r;
+          r = crt_fold(r * yl, mf, inv);
           r = r < 0.0f ? r + mf : r;
           r = r >= mf ? r - mf : r;
           word |= (uint32_t)r << (8 * s4);
@@ -692,7 +698,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
 }
 
 // Constants of the reconstruction for n moduli: X = sum_l t_l (M / m_l) mod M with
-// t_l = r_l y_l mod m_l, y_l = (M / m_l)^-1 mod m_l.
+// t_l = r_l y_l mod m_l, y_l = (M / m_l)^-1 mod m_l (t_l is what the product kernel stores).
 struct CrtRecon {
   uint32_t y[CRT_MAXMOD];
   uint32_t Nl[CRT_MAXMOD][4];  // M / m_l, 32-bit limbs, least significant first
@@ -734,14 +740,14 @@ __device__ __forceinline__ bool ge4(const uint32_t (&x)[4], const uint32_t (&y)[
   return true;
 }
 
-// The signed integer X with X = r_l (mod m_l) for the residues r_l at R[l * plane], |X| < M / 2,
-// as a double times 2^e.
+// The signed integer X with X y_l = t_l (mod m_l) for the weighted residues t_l at
+// R[l * plane], |X| < M / 2, as a double times 2^e.
 __device__ __forceinline__ double crt_value(const uint8_t* R, long long plane, const CrtRecon& cr, int e) {
   uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;  // S = sum_l t_l M / m_l < 16 M
 #pragma unroll
   for (int l = 0; l < CRT_MAXMOD; l++) {
     if (l < cr.n) {
-      const uint32_t t = ((uint32_t)R[l * plane] * cr.y[l]) % crt_mod(l);
+      const uint32_t t = R[l * plane];
       unsigned long long c = (unsigned long long)t * cr.Nl[l][0] + s0;
       s0 = (uint32_t)c;
       c = (c >> 32) + (unsigned long long)t * cr.Nl[l][1] + s1;
@@ -1000,6 +1006,7 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
     ca.kdev = kdev;
     ca.wait = wait;
     ca.skip_copy = skip_copy;
+    for (int l = 0; l < CRT_MAXMOD; l++) ca.y[l] = l < P ? (float)pl.cr.y[l] : 0.0f;
     cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM);
     count_launch(2);
     crt_tc_kernel<<<grid, tcg::THREADS, tcg::SMEM, s>>>(ma, mb, ca, status);

@@ -448,13 +448,199 @@ __global__ void widen_pad_kernel(const double* Z, int ldz, long long sZ, T* X, i
       X[(size_t)i * ldx + c] = i < m ? from_real<T>(Z[(size_t)i * ldz + c]) : zero<T>();
 }
 
+// Multi-CTA form of the panel QR: the panel's rows are split over G CTAs per item (rows
+// [g R, g R + R)), each keeping its rows in shared memory for the whole panel.  Per column,
+// two grid barriers: after the partial sums of the column's squared norm (and the pivot
+// entry, published by its owner), every CTA forms the same reflector from the G partials
+// summed in a fixed order; after the partial sums of v^H P for the columns to the right,
+// every CTA forms w and updates its rows.  The same arithmetic as panel_qr_kernel up to
+// the order of the sums.  The barrier is a global arrival counter (grid of G x count CTAs,
+// all resident: cooperative launch); every wait is bounded by wait_limit cycles, after
+// which the CTA sets err and the status (ETIMEOUT) and all CTAs leave.
+struct QrScratch {
+  double* pn;      // [count][G] partial squared norms
+  void* pw;        // [count][G][32] partial v^H P (type T)
+  void* palpha;    // [count] pivot entries (type T)
+  unsigned* bar;   // arrival counter
+  int* err;
+};
+
+__device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, int* err, DevStatus* st, int info,
+                                          long long limit, int* stop) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const volatile unsigned* pb = bar;
+    const long long t0 = clock64();
+    int s = 0;
+    while (*pb < target) {
+      if (*reinterpret_cast<volatile int*>(err)) {
+        s = 1;
+        break;
+      }
+      if (clock64() - t0 > limit) {
+        atomicExch(err, 1);
+        set_status(st, ST_ETIMEOUT, info);
+        s = 1;
+        break;
+      }
+    }
+    __threadfence();
+    *stop = s;
+  }
+  __syncthreads();
+  return *stop == 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) panel_qr_coop_kernel(T* A, int lda, long long sA, int r0, int k, int m, int b,
+                                                            int kb, T* taus, long long stau, int G, int R,
+                                                            QrScratch q, DevStatus* st, long long limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);  // R x (b + 1)
+  const int ld = b + 1;
+  __shared__ double red[8];
+  __shared__ T wpart[8][32];
+  __shared__ T wsum[32];
+  __shared__ T coef[2];
+  __shared__ int stop;
+  const int g = blockIdx.x, z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q0 = g * R, q1 = min(m, q0 + R), nr = max(0, q1 - q0);
+  const unsigned ncta = gridDim.x * gridDim.y;
+  unsigned inst = 0;
+  T* Ag = A + z * sA + (size_t)r0 * lda + k;
+  taus += z * stau;
+  double* pn = q.pn + (size_t)z * G;
+  T* pw = static_cast<T*>(q.pw) + (size_t)z * G * 32;
+  T* pal = static_cast<T*>(q.palpha) + z;
+  for (int e = tid; e < nr * b; e += blockDim.x) {
+    const int r = e / b, cc = e % b;
+    P[r * ld + cc] = Ag[(size_t)(q0 + r) * lda + cc];
+  }
+  __syncthreads();
+  for (int c = 0; c < kb; c++) {
+    // partial squared norm of column c below row c, and the pivot entry from its owner
+    double s2 = 0.0;
+    for (int r = max(c + 1 - q0, 0) + tid; r < nr; r += blockDim.x) s2 += absq(P[r * ld + c]);
+    s2 = warp_sum(s2);
+    if (lane == 0) red[warp] = s2;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; w++) t += red[w];
+      __stcg(pn + g, t);
+      if (c >= q0 && c < q1) stcg_s(pal, P[(c - q0) * ld + c]);
+    }
+    if (!grid_wait(q.bar, ++inst * ncta, q.err, st ? st + z : nullptr, c, limit, &stop)) return;
+    if (tid == 0) {
+      double t = 0.0;
+      for (int h = 0; h < G; h++) t += __ldcg(pn + h);
+      T tau, scale;
+      double beta;
+      householder_coef<T>(ldcg_s(pal), t, &tau, &scale, &beta);
+      coef[0] = tau;
+      coef[1] = scale;
+      if (g == 0) taus[c] = tau;
+      if (c >= q0 && c < q1) P[(c - q0) * ld + c] = from_real<T>(beta);
+    }
+    __syncthreads();
+    const T tau = coef[0], scale = coef[1];
+    for (int r = max(c + 1 - q0, 0) + tid; r < nr; r += blockDim.x) P[r * ld + c] = P[r * ld + c] * scale;
+    __syncthreads();
+    // partial sums of conj(v_r) P[r][j] for the columns j > c (v_c = 1)
+    const int ncol = b - c - 1;
+    const int rs = max(c - q0, 0);
+    T acc = zero<T>();
+    if (lane < ncol)
+      for (int r = rs + warp; r < nr; r += 8) {
+        const T v = (q0 + r == c) ? from_real<T>(1.0) : P[r * ld + c];
+        macc(acc, v, P[r * ld + c + 1 + lane]);
+      }
+    wpart[warp][lane] = acc;
+    __syncthreads();
+    if (tid < ncol) {
+      T t = zero<T>();
+      for (int w = 0; w < 8; w++) t += wpart[w][tid];
+      stcg_s(pw + (size_t)g * 32 + tid, t);
+    }
+    if (!grid_wait(q.bar, ++inst * ncta, q.err, st ? st + z : nullptr, c, limit, &stop)) return;
+    if (tid < ncol) {
+      T t = zero<T>();
+      for (int h = 0; h < G; h++) t += ldcg_s(pw + (size_t)h * 32 + tid);
+      wsum[tid] = conjg(tau) * t;
+    }
+    __syncthreads();
+    for (int e = tid; e < (nr - rs) * ncol; e += blockDim.x) {
+      const int r = rs + e / ncol, j = c + 1 + e % ncol;
+      const T v = (q0 + r == c) ? from_real<T>(1.0) : P[r * ld + c];
+      P[r * ld + j] = P[r * ld + j] - v * wsum[j - c - 1];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nr * b; e += blockDim.x) {
+    const int r = e / b, cc = e % b;
+    Ag[(size_t)(q0 + r) * lda + cc] = P[r * ld + cc];
+  }
+}
+
 // ------------------------------------------------------------------ launchers
+
+// Panel QR: the multi-CTA form when its grid fits the GPU at once (cooperative launch),
+// else one CTA per item.  scratch: qr_scratch_bytes(count, sizeof(T)) bytes.
+size_t qr_scratch_bytes(int count, int es) {
+  return 256 + (size_t)count * kQrMaxG * (8 + 32 * (size_t)es) + (size_t)count * es;
+}
 
 template <typename T>
 void panel_qr(T* A, int lda, long long sA, int r0, int k, int m, int b, int kb, T* taus, long long stau, int count,
-              cudaStream_t s) {
-  count_launch();
-  panel_qr_kernel<T><<<count, 1024, 0, s>>>(A, lda, sA, r0, k, m, b, kb, taus, stau);
+              void* scratch, DevStatus* st, long long wait_limit, cudaStream_t s) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  // rows per CTA: the most CTAs that fit at once (each CTA's rows within 200 KB of shared
+  // memory, at least 16 rows per CTA, at most kQrMaxG CTAs per item)
+  const size_t row_bytes = (size_t)(b + 1) * sizeof(T);
+  const int rmax = (int)((200 * 1024) / row_bytes);
+  const int gmin = (m + rmax - 1) / rmax;
+  int G = std::max(gmin, std::min({kQrMaxG, (m + 15) / 16, std::max(1, sms * 2 / std::max(1, count))}));
+  int R = (m + G - 1) / G;
+  size_t sm = (size_t)R * row_bytes;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(panel_qr_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_qr_coop_kernel<T>, 256, sm);
+  int items = per_sm > 0 ? (per_sm * sms) / G : 0;
+  if (G > kQrMaxG || items < 1) {
+    count_launch();
+    panel_qr_kernel<T><<<count, 1024, 0, s>>>(A, lda, sA, r0, k, m, b, kb, taus, stau);
+    return;
+  }
+  items = std::min(items, count);
+  char* base = static_cast<char*>(scratch);
+  QrScratch q;
+  q.bar = reinterpret_cast<unsigned*>(base);
+  q.err = reinterpret_cast<int*>(base + 64);
+  q.pn = reinterpret_cast<double*>(base + 256);
+  q.pw = base + 256 + (size_t)count * kQrMaxG * 8;
+  q.palpha = base + 256 + (size_t)count * kQrMaxG * (8 + 32 * sizeof(T));
+  for (int z0 = 0; z0 < count; z0 += items) {
+    const int cnt = std::min(items, count - z0);
+    T* Az = A + z0 * sA;
+    T* tz = taus + z0 * stau;
+    DevStatus* sz = st ? st + z0 : nullptr;
+    cudaMemsetAsync(base, 0, 128, s);
+    void* args[] = {&Az, &lda, &sA, &r0, &k, &m, &b, &kb, &tz, &stau, &G, &R, &q, &sz, &wait_limit};
+    count_launch();
+    if (cudaLaunchCooperativeKernel((const void*)panel_qr_coop_kernel<T>, dim3(G, cnt), dim3(256), args, sm, s) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      panel_qr_kernel<T><<<cnt, 1024, 0, s>>>(Az, lda, sA, r0, k, m, b, kb, tz, stau);
+    }
+  }
 }
 
 template <typename T>
@@ -556,7 +742,8 @@ void widen_pad(const double* Z, int ldz, long long sZ, T* X, int ldx, long long 
                          int*, DevStatus*, long long, int, int, cudaStream_t);                            \
   template void band_tridiag<T>(const T*, int, long long, int, double*, double*, long long, int,           \
                                 cudaStream_t);                                                            \
-  template void panel_qr<T>(T*, int, long long, int, int, int, int, int, T*, long long, int, cudaStream_t); \
+  template void panel_qr<T>(T*, int, long long, int, int, int, int, int, T*, long long, int, void*,      \
+                           DevStatus*, long long, cudaStream_t);                                        \
   template void panel_v<T>(const T*, int, long long, int, int, int, int, T*, int, long long, int,          \
                            cudaStream_t);                                                                 \
   template void panel_clear<T>(T*, int, long long, int, int, int, int, int, cudaStream_t);                 \

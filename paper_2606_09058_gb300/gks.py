@@ -20,6 +20,7 @@ GKS_FP64, GKS_MIXED_TF32, GKS_MIXED_SPLITBF16 = 0, 1, 2
 GKS_REUSE_S_FACTOR, GKS_SAVE_FOR_BACKWARD, GKS_EIGEN_ONLY = 1, 2, 4
 GKS_DEBUG_SKIP_COPY = 1
 GKS_SPLIT_RESIDUES, GKS_SPLIT_DIGITS = 0, 1
+GKS_HEMV_DIGITS, GKS_HEMV_FP64 = 0, 1
 _SPIN = {"collinear": GKS_COLLINEAR, "noncollinear": GKS_NONCOLLINEAR, "spin_polarized": GKS_SPIN_POLARIZED}
 _PREC = {"fp64": GKS_FP64, "mixed_tf32": GKS_MIXED_TF32, "mixed": GKS_MIXED_SPLITBF16,
          "mixed_splitbf16": GKS_MIXED_SPLITBF16}
@@ -41,7 +42,8 @@ class _Opts(ctypes.Structure):
                 ("gemm", ctypes.c_int), ("slices", ctypes.c_int), ("block", ctypes.c_int),
                 ("refine_sweeps", ctypes.c_int), ("n_ev", ctypes.c_int), ("wait_limit", ctypes.c_longlong),
                 ("autotune_cache", ctypes.c_char_p), ("debug", ctypes.c_int), ("reduction", ctypes.c_int),
-                ("tridiag", ctypes.c_int), ("band", ctypes.c_int), ("split", ctypes.c_int)]
+                ("tridiag", ctypes.c_int), ("band", ctypes.c_int), ("split", ctypes.c_int),
+                ("hemv", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -145,7 +147,7 @@ class Context:
                  block: int = 0, precision: str = "fp64", refine_sweeps: int = 0, n_ev: int = 0,
                  wait_limit: int = 0, autotune_cache: str | None = None, debug: int = 0,
                  reduction: str = "cholesky", tridiag: str = "one_stage", band: int = 0,
-                 split: str = "residues"):
+                 split: str = "residues", hemv: str = "digits"):
         if not torch.cuda.is_available():
             raise RuntimeError("gks needs a CUDA device")
         lib = load()
@@ -159,7 +161,8 @@ class Context:
                      1 if profile else 0, 1 if graph else 0, gm, int(slices), int(block), int(refine_sweeps),
                      int(n_ev), int(wait_limit), cache, int(debug), {"cholesky": 0, "lowdin": 1}[reduction],
                      {"one_stage": 0, "two_stage": 1}[tridiag], int(band),
-                     {"residues": GKS_SPLIT_RESIDUES, "digits": GKS_SPLIT_DIGITS}[split])
+                     {"residues": GKS_SPLIT_RESIDUES, "digits": GKS_SPLIT_DIGITS}[split],
+                     {"digits": GKS_HEMV_DIGITS, "fp64": GKS_HEMV_FP64}[hemv])
         h = ctypes.c_void_p()
         rc = lib.gks_create(ctypes.byref(h), ctypes.byref(opts))
         if rc:
