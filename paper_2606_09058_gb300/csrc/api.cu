@@ -293,8 +293,8 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   c->ouw = a.take<double>((size_t)3 * m * nk);
   c->oSg = es == 16 && !dig ? a.take<double>(MM * nk) : 0;
   if (dig) {
-    // digit planes of the stale block and of u (16 planes complex, 8 real), scale exponents
-    const size_t ldd = ((size_t)m + 15) / 16 * 16, npl = es == 16 ? 16 : 8;
+    // digit planes of the stale block and of u (14 planes complex, 7 real), scale exponents
+    const size_t ldd = ((size_t)m + 15) / 16 * 16, npl = es == 16 ? 14 : 7;
     c->oD = a.take<char>(ldd * ldd * npl * nk);  // rows up to the 16-multiple the panels reach
     c->oud = a.take<char>(ldd * npl * nk);
     c->ofu = a.take<int>((size_t)nk);
@@ -925,7 +925,7 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   const HemvDigits* hd = nullptr;
   if constexpr (std::is_same<T, double>::value || std::is_same<T, zc>::value) {
     if (c->wsdig) {
-      const int ldd = (M + 15) / 16 * 16, npl = es == 16 ? 16 : 8;
+      const int ldd = (M + 15) / 16 * 16, npl = es == 16 ? 14 : 7;
       hdv.D = at<signed char>(c, c->oD);
       hdv.sD = (long long)ldd * ldd * npl;
       hdv.ldd = ldd;
@@ -938,7 +938,7 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
   }
   double* uw = es == 16 && !hd ? at<double>(c, c->ouw) : nullptr;
   double* Sg = es == 16 && !hd ? at<double>(c, c->oSg) : nullptr;
-  const double npl = es == 16 ? 16.0 : 8.0;
+  const double npl = es == 16 ? 14.0 : 7.0;
   for (int jh = M - 1; jh >= 2; jh -= pw) {
     const int jl = std::max(2, jh - pw + 1);  // steps jh .. jl in this panel
     {

@@ -44,13 +44,13 @@ void tune_pencil(T* A, int m, int count, int hermitian, cudaStream_t s);
 // equilibrated symmetrically by powers of two, A = D Ã D with D = diag(2^{d_i}),
 // d_i = ceil(g_i / 2) for row maxima below 2^{g_i} (largest |Re|, |Im| over the full
 // row), so every |Re ã|, |Im ã| < 1; the full Hermitian Ã (upper triangle mirrored,
-// conjugated) is stored as 8 signed 7-bit digits of Re ã (planes 0..7, most significant
-// first) and Im ã (planes 8..15, complex only): ã = sum_s d_s 2^{-7 - 7s} up to 2^{-56}.
-// ũ = D u gets the same digits below its own scale 2^{fu}.  Then
-// (A u)_i = 2^{d_i} sum over digit pairs s + t <= 8 of exact integer dot products (dp4a,
-// int32 sums) weighted by 2^{fu - 14 - 7(s + t)}.
+// conjugated) is stored as 7 balanced base-256 digits (signed 8-bit) of round(2^54 Re ã)
+// (planes 0..6, most significant first) and of Im ã (planes 7..13, complex only):
+// ã = sum_s d_s 2^{-6 - 8s} up to 2^{-55}.  ũ = D u gets the same digits below its own
+// scale 2^{fu}.  Then (A u)_i = 2^{d_i} sum over digit pairs s + t <= 7 of exact integer
+// dot products (dp4a, int32 sums) weighted by 2^{fu - 12 - 8(s + t)}.
 // Layout: per row, blocks of 16 columns, each block the planes' 16 bytes one after the
-// other (a row's 16 columns of all planes are 128 or 256 contiguous bytes); ũ the same.
+// other (a row's 16 columns of all planes are 112 or 224 contiguous bytes); ũ the same.
 struct HemvDigits {
   signed char* D;            // [item][ldd][ldd / 16][planes][16]
   long long sD;              // item stride (bytes)

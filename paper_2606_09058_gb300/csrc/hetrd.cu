@@ -33,51 +33,79 @@ __device__ __forceinline__ void put_uw(double* uw, int i, double ur, double ui) 
   }
 }
 
-// Scale exponent of a block whose largest magnitude is mx (entries below 2^e).
-__device__ __forceinline__ int dscale(double mx) { return mx > 0.0 ? ilogb(mx) + 1 : 0; }
+// Scale exponent from the bits of a non-negative double (0 for zero): the e with the value
+// below 2^e, i.e. ilogb + 1 (subnormals are counted at the smallest normal exponent).
+__device__ __forceinline__ int bscale(unsigned long long bits) {
+  return bits ? (int)((bits >> 52) & 0x7ff) - 1022 : 0;
+}
 // Equilibration exponent d_i = ceil(g_i / 2) of a row whose maximum (bits) lies below 2^{g_i}.
-__device__ __forceinline__ int deq(unsigned long long bits) {
-  return (dscale(__longlong_as_double((long long)bits)) + 1) >> 1;
-}
+__device__ __forceinline__ int deq(unsigned long long bits) { return (bscale(bits) + 1) >> 1; }
 
-// The 8 signed 7-bit digits of x (|x| < 2^e): trunc(|x| 2^{56 - e}) in base 128, most
-// significant first, with the sign of x, into d[0..7].
-__device__ __forceinline__ void digits7v(double x, int e, int (&d)[8]) {
-  const long long q = __double2ll_rz(ldexp(fabs(x), 56 - e));
-  const int sg = x < 0.0 ? -1 : 1;
+// Digit format of the matrix-vector step: kDig balanced base-256 digits (signed 8-bit,
+// in [-128, 127]) of the integer round(|x| 2^{54 - e}) with the sign of x, for |x| < 2^e:
+// x = sum_s d_s 2^{e - 6 - 8s} up to 2^{e - 55}.
+constexpr int kDig = 7;
+constexpr int kMaxLevel = 7;  // digit pairs s + t <= kMaxLevel
+
+// The digits of x below 2^e into d[0..kDig), most significant first.  Integer operations on
+// the bits of x only (the FP64 pipe is slow on this GPU): |x| = m 2^{x_e - 1075} with the
+// 53-bit significand m, so trunc(|x| 2^{55 - e}) = m shifted by x_e - 1020 - e, and
+// rounding halves it with a carry.  Balanced digits from the least significant up keep the
+// leading one within [-65, 65].
+__device__ __forceinline__ void digits8(double x, int e, int (&d)[kDig]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int xe = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = (b & 0xfffffffffffffull) | (xe ? (1ull << 52) : 0ull);
+  const int sh = (xe ? xe : 1) - 1020 - e;
+  const unsigned long long q2 = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
+  const long long q = (long long)((q2 + 1) >> 1);
+  long long v = (b >> 63) ? -q : q;
 #pragma unroll
-  for (int s = 0; s < 8; s++) d[s] = sg * (int)((q >> (7 * (7 - s))) & 127);
+  for (int s = kDig - 1; s >= 1; s--) {
+    int t = (int)(v & 255);
+    t = t >= 128 ? t - 256 : t;
+    d[s] = t;
+    v = (v - t) >> 8;
+  }
+  d[0] = (int)v;
 }
 
-// Digits of 16 consecutive entries (vals, nv of them valid) packed as the layout's block:
-// NPL planes of 16 bytes (Re planes, then Im planes for complex), stored with 16-byte writes.
+// |Re|, |Im| maximum of a value as the bits of a non-negative double (bits of non-negative
+// doubles order like the values).
+__device__ __forceinline__ unsigned long long absbits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+template <typename T>
+__device__ __forceinline__ unsigned long long maxbits(T a) {
+  if constexpr (std::is_same<T, double>::value || std::is_same<T, float>::value) return absbits((double)a);
+  else return max(absbits((double)re(a)), absbits((double)im(a)));
+}
+
+// Digits of 16 consecutive entries packed as the layout's block: NPL planes of 16 bytes (the
+// kDig Re planes, then the Im planes for complex), stored with 16-byte writes.  Entry el is
+// cut below 2^{e[el]} (the scale and the equilibration folded into one exponent).
 template <typename T, int NPL>
-__device__ __forceinline__ void store_digit_block(const T (&vals)[16], int e, signed char* dst) {
+__device__ __forceinline__ void store_digit_block(const T (&vals)[16], const int (&e)[16], signed char* dst) {
   uint4 o[NPL];
 #pragma unroll
   for (int q = 0; q < NPL; q++) o[q] = make_uint4(0u, 0u, 0u, 0u);
+  auto put = [&](int plane, int el, int dv) {
+    const uint32_t bb = (uint32_t)(dv & 0xff) << (8 * (el & 3));
+    if ((el >> 2) == 0) o[plane].x |= bb;
+    else if ((el >> 2) == 1) o[plane].y |= bb;
+    else if ((el >> 2) == 2) o[plane].z |= bb;
+    else o[plane].w |= bb;
+  };
 #pragma unroll
   for (int el = 0; el < 16; el++) {
-    int d[8];
-    digits7v((double)re(vals[el]), e, d);
+    int d[kDig];
+    digits8((double)re(vals[el]), e[el], d);
 #pragma unroll
-    for (int sp = 0; sp < 8; sp++) {
-      const uint32_t b = (uint32_t)(d[sp] & 0xff) << (8 * (el & 3));
-      if ((el >> 2) == 0) o[sp].x |= b;
-      else if ((el >> 2) == 1) o[sp].y |= b;
-      else if ((el >> 2) == 2) o[sp].z |= b;
-      else o[sp].w |= b;
-    }
-    if constexpr (NPL == 16) {
-      digits7v((double)im(vals[el]), e, d);
+    for (int sp = 0; sp < kDig; sp++) put(sp, el, d[sp]);
+    if constexpr (NPL == 2 * kDig) {
+      digits8((double)im(vals[el]), e[el], d);
 #pragma unroll
-      for (int sp = 0; sp < 8; sp++) {
-        const uint32_t b = (uint32_t)(d[sp] & 0xff) << (8 * (el & 3));
-        if ((el >> 2) == 0) o[8 + sp].x |= b;
-        else if ((el >> 2) == 1) o[8 + sp].y |= b;
-        else if ((el >> 2) == 2) o[8 + sp].z |= b;
-        else o[8 + sp].w |= b;
-      }
+      for (int sp = 0; sp < kDig; sp++) put(kDig + sp, el, d[sp]);
     }
   }
   uint4* out = reinterpret_cast<uint4*>(dst);
@@ -91,42 +119,38 @@ __device__ __forceinline__ void store_digit_block(const T (&vals)[16], int e, si
 template <typename T>
 __device__ void u_digits(const T* u, int j, signed char* ud, int* fu, const unsigned long long* rmax) {
   constexpr bool CPX = !std::is_same<T, double>::value && !std::is_same<T, float>::value;
-  constexpr int NPL = CPX ? 16 : 8;
-  __shared__ double mred[32];
+  constexpr int NPL = CPX ? 2 * kDig : kDig;
+  __shared__ int mred[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   __syncthreads();
-  double m = 0.0;
+  // fu: the scale exponent of ũ = D u, the largest bscale(|u_i|) + d_i
+  int m = -100000;
   for (int i = tid; i < j; i += nt) {
-    const int d = deq(rmax[i]);
-    m = fmax(m, ldexp(fmax(fabs((double)re(u[i])), fabs((double)im(u[i]))), d));
+    const unsigned long long mb = maxbits(u[i]);
+    if (mb) m = max(m, bscale(mb) + deq(rmax[i]));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((tid & 31) == 0) mred[tid >> 5] = m;
   __syncthreads();
   if (tid < 32) {
-    double v = tid < (nt >> 5) ? mred[tid] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int v = tid < (nt >> 5) ? mred[tid] : -100000;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (tid == 0) mred[0] = v;
   }
   __syncthreads();
-  const int e = dscale(mred[0]);
+  const int e = mred[0] == -100000 ? 0 : mred[0];
   if (tid == 0) *fu = e;
   const int nblk = (j + 15) >> 4;
   for (int b = tid; b < nblk; b += nt) {
     T vals[16];
+    int ex[16];
 #pragma unroll
     for (int el = 0; el < 16; el++) {
       const int i = 16 * b + el;
-      T v = zero<T>();
-      if (i < j) {
-        const int d = deq(rmax[i]);
-        v = u[i];
-        if constexpr (CPX) v = T{ldexp(re(v), d), ldexp(im(v), d)};
-        else v = ldexp(v, d);
-      }
-      vals[el] = v;
+      vals[el] = i < j ? u[i] : zero<T>();
+      ex[el] = i < j ? e - deq(rmax[i]) : 0;  // ũ_i 2^{-fu} = u_i 2^{d_i - fu}
     }
-    store_digit_block<T, NPL>(vals, e, ud + (size_t)b * (NPL * 16));
+    store_digit_block<T, NPL>(vals, ex, ud + (size_t)b * (NPL * 16));
   }
 }
 
@@ -378,21 +402,15 @@ __global__ void __launch_bounds__(256) hetrd_dmax_kernel(const T* A, int lda, lo
   A += z * sA;
   rmax += (size_t)z * ldr;
   for (int r = r0 + warp; r < r1; r += 8) {
-    double m = 0.0;
-    for (int c = lane; c <= r; c += 32) {
-      const T a = A[(size_t)r * lda + c];
-      m = fmax(m, fmax(fabs(re(a)), fabs(im(a))));
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0 && m > 0.0) atomicMax(rmax + r, (unsigned long long)__double_as_longlong(m));
+    unsigned long long m = 0ull;
+    for (int c = lane; c <= r; c += 32) m = max(m, maxbits(A[(size_t)r * lda + c]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m) atomicMax(rmax + r, m);
   }
   for (int c = tid; c < r1 - 1; c += blockDim.x) {
-    double mc = 0.0;
-    for (int r = max(r0, c + 1); r < r1; r++) {
-      const T a = A[(size_t)r * lda + c];
-      mc = fmax(mc, fmax(fabs(re(a)), fabs(im(a))));
-    }
-    if (mc > 0.0) atomicMax(rmax + c, (unsigned long long)__double_as_longlong(mc));
+    unsigned long long mc = 0ull;
+    for (int r = max(r0, c + 1); r < r1; r++) mc = max(mc, maxbits(A[(size_t)r * lda + c]));
+    if (mc) atomicMax(rmax + c, mc);
   }
 }
 
@@ -401,7 +419,7 @@ __global__ void __launch_bounds__(256) hetrd_dmax_kernel(const T* A, int lda, lo
 // memory, conjugated.  64 threads: thread t packs row t / 2, columns 16 (t % 2) .. + 15.
 template <typename T>
 __global__ void __launch_bounds__(64) hetrd_digits_kernel(const T* A, int lda, long long sA, int n, HemvDigits hd) {
-  constexpr int NPL = sizeof(T) == 16 ? 16 : 8;
+  constexpr int NPL = sizeof(T) == 16 ? 2 * kDig : kDig;
   __shared__ T tile[32][33];
   const int z = blockIdx.z, tid = threadIdx.x;
   const int R0 = blockIdx.y * 32, C0 = blockIdx.x * 32;
@@ -423,6 +441,7 @@ __global__ void __launch_bounds__(64) hetrd_digits_kernel(const T* A, int lda, l
   if (r < n16 && C0 + 16 * cbk < n16) {
     const int dr = r < n ? deq(rm[r]) : 0;
     T vals[16];
+    int ex[16];
 #pragma unroll
     for (int el = 0; el < 16; el++) {
       const int cc = 16 * cbk + el, c = C0 + cc;
@@ -430,11 +449,10 @@ __global__ void __launch_bounds__(64) hetrd_digits_kernel(const T* A, int lda, l
       if (upper) v = conjg(tile[cc][rr]);
       else if (c <= r) v = tile[rr][cc];
       else v = (r < n && c < n) ? conjg(tile[cc][rr]) : zero<T>();  // diagonal tile, upper part
-      const int sh = -(dr + (c < n ? deq(rm[c]) : 0));                  // ã = a 2^{-d_r - d_c}
-      if constexpr (sizeof(T) == 16) vals[el] = T{ldexp(re(v), sh), ldexp(im(v), sh)};
-      else vals[el] = ldexp(v, sh);
+      vals[el] = v;
+      ex[el] = dr + (c < n ? deq(rm[c]) : 0);  // ã = a 2^{-d_r - d_c}, cut below 1
     }
-    store_digit_block<T, NPL>(vals, 0, hd.D + z * hd.sD + (size_t)r * hd.ldd * NPL + (size_t)(C0 / 16 + cbk) * (NPL * 16));
+    store_digit_block<T, NPL>(vals, ex, hd.D + z * hd.sD + (size_t)r * hd.ldd * NPL + (size_t)(C0 / 16 + cbk) * (NPL * 16));
   }
 }
 
@@ -458,8 +476,9 @@ __global__ void __launch_bounds__(256, 2) hetrd_phemv_dig_kernel(int j, const T*
                                                                  HemvDigits hd) {
   constexpr bool CPX = sizeof(T) == 16;
   constexpr int NP = CPX ? 4 : 1;  // real products
-  constexpr int NPL = CPX ? 16 : 8;
-  __shared__ int accs[NP * 9][33][8];
+  constexpr int NPL = CPX ? 2 * kDig : kDig;
+  constexpr int NL = kMaxLevel + 1;  // levels
+  __shared__ int accs[NP * NL][33][8];
   __shared__ uint4 ush[8][NPL];  // per warp: u's digits of the current 16 columns
   __shared__ T prow[32];
   const int z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -470,11 +489,11 @@ __global__ void __launch_bounds__(256, 2) hetrd_phemv_dig_kernel(int j, const T*
   const int cb = min(j16, warp * chunk), ce = min(j16, cb + chunk);
   const signed char* D = hd.D + z * hd.sD + (size_t)r * hd.ldd * NPL;
   const signed char* ud = hd.ud + z * hd.sud;
-  int acc[NP][9];
+  int acc[NP][NL];
 #pragma unroll
   for (int q = 0; q < NP; q++)
 #pragma unroll
-    for (int L = 0; L < 9; L++) acc[q][L] = 0;
+    for (int L = 0; L < NL; L++) acc[q][L] = 0;
   for (int c = cb; c < ce; c += 16) {
     // 16 columns: all digit planes of this lane's row (NPL x 16 contiguous bytes) in
     // flight at once; u's digits (the same for every lane) through shared memory
@@ -486,17 +505,17 @@ __global__ void __launch_bounds__(256, 2) hetrd_phemv_dig_kernel(int j, const T*
     if (lane < NPL) ush[warp][lane] = __ldg(reinterpret_cast<const uint4*>(ud + (size_t)(c >> 4) * (NPL * 16)) + lane);
     __syncwarp();
 #pragma unroll
-    for (int t = 0; t < 8; t++) {
+    for (int t = 0; t < kDig; t++) {
       const uint4 ur = ush[warp][t];
       uint4 ui;
-      if constexpr (CPX) ui = ush[warp][8 + t];
+      if constexpr (CPX) ui = ush[warp][kDig + t];
 #pragma unroll
-      for (int s = 0; s < 8 && s + t <= 8; s++) {
+      for (int s = 0; s < kDig && s + t <= kMaxLevel; s++) {
         acc[0][s + t] = dp4x4(av[s], ur, acc[0][s + t]);
         if constexpr (CPX) {
-          acc[1][s + t] = dp4x4(av[8 + s], ui, acc[1][s + t]);
+          acc[1][s + t] = dp4x4(av[kDig + s], ui, acc[1][s + t]);
           acc[2][s + t] = dp4x4(av[s], ui, acc[2][s + t]);
-          acc[3][s + t] = dp4x4(av[8 + s], ur, acc[3][s + t]);
+          acc[3][s + t] = dp4x4(av[kDig + s], ur, acc[3][s + t]);
         }
       }
     }
@@ -504,26 +523,26 @@ __global__ void __launch_bounds__(256, 2) hetrd_phemv_dig_kernel(int j, const T*
 #pragma unroll
   for (int q = 0; q < NP; q++)
 #pragma unroll
-    for (int L = 0; L < 9; L++) accs[q * 9 + L][lane][warp] = acc[q][L];
+    for (int L = 0; L < NL; L++) accs[q * NL + L][lane][warp] = acc[q][L];
   __syncthreads();
   if (tid < 32 && c0 + tid < cend) {
-    // exact sums over the warps, then 2^{d_i + fu - 14 - 7L} per level
-    const int E = deq(hd.rmax[(size_t)z * hd.ldd + c0 + tid]) + hd.fu[z] - 14;
+    // exact sums over the warps, then 2^{d_i + fu - 12 - 8L} per level
+    const int E = deq(hd.rmax[(size_t)z * hd.ldd + c0 + tid]) + hd.fu[z] - 12;
     double pre = 0.0, pim = 0.0;
 #pragma unroll
-    for (int L = 8; L >= 0; L--) {
+    for (int L = NL - 1; L >= 0; L--) {
       long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
       for (int w = 0; w < 8; w++) {
         s0 += accs[L][tid][w];
         if constexpr (CPX) {
-          s1 += accs[9 + L][tid][w];
-          s2 += accs[18 + L][tid][w];
-          s3 += accs[27 + L][tid][w];
+          s1 += accs[NL + L][tid][w];
+          s2 += accs[2 * NL + L][tid][w];
+          s3 += accs[3 * NL + L][tid][w];
         }
       }
-      pre += ldexp((double)(s0 - s1), E - 7 * L);
-      if constexpr (CPX) pim += ldexp((double)(s2 + s3), E - 7 * L);
+      pre += ldexp((double)(s0 - s1), E - 8 * L);
+      if constexpr (CPX) pim += ldexp((double)(s2 + s3), E - 8 * L);
     }
     if constexpr (CPX) prow[tid] = T{pre, pim};
     else prow[tid] = pre;
