@@ -551,8 +551,12 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="arithmetic of the timed step")
     ap.add_argument("--split", default="residues", choices=["residues", "digits"],
                     help="form of the FP64-accurate tensor-core products")
+    ap.add_argument("--hemv", default="digits", choices=["digits", "fp64"],
+                    help="form of the one-stage matrix-vector step")
     ap.add_argument("--per-k", action="store_true",
                     help="solve the k-points one call each (nk = 1, shared mu lost) instead of one batched call")
+    ap.add_argument("--k-points", type=int, default=0,
+                    help="keep only the first N k-points of the workload (a small case for kernel captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -583,6 +587,12 @@ def main():
     # (gks_occupy) before its own density matrices: strong scaling of one system.  A
     # workload with fewer k-points than ranks runs replicas (weak scaling).
     prob = make_problem(args.workload, str(dev))
+    if 0 < args.k_points < prob.H.shape[0]:
+        n_keep = args.k_points
+        prob.H, prob.S = prob.H[:n_keep].contiguous(), prob.S[:n_keep].contiguous()
+        prob.kweights = np.full(n_keep, 1.0 / n_keep)
+        prob.nk = n_keep
+        torch.cuda.empty_cache()
     nk_all = prob.H.shape[0]
     shard = world > 1 and nk_all >= world and prob.spin == "collinear" and not args.per_k
     k0, k1 = kshard_range(nk_all, world, rank) if shard else (0, nk_all)
@@ -595,7 +605,7 @@ def main():
     kw_local = kw[k0:k1].contiguous()
     stream = torch.cuda.current_stream(dev)
     ctx = gks.Context(local, stream, profile=True, gemm=args.gemm, block=args.block, tridiag=args.tridiag,
-                      precision=args.precision, split=args.split)
+                      precision=args.precision, split=args.split, hemv=args.hemv)
     eps = torch.empty(nk, M, dtype=torch.float64, device=dev)
     C = torch.empty(nk, M, M, dtype=H.dtype, device=dev)
     rho = torch.empty_like(C)
@@ -663,8 +673,10 @@ def main():
     # from one ncu capture of the kernel on the 64-atom k-batch (profiles/), where it matched
     # the algorithmic bytes of that launch to the ratio below; it scales with the bytes the
     # launch processes, so the live per-launch algorithmic bytes times that ratio is reported.
-    TRAFFIC_RATIO = {"hetrd_hemv": 1.04}
-    kern = [p for p in prof if not p["name"].startswith("stage:")]
+    # DRAM bytes / algorithmic bytes of one launch from an ncu capture (profiles/): the FP64
+    # matrix-vector step (16-row blocks on the 64-atom k-batch) and its digit form (one
+    # k-point of the 512-atom batch: DRAM bytes = the digit block)
+    TRAFFIC_RATIO = {("hetrd_hemv", "fp64"): 1.04, ("hetrd_hemv", "digits"): 1.01}
     dom = max(kern, key=lambda p: p["ms"]) if kern else None
     roof = None
     if dom:
@@ -672,15 +684,49 @@ def main():
         achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12 if dom["ms"] > 0 else 0.0
         scale = (clk["sm_mhz"] / peak["sm_mhz"]) if (clk["sm_mhz"] and peak["sm_mhz"]) else 1.0
         pk = peak["dfma_tflops"] * scale
-        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk,
-                "traffic": (TRAFFIC_RATIO[dom["name"]] * dom["bytes"] / dom["groups"]
-                            if dom["name"] in TRAFFIC_RATIO and dom.get("groups") else None),
-                "kernel": dom["name"],
-                "kernel_ms_per_step": dom["ms"] / per, "kernel_share": dom["ms"] / (ms * per),
-                "peak_basis": (f"FP64 DFMA pipe measured by gks_measure_peak in this run: {peak['dfma_tflops']:.3f} "
-                               f"TFLOP/s at {peak['sm_mhz']} MHz, scaled to the timed region's median SM clock "
-                               f"(DMMA measured {peak['dmma_tflops']:.3f})")}
+        form = args.hemv if dom["name"] == "hetrd_hemv" and args.precision == "fp64" else "fp64"
+        ratio = TRAFFIC_RATIO.get((dom["name"], form))
+        traffic = ratio * dom["bytes"] / dom["groups"] if ratio and dom.get("groups") else None
+        fp64_eq = {"achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                   "peak_basis": (f"FP64 DFMA pipe measured by gks_measure_peak in this run: "
+                                  f"{peak['dfma_tflops']:.3f} TFLOP/s at {peak['sm_mhz']} MHz, scaled to the "
+                                  f"timed region's median SM clock (DMMA measured {peak['dmma_tflops']:.3f})")}
+        common = {"traffic": traffic, "kernel": dom["name"], "kernel_ms_per_step": dom["ms"] / per,
+                  "kernel_share": dom["ms"] / (ms * per)}
+        if dom["name"] == "split_gemm":
+            # the tensor-core products: every bf16 product of the split form executes the
+            # nominal flops of the FP64 product (the complex embedding included), 16 of them
+            # for the residue form (16 moduli), 45 for nine-digit pairs; against the
+            # sustained bf16 peak (the kernels run inside a long step)
+            nprod = 16 if args.split == "residues" else 45
+            try:
+                pk_t = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+                bf = float(pk_t["bf16_tflops_sustained"])
+                basis = "bf16 dense sustained, MEASURED_PEAKS.json"
+            except (OSError, KeyError, ValueError):
+                bf, basis = 1700.0, "fallback 1.7 PFLOP/s sustained"
+            ex = achieved * nprod
+            roof = {"bound": "tensor", "achieved": ex, "peak": bf, "unit": "TFLOP/s", "frac": ex / bf, **common,
+                    "peak_basis": basis,
+                    "executed_per_nominal": nprod,
+                    "note": ("executed bf16 work = nominal FP64 flops x bf16 products per product; the class "
+                             "includes the splitting and reconstruction kernels"),
+                    "fp64_equivalent": fp64_eq}
+        elif form == "digits":
+            # the digit form reads its digit block once per step: bytes / time against the
+            # measured HBM copy rate (burst: the kernel runs inside a long step, but it is
+            # memory-bound, where the copy rate is the ceiling)
+            try:
+                hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+                basis = "HBM copy rate, MEASURED_PEAKS.json"
+            except (OSError, KeyError, ValueError):
+                hbm, basis = 6800.0, "fallback 6.8 TB/s"
+            gbs = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else 0.0
+            roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, **common,
+                    "peak_basis": basis, "fp64_equivalent": fp64_eq}
+        else:
+            roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                    **common, "peak_basis": fp64_eq["peak_basis"]}
     stages = {p["name"][6:]: round(p["ms"] / args.steps, 3) for p in prof if p["name"].startswith("stage:")}
     classes = {p["name"]: {"ms": round(p["ms"] / args.steps, 3),
                            "tflops": round(p["flops"] / (p["ms"] / 1e3) / 1e12, 4) if p["ms"] > 0 and p["flops"] > 0
@@ -707,7 +753,7 @@ def main():
             torch.cuda.synchronize()
             return a0.elapsed_time(a1) / steps
         if M <= 18000:
-            cm = gks.Context(local, stream, precision="mixed", block=args.block, split=args.split)
+            cm = gks.Context(local, stream, precision="mixed", block=args.block, split=args.split, hemv=args.hemv)
             eps_m = torch.empty_like(eps)
             C_m = torch.empty_like(C)
             rho_m = torch.empty_like(rho)
@@ -732,9 +778,11 @@ def main():
         # lowest n_ev (occupied + margin)
         n_ev = min(M, max(nrho) + 64)
         other = "digits" if args.split == "residues" else "residues"
-        for name, kw_ in ((f"split_{other}", dict(split=other)),
+        other_hemv = "fp64" if args.hemv == "digits" else "digits"
+        for name, kw_ in ((f"split_{other}", dict(split=other, hemv=args.hemv)),
+                          (f"hemv_{other_hemv}", dict(split=args.split, hemv=other_hemv)),
                           ("two_stage", dict(tridiag="two_stage", split=args.split)),
-                          ("one_stage_partial", dict(n_ev=n_ev, split=args.split)),
+                          ("one_stage_partial", dict(n_ev=n_ev, split=args.split, hemv=args.hemv)),
                           ("two_stage_partial", dict(tridiag="two_stage", n_ev=n_ev, split=args.split))):
             try:
                 cx = gks.Context(local, stream, block=args.block, **kw_)
@@ -830,7 +878,7 @@ def main():
                                            f"eps, shared mu on every rank)") if shard else
                            (f"{world} replicas" if world > 1 else "one GPU"),
                            "spin": spin, "precision": args.precision, "tridiag": args.tridiag,
-                           "products": args.gemm, "split_form": args.split,
+                           "products": args.gemm, "split_form": args.split, "hemv_form": args.hemv,
                            "block": args.block or (512 if M >= 4096 else 256),
                            "batching": "one call per k-point" if args.per_k else "all k-points in one call",
                            "l2": "inputs larger than L2 (no flush needed)",
