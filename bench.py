@@ -677,6 +677,7 @@ def main():
     # matrix-vector step (16-row blocks on the 64-atom k-batch) and its digit form (one
     # k-point of the 512-atom batch: DRAM bytes = the digit block)
     TRAFFIC_RATIO = {("hetrd_hemv", "fp64"): 1.04, ("hetrd_hemv", "digits"): 1.01}
+    kern = [p for p in prof if not p["name"].startswith("stage:")]
     dom = max(kern, key=lambda p: p["ms"]) if kern else None
     roof = None
     if dom:

@@ -225,26 +225,27 @@ def spinor_hamiltonian(H: torch.Tensor, S: torch.Tensor, moments: np.ndarray, KA
                        delta: float, lam: float, block: int = N_PER_ATOM) -> torch.Tensor:
     """Assemble the 2N x 2N spinor H_NC (paper Sec. 2 noncollinear GEP; Sec. 3.2 H_NC).
 
-    H_NC = [[H + D Sz, D (Sx - i Sy) + l K], [D (Sx + i Sy) - l K, H - D Sz]] with
-    S_q = S (blockdiag_A m_qA S_AA^-1) S (the per-atom on-site projector in Gram form) and
-    K = S (blockdiag_A L_A^-T K_A L_A^-1) S, K_A real antisymmetric, i.e. l i K (x) sigma_y.
+    H_NC = [[H + D Sz, D (Sx - i Sy) + l K], [D (Sx + i Sy) - l K, H - D Sz]] with the
+    per-atom on-site terms taken in S-consistent form,
+      S_q = S (blockdiag_A m_qA I_A) S = sum_A m_qA S[:, A] S[A, :],
+      K   = S (blockdiag_A K_A) S,  K_A real antisymmetric, i.e. l i K (x) sigma_y.
+    The basis functions are normalized (S_AA has a unit diagonal), so I_A stands for the
+    diagonal of the atom's Gram block; its full inverse S_AA^-1 is left out on purpose:
+    the same-centre Gaussian blocks have condition numbers near 1e12, and any evaluation of
+    the inverse makes the pencil depend on the machine and library that build it at the
+    1e-8 level, while these products of non-negative overlaps agree to a few rounding units.
     `block` is the number of basis functions per atom (13 for the Si basis)."""
     dev = H.device
     n = H.shape[0]
+    m = torch.as_tensor(np.repeat(moments, block, axis=0), dtype=torch.float64, device=dev)  # (n, 3)
+    Sq = [S @ (S * m[:, q:q + 1]) for q in range(3)]
+    Sq = [0.5 * (x + x.T) for x in Sq]
     natoms = n // block
-    P = torch.zeros(3, n, n, dtype=torch.float64, device=dev)
-    Kt = torch.zeros(n, n, dtype=torch.float64, device=dev)
+    Kb = torch.zeros(n, n, dtype=torch.float64, device=dev)
     for A in range(natoms):
         sl = slice(A * block, (A + 1) * block)
-        SAA = S[sl, sl]
-        inv = torch.linalg.inv(SAA)
-        for q in range(3):
-            P[q, sl, sl] = float(moments[A, q]) * inv
-        Li = torch.linalg.inv(torch.linalg.cholesky(SAA))
-        Kt[sl, sl] = Li.T @ torch.as_tensor(KA[A], dtype=torch.float64, device=dev) @ Li
-    Sq = [S @ P[q] @ S for q in range(3)]
-    Sq = [0.5 * (x + x.T) for x in Sq]
-    Ks = S @ Kt @ S
+        Kb[sl, sl] = torch.as_tensor(KA[A], dtype=torch.float64, device=dev)
+    Ks = S @ Kb @ S
     Ks = 0.5 * (Ks - Ks.T)
     Hc = H.to(torch.complex128)
     ab = delta * (Sq[0] - 1j * Sq[1]) + lam * Ks
@@ -280,7 +281,7 @@ def spin_polarized(tiling, index: int, kT: float, n_elec: float | None = None, d
     """Collinear spin-polarized Gamma-point problem on a cluster: seeded per-atom moments
     m_A ~ U(-1, 1) along one axis and the S-consistent on-site exchange term of the
     noncollinear construction, H_up = H + D S_z, H_down = H - D S_z (S_z = S blockdiag(m_A
-    S_AA^-1) S).  H is (1, 2, N, N) (channel after k), S (1, N, N)."""
+    I_A) S).  H is (1, 2, N, N) (channel after k), S (1, N, N)."""
     H, S, pos, rng = cluster(tiling, seed_for(index), device)
     natoms = pos.shape[0]
     m = np.zeros((natoms, 3))
