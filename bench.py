@@ -387,7 +387,8 @@ def run_uneven(args):
     probs = I.uneven_batch(device=str(dev))
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(dev)  # the batched solve forks its worker streams from a non-default stream
-    ctx = gks.Context(local, stream, graph=not args.no_graph)
+    ctx = gks.Context(local, stream, graph=not args.no_graph, precision=args.precision, split=args.split,
+                      hemv=args.hemv)
     tuned = {}
     if not args.no_tune:
         seen = set()
@@ -448,7 +449,7 @@ def run_uneven(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "systems": len(probs),
-                           "systems_per_s": len(probs) * world / (ms / 1e3), "precision": "fp64",
+                           "systems_per_s": len(probs) * world / (ms / 1e3), "precision": args.precision,
                            "graph": not args.no_graph,
                            "tuned_widths": tuned, "nominal_tflop_per_step": fl / 1e12,
                            "l2": "48 systems, 2.4 GB of inputs, larger than L2 (no flush needed)"},
