@@ -613,7 +613,24 @@ def main():
     mu = torch.empty(1, dtype=torch.float64, device=dev)
     eb = torch.empty(1, dtype=torch.float64, device=dev)
 
+    # the differentiation workload: one step is the forward solve plus the adjoint of a loss with
+    # a seeded Hermitian density-matrix cotangent and the band energy
+    adj = args.workload == "adjoint216" and not shard
+    rbar = None
+    if adj:
+        gen = torch.Generator(device=dev).manual_seed(9058004)
+        rbar = torch.randn(nk, M, M, generator=gen, device=dev, dtype=torch.float64)
+        if H.is_complex():
+            rbar = torch.complex(rbar, torch.randn(nk, M, M, generator=gen, device=dev, dtype=torch.float64))
+        rbar = 0.5 * (rbar + rbar.transpose(-1, -2).conj())
+
     def step(Hd, Sd, sync=False):
+        if adj:
+            ctx.solve_into(Hd, Sd, prob.kT, prob.n_elec, spin, kw, eps=eps, C=C, mu=mu, rho=rho, e_band=eb,
+                           sync=False, save_for_backward=True)
+            ctx.adjoint(None, Sd, prob.kT, spin, kw, rho_bar=rbar, e_band_bar=1.0, sync=sync,
+                        complex_=H.is_complex())
+            return
         if args.per_k:  # one problem per call: the per-problem baseline for the batched form
             for k in range(nk):
                 ctx.solve_into(Hd[k:k + 1], Sd[k:k + 1], prob.kT, prob.n_elec, spin, None,
@@ -662,6 +679,9 @@ def main():
         return exp(-x) / (1 + exp(-x)) if x > 0 else 1 / (1 + exp(x))
     nrho = [int(sum(1 for v in eps_h[k] if fermi((v - mu_h) / prob.kT) >= 1e-16)) for k in range(nk)]
     fl_step = nominal_flops(M, H.is_complex(), nrho)
+    if adj:
+        # the adjoint: six M x M x M products per item (C^H rho_bar C, C B_H C^H, C B_S C^H)
+        fl_step += (48.0 if H.is_complex() else 12.0) * M ** 3 * nk
     if shard:  # strong scaling: the k-points of one system over the ranks
         ft = torch.tensor([fl_step], dtype=torch.float64, device=dev)
         dist.all_reduce(ft)
