@@ -296,7 +296,7 @@ gks_status ensure_ws(gks_ctx* c, int m, int n, int nk, int es, int nc) {
   if (dig) {
     // digit planes of the stale block and of u (14 planes complex, 7 real), scale exponents
     const size_t ldd = ((size_t)m + 15) / 16 * 16, npl = es == 16 ? 14 : 7;
-    c->oD = a.take<char>(ldd * ldd * npl * nk);  // rows up to the 16-multiple the panels reach
+    c->oD = a.take<char>((ldd + 31) / 32 * 32 * ldd * npl * nk);  // rows in tiles of 32
     c->oud = a.take<char>(ldd * npl * nk);
     c->ofu = a.take<int>((size_t)nk);
     c->ormax = a.take<unsigned long long>(ldd * nk);
@@ -932,7 +932,7 @@ void hetrd_run(gks_ctx* c, T* A, int M, int nk) {
     if (c->wsdig) {
       const int ldd = (M + 15) / 16 * 16, npl = es == 16 ? 14 : 7;
       hdv.D = at<signed char>(c, c->oD);
-      hdv.sD = (long long)ldd * ldd * npl;
+      hdv.sD = (long long)((ldd + 31) / 32 * 32) * ldd * npl;
       hdv.ldd = ldd;
       hdv.ud = at<signed char>(c, c->oud);
       hdv.sud = (long long)ldd * npl;

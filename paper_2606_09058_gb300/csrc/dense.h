@@ -49,10 +49,11 @@ void tune_pencil(T* A, int m, int count, int hermitian, cudaStream_t s);
 // ã = sum_s d_s 2^{-6 - 8s} up to 2^{-55}.  ũ = D u gets the same digits below its own
 // scale 2^{fu}.  Then (A u)_i = 2^{d_i} sum over digit pairs s + t <= 7 of exact integer
 // dot products (dp4a, int32 sums) weighted by 2^{fu - 12 - 8(s + t)}.
-// Layout: per row, blocks of 16 columns, each block the planes' 16 bytes one after the
-// other (a row's 16 columns of all planes are 112 or 224 contiguous bytes); ũ the same.
+// Layout: tiles of 32 rows x 16 columns, row-tile-major, each tile contiguous (3584 or
+// 7168 bytes: the 32 rows one after the other, a row's 16 columns as the planes' 16 bytes
+// one after the other); ũ per 16 columns the same way.  Rows are padded to a multiple of 32.
 struct HemvDigits {
-  signed char* D;            // [item][ldd][ldd / 16][planes][16]
+  signed char* D;            // [item][ldd32 / 32][ldd / 16][32][planes][16], ldd32 = ldd rounded up to 32
   long long sD;              // item stride (bytes)
   int ldd;                   // columns per row, multiple of 16
   signed char* ud;           // [item][ldd / 16][planes][16] digits of ũ (zero beyond the step's length)

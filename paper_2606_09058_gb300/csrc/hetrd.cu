@@ -452,7 +452,8 @@ __global__ void __launch_bounds__(64) hetrd_digits_kernel(const T* A, int lda, l
       vals[el] = v;
       ex[el] = dr + (c < n ? deq(rm[c]) : 0);  // ã = a 2^{-d_r - d_c}, cut below 1
     }
-    store_digit_block<T, NPL>(vals, ex, hd.D + z * hd.sD + (size_t)r * hd.ldd * NPL + (size_t)(C0 / 16 + cbk) * (NPL * 16));
+    const size_t tile = (size_t)(r >> 5) * (hd.ldd >> 4) + (C0 >> 4) + cbk;
+    store_digit_block<T, NPL>(vals, ex, hd.D + z * hd.sD + tile * (32 * NPL * 16) + (size_t)(r & 31) * (NPL * 16));
   }
 }
 
@@ -461,54 +462,103 @@ __device__ __forceinline__ int dp4x4(uint4 a, uint4 b, int c) {
   return dp4(a.w, b.w, dp4(a.z, b.z, dp4(a.y, b.y, dp4(a.x, b.x, c))));
 }
 
+// 16-byte asynchronous global -> shared copies (L2 only), their groups and waits.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared-memory ring of the digit matrix-vector kernel: per warp STG stages, each the
+// digit planes of 32 rows x 16 columns (row stride RS 16-byte words: an odd count puts a
+// warp's 16-byte reads of 32 rows on distinct bank groups) followed by u's digits of the
+// same 16 columns.
+template <typename T>
+struct DigRing {
+  static constexpr int NPL = sizeof(T) == 16 ? 2 * kDig : kDig;
+  static constexpr int RS = NPL % 2 ? NPL : NPL + 1;
+  static constexpr int STG = 3;
+  static constexpr int SU4 = 32 * RS + NPL;
+  static constexpr int SMEM = 8 * STG * SU4 * 16;
+};
+
 // p_raw = A_stale[0:j, 0:j] u from the digits, 32 rows per CTA (lane = row), the columns in
 // eight ranges (warp w), exact int32 level sums per (row, product, level), summed over the
-// warps in shared memory, then weighted in FP64; then the common tail.  Digit pairs up to
-// level s + t = 8: the dropped rest lies below 2^-63 of the scales (the pairs of level 8
-// alone would otherwise add a one-signed error near the FP64 unit per term).  Complex: the four
-// real products Re a Re u, Im a Im u, Re a Im u, Im a Re u (Re p = first - second,
-// Im p = third + fourth); real: the first only.
+// warps in shared memory, then weighted in FP64; then the common tail.  Each warp streams its
+// 16-column blocks through its own ring of STG stages (asynchronous copies, STG - 1 blocks
+// ahead of the one it multiplies; a stage is one contiguous tile, consecutive lanes copying
+// consecutive 16-byte words), and the loads in flight hold no registers.
+// Digit pairs up to level s + t = 8: the dropped rest lies below 2^-63 of the scales (the
+// pairs of level 8 alone would otherwise add a one-signed error near the FP64 unit per term).
+// Complex: the four real products Re a Re u, Im a Im u, Re a Im u, Im a Re u
+// (Re p = first - second, Im p = third + fourth); real: the first only.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) hetrd_phemv_dig_kernel(int j, const T* u, T* p, long long sv,
+__global__ void __launch_bounds__(256, 1) hetrd_phemv_dig_kernel(int j, const T* u, T* p, long long sv,
                                                                  const double* tau, long long stau, const T* U,
                                                                  const T* Q, int ldu, long long sU, int k, T* part,
                                                                  long long spart, T* y, long long sy, int* ticket,
                                                                  HemvDigits hd) {
   constexpr bool CPX = sizeof(T) == 16;
   constexpr int NP = CPX ? 4 : 1;  // real products
-  constexpr int NPL = CPX ? 2 * kDig : kDig;
+  constexpr int NPL = DigRing<T>::NPL, RS = DigRing<T>::RS, STG = DigRing<T>::STG, SU4 = DigRing<T>::SU4;
   constexpr int NL = kMaxLevel + 1;  // levels
-  __shared__ int accs[NP * NL][33][8];
-  __shared__ uint4 ush[8][NPL];  // per warp: u's digits of the current 16 columns
+  static_assert(NP * NL * 33 * 8 * 4 <= DigRing<T>::SMEM, "level sums alias the ring");
+  extern __shared__ uint4 ring_all[];
   __shared__ T prow[32];
   const int z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c0 = blockIdx.x * 32, cend = min(c0 + 32, j);
-  const int r = min(c0 + lane, j - 1);  // lanes past the last row repeat it (results unused)
   const int j16 = (j + 15) & ~15;
   const int chunk = (((j16 + 7) / 8) + 15) & ~15;
   const int cb = min(j16, warp * chunk), ce = min(j16, cb + chunk);
-  const signed char* D = hd.D + z * hd.sD + (size_t)r * hd.ldd * NPL;
+  const int nit = (ce - cb) >> 4;
+  // the CTA's row tile: 16-column tiles of 32 rows, each 32 * NPL 16-byte words
+  const uint4* Dt = reinterpret_cast<const uint4*>(hd.D + z * hd.sD) + (size_t)blockIdx.x * (hd.ldd >> 4) * (32 * NPL);
   const signed char* ud = hd.ud + z * hd.sud;
+  uint4* ring = ring_all + warp * (STG * SU4);
+  // stage it % STG <- the contiguous tile of the CTA's 32 rows (rows past j - 1 hold stale
+  // digits; their results are unused) and u's digits, columns cb + 16 it .. + 15; an empty
+  // group past the range keeps the group count uniform
+  auto issue = [&](int it) {
+    if (it < nit) {
+      const int cbk = (cb >> 4) + it;
+      const uint4* src = Dt + (size_t)cbk * (32 * NPL);
+      uint4* st = ring + (it % STG) * SU4;
+#pragma unroll
+      for (int w = lane; w < 32 * NPL; w += 32) {
+        const int rr = w / NPL, q = w - rr * NPL;
+        cp_async16(st + rr * RS + q, src + w);
+      }
+      if (lane < NPL)
+        cp_async16(st + 32 * RS + lane, reinterpret_cast<const uint4*>(ud + (size_t)cbk * (NPL * 16)) + lane);
+    }
+    cp_async_commit();
+  };
   int acc[NP][NL];
 #pragma unroll
   for (int q = 0; q < NP; q++)
 #pragma unroll
     for (int L = 0; L < NL; L++) acc[q][L] = 0;
-  for (int c = cb; c < ce; c += 16) {
-    // 16 columns: all digit planes of this lane's row (NPL x 16 contiguous bytes) in
-    // flight at once; u's digits (the same for every lane) through shared memory
-    const uint4* ab = reinterpret_cast<const uint4*>(D + (size_t)(c >> 4) * (NPL * 16));
+#pragma unroll
+  for (int it = 0; it < STG - 1; it++) issue(it);
+  for (int it = 0; it < nit; it++) {
+    __syncwarp();  // every lane is done with the stage refilled next
+    issue(it + STG - 1);
+    cp_async_wait<STG - 1>();
+    __syncwarp();  // stage it is complete for every lane (each row comes from several lanes)
+    const uint4* st = ring + (it % STG) * SU4;
     uint4 av[NPL];
 #pragma unroll
-    for (int q = 0; q < NPL; q++) av[q] = __ldcs(ab + q);
-    __syncwarp();
-    if (lane < NPL) ush[warp][lane] = __ldg(reinterpret_cast<const uint4*>(ud + (size_t)(c >> 4) * (NPL * 16)) + lane);
-    __syncwarp();
+    for (int q = 0; q < NPL; q++) av[q] = st[lane * RS + q];
 #pragma unroll
     for (int t = 0; t < kDig; t++) {
-      const uint4 ur = ush[warp][t];
+      const uint4 ur = st[32 * RS + t];
       uint4 ui;
-      if constexpr (CPX) ui = ush[warp][kDig + t];
+      if constexpr (CPX) ui = st[32 * RS + kDig + t];
 #pragma unroll
       for (int s = 0; s < kDig && s + t <= kMaxLevel; s++) {
         acc[0][s + t] = dp4x4(av[s], ur, acc[0][s + t]);
@@ -520,6 +570,9 @@ __global__ void __launch_bounds__(256, 2) hetrd_phemv_dig_kernel(int j, const T*
       }
     }
   }
+  cp_async_wait<0>();
+  __syncthreads();  // every ring is idle: the level sums reuse its space
+  auto accs = reinterpret_cast<int(*)[33][8]>(ring_all);
 #pragma unroll
   for (int q = 0; q < NP; q++)
 #pragma unroll
@@ -753,8 +806,10 @@ void hetrd_phemv(const T* A, int lda, long long sA, int j, const T* u, T* p, lon
   count_launch();
   if constexpr (std::is_same<T, double>::value || std::is_same<T, zc>::value) {
     if (hd) {
-      hetrd_phemv_dig_kernel<T><<<dim3((j + 31) / 32, count), 256, 0, s>>>(j, u, p, sv, tau, stau, U, Q, ldu, sU,
-                                                                           k, part, spart, y, sy, ticket, *hd);
+      constexpr int sm = DigRing<T>::SMEM;
+      cudaFuncSetAttribute(hetrd_phemv_dig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      hetrd_phemv_dig_kernel<T><<<dim3((j + 31) / 32, count), 256, sm, s>>>(j, u, p, sv, tau, stau, U, Q, ldu, sU,
+                                                                            k, part, spart, y, sy, ticket, *hd);
       return;
     }
   }
