@@ -125,9 +125,17 @@ __device__ void u_digits(const T* u, int j, signed char* ud, int* fu, const unsi
   __syncthreads();
   // fu: the scale exponent of ũ = D u, the largest bscale(|u_i|) + d_i
   int m = -100000;
-  for (int i = tid; i < j; i += nt) {
-    const unsigned long long mb = maxbits(u[i]);
-    if (mb) m = max(m, bscale(mb) + deq(rmax[i]));
+  for (int i0 = tid; i0 < j; i0 += 8 * nt) {  // eight independent loads in flight per thread
+    unsigned long long mb[8], rb[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int i = i0 + q * nt;
+      mb[q] = i < j ? maxbits(u[i]) : 0ull;
+      rb[q] = i < j ? rmax[i] : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+      if (mb[q]) m = max(m, bscale(mb[q]) + deq(rb[q]));
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((tid & 31) == 0) mred[tid >> 5] = m;
@@ -161,7 +169,13 @@ __device__ void reflector_body(T* A, int lda, int j, T* u, double* tau, double* 
   const int tid = threadIdx.x, nt = blockDim.x;
   T* row = A + (size_t)j * lda;
   double s2 = 0.0;
-  for (int i = tid; i < j; i += nt) s2 += abs2(ldcg(row + i));
+  for (int i0 = tid; i0 < j; i0 += 8 * nt) {  // eight independent loads in flight per thread
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) v[q] = i0 + q * nt < j ? ldcg(row + i0 + q * nt) : zero<T>();
+#pragma unroll
+    for (int q = 0; q < 8; q++) s2 += abs2(v[q]);
+  }
   const double xnorm2 = block_sum(s2, redd);
   const T alpha = conjg(ldcg(row + j - 1));
   const double tail = xnorm2 - abs2(alpha);
@@ -181,11 +195,20 @@ __device__ void reflector_body(T* A, int lda, int j, T* u, double* tau, double* 
   const double beta = 2.0 / (tail + abs2(upiv));
   const T inv = conjg(upiv) * (1.0 / abs2(upiv));       // 1 / upiv
   __syncthreads();
-  for (int i = tid; i < j - 1; i += nt) {
-    T v = conjg(ldcg(row + i)) * inv;                 // u'_i = a_i / u_{j-1}
-    u[i] = v;
-    row[i] = v;
-    put_uw(uw, i, re(v), im(v));
+  for (int i0 = tid; i0 < j - 1; i0 += 8 * nt) {
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) v[q] = i0 + q * nt < j - 1 ? ldcg(row + i0 + q * nt) : zero<T>();
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int i = i0 + q * nt;
+      if (i < j - 1) {
+        const T w = conjg(v[q]) * inv;  // u'_i = a_i / u_{j-1}
+        u[i] = w;
+        row[i] = w;
+        put_uw(uw, i, re(w), im(w));
+      }
+    }
   }
   if (tid == 0) {
     u[j - 1] = from_real<T>(1.0);
@@ -225,6 +248,7 @@ template <typename T>
 __device__ void phemv_tail(const T* prow, int c0, int cend, const T* u, T* p, double t, const T* U, const T* Q,
                            int ldu, int k, T* part, T* y, int* ticket) {
   __shared__ T red[32];
+  __shared__ T gsum[256];
   __shared__ int last;
   const int tid = threadIdx.x;
   const int pst = 2 * ldu + 2;
@@ -239,10 +263,20 @@ __device__ void phemv_tail(const T* prow, int c0, int cend, const T* u, T* p, do
   if (tid == 0) mine[2 * ldu] = d0;
   for (int s = tid; s < k; s += blockDim.x) {
     T a1 = zero<T>(), a2 = zero<T>();
-    for (int r = c0; r < cend; r++) {
-      const T ur = u[r];
-      macc(a1, Q[(size_t)r * ldu + s], ur);
-      macc(a2, U[(size_t)r * ldu + s], ur);
+    for (int r0 = c0; r0 < cend; r0 += 8) {  // eight rows' loads in flight
+      T qv[8], uv[8], ur[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int r = min(r0 + q, cend - 1);
+        qv[q] = Q[(size_t)r * ldu + s];
+        uv[q] = U[(size_t)r * ldu + s];
+        ur[q] = r0 + q < cend ? u[r] : zero<T>();
+      }
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        macc(a1, qv[q], ur[q]);
+        macc(a2, uv[q], ur[q]);
+      }
     }
     mine[s] = a1;
     mine[ldu + s] = a2;
@@ -253,19 +287,37 @@ __device__ void phemv_tail(const T* prow, int c0, int cend, const T* u, T* p, do
   __syncthreads();
   if (!last) return;
   if (tid == 0) *ticket = 0;
-  const int nb = gridDim.x;
-  for (int e = tid; e < k; e += blockDim.x) {
-    T a1 = zero<T>(), a2 = zero<T>();
-    for (int b = 0; b < nb; b++) {
-      a1 += ldcg(part + (size_t)b * pst + e);
-      a2 += ldcg(part + (size_t)b * pst + ldu + e);
+  // Sums over the CTAs' shares of the E = 2k + 1 entries (Q^H u, U^H u, u^H p_raw): G groups
+  // of threads per entry take every G-th CTA with eight loads in flight, then one thread per
+  // entry adds the groups in order.
+  const int nb = gridDim.x, nt = blockDim.x, E = 2 * k + 1;
+  const int G = E <= nt ? nt / E : 1;
+  for (int t0 = tid; t0 < G * E; t0 += nt) {
+    const int e = t0 % E, g = t0 / E;
+    const size_t off = e < k ? e : (e < 2 * k ? ldu + (e - k) : 2 * ldu);
+    T a = zero<T>();
+    for (int b0 = g; b0 < nb; b0 += 8 * G) {
+      T v[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) v[q] = b0 + q * G < nb ? ldcg(part + (size_t)(b0 + q * G) * pst + off) : zero<T>();
+#pragma unroll
+      for (int q = 0; q < 8; q++) a += v[q];
     }
-    y[e] = a1;
-    y[ldu + e] = a2;
+    if (G > 1) gsum[t0] = a;
+    else if (e < k) y[e] = a;
+    else if (e < 2 * k) y[ldu + e - k] = a;
+    else red[0] = a;
   }
-  T tot = zero<T>();
-  if (tid == 0)
-    for (int b = 0; b < nb; b++) tot += ldcg(part + (size_t)b * pst + 2 * ldu);
+  __syncthreads();
+  if (G > 1 && tid < E) {
+    T a = gsum[tid];
+    for (int g = 1; g < G; g++) a += gsum[g * E + tid];
+    if (tid < k) y[tid] = a;
+    else if (tid < 2 * k) y[ldu + tid - k] = a;
+    else red[0] = a;
+  }
+  __syncthreads();
+  const T tot = red[0];
   __syncthreads();
   T w = zero<T>();
   for (int e = tid; e < k; e += blockDim.x) {
@@ -683,13 +735,25 @@ __global__ void __launch_bounds__(256) hetrd_pupdate_kernel(T* A, int lda, long 
     if (ok) {
       const T* Uc = U + (size_t)c * ldu;
       const T* Qc = Q + (size_t)c * ldu;
-      for (int s = gl; s < k; s += 8) {
-        const T uc = Uc[s], qc = Qc[s];
-        mac(corr, uc, y1s[s]);
-        mac(corr, qc, y2s[s]);
-        if (rowupd) {
-          mac(rs, ujs[s], conjg(qc));
-          mac(rs, qjs[s], conjg(uc));
+      for (int s0 = gl; s0 < k; s0 += 32) {  // four steps' loads in flight
+        T ucv[4], qcv[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int sq = min(s0 + 8 * q, k - 1);
+          ucv[q] = Uc[sq];
+          qcv[q] = Qc[sq];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int sq = s0 + 8 * q;
+          if (sq < k) {
+            mac(corr, ucv[q], y1s[sq]);
+            mac(corr, qcv[q], y2s[sq]);
+            if (rowupd) {
+              mac(rs, ujs[sq], conjg(qcv[q]));
+              mac(rs, qjs[sq], conjg(ucv[q]));
+            }
+          }
         }
       }
     }

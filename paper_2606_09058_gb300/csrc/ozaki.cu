@@ -508,6 +508,22 @@ struct CrtArgs {
   long long skip_copy;      // test hook: the producer leaves out this copy (-1 = none)
 };
 
+// Tile of the residue kernel: 128 x 256 outputs per CTA (the B operand tile twice as wide as
+// the digit-pair kernel's, so each A tile fetched into shared memory serves twice the MMA
+// work), four stages of 48 KB, and two 256-column FP32 accumulators filling the 512 columns
+// of tensor memory.
+namespace crtc {
+constexpr int BN = 256;
+constexpr int STAGES = 4;
+constexpr int B_BYTES = BN * tcg::BK * 2;
+constexpr int STAGE_BYTES = tcg::TILE_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 2 * BN;
+constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(tcg::BM >> 4) << 24);
+static_assert(SMEM <= 227 * 1024, "shared memory of the residue kernel");
+}  // namespace crtc
+
 // x - m round(x / m) for an integer-valued float |x| <= 2^24: the quotient is rounded with
 // the 1.5 * 2^23 shift (|x / m| < 2^22), and the fused multiply-add is exact because the
 // result is a small integer.
@@ -520,6 +536,10 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
     crt_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, CrtArgs a,
                   DevStatus* status) {
   using namespace tcg;
+  using crtc::BN;
+  using crtc::STAGE_BYTES;
+  using crtc::STAGES;
+  using crtc::TMEM_COLS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
   __shared__ uint32_t tmem_base;
@@ -620,7 +640,8 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
             const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TILE_BYTES);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; kk++) {
-              umma(tmem + (uint32_t)(b * BN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), accum);
+              tcg::umma<crtc::IDESC>(tmem + (uint32_t)(b * BN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2),
+                                     accum);
               accum = 1u;
             }
             umma_commit(&empty[stg]);
@@ -633,16 +654,17 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
       mbar_drain(&done, 0, a.wait);
     }
   } else {
-    // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31 (tile rows) and column half (w - 2) / 4
+    // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31 (tile rows) and column half
+    // (w - 2) / 4 (128 columns)
     const int lq = warp & 3, ch = (warp - 2) >> 2;
     const int i = m0 + lq * 32 + lane;
     int u = 0;
     bool ok = true;
     for (int l = 0; l < n && ok; l++) {
       const float mf = (float)crt_mod(l), inv = __frcp_rn(mf);
-      float acc[64];
+      float acc[128];
 #pragma unroll
-      for (int t = 0; t < 64; t++) acc[t] = 0.0f;
+      for (int t = 0; t < 128; t++) acc[t] = 0.0f;
       for (int c = 0; c < nchunk; c++, u++) {
         const int b = u & 1;
         const uint32_t uph = (uint32_t)((u >> 1) & 1);
@@ -651,40 +673,42 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * BN + ch * 64);
-        uint32_t v[32];
-        tmem_ld32(taddr, v);
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * BN + ch * 128);
 #pragma unroll
-        for (int t = 0; t < 32; t++) acc[t] += crt_fold(__uint_as_float(v[t]), mf, inv);
-        tmem_ld32(taddr + 32, v);
+        for (int g = 0; g < 4; g++) {
+          uint32_t v[32];
+          tmem_ld32(taddr + 32 * g, v);
 #pragma unroll
-        for (int t = 0; t < 32; t++) acc[32 + t] += crt_fold(__uint_as_float(v[t]), mf, inv);
+          for (int t = 0; t < 32; t++) acc[32 * g + t] += crt_fold(__uint_as_float(v[t]), mf, inv);
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
       }
       if (!ok) break;
-      // t_l = (X mod m_l) y_l mod m_l in [0, m_l) for this thread's row and 64 embedded
+      // t_l = (X mod m_l) y_l mod m_l in [0, m_l) for this thread's row and 128 embedded
       // columns, one byte each (both folds exact: |acc| < 2^24, r y_l < 2^16)
       const float yl = a.y[l];
-      uint32_t w[16];
+      uint4* dst = reinterpret_cast<uint4*>(a.R + z * a.zR + ((size_t)l * a.Mp + i) * a.Np + n0 + ch * 128);
 #pragma unroll
-      for (int t = 0; t < 16; t++) {
-        uint32_t word = 0;
+      for (int q = 0; q < 8; q++) {
+        uint32_t w[4];
 #pragma unroll
-        for (int s4 = 0; s4 < 4; s4++) {
-          float r = crt_fold(acc[4 * t + s4], mf, inv);
-          r = r < 0.0f ? r + mf : r;
-          r = crt_fold(r * yl, mf, inv);
-          r = r < 0.0f ? r + mf : r;
-          r = r >= mf ? r - mf : r;
-          word |= (uint32_t)r << (8 * s4);
+        for (int t = 0; t < 4; t++) {
+          uint32_t word = 0;
+#pragma unroll
+          for (int s4 = 0; s4 < 4; s4++) {
+            float r = crt_fold(acc[16 * q + 4 * t + s4], mf, inv);
+            r = r < 0.0f ? r + mf : r;
+            r = crt_fold(r * yl, mf, inv);
+            r = r < 0.0f ? r + mf : r;
+            r = r >= mf ? r - mf : r;
+            word |= (uint32_t)r << (8 * s4);
+          }
+          w[t] = word;
         }
-        w[t] = word;
+        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
       }
-      uint4* dst = reinterpret_cast<uint4*>(a.R + z * a.zR + ((size_t)l * a.Mp + i) * a.Np + n0 + ch * 64);
-#pragma unroll
-      for (int t = 0; t < 4; t++) dst[t] = make_uint4(w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);
     }
   }
   tc_fence_before();
@@ -740,14 +764,14 @@ __device__ __forceinline__ bool ge4(const uint32_t (&x)[4], const uint32_t (&y)[
   return true;
 }
 
-// The signed integer X with X y_l = t_l (mod m_l) for the weighted residues t_l at
-// R[l * plane], |X| < M / 2, as a double times 2^e.
-__device__ __forceinline__ double crt_value(const uint8_t* R, long long plane, const CrtRecon& cr, int e) {
+// The signed integer X with X y_l = t_l (mod m_l) for the weighted residues t_l (byte el of
+// the 16 loaded for modulus l), |X| < M / 2, as a double times 2^e.
+__device__ __forceinline__ double crt_value(const uint32_t (&w)[CRT_MAXMOD][4], int el, const CrtRecon& cr, int e) {
   uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;  // S = sum_l t_l M / m_l < 16 M
 #pragma unroll
   for (int l = 0; l < CRT_MAXMOD; l++) {
     if (l < cr.n) {
-      const uint32_t t = R[l * plane];
+      const uint32_t t = (w[l][el >> 2] >> (8 * (el & 3))) & 0xffu;
       unsigned long long c = (unsigned long long)t * cr.Nl[l][0] + s0;
       s0 = (uint32_t)c;
       c = (c >> 32) + (unsigned long long)t * cr.Nl[l][1] + s1;
@@ -813,28 +837,51 @@ __device__ __forceinline__ double crt_value(const uint8_t* R, long long plane, c
 }
 
 // C = alpha 2^{e_i + f_j - 2p} X + beta C for the logical outputs (lower: j <= i only).
+// A thread takes 16 consecutive embedded columns of a row: one 16-byte load per modulus (the
+// residue planes are Np bytes per row, Np a multiple of 256), then the 16 values (8 complex).
 template <typename T>
-__global__ void __launch_bounds__(256) crt_recon_kernel(const uint8_t* R, long long zR, int Mp, int Np, int M, int N,
+__global__ void __launch_bounds__(128) crt_recon_kernel(const uint8_t* R, long long zR, int Mp, int Np, int M, int N,
                                                         const int* ea, const int* eb, long long zEa, long long zEb,
                                                         int sc, const CrtRecon cr, T* C, int ldc, long long zC,
                                                         long long zC2, int nb2, double alpha, double beta,
                                                         int lower) {
-  const int z = blockIdx.z, j = blockIdx.x * 256 + threadIdx.x;
-  if (j >= N) return;
+  constexpr bool CPX = sizeof(T) == 16;
+  constexpr int PER = CPX ? 8 : 16;  // logical columns per thread
+  const int z = blockIdx.z, j0 = (blockIdx.x * 128 + threadIdx.x) * PER;
+  if (j0 >= N) return;
   const long long plane = (long long)Mp * Np;
   for (int i = blockIdx.y; i < M; i += gridDim.y) {
-    if (lower && j > i) continue;
-    const uint8_t* Rz = R + z * zR + (size_t)i * Np;
-    const int e = ea[z * zEa + i] + eb[z * zEb + j] + sc;
-    T* cp = C + item_off(z, zC, zC2, nb2) + (size_t)i * ldc + j;
-    if constexpr (sizeof(T) == 16) {
-      zc v{alpha * crt_value(Rz + 2 * j, plane, cr, e), alpha * crt_value(Rz + 2 * j + 1, plane, cr, e)};
-      if (beta != 0.0) v = v + beta * (*cp);
-      *cp = v;
-    } else {
-      double v = alpha * crt_value(Rz + j, plane, cr, e);
-      if (beta != 0.0) v += beta * (*cp);
-      *cp = v;
+    if (lower && j0 > i) continue;
+    const uint8_t* Rz = R + z * zR + (size_t)i * Np + (CPX ? 2 * j0 : j0);
+    uint32_t w[CRT_MAXMOD][4];
+#pragma unroll
+    for (int l = 0; l < CRT_MAXMOD; l++) {
+      if (l < cr.n) {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(Rz + l * plane));
+        w[l][0] = v.x;
+        w[l][1] = v.y;
+        w[l][2] = v.z;
+        w[l][3] = v.w;
+      } else {
+        w[l][0] = w[l][1] = w[l][2] = w[l][3] = 0u;
+      }
+    }
+    const int ei = ea[z * zEa + i] + sc;
+    T* cp = C + item_off(z, zC, zC2, nb2) + (size_t)i * ldc;
+#pragma unroll
+    for (int q = 0; q < PER; q++) {
+      const int j = j0 + q;
+      if (j >= N || (lower && j > i)) break;
+      const int e = ei + eb[z * zEb + j];
+      if constexpr (CPX) {
+        zc v{alpha * crt_value(w, 2 * q, cr, e), alpha * crt_value(w, 2 * q + 1, cr, e)};
+        if (beta != 0.0) v = v + beta * cp[j];
+        cp[j] = v;
+      } else {
+        double v = alpha * crt_value(w, q, cr, e);
+        if (beta != 0.0) v += beta * cp[j];
+        cp[j] = v;
+      }
     }
   }
 }
@@ -856,12 +903,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2-D bf16 map over rows x Kp (row stride Kp), box 64 (k) x 128 (rows), 128-byte swizzle.
-static bool digit_map(CUtensorMap* m, const void* base, long long rows, int Kp) {
+static bool digit_map(CUtensorMap* m, const void* base, long long rows, int Kp, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)tcg::BK, (cuuint32_t)tcg::BM};
+  cuuint32_t box[2] = {(cuuint32_t)tcg::BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -927,12 +974,16 @@ static bool crt_plan(int Kp, int bits, CrtPlan* pl) {
 // bits (digit pairs again when 16 moduli cannot).
 static bool residue_form(int S, int Kp, CrtPlan* pl) { return S < 0 && crt_plan(Kp, OZ_BITS * -S, pl); }
 
+// Embedded output columns padded to the product kernel's tile width.
+static int padded_n(int N, bool cplx, bool res) { return round_up(cplx ? 2 * N : N, res ? crtc::BN : OZ_BN); }
+
 size_t ozaki_workspace_bytes(int M, int N, int K, bool cplx, int S) {
   const int Kp = padded_k(K, cplx);
-  const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
   CrtPlan pl;
+  const bool res = residue_form(S, Kp, &pl);
+  const int Mp = round_up(M, OZ_BM), Np = padded_n(N, cplx, res);
   size_t b;
-  if (residue_form(S, Kp, &pl))
+  if (res)
     b = (size_t)pl.n * (((size_t)Mp + Np) * Kp * 2 + (size_t)Mp * Np);
   else
     b = (size_t)std::abs(S) * ((size_t)Mp + Np) * Kp * 2;
@@ -957,9 +1008,9 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   if (M <= 0 || N <= 0 || count <= 0) return true;
   const bool cplx = sizeof(T) == 16;
   const int Kp = padded_k(K, cplx);
-  const int Mp = round_up(M, OZ_BM), Np = round_up(cplx ? 2 * N : N, OZ_BN);
   CrtPlan pl;
   const bool res = residue_form(S, Kp, &pl);
+  const int Mp = round_up(M, OZ_BM), Np = padded_n(N, cplx, res);
   const int P = res ? pl.n : std::abs(S);  // planes per operand
   const long long zA = (long long)P * Mp * Kp, zB = (long long)P * Np * Kp;
   const long long zR = res ? (long long)P * Mp * Np : 0;
@@ -987,9 +1038,10 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
     }
   }
   const long long wait = wait_cycles > 0 ? wait_cycles : (1ll << 32);
-  dim3 grid(Np / OZ_BN, Mp / OZ_BM, count);
+  dim3 grid(Np / (res ? crtc::BN : OZ_BN), Mp / OZ_BM, count);
   CUtensorMap ma, mb;
-  if (!digit_map(&ma, Ad, (long long)count * P * Mp, Kp) || !digit_map(&mb, Bd, (long long)count * P * Np, Kp))
+  if (!digit_map(&ma, Ad, (long long)count * P * Mp, Kp, tcg::BM) ||
+      !digit_map(&mb, Bd, (long long)count * P * Np, Kp, res ? crtc::BN : tcg::BN))
     return false;
   if (res) {
     CrtArgs ca;
@@ -1007,12 +1059,12 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
     ca.wait = wait;
     ca.skip_copy = skip_copy;
     for (int l = 0; l < CRT_MAXMOD; l++) ca.y[l] = l < P ? (float)pl.cr.y[l] : 0.0f;
-    cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM);
+    cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, crtc::SMEM);
     count_launch(2);
-    crt_tc_kernel<<<grid, tcg::THREADS, tcg::SMEM, s>>>(ma, mb, ca, status);
-    crt_recon_kernel<T><<<dim3((N + 255) / 256, std::min(M, 65535), count), 256, 0, s>>>(R, zR, Mp, Np, M, N, ea, eb, Mp, Np,
-                                                                         -2 * pl.p, pl.cr, C, ldc, sC, sC2, nb2,
-                                                                         alpha, beta, lower);
+    crt_tc_kernel<<<grid, tcg::THREADS, crtc::SMEM, s>>>(ma, mb, ca, status);
+    const int per = cplx ? 8 : 16;
+    crt_recon_kernel<T><<<dim3((N + 128 * per - 1) / (128 * per), std::min(M, 65535), count), 128, 0, s>>>(
+        R, zR, Mp, Np, M, N, ea, eb, Mp, Np, -2 * pl.p, pl.cr, C, ldc, sC, sC2, nb2, alpha, beta, lower);
     return true;
   }
   OzArgs oa;

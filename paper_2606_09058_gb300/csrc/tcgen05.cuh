@@ -83,11 +83,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// The bf16 MMA with instruction descriptor ID (the BM x BN shape above by default).
+template <uint32_t ID = IDESC>
 __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
           dtmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+      "l"(adesc), "l"(bdesc), "r"(ID), "r"(acc));
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
