@@ -694,10 +694,10 @@ def main():
     # from one ncu capture of the kernel on the 64-atom k-batch (profiles/), where it matched
     # the algorithmic bytes of that launch to the ratio below; it scales with the bytes the
     # launch processes, so the live per-launch algorithmic bytes times that ratio is reported.
-    # DRAM bytes / algorithmic bytes of one launch from an ncu capture (profiles/): the FP64
-    # matrix-vector step (16-row blocks on the 64-atom k-batch) and its digit form (one
-    # k-point of the 512-atom batch: DRAM bytes = the digit block)
-    TRAFFIC_RATIO = {("hetrd_hemv", "fp64"): 1.04, ("hetrd_hemv", "digits"): 1.01}
+    # DRAM bytes / algorithmic bytes of one launch from an ncu capture (profiles/) of the
+    # kernel as it stands: the FP64 matrix-vector step (16-row blocks on the 64-atom k-batch);
+    # the digit form has no capture of its current (tiled, asynchronous-copy) version yet
+    TRAFFIC_RATIO = {("hetrd_hemv", "fp64"): 1.04}
     kern = [p for p in prof if not p["name"].startswith("stage:")]
     dom = max(kern, key=lambda p: p["ms"]) if kern else None
     roof = None
