@@ -96,7 +96,6 @@ struct gks_ctx {
   int slices = 9;                      // split products: 6-bit digits per operand, or 6 slices bits
   int split = 0;                       // split-product form: 0 residues (CRT), 1 digit pairs
   int hemv = 0;                        // one-stage matrix-vector step: 0 integer digits, 1 FP64 pipe
-  bool thin_split = false;             // thin batched products also go to the tensor cores
   int wsdig = 0;                       // workspace holds the digit planes of the stale block
   int nbb = 256;                       // outer block of the two-level blocked stages (active)
   int nbb_default = 256;               // opts.block, used for shapes the tuner has not seen
@@ -534,10 +533,6 @@ int oz_reserve(gks_ctx* c, size_t item, int count) {
 
 bool split_worth(gks_ctx* c, int count, int M, int N, int K, int es, double fl) {
   if (c->gemm_mode == 2) return true;
-  // many thin products in one launch (the Q2 wavefronts): the tensor cores win even below
-  // the per-product size threshold once the batch fills the GPU
-  if (c->gemm_mode == 0 && c->thin_split && K >= 16 && (long long)ozaki_tiles(M, N, es == 16) * count >= 152)
-    return true;
   const int Ne = es == 16 ? 2 * N : N;  // embedded output columns
   return c->gemm_mode == 0 && fl >= 2e8 * count && M >= 64 && Ne >= 64 && K >= 64 &&
          (long long)ozaki_tiles(M, N, es == 16) * count >= 152;
@@ -1080,11 +1075,6 @@ void q2_apply_run(gks_ctx* c, T* Xp, long long sXp, int M, int ncols, int items)
   T* Tw = at<T>(c, c->oTw);
   T* Yw = at<T>(c, c->oYw);
   T* Y2w = at<T>(c, c->oY2w);
-  struct ThinScope {
-    gks_ctx* c;
-    explicit ThinScope(gks_ctx* c_) : c(c_) { c->thin_split = true; }
-    ~ThinScope() { c->thin_split = false; }
-  } thin(c);
   for (int t = 0;; t++) {
     const int g_lo = std::max(0, (2 * (G - 1) - t + 1) / 2);
     int nblk = 0;
