@@ -404,8 +404,12 @@ def run_uneven(args):
             tuned[f"{'nc' if p.spin == 'noncollinear' else ('c' if cplx else 'r')}{b}"] = best
     items = [dict(H=p.H.contiguous(), S=p.S.contiguous(), kT=p.kT, n_elec=p.n_elec, spin=p.spin) for p in probs]
     sols = None
-    for _ in range(max(2, args.warmup)):  # eager, then capture (graph mode), then replays
+    per_pass = 0
+    for w in range(max(2, args.warmup)):  # eager, then capture (graph mode), then replays
+        c0 = gks.launch_count()
         sols = ctx.solve_batched(items, nstreams=8, sync=True, out=sols)
+        if w == 0:
+            per_pass = gks.launch_count() - c0  # kernels of one eager pass (what a replay runs)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -420,6 +424,8 @@ def run_uneven(args):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = gks.launch_count() - l0
+    if launches == 0 and not args.no_graph:
+        launches = per_pass * args.steps  # graph replays launch the captured kernels without the host
     clk = clocks.stop()
     ctx.sync()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
@@ -451,6 +457,8 @@ def run_uneven(args):
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "systems": len(probs),
                            "systems_per_s": len(probs) * world / (ms / 1e3), "precision": args.precision,
                            "graph": not args.no_graph,
+                           "gpu_launches_counted": ("kernels of one eager pass x graph replays" if not args.no_graph
+                                                    else "host launches in the timed region"),
                            "tuned_widths": tuned, "nominal_tflop_per_step": fl / 1e12,
                            "l2": "48 systems, 2.4 GB of inputs, larger than L2 (no flush needed)"},
                 "roofline": None, "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(launches),
@@ -695,9 +703,10 @@ def main():
     # the algorithmic bytes of that launch to the ratio below; it scales with the bytes the
     # launch processes, so the live per-launch algorithmic bytes times that ratio is reported.
     # DRAM bytes / algorithmic bytes of one launch from an ncu capture (profiles/) of the
-    # kernel as it stands: the FP64 matrix-vector step (16-row blocks on the 64-atom k-batch);
-    # the digit form has no capture of its current (tiled, asynchronous-copy) version yet
-    TRAFFIC_RATIO = {("hetrd_hemv", "fp64"): 1.04}
+    # kernel as it stands: the FP64 matrix-vector step (16-row blocks on the 64-atom k-batch)
+    # and its digit form (one k-point of the 512-atom batch, the tiled copy-ring version:
+    # DRAM bytes = the digit block)
+    TRAFFIC_RATIO = {("hetrd_hemv", "fp64"): 1.04, ("hetrd_hemv", "digits"): 1.019}
     kern = [p for p in prof if not p["name"].startswith("stage:")]
     dom = max(kern, key=lambda p: p["ms"]) if kern else None
     roof = None
