@@ -131,47 +131,60 @@ __device__ __forceinline__ void emit(zc x, int e, int role, int v, int k, __nv_b
   }
 }
 
-// One CTA (256 threads) per 32 vectors.  Pass 1: per-vector max (thread per vector when the
-// vector index is the contiguous direction, else a warp sweeps each vector along k).
-// Pass 2: the S digits or residues (RES; residues of trunc(x 2^{p - e})).  Padding vectors
-// and k beyond K are written as zeros elsewhere.  blockIdx.y runs over the batch items
-// (strides sX, sD, sE).  Optional per item: kdev (device) cuts K to its value, ksc scales
-// element k by ksc[k] before splitting.
-template <typename T, bool RES>
-__global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long long sX, int role, int op, int nvec,
-                                                       int K, __nv_bfloat16* D, int Kp, long long sstride,
-                                                       long long sD, int S, int p, int* ex, long long sE,
-                                                       const double* ksc, long long sks, const int* kdev,
-                                                       long long sX2, int nb2) {
-  __shared__ double smax[32];
-  __shared__ int sexp[32];
-  const int v0 = blockIdx.x * 32, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  X += item_off(blockIdx.y, sX, sX2, nb2);
-  D += blockIdx.y * sD;
-  ex += blockIdx.y * sE;
-  if (kdev) K = min(K, max(0, kdev[blockIdx.y]));
-  if (ksc) ksc += blockIdx.y * sks;
-  auto elem = [&](int v, int k) -> T {
+// Item z of the split operand with the optional per-item K (device) and k scaling.
+template <typename T>
+struct SplitSrc {
+  const T* X;
+  int ld, role, op;
+  const double* ksc;
+  __device__ T operator()(int v, int k) const {
     T x = split_elem(X, ld, role, op, v, k);
     return ksc ? x * ksc[k] : x;
-  };
+  }
+};
+
+// Pass 1, one CTA (256 threads) per 32 vectors: the per-vector scale exponents (thread per
+// vector when the vector index is the contiguous direction, else a warp sweeps each vector
+// along k, four loads in flight per lane).  blockIdx.y runs over the batch items (strides
+// sX, sE); kdev (device, per item) cuts K, ksc scales element k by ksc[k] first.
+template <typename T>
+__global__ void __launch_bounds__(256) oz_scale_kernel(const T* X, int ld, long long sX, int role, int op, int nvec,
+                                                       int K, int* ex, long long sE, const double* ksc,
+                                                       long long sks, const int* kdev, long long sX2, int nb2) {
+  __shared__ double smax[32];
+  __shared__ double pm[8][32];
+  const int v0 = blockIdx.x * 32, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (kdev) K = min(K, max(0, kdev[blockIdx.y]));
+  const SplitSrc<T> elem{X + item_off(blockIdx.y, sX, sX2, nb2), ld, role, op, ksc ? ksc + blockIdx.y * sks : nullptr};
+  ex += blockIdx.y * sE;
   const bool contig = (role == 0) == (op == OP_N);  // k contiguous in memory
   if (contig) {
     for (int vv = warp; vv < 32; vv += 8) {
       const int v = v0 + vv;
       double m = 0.0;
       if (v < nvec)
-        for (int k = lane; k < K; k += 32) m = fmax(m, amax(elem(v, k)));
+        for (int k0 = lane; k0 < K; k0 += 128) {
+          T x[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) x[q] = k0 + 32 * q < K ? elem(v, k0 + 32 * q) : zero<T>();
+#pragma unroll
+          for (int q = 0; q < 4; q++) m = fmax(m, amax(x[q]));
+        }
       for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
       if (lane == 0) smax[vv] = m;
     }
   } else {
     // 8 warps sweep k in parallel, lanes run over the 32 vectors (coalesced), then reduce
-    __shared__ double pm[8][32];
     double m = 0.0;
     const int v = v0 + lane;
     if (v < nvec)
-      for (int k = warp; k < K; k += 8) m = fmax(m, amax(elem(v, k)));
+      for (int k0 = warp; k0 < K; k0 += 32) {
+        T x[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) x[q] = k0 + 8 * q < K ? elem(v, k0 + 8 * q) : zero<T>();
+#pragma unroll
+        for (int q = 0; q < 4; q++) m = fmax(m, amax(x[q]));
+      }
     pm[warp][lane] = m;
     __syncthreads();
     if (tid < 32) {
@@ -181,33 +194,45 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long 
     }
   }
   __syncthreads();
-  if (tid < 32) {
-    sexp[tid] = scale_exp(smax[tid]);
-    if (v0 + tid < nvec) ex[v0 + tid] = sexp[tid];
+  if (tid < 32 && v0 + tid < nvec) ex[v0 + tid] = scale_exp(smax[tid]);
+}
+
+// Pass 2, one CTA (256 threads) per tile of 32 vectors x 32 k (grid x: vectors, y: k,
+// z: items) over the padded plane: nvp vectors (padding rows included; complex B: half the
+// embedded rows) and kpl k (complex: half the padded K').  The tile is staged through shared
+// memory (read along the contiguous direction), then its S digits or residues (RES; residues
+// of trunc(x 2^{p - e})) are written with lanes along k; padding vectors and k beyond K
+// (the item's, after kdev) get the split values of zero, so the planes need no clearing.
+template <typename T, bool RES>
+__global__ void __launch_bounds__(256) oz_split_kernel(const T* X, int ld, long long sX, int role, int op, int nvec,
+                                                       int K, __nv_bfloat16* D, int Kp, long long sstride,
+                                                       long long sD, int S, int p, const int* ex, long long sE,
+                                                       const double* ksc, long long sks, const int* kdev,
+                                                       long long sX2, int nb2, int nvp, int kpl) {
+  __shared__ T tile[32][33];
+  __shared__ int sexp[32];
+  const int v0 = blockIdx.x * 32, k0 = blockIdx.y * 32, z = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (kdev) K = min(K, max(0, kdev[z]));
+  const SplitSrc<T> elem{X + item_off(z, sX, sX2, nb2), ld, role, op, ksc ? ksc + z * sks : nullptr};
+  D += z * sD;
+  ex += z * sE;
+  if (tid < 32) sexp[tid] = v0 + tid < nvec ? ex[v0 + tid] : 0;
+  if ((role == 0) == (op == OP_N)) {  // k contiguous: lanes along k
+    for (int vv = warp; vv < 32; vv += 8) {
+      const int v = v0 + vv, k = k0 + lane;
+      tile[lane][vv] = (v < nvec && k < K) ? elem(v, k) : zero<T>();
+    }
+  } else {  // vectors contiguous: lanes along the vectors
+    for (int kk = warp; kk < 32; kk += 8) {
+      const int k = k0 + kk, v = v0 + lane;
+      tile[kk][lane] = (k < K && v < nvec) ? elem(v, k) : zero<T>();
+    }
   }
   __syncthreads();
-  if (contig) {
-    for (int vv = warp; vv < 32; vv += 8) {
-      const int v = v0 + vv;
-      if (v >= nvec) continue;
-      for (int k = lane; k < K; k += 32) emit<RES>(elem(v, k), sexp[vv], role, v, k, D, Kp, sstride, S, p);
-    }
-  } else {
-    // k strided in memory: stage 32 (k) x 32 (vectors) tiles through shared memory so that
-    // the reads run along the vectors and the digit writes along k
-    __shared__ T tile[32][33];
-    for (int k0 = 0; k0 < K; k0 += 32) {
-      for (int kk = warp; kk < 32; kk += 8) {
-        const int k = k0 + kk, v = v0 + lane;
-        tile[kk][lane] = (k < K && v < nvec) ? elem(v, k) : zero<T>();
-      }
-      __syncthreads();
-      for (int vv = warp; vv < 32; vv += 8) {
-        const int v = v0 + vv, k = k0 + lane;
-        if (v < nvec && k < K) emit<RES>(tile[lane][vv], sexp[vv], role, v, k, D, Kp, sstride, S, p);
-      }
-      __syncthreads();
-    }
+  for (int vv = warp; vv < 32; vv += 8) {
+    const int v = v0 + vv, k = k0 + lane;
+    if (v < nvp && k < kpl) emit<RES>(tile[lane][vv], sexp[vv], role, v, k, D, Kp, sstride, S, p);
   }
 }
 
@@ -1019,22 +1044,28 @@ bool ozaki_gemm(int opA, int opB, int M, int N, int K, double alpha, const T* A,
   uint8_t* R = reinterpret_cast<uint8_t*>(Bd + zB * count);
   int* ea = reinterpret_cast<int*>(R + zR * count);
   int* eb = ea + (size_t)Mp * count;
-  // zero planes and exponents (padding rows/columns and k beyond K stay zero)
-  cudaMemsetAsync(work, 0, (size_t)(zA + zB) * 2 * count, s);
+  // exponents zero for the padding rows and columns; the planes are written whole by the
+  // split kernels (zeros in the padding), also for K = 0
   cudaMemsetAsync(ea, 0, sizeof(int) * ((size_t)Mp + Np) * count, s);
-  if (K > 0) {
+  {
+    // padded extents in the split kernels' terms: vectors (complex B: embedded rows 2v, 2v + 1)
+    // and logical k (complex: positions 2k, 2k + 1 of the padded K')
+    const int nva = Mp, nvb = cplx ? Np / 2 : Np, kpl = cplx ? Kp / 2 : Kp;
     const dim3 ga((M + 31) / 32, count), gb((N + 31) / 32, count);
-    count_launch(2);
+    const dim3 ta((nva + 31) / 32, (kpl + 31) / 32, count), tb((nvb + 31) / 32, (kpl + 31) / 32, count);
+    count_launch(4);
+    oz_scale_kernel<T><<<ga, 256, 0, s>>>(A, lda, sA, 0, opA, M, K, ea, Mp, kscale, sks, kdev, sA2, nb2);
+    oz_scale_kernel<T><<<gb, 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, eb, Np, nullptr, 0, kdev, sB2, nb2);
     if (res) {
-      oz_split_kernel<T, true><<<ga, 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, zA, P, pl.p,
-                                                  ea, Mp, kscale, sks, kdev, sA2, nb2);
-      oz_split_kernel<T, true><<<gb, 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, zB, P, pl.p,
-                                                  eb, Np, nullptr, 0, kdev, sB2, nb2);
+      oz_split_kernel<T, true><<<ta, 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, zA, P, pl.p,
+                                                  ea, Mp, kscale, sks, kdev, sA2, nb2, nva, kpl);
+      oz_split_kernel<T, true><<<tb, 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, zB, P, pl.p,
+                                                  eb, Np, nullptr, 0, kdev, sB2, nb2, nvb, kpl);
     } else {
-      oz_split_kernel<T, false><<<ga, 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, zA, P, 0,
-                                                   ea, Mp, kscale, sks, kdev, sA2, nb2);
-      oz_split_kernel<T, false><<<gb, 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, zB, P, 0,
-                                                   eb, Np, nullptr, 0, kdev, sB2, nb2);
+      oz_split_kernel<T, false><<<ta, 256, 0, s>>>(A, lda, sA, 0, opA, M, K, Ad, Kp, (long long)Mp * Kp, zA, P, 0,
+                                                   ea, Mp, kscale, sks, kdev, sA2, nb2, nva, kpl);
+      oz_split_kernel<T, false><<<tb, 256, 0, s>>>(B, ldb, sB, 1, opB, N, K, Bd, Kp, (long long)Np * Kp, zB, P, 0,
+                                                   eb, Np, nullptr, 0, kdev, sB2, nb2, nvb, kpl);
     }
   }
   const long long wait = wait_cycles > 0 ? wait_cycles : (1ll << 32);
