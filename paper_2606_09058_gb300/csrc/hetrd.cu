@@ -545,8 +545,9 @@ struct DigRing {
 // 16-column blocks through its own ring of STG stages (asynchronous copies, STG - 1 blocks
 // ahead of the one it multiplies; a stage is one contiguous tile, consecutive lanes copying
 // consecutive 16-byte words), and the loads in flight hold no registers.
-// Digit pairs up to level s + t = 8: the dropped rest lies below 2^-63 of the scales (the
-// pairs of level 8 alone would otherwise add a one-signed error near the FP64 unit per term).
+// Digit pairs (digits numbered from 0, most significant first) up to level s + t = 7: the
+// dropped pairs lie below 2^-59 of the scales (stopping one level earlier would leave a
+// one-signed error near the FP64 unit per term).
 // Complex: the four real products Re a Re u, Im a Im u, Re a Im u, Im a Re u
 // (Re p = first - second, Im p = third + fourth); real: the first only.
 template <typename T>
